@@ -1,0 +1,202 @@
+"""FP64 CPU oracle for the IVHD embedding iteration -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it, and it
+never calls the CUDA library.  The arithmetic lives in ``ivhd_oracle.c``; this
+module marshals numpy arrays through ctypes and adds nothing to the method.
+
+Functions mirror the paper's steps (see the C file's header for citations and
+the readings taken where the paper is ambiguous):
+
+* ``random_neighbors`` -- fixed random neighbours O_rn(i), SplitMix64 draws.
+* ``init_positions``   -- y0 ~ U(0,1)^2 from SplitMix64.
+* ``build_terms``      -- the nn / rn term list of the stress (Eq. 3.16).
+* ``stress``, ``forces`` -- E and F = -1/2 grad E.
+* ``step`` / ``run``   -- momentum (force-directed), Nesterov, Adadelta.
+* ``knn_f32`` / ``knn_u8`` -- exact brute-force kNN.
+* ``qnx``, ``cf``      -- Q_NX(k) and neighbour hit cf_nn.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from .build import build_oracle
+
+OPT_MOMENTUM, OPT_NESTEROV, OPT_ADADELTA = 0, 1, 2
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_oracle())
+        P = ctypes.c_void_p
+        i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double
+        lib.ivo_splitmix64.argtypes = [u64, u64]
+        lib.ivo_splitmix64.restype = u64
+        lib.ivo_random_neighbors.argtypes = [P, i64, i32, i32, u64, P]
+        lib.ivo_random_neighbors.restype = i64
+        lib.ivo_init_positions.argtypes = [i64, u64, P]
+        lib.ivo_init_positions.restype = None
+        lib.ivo_build_terms.argtypes = [P, P, i64, i32, i32, i32, P, P, P]
+        lib.ivo_build_terms.restype = i64
+        lib.ivo_stress.argtypes = [P, P, P, P, i64, dbl]
+        lib.ivo_stress.restype = dbl
+        lib.ivo_forces.argtypes = [P, i64, P, P, P, i64, dbl, P]
+        lib.ivo_forces.restype = None
+        lib.ivo_step.argtypes = [i32, P, P, P, i64, P, P, P, i64, dbl, dbl, dbl, dbl, dbl, P, P]
+        lib.ivo_step.restype = None
+        lib.ivo_run.argtypes = [i32, P, P, P, i64, P, P, P, i64, dbl, dbl, dbl, dbl, dbl, i64]
+        lib.ivo_run.restype = i32
+        lib.ivo_knn_f32.argtypes = [P, i64, i32, i32, P, i64, P]
+        lib.ivo_knn_f32.restype = i32
+        lib.ivo_knn_u8.argtypes = [P, i64, i32, i32, P, i64, P]
+        lib.ivo_knn_u8.restype = i32
+        lib.ivo_qnx.argtypes = [P, i64, P, i32, P, i64, P]
+        lib.ivo_qnx.restype = dbl
+        lib.ivo_cf.argtypes = [P, i64, P, i32, P, i64]
+        lib.ivo_cf.restype = dbl
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def splitmix64(seed: int, t: int) -> int:
+    return int(_L().ivo_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, t))
+
+
+def random_neighbors(knn, r: int, seed: int):
+    """Returns (rn int32 [M, r] with -1 for unfillable slots, number of -1 slots)."""
+    knn = _c(knn, np.int32)
+    M, k = knn.shape
+    rn = np.empty((M, r), dtype=np.int32)
+    empty = _L().ivo_random_neighbors(_p(knn), M, k, r, seed & 0xFFFFFFFFFFFFFFFF, _p(rn))
+    return rn, int(empty)
+
+
+def init_positions(M: int, seed: int) -> np.ndarray:
+    Y = np.empty((M, 2), dtype=np.float64)
+    _L().ivo_init_positions(M, seed & 0xFFFFFFFFFFFFFFFF, _p(Y))
+    return Y
+
+
+@dataclasses.dataclass
+class Terms:
+    ti: np.ndarray
+    tj: np.ndarray
+    kind: np.ndarray
+    M: int
+
+    @property
+    def T(self) -> int:
+        return int(self.ti.shape[0])
+
+
+def build_terms(knn, rn, dedup: bool = False) -> Terms:
+    knn = _c(knn, np.int32)
+    M, k = knn.shape
+    rn = _c(rn, np.int32).reshape(M, -1)
+    r = rn.shape[1]
+    cap = max(1, M * (k + r))
+    ti = np.empty(cap, np.int64)
+    tj = np.empty(cap, np.int64)
+    kind = np.empty(cap, np.int8)
+    T = _L().ivo_build_terms(_p(knn), _p(rn), M, k, r, int(dedup), _p(ti), _p(tj), _p(kind))
+    return Terms(ti[:T].copy(), tj[:T].copy(), kind[:T].copy(), M)
+
+
+def stress(Y, terms: Terms, c: float) -> float:
+    Y = _c(Y, np.float64)
+    return float(_L().ivo_stress(_p(Y), _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c))
+
+
+def forces(Y, terms: Terms, c: float) -> np.ndarray:
+    Y = _c(Y, np.float64)
+    F = np.empty_like(Y)
+    _L().ivo_forces(_p(Y), terms.M, _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c, _p(F))
+    return F
+
+
+@dataclasses.dataclass
+class State:
+    """Oracle optimiser state: positions Y, S1 (velocity or E[g^2]), S2 (E[dx^2])."""
+    Y: np.ndarray
+    S1: np.ndarray
+    S2: np.ndarray
+
+    @classmethod
+    def fresh(cls, Y):
+        Y = np.array(Y, dtype=np.float64, copy=True).reshape(-1, 2)
+        return cls(Y, np.zeros_like(Y), np.zeros_like(Y))
+
+
+def step(state: State, terms: Terms, c: float, opt: int = OPT_MOMENTUM, a: float = 0.9,
+         b: float = 0.01, rho: float = 0.95, eps: float = 1e-6) -> State:
+    M = terms.M
+    F = np.empty((M, 2))
+    W = np.empty((M, 2))
+    _L().ivo_step(opt, _p(state.Y), _p(state.S1), _p(state.S2), M, _p(terms.ti), _p(terms.tj),
+                  _p(terms.kind), terms.T, c, a, b, rho, eps, _p(F), _p(W))
+    return state
+
+
+def run(state: State, terms: Terms, c: float, n_iter: int, opt: int = OPT_MOMENTUM,
+        a: float = 0.9, b: float = 0.01, rho: float = 0.95, eps: float = 1e-6) -> State:
+    rc = _L().ivo_run(opt, _p(state.Y), _p(state.S1), _p(state.S2), terms.M, _p(terms.ti),
+                      _p(terms.tj), _p(terms.kind), terms.T, c, a, b, rho, eps, n_iter)
+    if rc != 0:
+        raise MemoryError("oracle run")
+    return state
+
+
+def knn_f32(X, k: int, rows=None) -> np.ndarray:
+    X = _c(X, np.float32)
+    M, N = X.shape
+    rows_a = None if rows is None else _c(rows, np.int64)
+    n = M if rows_a is None else rows_a.shape[0]
+    out = np.empty((n, k), dtype=np.int32)
+    if _L().ivo_knn_f32(_p(X), M, N, k, _p(rows_a), n, _p(out)) != 0:
+        raise ValueError("oracle knn: need 1 <= k <= M-1")
+    return out
+
+
+def knn_u8(X, k: int, rows=None) -> np.ndarray:
+    X = _c(X, np.uint8)
+    M, N = X.shape
+    rows_a = None if rows is None else _c(rows, np.int64)
+    n = M if rows_a is None else rows_a.shape[0]
+    out = np.empty((n, k), dtype=np.int32)
+    if _L().ivo_knn_u8(_p(X), M, N, k, _p(rows_a), n, _p(out)) != 0:
+        raise ValueError("oracle knn: need 1 <= k <= M-1")
+    return out
+
+
+def qnx(Y, knn, rows=None, return_lowd: bool = False):
+    Y = _c(Y, np.float32)
+    knn = _c(knn, np.int32)
+    M, k = knn.shape
+    rows_a = None if rows is None else _c(rows, np.int64)
+    n = M if rows_a is None else rows_a.shape[0]
+    low = np.empty((n, k), dtype=np.int32) if return_lowd else None
+    q = float(_L().ivo_qnx(_p(Y), M, _p(knn), k, _p(rows_a), n, _p(low)))
+    return (q, low) if return_lowd else q
+
+
+def cf(Y, labels, nn: int, rows=None) -> float:
+    Y = _c(Y, np.float32)
+    labels = _c(labels, np.int32)
+    M = Y.shape[0]
+    rows_a = None if rows is None else _c(rows, np.int64)
+    n = M if rows_a is None else rows_a.shape[0]
+    return float(_L().ivo_cf(_p(Y), M, _p(labels), nn, _p(rows_a), n))

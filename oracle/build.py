@@ -1,0 +1,32 @@
+"""Compile the C oracle into ``oracle/_build/libivhd_oracle.so`` with gcc.
+
+Test infrastructure only (see ``oracle/__init__.py``).  Plain C99 plus
+``unsigned __int128``; no x86 or Arm intrinsics, so it builds on both hosts.
+``-ffp-contract=off`` keeps every float operation as written (the only fused
+operations are the explicit ``fmaf`` calls).
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "ivhd_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libivhd_oracle.so")
+
+
+def build_oracle(force: bool = False) -> str:
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_oracle(force=True))

@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the benchmark.
+
+This module draws data only: Gaussian-mixture feature matrices, MNIST-shaped
+uint8 images, random kNN-shaped graphs and random 2-D positions.  It holds
+none of the IVHD arithmetic (no distances, forces, updates or neighbour
+sampling), so both implementations can consume the same inputs without
+sharing any of the method.
+
+All draws use numpy's PCG64 with an explicit seed.  Feature rows are shuffled
+after generation so that vertex order carries no cluster structure, as with
+a real dataset stored in arbitrary order.
+
+Workloads (named by content):
+
+* ``gmm2k``    - M=2,000 points in N=50 dims, 10 equal isotropic components,
+                 centres ~ N(0, 25 I), unit variance; k=2, r=1, c=0.01,
+                 1,000 momentum steps (a=0.9, b=0.01).
+* ``mnist70k`` - M=70,000 uint8 images of N=784 pixels: 10 prototypes with
+                 i.i.d. U{0..255} pixels, x = clip(rint(p + 40 z), 0, 255),
+                 7,000 per class; k=5, r=1, c=0.01, 2,000 steps.  Stands in
+                 for MNIST (Sec. 4.2, Table of datasets).
+* ``gmm1p4m``  - M=1,400,000 points in N=100 dims, 50 components whose sizes
+                 follow a power law with exponent 1.5 (largest-remainder
+                 rounding), centres ~ N(0, 25 I), unit variance; k=5, r=1,
+                 c=0.01, 2,000 steps.  Stands in for YAHOO (M=1.4e6, N=100,
+                 Sec. 5.2 comparison table).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    M: int
+    N: int
+    k: int
+    r: int
+    c: float
+    n_iter: int
+    a: float = 0.9
+    b: float = 0.01
+    dtype: str = "f32"          # feature dtype: "f32" or "u8"
+    seed: int = 0
+
+
+WORKLOADS = {
+    "gmm2k": Workload("gmm2k", M=2000, N=50, k=2, r=1, c=0.01, n_iter=1000, seed=2000),
+    "mnist70k": Workload("mnist70k", M=70000, N=784, k=5, r=1, c=0.01, n_iter=2000,
+                         dtype="u8", seed=70000),
+    "gmm1p4m": Workload("gmm1p4m", M=1400000, N=100, k=5, r=1, c=0.01, n_iter=2000,
+                        seed=1400000),
+}
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def powerlaw_sizes(M: int, n_comp: int, exponent: float) -> np.ndarray:
+    """Component sizes proportional to c^-exponent (c = 1..n_comp), summing to M.
+
+    Largest-remainder rounding keeps the total exact.
+    """
+    w = np.arange(1, n_comp + 1, dtype=np.float64) ** (-exponent)
+    q = w / w.sum() * M
+    sizes = np.floor(q).astype(np.int64)
+    short = M - int(sizes.sum())
+    order = np.argsort(-(q - sizes), kind="stable")
+    sizes[order[:short]] += 1
+    return sizes
+
+
+def gaussian_mixture(M: int, N: int, n_comp: int, seed: int, *, centre_std: float = 5.0,
+                     sizes: np.ndarray | None = None, shuffle: bool = True):
+    """Isotropic Gaussian mixture: centres ~ N(0, centre_std^2 I), unit variance.
+
+    Returns ``(X float32 [M, N], labels int32 [M])``.
+    """
+    rng = _rng(seed)
+    if sizes is None:
+        sizes = np.full(n_comp, M // n_comp, dtype=np.int64)
+        sizes[: M - int(sizes.sum())] += 1
+    sizes = np.asarray(sizes, dtype=np.int64)
+    assert int(sizes.sum()) == M
+    centres = (rng.standard_normal((n_comp, N)) * centre_std).astype(np.float32)
+    labels = np.repeat(np.arange(n_comp, dtype=np.int32), sizes)
+    X = rng.standard_normal((M, N), dtype=np.float32)
+    X += centres[labels]
+    if shuffle:
+        perm = rng.permutation(M)
+        X = X[perm]
+        labels = labels[perm]
+    return np.ascontiguousarray(X), np.ascontiguousarray(labels)
+
+
+def mnist_like(M: int, seed: int, *, N: int = 784, n_proto: int = 10, sigma: float = 40.0,
+               shuffle: bool = True):
+    """uint8 images: prototypes with i.i.d. U{0..255} pixels plus N(0, sigma^2) noise, clipped.
+
+    Returns ``(X uint8 [M, N], labels int32 [M])``.
+    """
+    rng = _rng(seed)
+    protos = rng.integers(0, 256, size=(n_proto, N)).astype(np.float32)
+    labels = np.repeat(np.arange(n_proto, dtype=np.int32), -(-M // n_proto))[:M]
+    X = np.empty((M, N), dtype=np.uint8)
+    chunk = 8192
+    for s in range(0, M, chunk):
+        e = min(M, s + chunk)
+        z = rng.standard_normal((e - s, N), dtype=np.float32)
+        X[s:e] = np.clip(np.rint(protos[labels[s:e]] + sigma * z), 0, 255).astype(np.uint8)
+    if shuffle:
+        perm = rng.permutation(M)
+        X = X[perm]
+        labels = labels[perm]
+    return np.ascontiguousarray(X), np.ascontiguousarray(labels)
+
+
+def workload_features(w: Workload):
+    """Feature matrix and mixture labels of a named workload."""
+    if w.name == "gmm2k":
+        return gaussian_mixture(w.M, w.N, 10, w.seed)
+    if w.name == "mnist70k":
+        return mnist_like(w.M, w.seed, N=w.N)
+    if w.name == "gmm1p4m":
+        return gaussian_mixture(w.M, w.N, 50, w.seed, sizes=powerlaw_sizes(w.M, 50, 1.5))
+    raise KeyError(w.name)
+
+
+def random_knn_graph(M: int, k: int, seed: int, *, hub_frac: float = 0.0,
+                     n_hubs: int = 0) -> np.ndarray:
+    """A kNN-shaped graph: k distinct neighbours per row, never the row itself.
+
+    ``n_hubs`` vertices (ids 0..n_hubs-1) are drawn with probability
+    ``hub_frac`` per slot, producing heavily skewed in-degrees like the hubs of
+    high-dimensional kNN graphs.  Returns int32 [M, k].
+    """
+    assert 1 <= k <= M - 1
+    rng = _rng(seed)
+    out = np.empty((M, k), dtype=np.int32)
+    for i in range(M):
+        row: list[int] = []
+        while len(row) < k:
+            if n_hubs > 0 and rng.random() < hub_frac:
+                j = int(rng.integers(0, n_hubs))
+            else:
+                j = int(rng.integers(0, M))
+            if j != i and j not in row:
+                row.append(j)
+        out[i] = row
+    return out
+
+
+def uniform_positions(M: int, seed: int, *, scale: float = 1.0) -> np.ndarray:
+    """Random 2-D positions ~ U(0, scale)^2 as float32 [M, 2]."""
+    rng = _rng(seed)
+    return (rng.random((M, 2)) * scale).astype(np.float32)
+
+
+def sample_rows(M: int, n: int, seed: int) -> np.ndarray:
+    """A sorted seeded sample of ``min(n, M)`` distinct row ids (int64)."""
+    if n >= M:
+        return np.arange(M, dtype=np.int64)
+    rng = _rng(seed)
+    return np.sort(rng.choice(M, size=n, replace=False)).astype(np.int64)

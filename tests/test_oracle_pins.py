@@ -1,0 +1,357 @@
+"""Pins of the FP64 oracle against closed forms, invariants and brute force.
+
+None of these compare the oracle with itself: each expected value comes from
+mathematics the paper fixes (a 2x2 linear recurrence, the gradient of the
+stress, symmetry of the stress, textbook kNN on a line, published generator
+vectors), so a dropped term, a wrong sign or a swapped index fails one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_05455_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _terms(pairs, M):
+    ti = np.array([p[0] for p in pairs], np.int64)
+    tj = np.array([p[1] for p in pairs], np.int64)
+    kind = np.array([p[2] for p in pairs], np.int8)
+    return oracle.Terms(ti, tj, kind, M)
+
+
+# ---------------------------------------------------------------- generator
+
+
+def test_splitmix64_published_vectors():
+    for line in open(os.path.join(GOLD, "splitmix64.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        seed, t, val = (int(x) for x in line.split())
+        assert oracle.splitmix64(seed, t) == val
+
+
+def test_init_positions_grid_and_uniformity():
+    Y = oracle.init_positions(20000, 7)
+    assert Y.shape == (20000, 2)
+    assert np.all((Y >= 0) & (Y < 1))
+    assert np.all(Y * 2 ** 24 == np.floor(Y * 2 ** 24))   # exact 24-bit grid, fits FP32
+    assert abs(Y.mean() - 0.5) < 0.01
+    assert abs(Y.var() - 1 / 12) < 0.003
+    assert abs(np.corrcoef(Y[:, 0], Y[:, 1])[0, 1]) < 0.03
+    assert not np.array_equal(Y, oracle.init_positions(20000, 8))
+
+
+# ------------------------------------------------------------ random neighbours
+
+
+def _connected(knn, i, j):
+    return i == j or j in knn[i] or i in knn[j]
+
+
+def test_random_neighbors_rules_and_uniformity():
+    M, k, r = 3000, 5, 2
+    knn = synth.random_knn_graph(M, k, 11, hub_frac=0.2, n_hubs=10)
+    rn, empty = oracle.random_neighbors(knn, r, 123)
+    assert empty == 0
+    for i in range(M):
+        assert len(set(rn[i].tolist())) == r
+        for j in rn[i]:
+            assert 0 <= j < M and not _connected(knn, i, int(j))
+    # draws are uniform over vertices: chi-square over 30 bins of the id range
+    h = np.bincount(rn.ravel() * 30 // M, minlength=30)
+    exp = rn.size / 30
+    chi2 = ((h - exp) ** 2 / exp).sum()
+    assert chi2 < 70  # 29 dof, p ~ 1e-4
+    # deterministic in the seed, different across seeds
+    assert np.array_equal(rn, oracle.random_neighbors(knn, r, 123)[0])
+    assert not np.array_equal(rn, oracle.random_neighbors(knn, r, 124)[0])
+
+
+def test_random_neighbors_fallback_and_empty_slots():
+    # vertex 0 is connected to every other vertex: no random neighbour exists
+    M = 5
+    knn = np.array([[1, 2], [0, 2], [0, 1], [0, 1], [0, 1]], np.int32)
+    knn[0] = [1, 2]
+    knn[3] = [0, 4]
+    knn[4] = [0, 3]
+    rn, empty = oracle.random_neighbors(knn, 2, 5)
+    # 0 is joined to 1, 2 (out) and 3, 4 (in): both slots empty
+    assert rn[0].tolist() == [-1, -1]
+    # 1 is joined to 0, 2 only: its eligible set is exactly {3, 4}
+    assert sorted(rn[1].tolist()) == [3, 4]
+    # 3 is joined to 0, 4: eligible {1, 2}
+    assert sorted(rn[3].tolist()) == [1, 2]
+    assert empty == 2
+
+
+# ---------------------------------------------------------------- terms
+
+
+def test_term_counts_multiplicity_and_dedup():
+    M, k, r = 400, 4, 1
+    knn = synth.random_knn_graph(M, k, 3)  # ~k^2/2 mutual pairs expected
+    rn, _ = oracle.random_neighbors(knn, r, 9)
+    t_mult = oracle.build_terms(knn, rn, dedup=False)
+    t_dedup = oracle.build_terms(knn, rn, dedup=True)
+    mutual = sum(1 for i in range(M) for j in knn[i] if j < i and i in knn[j])
+    assert mutual >= 1
+    assert t_mult.T == M * k + M * r
+    assert t_dedup.T == M * k - mutual + M * r
+    undirected = {(min(i, int(j)), max(i, int(j))) for i in range(M) for j in knn[i]}
+    got = {(min(a, b), max(a, b)) for a, b, t in zip(t_dedup.ti, t_dedup.tj, t_dedup.kind) if t == 0}
+    assert got == undirected and (t_dedup.kind == 0).sum() == len(undirected)
+
+
+# ---------------------------------------------------------------- stress
+
+
+def test_stress_hand_example():
+    Y = np.array([[0.0, 0.0], [3.0, 4.0], [0.0, 1.0]])
+    c = 0.1
+    t = _terms([(0, 1, 0), (0, 2, 1), (1, 2, 1)], 3)
+    want = 25.0 + c * (1 - 1.0) ** 2 + c * (1 - np.sqrt(18.0)) ** 2
+    assert oracle.stress(Y, t, c) == pytest.approx(want, rel=1e-15)
+
+
+def _random_case(M, k, r, seed, dedup=False):
+    knn = synth.random_knn_graph(M, k, seed)
+    rn, _ = oracle.random_neighbors(knn, r, seed + 1)
+    t = oracle.build_terms(knn, rn, dedup=dedup)
+    Y = np.random.default_rng(seed).random((M, 2)) * 2.0
+    return knn, rn, t, Y
+
+
+@pytest.mark.parametrize("dedup", [False, True])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_force_is_half_negative_gradient(seed, dedup):
+    M = 12 + seed * 2
+    _, _, t, Y = _random_case(M, 3, 2, seed, dedup)
+    c = 0.3
+    F = oracle.forces(Y, t, c)
+    h = 1e-6
+    G = np.zeros_like(Y)
+    for i in range(M):
+        for q in range(2):
+            Yp = Y.copy()
+            Ym = Y.copy()
+            Yp[i, q] += h
+            Ym[i, q] -= h
+            G[i, q] = (oracle.stress(Yp, t, c) - oracle.stress(Ym, t, c)) / (2 * h)
+    err = np.abs(F - (-0.5 * G)).max() / np.abs(F).max()
+    assert err < 1e-7
+
+
+def test_net_force_zero_and_centroid_fixed():
+    _, _, t, Y = _random_case(300, 5, 1, 7)
+    F = oracle.forces(Y, t, 0.01)
+    scale = np.abs(F).sum()
+    assert np.abs(F.sum(axis=0)).max() <= 1e-12 * scale
+    st = oracle.State.fresh(Y)
+    c0 = st.Y.mean(axis=0)
+    oracle.run(st, t, 0.01, 50, oracle.OPT_MOMENTUM, a=0.9, b=0.01)
+    assert np.abs(st.Y.mean(axis=0) - c0).max() < 1e-12
+    st2 = oracle.State.fresh(Y)
+    oracle.run(st2, t, 0.01, 50, oracle.OPT_NESTEROV, a=0.9, b=0.01)
+    assert np.abs(st2.Y.mean(axis=0) - c0).max() < 1e-12
+
+
+def test_rigid_motion_invariance():
+    _, _, t, Y = _random_case(60, 4, 2, 5)
+    c = 0.05
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    Refl = np.array([[1.0, 0.0], [0.0, -1.0]])
+    shift = np.array([3.0, -2.0])
+    E0 = oracle.stress(Y, t, c)
+    F0 = oracle.forces(Y, t, c)
+    for Q in (R, Refl, R @ Refl):
+        Y2 = Y @ Q.T + shift
+        assert oracle.stress(Y2, t, c) == pytest.approx(E0, rel=1e-12)
+        np.testing.assert_allclose(oracle.forces(Y2, t, c), F0 @ Q.T, atol=1e-12)
+
+
+def test_gradient_descent_decreases_stress():
+    _, _, t, Y = _random_case(200, 3, 1, 9)
+    st = oracle.State.fresh(Y)
+    c = 0.1
+    E = [oracle.stress(st.Y, t, c)]
+    for _ in range(40):
+        oracle.step(st, t, c, oracle.OPT_MOMENTUM, a=0.0, b=0.002)
+        E.append(oracle.stress(st.Y, t, c))
+    assert all(e1 < e0 for e0, e1 in zip(E, E[1:]))
+
+
+# ------------------------------------------------------- closed-form dynamics
+
+
+def _recurrence(s0, w0, kstiff, a, b, n):
+    """[s; w]_{n+1} = [[1 - b K, a], [-b K, a]] [s; w]_n for relative coordinate s."""
+    A = np.array([[1 - b * kstiff, a], [-b * kstiff, a]])
+    return np.linalg.matrix_power(A, n) @ np.array([s0, w0])
+
+
+@pytest.mark.parametrize("dedup,stiff", [(False, 4.0), (True, 2.0)])
+def test_single_nn_pair_collapses(dedup, stiff):
+    # M = 2, k = 1: a mutual pair -> two nn terms (multiplicity) or one (dedup)
+    knn = np.array([[1], [0]], np.int32)
+    rn = np.full((2, 0), -1, np.int32)
+    t = oracle.build_terms(knn, rn, dedup=dedup)
+    a, b = 0.9, 0.01
+    Y0 = np.array([[0.3, -0.2], [1.1, 0.5]])
+    st = oracle.State.fresh(Y0)
+    for n in (1, 5, 37, 200):
+        st = oracle.State.fresh(Y0)
+        oracle.run(st, t, 0.01, n, oracle.OPT_MOMENTUM, a=a, b=b)
+        s = st.Y[0] - st.Y[1]
+        for q in range(2):
+            want = _recurrence(Y0[0, q] - Y0[1, q], 0.0, stiff, a, b, n)[0]
+            assert s[q] == pytest.approx(want, abs=1e-12)
+    st = oracle.State.fresh(Y0)
+    oracle.run(st, t, 0.01, 3000, oracle.OPT_MOMENTUM, a=a, b=b)
+    assert np.linalg.norm(st.Y[0] - st.Y[1]) < 1e-9
+
+
+def test_single_rn_pair_settles_at_unit_distance():
+    # one rn term: along the joining line the force is exactly c (1 - d), so the
+    # separation error e = d - 1 follows the same recurrence with stiffness 2c.
+    t = _terms([(0, 1, 1)], 2)
+    c, a, b = 0.5, 0.9, 0.05
+    Y0 = np.array([[0.0, 0.0], [0.24, 0.32]])  # d0 = 0.4 on a fixed direction
+    u = Y0[1] / np.linalg.norm(Y0[1])
+    for n in (1, 10, 60):
+        st = oracle.State.fresh(Y0)
+        oracle.run(st, t, c, n, oracle.OPT_MOMENTUM, a=a, b=b)
+        d = np.linalg.norm(st.Y[1] - st.Y[0])
+        want = 1.0 + _recurrence(0.4 - 1.0, 0.0, 2 * c, a, b, n)[0]
+        assert d == pytest.approx(want, abs=1e-12)
+        # motion stays on the line through the initial pair
+        dirv = (st.Y[1] - st.Y[0]) / d
+        assert np.abs(dirv - u).max() < 1e-12
+    st = oracle.State.fresh(Y0)
+    oracle.run(st, t, c, 2000, oracle.OPT_MOMENTUM, a=a, b=b)
+    assert np.linalg.norm(st.Y[1] - st.Y[0]) == pytest.approx(1.0, abs=1e-9)
+
+
+def test_rn_pair_at_zero_distance_has_no_force():
+    t = _terms([(0, 1, 1), (1, 2, 0)], 3)
+    Y = np.array([[0.5, 0.5], [0.5, 0.5], [1.0, 2.0]])
+    F = oracle.forces(Y, t, 0.1)
+    np.testing.assert_allclose(F[0], [0.0, 0.0], atol=0)
+    np.testing.assert_allclose(F[1], Y[2] - Y[1], atol=1e-15)
+
+
+def test_nesterov_matches_lookahead_definition():
+    # on a single nn pair Nesterov is the linear map with the force taken at
+    # s + a w:  w' = a w - bK (s + a w), s' = s + w'.
+    knn = np.array([[1], [0]], np.int32)
+    t = oracle.build_terms(knn, np.full((2, 0), -1, np.int32), dedup=True)
+    a, b, K = 0.8, 0.05, 2.0
+    A = np.array([[1 - b * K, a - b * K * a], [-b * K, a - b * K * a]])
+    Y0 = np.array([[0.0, 0.0], [1.0, 0.0]])
+    st = oracle.State.fresh(Y0)
+    oracle.run(st, t, 0.01, 25, oracle.OPT_NESTEROV, a=a, b=b)
+    want = (np.linalg.matrix_power(A, 25) @ np.array([-1.0, 0.0]))[0]
+    assert (st.Y[0] - st.Y[1])[0] == pytest.approx(want, abs=1e-12)
+
+
+def test_adadelta_first_steps_closed_form():
+    # one nn pair (dedup): per coordinate g = -F; with zero accumulators the
+    # first update is -sqrt(eps)/sqrt((1-rho) g^2 + eps) * g.
+    knn = np.array([[1], [0]], np.int32)
+    t = oracle.build_terms(knn, np.full((2, 0), -1, np.int32), dedup=True)
+    rho, eps = 0.95, 1e-6
+    Y0 = np.array([[0.0, 0.0], [2.0, -1.0]])
+    st = oracle.State.fresh(Y0)
+    oracle.step(st, t, 0.01, oracle.OPT_ADADELTA, rho=rho, eps=eps)
+    g0 = -(Y0[1] - Y0[0])  # g for vertex 0 = (y0 - y1)
+    dx = -np.sqrt(eps) / np.sqrt((1 - rho) * g0 ** 2 + eps) * g0
+    np.testing.assert_allclose(st.Y[0], Y0[0] + dx, rtol=1e-14)
+    np.testing.assert_allclose(st.S1[0], (1 - rho) * g0 ** 2, rtol=1e-14)
+    np.testing.assert_allclose(st.S2[0], (1 - rho) * dx ** 2, rtol=1e-14)
+    # Adadelta descends on a single pair
+    E0 = oracle.stress(Y0, t, 0.01)
+    oracle.run(st, t, 0.01, 200, oracle.OPT_ADADELTA, rho=rho, eps=eps)
+    assert oracle.stress(st.Y, t, 0.01) < E0
+
+
+# ---------------------------------------------------------------- kNN
+
+
+def test_knn_on_a_line_textbook():
+    # points 0, 1, ..., M-1 on a line: neighbours alternate left/right, the
+    # left one first on ties (lower index), edges clipped at the ends.
+    M, k = 40, 4
+    X = np.arange(M, dtype=np.float32)[:, None] * 1.0
+    out = oracle.knn_f32(X, k)
+    for i in range(M):
+        cand = sorted((abs(i - j), j) for j in range(M) if j != i)
+        assert out[i].tolist() == [j for _, j in cand[:k]]
+    assert out[10].tolist() == [9, 11, 8, 12]
+    Xu = (np.arange(M, dtype=np.int64)[:, None] * 3).clip(0, 255).astype(np.uint8)
+    assert np.array_equal(oracle.knn_u8(Xu, k), out)
+
+
+def test_knn_matches_float64_brute_force_when_gaps_are_large():
+    X, _ = synth.gaussian_mixture(300, 20, 3, 5)
+    out = oracle.knn_f32(X, 6)
+    D = ((X.astype(np.float64)[:, None, :] - X.astype(np.float64)[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(D, np.inf)
+    ref = np.argsort(D, axis=1, kind="stable")[:, :6]
+    srt = np.sort(D, axis=1)
+    safe = (srt[:, 6] - srt[:, 5]) > 1e-3 * srt[:, 5]  # rows with no FP32 near-tie at the cut
+    assert safe.mean() > 0.9
+    for i in np.nonzero(safe)[0]:
+        assert set(out[i].tolist()) == set(ref[i].tolist())
+    rows = np.array([3, 77, 150], np.int64)
+    assert np.array_equal(oracle.knn_f32(X, 6, rows), out[rows])
+
+
+def test_knn_u8_integer_exact():
+    X, _ = synth.mnist_like(200, 3, N=64)
+    out = oracle.knn_u8(X, 5)
+    D = ((X.astype(np.int64)[:, None, :] - X.astype(np.int64)[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(D, np.iinfo(np.int64).max)
+    order = np.lexsort((np.broadcast_to(np.arange(200), D.shape), D), axis=1)[:, :5]
+    assert np.array_equal(out, order)
+
+
+# ---------------------------------------------------------------- metrics
+
+
+def test_qnx_identity_embedding_is_one():
+    X = synth.uniform_positions(500, 4)
+    knn = oracle.knn_f32(X, 5)
+    assert oracle.qnx(X, knn) == 1.0
+
+
+def test_qnx_random_embedding_is_k_over_m_minus_1():
+    M, k = 3000, 10
+    knn = synth.random_knn_graph(M, k, 6)
+    Y = synth.uniform_positions(M, 99)
+    rows = synth.sample_rows(M, 1500, 1)
+    q = oracle.qnx(Y, knn, rows)
+    mean = k / (M - 1)
+    sd = np.sqrt(mean / (k * len(rows)))
+    assert abs(q - mean) < 5 * sd
+
+
+def test_qnx_ties_prefer_lower_index():
+    # a 3x3 unit grid: the centre (id 4) has four neighbours at distance 1
+    Y = np.array([[x, y] for y in range(3) for x in range(3)], np.float32)
+    knn = np.tile(np.arange(2, dtype=np.int32), (9, 1))
+    _, low = oracle.qnx(Y, knn, rows=np.array([4]), return_lowd=True)
+    assert low[0].tolist() == [1, 3]
+
+
+def test_cf_separated_and_mixed_labels():
+    rng = np.random.default_rng(0)
+    M = 600
+    lab = np.repeat(np.arange(3), 200).astype(np.int32)
+    Y = (rng.standard_normal((M, 2)) * 0.1 + lab[:, None] * 10.0).astype(np.float32)
+    assert oracle.cf(Y, lab, 10) == 1.0
+    lab_rand = rng.integers(0, 3, M).astype(np.int32)
+    assert abs(oracle.cf(Y, lab_rand, 10) - 1 / 3) < 0.05
