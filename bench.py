@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""IVHD benchmark: edge-updates/s and seconds-to-embed on one GB300.
+
+One timed step is one whole embedding of the workload (default ``gmm1p4m``:
+M = 1.4e6 points, N = 100, k = 5, r = 1, c = 0.01, 2,000 momentum steps):
+``ivhd_create`` (random neighbours, symmetric layout, initial positions) +
+``ivhd_step(2000)`` + positions read-back, all through the C ABI with the kNN
+graph already resident in HBM.  The exact kNN graph is built once before the
+timed region (untimed, as the paper's time_emb excludes the graph build).
+
+    value = terms x iterations / seconds per embedding      (edge-updates/s)
+
+``e2e`` repeats the step from pinned host memory (kNN upload and positions
+download inside the timed region).  ``roofline`` reports the fused step
+kernel against the measured HBM copy bandwidth.  ``cpu_baseline`` times the
+FP64 oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+project has) on the same metric; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2303_05455_gb300 import synth  # noqa: E402
+
+METRIC = "IVHD edge-updates/s & s-to-embed @M=1.4M vs plain FP32, at equal kNN precision"
+UNIT = "edge-updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="gmm1p4m", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--n-iter", type=int, default=None, help="iterations per embedding")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU seconds of the oracle baseline sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload_config(w: synth.Workload, n_iter: int) -> dict:
+    return {
+        "workload": w.name, "M": w.M, "N": w.N, "features": w.dtype, "k": w.k, "r": w.r,
+        "c": w.c, "n_iter": n_iter, "optimizer": "momentum", "a": w.a, "b": w.b,
+        "terms": "multiplicity (mutual kNN pairs give two nn terms)",
+        "step": "ivhd_create + n_iter fused steps + positions read-back (one embedding)",
+        "knn_graph": "exact, built on the GPU before the timed region (untimed)",
+        "l2": "256 MiB buffer written between timed steps; the per-iteration working "
+              "set (~110 MB) stays in L2 within an embedding",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def step_kernel_traffic():
+    """dram bytes per launch of the step kernel from the committed ncu summary,
+    only while the kernel source is unchanged since the capture."""
+    src = os.path.join(ROOT, "paper_2303_05455_gb300", "csrc", "ivhd_step.cu")
+    meta = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        with open(meta) as f:
+            d = json.load(f)
+        if d.get("kernel_src_sha256") == sha and d.get("workload"):
+            return d
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# ------------------------------------------------------------- oracle leg
+
+
+def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200):
+    """Times the FP64 oracle's step loop on a graph of the workload's shape.
+
+    The graph comes from the input generators (a kNN-shaped graph with hubs,
+    M x k), not from the GPU path.  Returns (edge-updates/s, iterations, seconds,
+    terms, setup seconds).
+    """
+    import oracle
+
+    t0 = time.perf_counter()
+    knn = synth.random_knn_graph(w.M, w.k, w.seed + 1, hub_frac=0.02, n_hubs=max(w.k + 1, w.M // 1000))
+    rn, _ = oracle.random_neighbors(knn, w.r, w.seed)
+    terms = oracle.build_terms(knn, rn)
+    st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
+    setup = time.perf_counter() - t0
+    t = time.perf_counter()
+    oracle.run(st, terms, w.c, 1, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    one = max(time.perf_counter() - t, 1e-6)
+    iters = int(max(1, min(max_iters, target_s / one)))
+    t = time.perf_counter()
+    oracle.run(st, terms, w.c, iters, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    dt = time.perf_counter() - t
+    return terms.T * iters / dt, iters, dt, terms.T, setup
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    w = synth.WORKLOADS[args.workload]
+    n_iter = args.n_iter or w.n_iter
+    import oracle
+
+    knn = synth.random_knn_graph(w.M, w.k, w.seed + 1, hub_frac=0.02, n_hubs=max(w.k + 1, w.M // 1000))
+    rn, _ = oracle.random_neighbors(knn, w.r, w.seed)
+    terms = oracle.build_terms(knn, rn)
+    st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
+    t = time.perf_counter()
+    oracle.run(st, terms, w.c, 1, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    one = max(time.perf_counter() - t, 1e-6)
+    per_step = int(max(1, min(n_iter, 6.0 / one)))   # ~6 s of oracle work per step
+    for _ in range(args.warmup):
+        oracle.run(st, terms, w.c, per_step, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.run(st, terms, w.c, per_step, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * statistics.mean(times)
+    value = terms.T * per_step / (ms / 1e3)
+    sample = (f"{per_step} of {n_iter} iterations per step on a {w.M} x {w.k} kNN-shaped "
+              f"graph from the input generators (r={w.r}), FP64, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {**workload_config(w, n_iter), "iterations_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU leg
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2303_05455_gb300 import ivhd
+
+    rank, local_rank, world = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for the GPU leg")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    w = synth.WORKLOADS[args.workload]
+    n_iter = args.n_iter or w.n_iter
+
+    # untimed set-up: data, exact kNN graph (replicas: every rank embeds its own copy)
+    X, _ = synth.workload_features(w)
+    Xd = torch.from_numpy(X).to(dev)
+    t = time.perf_counter()
+    knn = ivhd.knn_build(Xd, w.k)
+    torch.cuda.synchronize()
+    knn_seconds = time.perf_counter() - t
+    del Xd, X
+    torch.cuda.empty_cache()
+
+    stream = torch.cuda.current_stream()
+    out = torch.empty((w.M, 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_embedding(knn_in, out_buf, evs=None):
+        emb = ivhd.Embedding(knn_in, r=w.r, c=w.c, opt="momentum", a=w.a, b=w.b, seed=w.seed,
+                             stream=stream, device=dev)
+        if evs is not None:
+            evs[0].record(stream)
+        emb.step(n_iter)
+        if evs is not None:
+            evs[1].record(stream)
+        emb.positions(out=out_buf)
+        info = emb.info()
+        emb.close()
+        return info
+
+    for _ in range(args.warmup):
+        info = one_embedding(knn, out)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    launches = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        info = one_embedding(knn, out, kev[s])
+        ends[s].record(stream)
+        launches += info["setup_launches"] + info["kernel_launches"] + info["aux_launches"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    ms = statistics.mean(step_ms)
+    kms = statistics.mean(kern_ms)
+    terms = info["n_terms"]
+    units = terms * n_iter * args.steps
+
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([sum(step_ms) / 1e3, kms, float(units)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        total_s, total_units = float(mx[0]), float(tt[2])
+        kms = float(mx[1])
+    else:
+        total_s, total_units = sum(step_ms) / 1e3, float(units)
+    value = total_units / total_s
+
+    # e2e through the public API from pinned host memory
+    e2e = None
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(1, args.steps)
+    knn_host = torch.empty((w.M, w.k), dtype=torch.int32, pin_memory=True)
+    knn_host.copy_(knn)
+    out_host = torch.empty((w.M, 2), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        one_embedding(knn_host, out_host)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t)
+    e2e = {"value": terms * n_iter / statistics.mean(e2e_t) * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(knn_host.numel() * 4),
+           "d2h_bytes_per_step": int(out_host.numel() * 4), "steps": e2e_steps}
+
+    # roofline of the fused step kernel (algorithmic bytes per launch)
+    M = w.M
+    nnz = info["nnz_sym"]
+    n_slices = (M - info["n_hub"] + 31) // 32
+    alg_bytes = 32 * M + 4 * nnz + 8 * n_slices + 4 * (info["n_hub"] + 1)
+    launch_s = kms / 1e3 / n_iter
+    achieved = alg_bytes / launch_s / 1e9
+    peaks = measured_peaks()
+    tr = step_kernel_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "peak_source": peaks["source"], "kernel": "k_step<momentum>",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "launch_us": launch_s * 1e6,
+                "gathers_per_s": nnz / launch_s}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**workload_config(w, n_iter), "parallelism": "replicas" if world > 1 else "single"},
+        "s_to_embed": ms / 1e3,
+        "kernel_edge_updates_per_s": terms * n_iter / (kms / 1e3),
+        "terms": terms, "nnz_sym": nnz, "n_hub": info["n_hub"], "max_degree": info["max_degree"],
+        "knn_build_s_untimed": knn_seconds,
+        "wall_s_timed_region": wall,
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, iters, dt, T, setup = oracle_sample(w, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} of {n_iter} momentum iterations (FP64, single thread) on a "
+                      f"{w.M} x {w.k} kNN-shaped graph with r={w.r} ({T} terms), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * ivhd.h -- C ABI of the GB300 IVHD embedding library (libivhd.so).
+ *
+ * IVHD embeds the kNN graph of a high-dimensional dataset in 2-D by
+ * minimising the stress of Sec. 3.3.1, Eq. 3.16 of B. Minch, "In search of the
+ * most efficient and memory-saving visualization of high dimensional data"
+ * (2023):
+ *
+ *     E = sum_i [ sum_{j in O_nn(i)} d_ij^2  +  c * sum_{k in O_rn(i)} (1 - d_ik)^2 ],
+ *
+ * i.e. every vertex is pulled to distance 0 from its k nearest neighbours and
+ * held at distance 1 from r random, unconnected vertices (binary targets,
+ * Eq. 3.15).  Each step computes the force F = -1/2 grad E over the
+ * symmetrised graph and applies the optimiser update (force-directed momentum
+ * Eq. 3.34, or the Nesterov / Adadelta variants of Sec. 3.3.2) in one fused
+ * CUDA kernel.  The graph is the problem statement of Sec. 3.3 (embedding of
+ * the kNN graph G(V, E)); the brute-force kNN build of Sec. 5.1 is exposed as a
+ * separate, untimed set-up call.
+ *
+ * Conventions for every call:
+ *   - Return an ivhd_status; no call aborts, traps, prints or throws.
+ *   - "Device" pointers are CUDA global-memory addresses on the current
+ *     device (e.g. torch tensor data pointers); "host" pointers are ordinary
+ *     (pageable or pinned) host memory.  Layouts are row-major and packed.
+ *   - Work is enqueued on the stream given at create time (NULL = the legacy
+ *     default stream) and is asynchronous unless a call says it synchronises.
+ *     Device outputs are valid once that stream reaches the call.
+ *   - The library copies every input it keeps; it never retains a caller
+ *     pointer after a call returns.  Caller buffers stay caller-owned.
+ *   - After IVHD_ERR_CUDA the context is poisoned: later calls on it return
+ *     IVHD_ERR_STATE, except ivhd_destroy.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef IVHD_H_
+#define IVHD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ivhd_ctx ivhd_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    IVHD_OK = 0,
+    IVHD_ERR_ARG = -1,        /* bad size, parameter or null pointer */
+    IVHD_ERR_INDEX = -2,      /* graph id out of range, self loop or duplicate in a row */
+    IVHD_ERR_OOM = -3,        /* device allocation failed */
+    IVHD_ERR_CUDA = -4,       /* a CUDA runtime call or kernel failed */
+    IVHD_ERR_NONFINITE = -5,  /* NaN or Inf found in the embedding */
+    IVHD_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up */
+    IVHD_ERR_STATE = -7       /* context poisoned, or checkpoint does not match */
+} ivhd_status;
+
+typedef enum {
+    IVHD_OPT_MOMENTUM = 0, /* force-directed / momentum: v <- a v + b F; y <- y + v (Eq. 3.34) */
+    IVHD_OPT_NESTEROV = 1, /* v <- a v + b F(y + a v); y <- y + v (Sec. 3.3.2) */
+    IVHD_OPT_ADADELTA = 2  /* Zeiler's Adadelta on g = -F (Sec. 3.3.2), no learning rate */
+} ivhd_opt;
+
+typedef enum {
+    IVHD_KNN_F32 = 0, /* float32 features; decided by the FP32 chain acc = fma(x-y, x-y, acc) */
+    IVHD_KNN_U8 = 1   /* uint8 features; exact integer squared distances */
+} ivhd_knn_dtype;
+
+typedef struct {
+    int32_t opt;          /* ivhd_opt; default IVHD_OPT_MOMENTUM */
+    float a;              /* friction / momentum a in [0, 1]; default 0.9 */
+    float b;              /* force scale (learning rate) b > 0; default 0.01 */
+    float rho;            /* Adadelta decay in (0, 1); default 0.95 */
+    float eps;            /* Adadelta epsilon > 0; default 1e-6 */
+    uint64_t seed;        /* seeds random neighbours and initial positions; default 0 */
+    int32_t dedup_mutual; /* 0: a mutual kNN pair gives two nn terms (literal Eq. 3.16);
+                             1: each unordered nn pair gives one term; default 0 */
+    int32_t init_uniform; /* 1: y0 ~ U(0,1)^2 drawn from seed; 0: y0 = 0 until
+                             ivhd_set_positions; default 1 */
+    int32_t hub_threshold;/* vertices with at least this many symmetric terms are
+                             processed warp-per-vertex; 0 = library default (128) */
+    int32_t reserved;     /* must be 0 */
+    void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
+} ivhd_params;
+
+/* Fills *p with the defaults listed above.  p must not be NULL. */
+void ivhd_default_params(ivhd_params *p);
+
+/*
+ * Creates an embedding context for the kNN graph `knn` (M rows of k vertex
+ * ids, row-major int32, row i lists O_nn(i); Sec. 3.3).  Draws r random
+ * neighbours per vertex (a vertex connected to i in either direction is never
+ * its random neighbour, Sec. 3.3.3; draws use SplitMix64 from p->seed, fixed
+ * for the life of the context), symmetrises the graph so that every term acts
+ * on both endpoints, lays it out for the step kernel, and initialises the
+ * positions and optimiser state (velocity or Adadelta accumulators = 0).
+ *
+ *   knn           M*k int32; host memory if knn_on_device == 0, else device.
+ *                 Copied; the caller keeps ownership.
+ *   M             number of vertices, 2 <= M < 2^31 - 1.
+ *   k             nearest neighbours per row, 1 <= k <= M - 1.
+ *   r             random neighbours per vertex, r >= 0.  When fewer than r
+ *                 unconnected vertices exist the missing slots stay empty.
+ *   c             random-neighbour weight, c > 0 and finite (Eq. 3.16).
+ *   p             parameters (NULL = defaults).
+ *   out           receives the new context; set to NULL on failure.
+ *
+ * Synchronises the stream once (to read validation results and layout sizes).
+ * Errors: IVHD_ERR_ARG for sizes/parameters (including a symmetrised graph
+ * whose layout needs 2^31 or more slots), IVHD_ERR_INDEX when an id is outside
+ * [0, M), equals its row index or repeats within its row, IVHD_ERR_OOM,
+ * IVHD_ERR_CUDA.
+ */
+ivhd_status ivhd_create(const int32_t *knn, int64_t M, int32_t k, int32_t r, float c,
+                        const ivhd_params *p, int32_t knn_on_device, ivhd_ctx **out);
+
+/*
+ * Overwrites the positions with xy (M*2 float32, row-major, vertex order of
+ * the input graph) and zeroes the optimiser state.  on_device selects the
+ * memory space of xy.  Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA, IVHD_ERR_STATE.
+ */
+ivhd_status ivhd_set_positions(ivhd_ctx *ctx, const float *xy, int32_t on_device);
+
+/*
+ * Runs n_iter synchronous steps (Sec. 5.2 scheme: all forces from the same
+ * configuration, then all updates).  Each step is one launch of the fused
+ * gather-force + optimiser kernel; steps are replayed from a CUDA graph.
+ * Asynchronous.  n_iter = 0 is a no-op.  Errors: IVHD_ERR_ARG (n_iter < 0),
+ * IVHD_ERR_CUDA, IVHD_ERR_STATE.
+ */
+ivhd_status ivhd_step(ivhd_ctx *ctx, int64_t n_iter);
+
+/*
+ * Writes the current positions y (M*2 float32, input vertex order) to out.
+ * For Nesterov the positions are y, not the look-ahead point.  With
+ * on_device == 0 out is host memory and the call synchronises the stream.
+ */
+ivhd_status ivhd_positions(ivhd_ctx *ctx, float *out, int32_t on_device);
+
+/*
+ * Writes F = -1/2 grad E at the current positions y (M*2 float32, input
+ * vertex order; Sec. 3.3.1, Eq. 3.14 with the sign reading that makes F the
+ * descent direction).  For Nesterov this is y, not the look-ahead point.
+ * Does not change the state.  Host output synchronises.
+ */
+ivhd_status ivhd_forces(ivhd_ctx *ctx, float *out, int32_t on_device);
+
+/*
+ * Computes the stress E of Eq. 3.16 at the current positions y (FP32 terms,
+ * FP64 deterministic reduction) into *out (host) and checks every position
+ * for NaN/Inf.  Synchronises.  Returns IVHD_ERR_NONFINITE (with *out set to
+ * the computed value) when a position is not finite.
+ */
+ivhd_status ivhd_stress(ivhd_ctx *ctx, double *out);
+
+/*
+ * Copies the random neighbours drawn at create (M*r int32, input vertex ids,
+ * -1 for an empty slot) to out.  Host output synchronises.
+ */
+ivhd_status ivhd_random_neighbors(ivhd_ctx *ctx, int32_t *out, int32_t on_device);
+
+/* Counters of a context. */
+typedef struct {
+    int64_t M;
+    int32_t k, r;
+    int64_t n_terms;       /* undirected terms of Eq. 3.16 (nn + rn) */
+    int64_t nnz_sym;       /* symmetric adjacency entries gathered per step (2 per term) */
+    int64_t layout_slots;  /* id slots stored, including padding */
+    int64_t n_hub;         /* vertices processed warp-per-vertex */
+    int32_t max_degree;    /* largest symmetric degree */
+    int32_t empty_rn;      /* random-neighbour slots left empty */
+    int64_t steps_done;
+    int64_t kernel_launches; /* step kernels launched since create */
+    int64_t setup_launches;  /* kernels launched by ivhd_create (layout set-up) */
+    int64_t aux_launches;    /* other kernels (positions, forces, stress, set/init) */
+} ivhd_info_t;
+
+/* Fills *out.  Host only; does not synchronise. */
+ivhd_status ivhd_info(ivhd_ctx *ctx, ivhd_info_t *out);
+
+/*
+ * Checkpoint / resume.  The state holds the positions, the optimiser state,
+ * the step counter and a fingerprint of (M, k, r, c, parameters, seed), so a
+ * state only loads into a context created from the same graph and
+ * parameters (IVHD_ERR_STATE otherwise).  Resuming reproduces an
+ * uninterrupted run bit for bit.  Buffers are host memory; get/set
+ * synchronise.  ivhd_state_size gives the byte count.
+ */
+ivhd_status ivhd_state_size(ivhd_ctx *ctx, size_t *bytes);
+ivhd_status ivhd_get_state(ivhd_ctx *ctx, void *buf, size_t bytes);
+ivhd_status ivhd_set_state(ivhd_ctx *ctx, const void *buf, size_t bytes);
+
+/* Frees the context and its device memory (after its stream drains).  NULL is a no-op. */
+void ivhd_destroy(ivhd_ctx *ctx);
+
+/* A static, human-readable name for a status.  Never NULL. */
+const char *ivhd_status_string(ivhd_status s);
+
+/* Library version as (major << 16) | (minor << 8) | patch. */
+int32_t ivhd_version(void);
+
+/*
+ * Exact brute-force kNN graph (the set-up step of Sec. 5.1, untimed in the
+ * paper's time_emb): for every row q of X, the k nearest other rows, nearest
+ * first, ties broken by the lower index.  Float data are compared by the FP32
+ * chain acc = fma(x_d - y_d, x_d - y_d, acc), d = 0..N-1; uint8 data by exact
+ * integer squared distances.
+ *
+ *   X        device, M*N elements of `dtype` (ivhd_knn_dtype), row-major.
+ *   out_knn  device, M*k int32.
+ *   stream   cudaStream_t or NULL.
+ * Constraints: 2 <= M < 2^31, 1 <= N <= 65536, 1 <= k <= min(M - 1, 64).
+ * Asynchronous.  Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA.
+ */
+ivhd_status ivhd_knn_build(const void *X, int32_t dtype, int64_t M, int32_t N, int32_t k,
+                           int32_t *out_knn, void *stream);
+
+/*
+ * Neighbourhood preservation Q_NX(k) of Sec. 4.1 on sampled rows: for each
+ * row q in `rows`, the k nearest other points of y_q in the embedding (FP32
+ * squared distance dx*dx rounded then fma(dy, dy, .), ties by lower index)
+ * are intersected with the kNN row q; *out_q = hits / (k * nrows).
+ *
+ *   Y        device, M*2 float32.      knn   device, M*k int32.
+ *   rows     device, nrows int64 row ids in [0, M).
+ *   out_lowd device, nrows*k int32 or NULL: the embedded neighbours found.
+ *   out_q    host double.
+ * Constraints: 1 <= k <= min(M - 1, 128), nrows >= 1.  Synchronises.
+ */
+ivhd_status ivhd_eval_qnx(const float *Y, int64_t M, const int32_t *knn, int32_t k,
+                          const int64_t *rows, int64_t nrows, int32_t *out_lowd,
+                          double *out_q, void *stream);
+
+/*
+ * Neighbour hit cf_nn of Sec. 4.1, Eq. 4.4 on sampled rows: the fraction of
+ * the nn nearest embedded neighbours (same distance and tie rule as
+ * ivhd_eval_qnx) that carry the label of the query row.
+ *
+ *   Y device M*2 float32; labels device M int32; rows device nrows int64.
+ * Constraints: 1 <= nn <= min(M - 1, 128).  Synchronises.
+ */
+ivhd_status ivhd_eval_cf(const float *Y, int64_t M, const int32_t *labels, int32_t nn,
+                         const int64_t *rows, int64_t nrows, double *out_cf, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IVHD_H_ */

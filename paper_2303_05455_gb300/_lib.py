@@ -1,0 +1,112 @@
+"""ctypes loader for ``libivhd.so`` (the C ABI declared in ``include/ivhd.h``).
+
+Only argument marshalling lives here.  The library must have been built
+(``__graft_entry__.build()`` or ``python -m paper_2303_05455_gb300.build_lib``);
+there is no fallback implementation, so a missing library is an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build_lib
+
+STATUS = {
+    0: "IVHD_OK", -1: "IVHD_ERR_ARG", -2: "IVHD_ERR_INDEX", -3: "IVHD_ERR_OOM",
+    -4: "IVHD_ERR_CUDA", -5: "IVHD_ERR_NONFINITE", -6: "IVHD_ERR_TIMEOUT", -7: "IVHD_ERR_STATE",
+}
+
+# exported symbols declared in include/ivhd.h
+SYMBOLS = (
+    "ivhd_default_params", "ivhd_create", "ivhd_set_positions", "ivhd_step", "ivhd_positions",
+    "ivhd_forces", "ivhd_stress", "ivhd_random_neighbors", "ivhd_info", "ivhd_state_size",
+    "ivhd_get_state", "ivhd_set_state", "ivhd_destroy", "ivhd_status_string", "ivhd_version",
+    "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf",
+)
+
+
+class IvhdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("opt", ctypes.c_int32), ("a", ctypes.c_float), ("b", ctypes.c_float),
+        ("rho", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64),
+        ("dedup_mutual", ctypes.c_int32), ("init_uniform", ctypes.c_int32),
+        ("hub_threshold", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int64), ("k", ctypes.c_int32), ("r", ctypes.c_int32),
+        ("n_terms", ctypes.c_int64), ("nnz_sym", ctypes.c_int64),
+        ("layout_slots", ctypes.c_int64), ("n_hub", ctypes.c_int64),
+        ("max_degree", ctypes.c_int32), ("empty_rn", ctypes.c_int32),
+        ("steps_done", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+        ("setup_launches", ctypes.c_int64), ("aux_launches", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libivhd.so; raises if it is absent (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_lib.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            build_lib.build()
+        else:
+            raise RuntimeError(f"libivhd.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    L.ivhd_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.ivhd_default_params.restype = None
+    L.ivhd_create.argtypes = [P, i64, i32, i32, ctypes.c_float, ctypes.POINTER(Params), i32,
+                              ctypes.POINTER(P)]
+    L.ivhd_create.restype = i32
+    L.ivhd_set_positions.argtypes = [P, P, i32]
+    L.ivhd_step.argtypes = [P, i64]
+    L.ivhd_positions.argtypes = [P, P, i32]
+    L.ivhd_forces.argtypes = [P, P, i32]
+    L.ivhd_stress.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    L.ivhd_random_neighbors.argtypes = [P, P, i32]
+    L.ivhd_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.ivhd_state_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.ivhd_get_state.argtypes = [P, P, ctypes.c_size_t]
+    L.ivhd_set_state.argtypes = [P, P, ctypes.c_size_t]
+    for name in ("ivhd_set_positions", "ivhd_step", "ivhd_positions", "ivhd_forces",
+                 "ivhd_stress", "ivhd_random_neighbors", "ivhd_info", "ivhd_state_size",
+                 "ivhd_get_state", "ivhd_set_state"):
+        getattr(L, name).restype = i32
+    L.ivhd_destroy.argtypes = [P]
+    L.ivhd_destroy.restype = None
+    L.ivhd_status_string.argtypes = [i32]
+    L.ivhd_status_string.restype = ctypes.c_char_p
+    L.ivhd_version.argtypes = []
+    L.ivhd_version.restype = i32
+    L.ivhd_knn_build.argtypes = [P, i32, i64, i32, i32, P, P]
+    L.ivhd_knn_build.restype = i32
+    L.ivhd_eval_qnx.argtypes = [P, i64, P, i32, P, i64, P, ctypes.POINTER(ctypes.c_double), P]
+    L.ivhd_eval_qnx.restype = i32
+    L.ivhd_eval_cf.argtypes = [P, i64, P, i32, P, i64, ctypes.POINTER(ctypes.c_double), P]
+    L.ivhd_eval_cf.restype = i32
+    _lib = L
+    return L
+
+
+def check(status: int, what: str):
+    if status != 0:
+        raise IvhdError(status, what)

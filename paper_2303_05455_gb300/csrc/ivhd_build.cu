@@ -1,0 +1,576 @@
+// ivhd_build.cu -- create-time set-up of one embedding context (all on the GPU).
+//
+//   1. validate the kNN rows (range, self loops, duplicates)
+//   2. draw r random neighbours per vertex (Sec. 3.3.1 "generated ad hoc";
+//      Sec. 3.3.3: never a vertex connected to i), SplitMix64 draws
+//   3. count the symmetric degree of every vertex (each stress term of
+//      Eq. 3.16 appears in the rows of both endpoints)
+//   4. order vertices by degree, descending (stable LSD radix sort), so that
+//      the 32 vertices of a warp have near-equal work -- the paper's IVHD-CUDA
+//      also sorts particles by connection count (Sec. 5.2)
+//   5. size hub rows and SELL slices, scan offsets, fill out- and in-entries,
+//      and sort each row's in-part so the layout (and the summation order of
+//      the step kernel) is deterministic.
+#include <vector>
+
+#include "ivhd_internal.cuh"
+
+namespace ivhd {
+
+namespace {
+
+constexpr int kB = 256;
+
+inline int nblk(int64_t n, int b = kB) { return (int)((n + b - 1) / b); }
+
+__device__ __forceinline__ bool row_has(const int32_t* row, int n, int32_t j) {
+  for (int s = 0; s < n; ++s)
+    if (row[s] == j) return true;
+  return false;
+}
+
+// bit 0: id out of range, bit 1: self loop, bit 2: duplicate in a row
+__global__ void k_validate(const int32_t* __restrict__ knn, int64_t M, int k, int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int32_t* row = knn + i * k;
+  int bad = 0;
+  for (int s = 0; s < k; ++s) {
+    const int32_t j = row[s];
+    if (j < 0 || (int64_t)j >= M) bad |= 1;
+    if ((int64_t)j == i) bad |= 2;
+    for (int t = 0; t < s; ++t)
+      if (row[t] == j) bad |= 4;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+__device__ __forceinline__ bool connected(const int32_t* __restrict__ knn, int k, int64_t i,
+                                          const int32_t* rowi, int64_t j) {
+  if (j == i) return true;
+  if (row_has(rowi, k, (int32_t)j)) return true;
+  return row_has(knn + j * k, k, (int32_t)i);
+}
+
+// Draw t of vertex i: x = output t of SplitMix64 seeded with
+// s_i = output i of SplitMix64 seeded with (seed ^ "rn_lists");
+// candidate floor(x * M / 2^64).  Kept unless connected to i or already kept;
+// after 64 r draws missing slots are filled by scanning 0..M-1; the rest
+// stay -1.
+__global__ void k_rn_sample(const int32_t* __restrict__ knn, int64_t M, int k, int r,
+                            uint64_t seed, int32_t* __restrict__ rn, int32_t* __restrict__ rc,
+                            unsigned long long* empty) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int32_t* rowi = knn + i * k;
+  int32_t* out = rn + i * r;
+  int got = 0;
+  const uint64_t si = sm64_out(seed ^ kDomainRn, (uint64_t)i);
+  const int64_t tmax = 64 * (int64_t)r;
+  for (int64_t t = 0; t < tmax && got < r; ++t) {
+    const int64_t j = (int64_t)__umul64hi(sm64_out(si, (uint64_t)t), (uint64_t)M);
+    if (connected(knn, k, i, rowi, j) || row_has(out, got, (int32_t)j)) continue;
+    out[got++] = (int32_t)j;
+  }
+  for (int64_t j = 0; j < M && got < r; ++j) {
+    if (connected(knn, k, i, rowi, j) || row_has(out, got, (int32_t)j)) continue;
+    out[got++] = (int32_t)j;
+  }
+  for (int s = got; s < r; ++s) out[s] = -1;
+  rc[i] = got;
+  if (got < r) atomicAdd(empty, (unsigned long long)(r - got));
+}
+
+// In-degree of every vertex: nn entries (i -> j) and kept rn entries.  With
+// dedup an nn entry is not mirrored when j already lists i (mutual pair).
+__global__ void k_count_in(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
+                           int64_t M, int k, int r, int dedup, int32_t* __restrict__ in_nn,
+                           int32_t* __restrict__ in_rn) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n_nn = M * k;
+  if (e < n_nn) {
+    const int64_t i = e / k;
+    const int32_t j = knn[e];
+    if (dedup && row_has(knn + (int64_t)j * k, k, (int32_t)i)) return;
+    atomicAdd(&in_nn[j], 1);
+  } else if (e < n_nn + M * r) {
+    const int32_t j = rn[e - n_nn];
+    if (j >= 0) atomicAdd(&in_rn[j], 1);
+  }
+}
+
+// Degree and the descending-degree sort key; per-context totals.
+__global__ void k_degree(const int32_t* __restrict__ rc, const int32_t* __restrict__ in_nn,
+                         const int32_t* __restrict__ in_rn, int64_t M, int k,
+                         int32_t* __restrict__ deg, uint32_t* __restrict__ key,
+                         int32_t* __restrict__ val, unsigned long long* sum_deg,
+                         int32_t* max_deg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int32_t d = k + rc[i] + in_nn[i] + in_rn[i];
+  deg[i] = d;
+  key[i] = 0xFFFFu - (uint32_t)min(d, 0xFFFF);
+  val[i] = (int32_t)i;
+  atomicAdd(sum_deg, (unsigned long long)d);
+  atomicMax(max_deg, d);
+}
+
+// ---- stable LSD radix sort, 8-bit digits, 1024 elements per block --------
+
+constexpr int kRadixBlock = 1024;
+
+__global__ void __launch_bounds__(kRadixBlock) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                            int64_t n, int shift, int nblocks,
+                                                            int32_t* __restrict__ counts) {
+  __shared__ int32_t h[256];
+  if (threadIdx.x < 256) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t e = (int64_t)blockIdx.x * kRadixBlock + threadIdx.x;
+  if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1);
+  __syncthreads();
+  if (threadIdx.x < 256) counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    int32_t* __restrict__ vout, int64_t n, int shift, int nblocks,
+    const int32_t* __restrict__ offs) {
+  __shared__ int32_t wc[kRadixBlock / 32][256];
+  for (int t = threadIdx.x; t < (kRadixBlock / 32) * 256; t += kRadixBlock) (&wc[0][0])[t] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * kRadixBlock + threadIdx.x;
+  const bool act = e < n;
+  const unsigned amask = __ballot_sync(0xffffffffu, act);
+  uint32_t key = 0, d = 0;
+  int rank = 0;
+  if (act) {
+    key = kin[e];
+    d = (key >> shift) & 255u;
+    const unsigned peers = __match_any_sync(amask, d);
+    rank = __popc(peers & ((1u << lane) - 1u));
+    if (rank == 0) wc[w][d] = __popc(peers);
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    int run = 0;
+    for (int q = 0; q < kRadixBlock / 32; ++q) {
+      const int t = wc[q][threadIdx.x];
+      wc[q][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  if (act) {
+    const int64_t pos = (int64_t)offs[(int64_t)d * nblocks + blockIdx.x] + wc[w][d] + rank;
+    kout[pos] = key;
+    vout[pos] = vin[e];
+  }
+}
+
+// ---- layout sizing ---------------------------------------------------------
+
+__global__ void k_sorted_info(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg,
+                              const int32_t* __restrict__ rc, int64_t M, int k, int hub_thr,
+                              int32_t* __restrict__ inv, int32_t* __restrict__ deg_p,
+                              int32_t* __restrict__ outc_p, int32_t* n_hub) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= M) return;
+  const int32_t i = perm[p];
+  inv[i] = (int32_t)p;
+  const int32_t d = deg[i];
+  deg_p[p] = d;
+  outc_p[p] = k + rc[i];
+  if (d >= hub_thr) atomicAdd(n_hub, 1);
+}
+
+// Storage (in uint32 slots) of hub row p and of SELL slice s; 0 past the end.
+__global__ void k_sizes(const int32_t* __restrict__ deg_p, int64_t M, const int32_t* n_hub_d,
+                        int64_t max_slices, int64_t* __restrict__ hub_sz,
+                        int64_t* __restrict__ slice_sz, int32_t* __restrict__ slice_w) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n_hub = *n_hub_d;
+  if (t < M) hub_sz[t] = (t < n_hub) ? (int64_t)((deg_p[t] + 3) & ~3) : 0;
+  if (t < max_slices) {
+    const int64_t p0 = n_hub + 32 * t;
+    int32_t w = 0;
+    if (p0 < M) w = (deg_p[p0] + 3) >> 2;  // sorted descending: first of the slice is the max
+    slice_w[t] = w;
+    slice_sz[t] = (int64_t)w * 128;
+  }
+}
+
+__global__ void k_widen(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = a[t];
+}
+
+__global__ void k_offsets_i32(const int64_t* __restrict__ in, int64_t n, int64_t add,
+                              int32_t* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= n) out[t] = (int32_t)(in[t] + add);
+}
+
+__device__ __forceinline__ int64_t slot_addr(int64_t p, int t, int64_t n_hub,
+                                             const int32_t* __restrict__ hub_off,
+                                             const int32_t* __restrict__ slice_off) {
+  if (p < n_hub) return (int64_t)hub_off[p] + t;
+  const int64_t q = p - n_hub;
+  return (int64_t)slice_off[q >> 5] + ((int64_t)(t >> 2) * 32 + (q & 31)) * 4 + (t & 3);
+}
+
+// Out-entries of input vertex i: its k nn ids, then its kept rn ids (rn bit set).
+__global__ void k_fill_out(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
+                           const int32_t* __restrict__ rc, const int32_t* __restrict__ inv,
+                           int64_t M, int k, int r, int64_t n_hub,
+                           const int32_t* __restrict__ hub_off,
+                           const int32_t* __restrict__ slice_off, uint32_t* __restrict__ ids) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int64_t p = inv[i];
+  for (int s = 0; s < k; ++s)
+    ids[slot_addr(p, s, n_hub, hub_off, slice_off)] = (uint32_t)inv[knn[i * k + s]];
+  const int n = rc[i];
+  for (int s = 0; s < n; ++s)
+    ids[slot_addr(p, k + s, n_hub, hub_off, slice_off)] = (uint32_t)inv[rn[i * r + s]] | kRnBit;
+}
+
+// In-entries: the mirror of every out-entry (i -> j) lands in row j.
+__global__ void k_fill_in(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
+                          const int32_t* __restrict__ inv, const int32_t* __restrict__ outc_p,
+                          int64_t M, int k, int r, int dedup, int64_t n_hub,
+                          const int32_t* __restrict__ hub_off,
+                          const int32_t* __restrict__ slice_off, int32_t* __restrict__ cursor,
+                          uint32_t* __restrict__ ids) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n_nn = M * k;
+  int64_t i;
+  int32_t j;
+  uint32_t bit;
+  if (e < n_nn) {
+    i = e / k;
+    j = knn[e];
+    if (dedup && row_has(knn + (int64_t)j * k, k, (int32_t)i)) return;
+    bit = 0;
+  } else if (e < n_nn + M * r) {
+    i = (e - n_nn) / r;
+    j = rn[e - n_nn];
+    if (j < 0) return;
+    bit = kRnBit;
+  } else {
+    return;
+  }
+  const int64_t pj = inv[j];
+  const int slot = outc_p[pj] + atomicAdd(&cursor[pj], 1);
+  ids[slot_addr(pj, slot, n_hub, hub_off, slice_off)] = (uint32_t)inv[i] | bit;
+}
+
+// Sorts the in-part of each SELL row (thread per row, insertion sort; rows are short).
+__global__ void k_sort_in_sell(const int32_t* __restrict__ deg_p, const int32_t* __restrict__ outc_p,
+                               int64_t M, int64_t n_hub, const int32_t* __restrict__ slice_off,
+                               uint32_t* __restrict__ ids) {
+  const int64_t p = n_hub + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= M) return;
+  const int b = outc_p[p], n = deg_p[p];
+  for (int t = b + 1; t < n; ++t) {
+    const uint32_t v = ids[slot_addr(p, t, n_hub, nullptr, slice_off)];
+    int u = t - 1;
+    while (u >= b) {
+      const uint32_t w = ids[slot_addr(p, u, n_hub, nullptr, slice_off)];
+      if (w <= v) break;
+      ids[slot_addr(p, u + 1, n_hub, nullptr, slice_off)] = w;
+      --u;
+    }
+    ids[slot_addr(p, u + 1, n_hub, nullptr, slice_off)] = v;
+  }
+}
+
+// Sorts the in-part of each hub row: warp per row, stable rank sort from a copy.
+__global__ void k_sort_in_hub(const int32_t* __restrict__ deg_p, const int32_t* __restrict__ outc_p,
+                              int64_t n_hub, const int32_t* __restrict__ hub_off,
+                              const uint32_t* __restrict__ copy, uint32_t* __restrict__ ids) {
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= n_hub) return;
+  const int64_t base = hub_off[p];
+  const int b = outc_p[p], n = deg_p[p];
+  for (int t = b + lane; t < n; t += 32) {
+    const uint32_t v = copy[base + t];
+    int rank = 0;
+    for (int u = b; u < n; ++u) {
+      const uint32_t w = copy[base + u];
+      rank += (w < v) || (w == v && u < t);
+    }
+    ids[base + b + rank] = v;
+  }
+}
+
+// ---- exclusive scan of int64 values; out has n + 1 entries ----------------
+
+constexpr int kScanBlock = 1024, kScanItems = 4, kScanTile = kScanBlock * kScanItems;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_tile(const int64_t* __restrict__ in, int64_t n,
+                                                          int64_t* __restrict__ out,
+                                                          int64_t* __restrict__ bsum) {
+  __shared__ int64_t wsum[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t tot = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = (base + q < n) ? in[base + q] : 0;
+    tot += v[q];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t s = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    wsum[lane] = s;
+  }
+  __syncthreads();
+  int64_t run = incl - tot + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    run += v[q];
+    if (base + q < n) out[base + q + 1] = run;
+  }
+  if (threadIdx.x == kScanBlock - 1 && bsum) bsum[blockIdx.x] = wsum[31];
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ boff) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t + 1] += boff[t / kScanTile];
+}
+
+// Device buffers freed on scope exit.
+struct Scratch {
+  std::vector<void*> bufs;
+  cudaStream_t s;
+  bool ok = true;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  template <class T>
+  T* get(int64_t n) {
+    void* q = nullptr;
+    if (cudaMallocAsync(&q, (size_t)(n > 0 ? n : 1) * sizeof(T), s) != cudaSuccess) {
+      ok = false;
+      return nullptr;
+    }
+    bufs.push_back(q);
+    return (T*)q;
+  }
+  ~Scratch() {
+    for (void* q : bufs) cudaFreeAsync(q, s);
+  }
+};
+
+cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, Scratch& sc,
+                     int64_t* launches) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    k_scan_tile<<<1, kScanBlock, 0, s>>>(in, n, out, nullptr);
+    ++*launches;
+    return cudaGetLastError();
+  }
+  int64_t* bsum = sc.get<int64_t>(tiles);
+  int64_t* boff = sc.get<int64_t>(tiles + 1);
+  if (!sc.ok) return cudaErrorMemoryAllocation;
+  k_scan_tile<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, n, out, bsum);
+  ++*launches;
+  cudaError_t e = scan_i64(bsum, boff, tiles, s, sc, launches);
+  if (e != cudaSuccess) return e;
+  k_scan_add<<<nblk(n), kB, 0, s>>>(out, n, boff);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+struct HostTotals {
+  int32_t err;
+  int32_t n_hub;
+  int32_t max_deg;
+  int32_t pad;
+  unsigned long long sum_deg;
+  unsigned long long empty;
+  int64_t hub_total;
+  int64_t sell_total;
+};
+
+#define IVHD_TRY(x)                                                      \
+  do {                                                                   \
+    cudaError_t e_ = (x);                                                \
+    if (e_ != cudaSuccess)                                               \
+      return (e_ == cudaErrorMemoryAllocation) ? IVHD_ERR_OOM : IVHD_ERR_CUDA; \
+  } while (0)
+
+ivhd_status build_layout(ivhd_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  const int k = ctx->k, r = ctx->r;
+  const int dedup = ctx->p.dedup_mutual ? 1 : 0;
+  Scratch sc(s);
+
+  // totals block lives in device memory, read back twice
+  HostTotals* tot_d = sc.get<HostTotals>(1);
+  if (!sc.ok) return IVHD_ERR_OOM;
+  IVHD_TRY(cudaMemsetAsync(tot_d, 0, sizeof(HostTotals), s));
+
+  // 1. validation -- nothing below may index with an unchecked id
+  k_validate<<<nblk(M), kB, 0, s>>>(ctx->knn, M, k, &tot_d->err);
+  ++ctx->setup_launches;
+  IVHD_TRY(cudaGetLastError());
+  HostTotals h{};
+  IVHD_TRY(cudaMemcpyAsync(&h, tot_d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  IVHD_TRY(cudaStreamSynchronize(s));
+  if (h.err) return IVHD_ERR_INDEX;
+
+  // 2. random neighbours
+  int32_t* rc = sc.get<int32_t>(M);
+  int32_t* in_nn = sc.get<int32_t>(M);
+  int32_t* in_rn = sc.get<int32_t>(M);
+  int32_t* deg = sc.get<int32_t>(M);
+  uint32_t* key0 = sc.get<uint32_t>(M);
+  uint32_t* key1 = sc.get<uint32_t>(M);
+  int32_t* val0 = sc.get<int32_t>(M);
+  int32_t* deg_p = sc.get<int32_t>(M);
+  int32_t* outc_p = sc.get<int32_t>(M);
+  int32_t* cursor = sc.get<int32_t>(M);
+  if (!sc.ok) return IVHD_ERR_OOM;
+  if (r > 0) {
+    k_rn_sample<<<nblk(M), kB, 0, s>>>(ctx->knn, M, k, r, ctx->p.seed, ctx->rn, rc, &tot_d->empty);
+    ++ctx->setup_launches;
+  } else {
+    IVHD_TRY(cudaMemsetAsync(rc, 0, M * sizeof(int32_t), s));
+  }
+  IVHD_TRY(cudaGetLastError());
+
+  // 3. degrees
+  IVHD_TRY(cudaMemsetAsync(in_nn, 0, M * sizeof(int32_t), s));
+  IVHD_TRY(cudaMemsetAsync(in_rn, 0, M * sizeof(int32_t), s));
+  IVHD_TRY(cudaMemsetAsync(cursor, 0, M * sizeof(int32_t), s));
+  const int64_t n_entries = M * (int64_t)(k + r);
+  k_count_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, M, k, r, dedup, in_nn, in_rn);
+  ++ctx->setup_launches;
+  k_degree<<<nblk(M), kB, 0, s>>>(rc, in_nn, in_rn, M, k, deg, key0, val0, &tot_d->sum_deg,
+                                  &tot_d->max_deg);
+  ++ctx->setup_launches;
+  IVHD_TRY(cudaGetLastError());
+
+  // 4. stable sort by descending degree: two 8-bit passes over the 16-bit key
+  {
+    const int nb = (int)((M + kRadixBlock - 1) / kRadixBlock);
+    const int64_t nc = (int64_t)nb * 256;
+    int32_t* counts = sc.get<int32_t>(nc);
+    int64_t* c64 = sc.get<int64_t>(nc);
+    int64_t* o64 = sc.get<int64_t>(nc + 1);
+    int32_t* offs = sc.get<int32_t>(nc + 1);
+    if (!sc.ok) return IVHD_ERR_OOM;
+    int32_t* val1 = sc.get<int32_t>(M);
+    if (!sc.ok) return IVHD_ERR_OOM;
+    // pass 0: (key0, val0) -> (key1, val1); pass 1: (key1, val1) -> (key0, perm)
+    for (int pass = 0; pass < 2; ++pass) {
+      const int shift = 8 * pass;
+      const uint32_t* kin = pass ? key1 : key0;
+      const int32_t* vin = pass ? val1 : val0;
+      uint32_t* kout = pass ? key0 : key1;
+      int32_t* vout = pass ? ctx->perm : val1;
+      k_radix_hist<<<nb, kRadixBlock, 0, s>>>(kin, M, shift, nb, counts);
+      ++ctx->setup_launches;
+      k_widen<<<nblk(nc), kB, 0, s>>>(counts, c64, nc);
+      ++ctx->setup_launches;
+      IVHD_TRY(cudaGetLastError());
+      IVHD_TRY(scan_i64(c64, o64, nc, s, sc, &ctx->setup_launches));
+      k_offsets_i32<<<nblk(nc + 1), kB, 0, s>>>(o64, nc, 0, offs);
+      ++ctx->setup_launches;
+      k_radix_scatter<<<nb, kRadixBlock, 0, s>>>(kin, vin, kout, vout, M, shift, nb, offs);
+      ++ctx->setup_launches;
+      IVHD_TRY(cudaGetLastError());
+    }
+  }
+
+  // 5. sizes and offsets
+  k_sorted_info<<<nblk(M), kB, 0, s>>>(ctx->perm, deg, rc, M, k, ctx->hub_threshold, ctx->inv,
+                                       deg_p, outc_p, &tot_d->n_hub);
+  ++ctx->setup_launches;
+  const int64_t max_slices = (M + 31) / 32;
+  int64_t* hub_sz = sc.get<int64_t>(M);
+  int64_t* hub_o64 = sc.get<int64_t>(M + 1);
+  int64_t* sl_sz = sc.get<int64_t>(max_slices);
+  int64_t* sl_o64 = sc.get<int64_t>(max_slices + 1);
+  int32_t* slice_w = sc.get<int32_t>(max_slices);
+  if (!sc.ok) return IVHD_ERR_OOM;
+  k_sizes<<<nblk(M > max_slices ? M : max_slices), kB, 0, s>>>(deg_p, M, &tot_d->n_hub,
+                                                               max_slices, hub_sz, sl_sz, slice_w);
+  ++ctx->setup_launches;
+  IVHD_TRY(cudaGetLastError());
+  IVHD_TRY(scan_i64(hub_sz, hub_o64, M, s, sc, &ctx->setup_launches));
+  IVHD_TRY(scan_i64(sl_sz, sl_o64, max_slices, s, sc, &ctx->setup_launches));
+  IVHD_TRY(cudaMemcpyAsync(&tot_d->hub_total, hub_o64 + M, sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, s));
+  IVHD_TRY(cudaMemcpyAsync(&tot_d->sell_total, sl_o64 + max_slices, sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, s));
+  IVHD_TRY(cudaMemcpyAsync(&h, tot_d, sizeof(h), cudaMemcpyDeviceToHost, s));
+  IVHD_TRY(cudaStreamSynchronize(s));
+
+  ctx->n_hub = h.n_hub;
+  ctx->n_slices = (M - h.n_hub + 31) / 32;
+  ctx->n_slots = h.hub_total + h.sell_total;
+  ctx->nnz_sym = (int64_t)h.sum_deg;
+  ctx->n_terms = ctx->nnz_sym / 2;
+  ctx->max_degree = h.max_deg;
+  ctx->empty_rn = (int32_t)h.empty;
+  if (ctx->n_slots >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
+
+  IVHD_TRY(cudaMallocAsync((void**)&ctx->ids, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
+  IVHD_TRY(cudaMallocAsync((void**)&ctx->hub_off, (size_t)(ctx->n_hub + 1) * sizeof(int32_t), s));
+  IVHD_TRY(cudaMallocAsync((void**)&ctx->slice_off, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
+  IVHD_TRY(cudaMallocAsync((void**)&ctx->slice_w, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
+  IVHD_TRY(cudaMemsetAsync(ctx->ids, 0xFF, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
+  k_offsets_i32<<<nblk(ctx->n_hub + 1), kB, 0, s>>>(hub_o64, ctx->n_hub, 0, ctx->hub_off);
+  ++ctx->setup_launches;
+  k_offsets_i32<<<nblk(ctx->n_slices + 1), kB, 0, s>>>(sl_o64, ctx->n_slices, h.hub_total,
+                                                       ctx->slice_off);
+  ++ctx->setup_launches;
+  IVHD_TRY(cudaMemcpyAsync(ctx->slice_w, slice_w, (size_t)ctx->n_slices * sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, s));
+  IVHD_TRY(cudaGetLastError());
+
+  k_fill_out<<<nblk(M), kB, 0, s>>>(ctx->knn, ctx->rn, rc, ctx->inv, M, k, r, ctx->n_hub,
+                                    ctx->hub_off, ctx->slice_off, ctx->ids);
+  ++ctx->setup_launches;
+  k_fill_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, ctx->inv, outc_p, M, k, r, dedup,
+                                           ctx->n_hub, ctx->hub_off, ctx->slice_off, cursor,
+                                           ctx->ids);
+  ++ctx->setup_launches;
+  IVHD_TRY(cudaGetLastError());
+  if (M - ctx->n_hub > 0)
+    k_sort_in_sell<<<nblk(M - ctx->n_hub), kB, 0, s>>>(deg_p, outc_p, M, ctx->n_hub,
+                                                        ctx->slice_off, ctx->ids);
+    ++ctx->setup_launches;
+  if (ctx->n_hub > 0) {
+    uint32_t* copy = sc.get<uint32_t>(h.hub_total);
+    if (!sc.ok) return IVHD_ERR_OOM;
+    IVHD_TRY(cudaMemcpyAsync(copy, ctx->ids, (size_t)h.hub_total * sizeof(uint32_t),
+                             cudaMemcpyDeviceToDevice, s));
+    k_sort_in_hub<<<nblk(ctx->n_hub * 32), kB, 0, s>>>(deg_p, outc_p, ctx->n_hub, ctx->hub_off,
+                                                       copy, ctx->ids);
+    ++ctx->setup_launches;
+  }
+  IVHD_TRY(cudaGetLastError());
+  return IVHD_OK;
+}
+
+}  // namespace ivhd

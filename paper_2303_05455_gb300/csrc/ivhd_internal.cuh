@@ -1,0 +1,139 @@
+// ivhd_internal.cuh -- shared definitions of the libivhd CUDA sources.
+//
+// Device layout of one embedding context (all arrays in HBM, vertex order
+// "p" = the degree-sorted order chosen at create, see ivhd_build.cu):
+//
+//   y[2]       float2[M]  positions, ping-pong (step reads y[cur], writes y[cur^1]);
+//                         for Nesterov they hold the look-ahead point y + a v
+//   s1         float2[M]  velocity (momentum, Nesterov) or E[g^2] (Adadelta)
+//   s2         float2[M]  E[dx^2] (Adadelta only)
+//   ids        uint32[]   symmetric adjacency; entry = neighbour p-index,
+//                         bit 31 set for a random-neighbour term, 0xFFFFFFFF = padding
+//   hub rows   p < n_hub: contiguous rows ids[hub_off[p] .. hub_off[p+1]),
+//                         lengths padded to a multiple of 4, one warp per row
+//   SELL rows  p >= n_hub: slices of 32 consecutive vertices; slice s starts at
+//                         ids[slice_off[s]] and stores slice_w[s] groups of 4 slots
+//                         as [group][lane][4] so that a warp reads one group with
+//                         one coalesced 512-byte int4 load
+//   perm/inv   int32[M]   p -> input vertex id, input vertex id -> p
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ivhd.h"
+
+namespace ivhd {
+
+constexpr uint32_t kRnBit = 0x80000000u;
+constexpr uint32_t kIdxMask = 0x7FFFFFFFu;
+constexpr uint32_t kPad = 0xFFFFFFFFu;
+constexpr int kDefaultHubThreshold = 128;
+constexpr int kStepBlock = 256;  // 8 warps
+constexpr int kWarpsPerBlock = kStepBlock / 32;
+
+enum Mode { kMomentum = 0, kNesterov = 1, kAdadelta = 2, kForces = 3, kStress = 4 };
+
+// SplitMix64 (Steele, Lea, Flood 2014): output t of the generator seeded
+// with s is mix(s + (t+1) * gamma), mix = the variant-13 finaliser.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kDomainRn = 0x726E5F6C69737473ull;    // "rn_lists"
+constexpr uint64_t kDomainInit = 0x696E69745F706F73ull;  // "init_pos"
+
+__host__ __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_out(uint64_t seed, uint64_t t) {
+  return sm64_mix(seed + (t + 1) * kGamma);
+}
+
+// Read-only streaming load that does not allocate in L1 (the id stream is
+// touched once per step; L1 is left to the position gathers).
+__device__ __forceinline__ int4 ld_stream_v4(const int4* p) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Per-step arguments of the fused kernel (passed by value).
+struct StepArgs {
+  const uint32_t* __restrict__ ids;
+  const int32_t* __restrict__ hub_off;
+  const int32_t* __restrict__ slice_off;
+  const int32_t* __restrict__ slice_w;
+  const float2* __restrict__ y_in;
+  float2* __restrict__ y_out;
+  float2* __restrict__ s1;
+  float2* __restrict__ s2;
+  const int32_t* __restrict__ perm;  // forces mode: scatter to input order
+  float2* __restrict__ f_out;        // forces mode output
+  double* __restrict__ partials;     // stress mode: one double per block
+  int32_t* __restrict__ flag;        // stress mode: non-finite flag
+  int32_t M, n_hub, n_slices, nb_hub;
+  float c, a, b, rho, eps;
+};
+
+}  // namespace ivhd
+
+// The opaque context of the public ABI.
+struct ivhd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ivhd_params p{};
+  int64_t M = 0;
+  int32_t k = 0, r = 0;
+  float c = 0.f;
+  int hub_threshold = ivhd::kDefaultHubThreshold;
+  bool poisoned = false;
+
+  // graph and layout
+  int32_t* knn = nullptr;   // M*k, input ids
+  int32_t* rn = nullptr;    // M*r, input ids, -1 empty
+  int32_t* perm = nullptr;  // p -> i
+  int32_t* inv = nullptr;   // i -> p
+  uint32_t* ids = nullptr;
+  int32_t* hub_off = nullptr;
+  int32_t* slice_off = nullptr;
+  int32_t* slice_w = nullptr;
+  int64_t n_slots = 0, n_hub = 0, n_slices = 0;
+
+  // state
+  float2* y[2] = {nullptr, nullptr};
+  int cur = 0;
+  float2* s1 = nullptr;
+  float2* s2 = nullptr;
+
+  // scratch for reductions
+  double* partials = nullptr;
+  double* red_out = nullptr;
+  int32_t* flag = nullptr;
+  int64_t n_partials = 0;
+
+  // CUDA graph of kGraphSteps steps, one per starting parity
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+
+  // counters
+  int64_t n_terms = 0, nnz_sym = 0;
+  int32_t max_degree = 0, empty_rn = 0;
+  int64_t steps_done = 0, launches = 0, setup_launches = 0, aux_launches = 0;
+};
+
+namespace ivhd {
+
+// ivhd_build.cu
+ivhd_status build_layout(ivhd_ctx* ctx);
+
+// ivhd_step.cu
+cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s);
+cudaError_t launch_forces(ivhd_ctx* ctx, float2* out_input_order);
+cudaError_t launch_stress(ivhd_ctx* ctx);  // result in ctx->red_out[0], flag in ctx->flag
+cudaError_t launch_unpermute(ivhd_ctx* ctx, float2* out_input_order);
+cudaError_t launch_set_positions(ivhd_ctx* ctx, const float2* in_input_order);
+cudaError_t launch_init_positions(ivhd_ctx* ctx);
+int step_grid(const ivhd_ctx* ctx);
+
+}  // namespace ivhd

@@ -1,0 +1,245 @@
+// ivhd_knn.cu -- exact brute-force kNN graph (the set-up step of Sec. 5.1).
+//
+// The paper builds the kNN graph with FAISS (IVFADC, approximate) and keeps
+// it out of the embedding time.  Here the graph is exact and its decisions are
+// reproducible bit for bit on the CPU:
+//   float data:  d(q, j) = the FP32 chain acc = fma(x_qd - x_jd, x_qd - x_jd, acc),
+//                d = 0 .. N-1 in order, starting from acc = 0;
+//   uint8 data:  exact integer |x_q|^2 + |x_j|^2 - 2 <x_q, x_j> via dp4a.
+// Ties go to the lower index.  Each CTA owns 128 queries and sweeps all
+// candidates in tiles of 128 with an 8x8 register block per thread; after each
+// tile the 128x128 distances go through shared memory into a per-query sorted
+// list of the k best.
+#include "ivhd_internal.cuh"
+
+namespace ivhd {
+namespace {
+
+constexpr int kTQ = 128;     // queries per CTA
+constexpr int kTC = 128;     // candidates per tile
+constexpr int kDK = 32;      // feature chunk (floats) / 4-byte words (uint8)
+constexpr int kThreads = 256;
+constexpr int kDStride = kTC + 4;  // distance-tile row stride (floats)
+
+struct SmemLayout {
+  // [kDK][kTQ] + [kDK][kTC] staging, then the distance tile, then the lists
+  static constexpr size_t stage_bytes = (size_t)2 * kDK * (kTQ + 4) * 4;
+  static constexpr size_t tile_bytes = (size_t)kTQ * kDStride * 4;
+  static size_t lists_bytes(int k) { return (size_t)kTQ * k * 8; }
+  static size_t total(int k) { return stage_bytes + tile_bytes + lists_bytes(k); }
+};
+
+template <class D>
+__device__ __forceinline__ bool better(D d, int j, D bd, int bj) {
+  return d < bd || (d == bd && j < bj);
+}
+
+// Merge one 128-candidate row of the tile into query t's sorted list.
+template <class D>
+__device__ __forceinline__ void merge_row(const D* row, int c0, int64_t M, int64_t q, int k,
+                                          D* ld, int* lj, int& n) {
+  for (int b = 0; b < kTC; ++b) {
+    const int64_t j = c0 + b;
+    if (j >= M) break;
+    if (j == q) continue;
+    const D d = row[b];
+    if (n == k && !better(d, (int)j, ld[k - 1], lj[k - 1])) continue;
+    int pos = (n < k) ? n : k - 1;
+    while (pos > 0 && better(d, (int)j, ld[pos - 1], lj[pos - 1])) {
+      ld[pos] = ld[pos - 1];
+      lj[pos] = lj[pos - 1];
+      --pos;
+    }
+    ld[pos] = d;
+    lj[pos] = (int)j;
+    if (n < k) ++n;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ X, int64_t M,
+                                                      int N, int k, int32_t* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* Qs = reinterpret_cast<float*>(smem);                    // [kDK][kTQ + 4]
+  float* Cs = Qs + kDK * (kTQ + 4);                              // [kDK][kTC + 4]
+  float* Dt = reinterpret_cast<float*>(smem + SmemLayout::stage_bytes);  // [kTQ][kDStride]
+  float* Ld = reinterpret_cast<float*>(smem + SmemLayout::stage_bytes + SmemLayout::tile_bytes);
+  int* Lj = reinterpret_cast<int*>(Ld + kTQ * k);
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t q0 = (int64_t)blockIdx.x * kTQ;
+  int nlist = 0;  // used by threads tid < kTQ
+
+  for (int64_t c0 = 0; c0 < M; c0 += kTC) {
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+    for (int d0 = 0; d0 < N; d0 += kDK) {
+      // stage a [kDK x 128] slab of queries and candidates, transposed
+      for (int e = tid; e < kDK * kTQ; e += kThreads) {
+        const int row = e / kDK, dd = e % kDK;
+        const int64_t gq = q0 + row, gc = c0 + row;
+        const int d = d0 + dd;
+        Qs[dd * (kTQ + 4) + row] = (gq < M && d < N) ? X[gq * N + d] : 0.f;
+        Cs[dd * (kTC + 4) + row] = (gc < M && d < N) ? X[gc * N + d] : 0.f;
+      }
+      __syncthreads();
+      const int dn = min(kDK, N - d0);
+      for (int dd = 0; dd < dn; ++dd) {
+        const float4 qa = *reinterpret_cast<const float4*>(&Qs[dd * (kTQ + 4) + ty * 8]);
+        const float4 qb = *reinterpret_cast<const float4*>(&Qs[dd * (kTQ + 4) + ty * 8 + 4]);
+        const float4 ca = *reinterpret_cast<const float4*>(&Cs[dd * (kTC + 4) + tx * 8]);
+        const float4 cb = *reinterpret_cast<const float4*>(&Cs[dd * (kTC + 4) + tx * 8 + 4]);
+        const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const float diff = __fsub_rn(qv[a], cv[b]);
+            acc[a][b] = __fmaf_rn(diff, diff, acc[a][b]);
+          }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) Dt[(ty * 8 + a) * kDStride + tx * 8 + b] = acc[a][b];
+    __syncthreads();
+    if (tid < kTQ && q0 + tid < M)
+      merge_row<float>(Dt + tid * kDStride, (int)c0, M, q0 + tid, k, Ld + tid * k, Lj + tid * k,
+                       nlist);
+    __syncthreads();
+  }
+  if (tid < kTQ && q0 + tid < M)
+    for (int s = 0; s < k; ++s) out[(q0 + tid) * k + s] = Lj[tid * k + s];
+}
+
+__global__ void k_norms_u8(const uint8_t* __restrict__ X, int64_t M, int N,
+                           int32_t* __restrict__ nrm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  int32_t s = 0;
+  for (int d = 0; d < N; ++d) {
+    const int32_t v = X[i * N + d];
+    s += v * v;
+  }
+  nrm[i] = s;
+}
+
+__device__ __forceinline__ uint32_t pack4(const uint8_t* __restrict__ X, int64_t row, int64_t M,
+                                          int N, int d) {
+  uint32_t w = 0;
+  if (row < M) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (d + b < N) w |= (uint32_t)X[row * N + d + b] << (8 * b);
+  }
+  return w;
+}
+
+__global__ void __launch_bounds__(kThreads) k_knn_u8(const uint8_t* __restrict__ X,
+                                                     const int32_t* __restrict__ nrm, int64_t M,
+                                                     int N, int k, int32_t* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* Qs = reinterpret_cast<uint32_t*>(smem);  // [kDK words][kTQ + 4]
+  uint32_t* Cs = Qs + kDK * (kTQ + 4);
+  int32_t* Dt = reinterpret_cast<int32_t*>(smem + SmemLayout::stage_bytes);
+  int32_t* Ld = reinterpret_cast<int32_t*>(smem + SmemLayout::stage_bytes + SmemLayout::tile_bytes);
+  int* Lj = reinterpret_cast<int*>(Ld + kTQ * k);
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t q0 = (int64_t)blockIdx.x * kTQ;
+  int nlist = 0;
+  const int nwords = (N + 3) / 4;
+
+  for (int64_t c0 = 0; c0 < M; c0 += kTC) {
+    uint32_t acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0u;
+    for (int w0 = 0; w0 < nwords; w0 += kDK) {
+      for (int e = tid; e < kDK * kTQ; e += kThreads) {
+        const int row = e / kDK, ww = e % kDK;
+        const int d = (w0 + ww) * 4;
+        Qs[ww * (kTQ + 4) + row] = (w0 + ww < nwords) ? pack4(X, q0 + row, M, N, d) : 0u;
+        Cs[ww * (kTC + 4) + row] = (w0 + ww < nwords) ? pack4(X, c0 + row, M, N, d) : 0u;
+      }
+      __syncthreads();
+      const int wn = min(kDK, nwords - w0);
+      for (int ww = 0; ww < wn; ++ww) {
+        const uint4 qa = *reinterpret_cast<const uint4*>(&Qs[ww * (kTQ + 4) + ty * 8]);
+        const uint4 qb = *reinterpret_cast<const uint4*>(&Qs[ww * (kTQ + 4) + ty * 8 + 4]);
+        const uint4 ca = *reinterpret_cast<const uint4*>(&Cs[ww * (kTC + 4) + tx * 8]);
+        const uint4 cb = *reinterpret_cast<const uint4*>(&Cs[ww * (kTC + 4) + tx * 8 + 4]);
+        const uint32_t qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+        const uint32_t cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = __dp4a(qv[a], cv[b], acc[a][b]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t gq = q0 + ty * 8 + a;
+      const int32_t nq = (gq < M) ? nrm[gq] : 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int64_t gc = c0 + tx * 8 + b;
+        const int32_t nc = (gc < M) ? nrm[gc] : 0;
+        Dt[(ty * 8 + a) * kDStride + tx * 8 + b] = nq + nc - 2 * (int32_t)acc[a][b];
+      }
+    }
+    __syncthreads();
+    if (tid < kTQ && q0 + tid < M)
+      merge_row<int32_t>(Dt + tid * kDStride, (int)c0, M, q0 + tid, k, Ld + tid * k, Lj + tid * k,
+                         nlist);
+    __syncthreads();
+  }
+  if (tid < kTQ && q0 + tid < M)
+    for (int s = 0; s < k; ++s) out[(q0 + tid) * k + s] = Lj[tid * k + s];
+}
+
+}  // namespace
+}  // namespace ivhd
+
+using namespace ivhd;
+
+extern "C" ivhd_status ivhd_knn_build(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                      int32_t k, int32_t* out_knn, void* stream) {
+  if (!X || !out_knn) return IVHD_ERR_ARG;
+  if (M < 2 || M >= (int64_t)0x7FFFFFFF || N < 1 || N > 65536) return IVHD_ERR_ARG;
+  if (k < 1 || (int64_t)k > M - 1 || k > 64) return IVHD_ERR_ARG;
+  if (dtype != IVHD_KNN_F32 && dtype != IVHD_KNN_U8) return IVHD_ERR_ARG;
+  if (dtype == IVHD_KNN_U8 && (int64_t)N * 255 * 255 > 0x3FFFFFFF) return IVHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t sm = SmemLayout::total(k);
+  const unsigned grid = (unsigned)((M + kTQ - 1) / kTQ);
+  cudaError_t e;
+  if (dtype == IVHD_KNN_F32) {
+    e = cudaFuncSetAttribute(k_knn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return IVHD_ERR_CUDA;
+    k_knn_f32<<<grid, kThreads, sm, s>>>((const float*)X, M, N, k, out_knn);
+    e = cudaGetLastError();
+  } else {
+    int32_t* nrm = nullptr;
+    e = cudaMallocAsync((void**)&nrm, (size_t)M * sizeof(int32_t), s);
+    if (e != cudaSuccess) return IVHD_ERR_OOM;
+    k_norms_u8<<<(unsigned)((M + 255) / 256), 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
+    e = cudaFuncSetAttribute(k_knn_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) {
+      k_knn_u8<<<grid, kThreads, sm, s>>>((const uint8_t*)X, nrm, M, N, k, out_knn);
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(nrm, s);
+  }
+  return e == cudaSuccess ? IVHD_OK : IVHD_ERR_CUDA;
+}

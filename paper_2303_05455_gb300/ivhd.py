@@ -1,0 +1,205 @@
+"""Python binding of the IVHD C ABI (argument marshalling only).
+
+Every computation runs in libivhd's CUDA kernels.  Tensors are torch tensors
+(device memory and streams come from PyTorch); numpy arrays are accepted for
+host inputs.  The names follow the C entry points:
+
+    emb = Embedding(knn, r=1, c=0.01, opt="momentum", a=0.9, b=0.01, seed=0)
+    emb.step(2000)
+    y = emb.positions()          # torch.float32 [M, 2] on the device
+
+plus ``knn_build`` (exact brute-force kNN graph) and ``eval_qnx`` / ``eval_cf``
+(Sec. 4.1 quality criteria on sampled rows).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import IvhdError, Info, Params, check
+
+OPTS = {"momentum": 0, "nesterov": 1, "adadelta": 2}
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _dev_i32(a, device) -> torch.Tensor:
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32))
+    return a.to(device=device, dtype=torch.int32).contiguous()
+
+
+class Embedding:
+    """One IVHD embedding context (``ivhd_create`` .. ``ivhd_destroy``).
+
+    knn: int32 [M, k] kNN rows (torch CUDA tensor, torch CPU tensor or numpy);
+    host inputs are copied by the library itself.
+    """
+
+    def __init__(self, knn, r: int = 1, c: float = 0.01, *, opt: str = "momentum",
+                 a: float = 0.9, b: float = 0.01, rho: float = 0.95, eps: float = 1e-6,
+                 seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
+                 hub_threshold: int = 0, stream=None, device=None):
+        self._L = _lib.load()
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if isinstance(knn, np.ndarray):
+            knn_t = torch.from_numpy(np.ascontiguousarray(knn, dtype=np.int32))
+        else:
+            knn_t = knn.to(dtype=torch.int32).contiguous()
+        if knn_t.dim() != 2:
+            raise ValueError("knn must be [M, k]")
+        self.M, self.k = int(knn_t.shape[0]), int(knn_t.shape[1])
+        self.r, self.c = int(r), float(c)
+        p = Params()
+        self._L.ivhd_default_params(ctypes.byref(p))
+        p.opt = OPTS[opt]
+        p.a, p.b, p.rho, p.eps = a, b, rho, eps
+        p.seed = seed & 0xFFFFFFFFFFFFFFFF
+        p.dedup_mutual = int(dedup_mutual)
+        p.init_uniform = int(init_uniform)
+        p.hub_threshold = int(hub_threshold)
+        p.stream = self.stream.cuda_stream or None
+        self.opt = opt
+        self.params = p
+        h = ctypes.c_void_p()
+        on_dev = int(knn_t.is_cuda)
+        check(self._L.ivhd_create(knn_t.data_ptr(), self.M, self.k, self.r, self.c,
+                                  ctypes.byref(p), on_dev, ctypes.byref(h)), "ivhd_create")
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.ivhd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- steps and state ----------------------------------------------------
+    def step(self, n_iter: int = 1):
+        check(self._L.ivhd_step(self._h, int(n_iter)), "ivhd_step")
+
+    def set_positions(self, xy):
+        if isinstance(xy, np.ndarray):
+            arr = np.ascontiguousarray(xy, dtype=np.float32)
+            check(self._L.ivhd_set_positions(self._h, arr.ctypes.data, 0), "ivhd_set_positions")
+            return
+        t = xy.to(dtype=torch.float32).contiguous()
+        check(self._L.ivhd_set_positions(self._h, t.data_ptr(), int(t.is_cuda)),
+              "ivhd_set_positions")
+        if not t.is_cuda:
+            return
+        self._keep = t  # the copy is stream-ordered; keep the source alive until then
+
+    def positions(self, out: torch.Tensor | None = None, host: bool = False):
+        if host:
+            arr = np.empty((self.M, 2), dtype=np.float32)
+            check(self._L.ivhd_positions(self._h, arr.ctypes.data, 0), "ivhd_positions")
+            return arr
+        if out is None:
+            out = torch.empty((self.M, 2), dtype=torch.float32, device=self.device)
+        assert out.dtype == torch.float32 and out.is_contiguous() and out.numel() == 2 * self.M
+        check(self._L.ivhd_positions(self._h, out.data_ptr(), int(out.is_cuda)), "ivhd_positions")
+        return out
+
+    def forces(self, host: bool = True):
+        if host:
+            arr = np.empty((self.M, 2), dtype=np.float32)
+            check(self._L.ivhd_forces(self._h, arr.ctypes.data, 0), "ivhd_forces")
+            return arr
+        out = torch.empty((self.M, 2), dtype=torch.float32, device=self.device)
+        check(self._L.ivhd_forces(self._h, out.data_ptr(), 1), "ivhd_forces")
+        return out
+
+    def stress(self) -> float:
+        v = ctypes.c_double()
+        check(self._L.ivhd_stress(self._h, ctypes.byref(v)), "ivhd_stress")
+        return v.value
+
+    def random_neighbors(self) -> np.ndarray:
+        arr = np.empty((self.M, self.r), dtype=np.int32)
+        check(self._L.ivhd_random_neighbors(self._h, arr.ctypes.data, 0), "ivhd_random_neighbors")
+        return arr
+
+    def info(self) -> dict:
+        inf = Info()
+        check(self._L.ivhd_info(self._h, ctypes.byref(inf)), "ivhd_info")
+        return {name: getattr(inf, name) for name, _ in Info._fields_}
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        check(self._L.ivhd_state_size(self._h, ctypes.byref(n)), "ivhd_state_size")
+        buf = ctypes.create_string_buffer(n.value)
+        check(self._L.ivhd_get_state(self._h, buf, n.value), "ivhd_get_state")
+        return buf.raw
+
+    def set_state(self, state: bytes):
+        buf = ctypes.create_string_buffer(state, len(state))
+        check(self._L.ivhd_set_state(self._h, buf, len(state)), "ivhd_set_state")
+
+
+def knn_build(X: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+    """Exact kNN graph of the rows of X (float32 or uint8 CUDA tensor) -> int32 [M, k]."""
+    L = _lib.load()
+    if not X.is_cuda:
+        raise ValueError("knn_build expects a CUDA tensor")
+    X = X.contiguous()
+    if X.dtype == torch.float32:
+        dt = 0
+    elif X.dtype == torch.uint8:
+        dt = 1
+    else:
+        raise ValueError("X must be float32 or uint8")
+    M, N = int(X.shape[0]), int(X.shape[1])
+    out = torch.empty((M, k), dtype=torch.int32, device=X.device)
+    check(L.ivhd_knn_build(X.data_ptr(), dt, M, N, int(k), out.data_ptr(), _stream_ptr(stream)),
+          "ivhd_knn_build")
+    return out
+
+
+def eval_qnx(Y: torch.Tensor, knn: torch.Tensor, rows: torch.Tensor, return_lowd: bool = False,
+             stream=None):
+    """Q_NX(k) on the sampled rows (Sec. 4.1); optionally the embedded neighbours found."""
+    L = _lib.load()
+    Y = Y.to(dtype=torch.float32).contiguous()
+    knn = _dev_i32(knn, Y.device)
+    rows = rows.to(device=Y.device, dtype=torch.int64).contiguous()
+    k = int(knn.shape[1])
+    low = torch.empty((rows.numel(), k), dtype=torch.int32, device=Y.device) if return_lowd else None
+    q = ctypes.c_double()
+    check(L.ivhd_eval_qnx(Y.data_ptr(), int(Y.shape[0]), knn.data_ptr(), k, rows.data_ptr(),
+                          rows.numel(), low.data_ptr() if low is not None else None,
+                          ctypes.byref(q), _stream_ptr(stream)), "ivhd_eval_qnx")
+    return (q.value, low) if return_lowd else q.value
+
+
+def eval_cf(Y: torch.Tensor, labels, nn: int, rows: torch.Tensor, stream=None) -> float:
+    """Neighbour hit cf_nn (Sec. 4.1, Eq. 4.4) on the sampled rows."""
+    L = _lib.load()
+    Y = Y.to(dtype=torch.float32).contiguous()
+    lab = _dev_i32(labels, Y.device)
+    rows = rows.to(device=Y.device, dtype=torch.int64).contiguous()
+    v = ctypes.c_double()
+    check(L.ivhd_eval_cf(Y.data_ptr(), int(Y.shape[0]), lab.data_ptr(), int(nn), rows.data_ptr(),
+                         rows.numel(), ctypes.byref(v), _stream_ptr(stream)), "ivhd_eval_cf")
+    return v.value

@@ -136,22 +136,31 @@ def random_knn_graph(M: int, k: int, seed: int, *, hub_frac: float = 0.0,
 
     ``n_hubs`` vertices (ids 0..n_hubs-1) are drawn with probability
     ``hub_frac`` per slot, producing heavily skewed in-degrees like the hubs of
-    high-dimensional kNN graphs.  Returns int32 [M, k].
+    high-dimensional kNN graphs.  Rows that come out invalid (self or repeated
+    id) are redrawn whole until none is left.  Returns int32 [M, k].
     """
     assert 1 <= k <= M - 1
+    if n_hubs > 0:
+        assert n_hubs > k, "need more hubs than k so hub-only rows stay possible"
     rng = _rng(seed)
-    out = np.empty((M, k), dtype=np.int32)
-    for i in range(M):
-        row: list[int] = []
-        while len(row) < k:
-            if n_hubs > 0 and rng.random() < hub_frac:
-                j = int(rng.integers(0, n_hubs))
-            else:
-                j = int(rng.integers(0, M))
-            if j != i and j not in row:
-                row.append(j)
-        out[i] = row
-    return out
+
+    def draw(n):
+        c = rng.integers(0, M, size=(n, k), dtype=np.int64)
+        if n_hubs > 0 and hub_frac > 0:
+            hub = rng.random((n, k)) < hub_frac
+            c[hub] = rng.integers(0, n_hubs, size=int(hub.sum()))
+        return c
+
+    out = draw(M)
+    todo = np.arange(M)
+    while todo.size:
+        rows = out[todo]
+        srt = np.sort(rows, axis=1)
+        bad = (rows == todo[:, None]).any(axis=1) | (srt[:, 1:] == srt[:, :-1]).any(axis=1)
+        todo = todo[bad]
+        if todo.size:
+            out[todo] = draw(todo.size)
+    return out.astype(np.int32)
 
 
 def uniform_positions(M: int, seed: int, *, scale: float = 1.0) -> np.ndarray:

@@ -1,0 +1,119 @@
+"""Host-only checks of the C ABI: the library loads, exports every declared
+symbol, and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2303_05455_gb300 import _lib, build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ivhd.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build_lib.build()
+    return _lib.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ivhd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_symbols():
+    assert set(declared_symbols()) == set(_lib.SYMBOLS)
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_params_struct_layout_and_defaults(L):
+    p = _lib.Params()
+    L.ivhd_default_params(ctypes.byref(p))
+    assert ctypes.sizeof(_lib.Params) == 56  # C layout: 20 B + pad, seed, 4 x int32, stream
+    assert (p.opt, p.init_uniform, p.dedup_mutual, p.hub_threshold) == (0, 1, 0, 0)
+    assert p.a == pytest.approx(0.9) and p.b == pytest.approx(0.01)
+    assert p.rho == pytest.approx(0.95) and p.eps == pytest.approx(1e-6)
+    assert L.ivhd_version() == (0 << 16) | (1 << 8)
+    for s in (0, -1, -2, -3, -4, -5, -6, -7, 42):
+        assert isinstance(L.ivhd_status_string(s), bytes)
+
+
+def _create(L, knn, M, k, r, c, p=None, on_dev=0):
+    h = ctypes.c_void_p()
+    pp = ctypes.byref(p) if p is not None else None
+    data = knn.ctypes.data if knn is not None else None
+    st = L.ivhd_create(data, M, k, r, c, pp, on_dev, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("M,k,r,c", [
+    (1, 1, 1, 0.1),      # M < 2
+    (10, 0, 1, 0.1),     # k = 0
+    (10, 10, 1, 0.1),    # k > M - 1
+    (10, 2, -1, 0.1),    # r < 0
+    (10, 2, 1, 0.0),     # c <= 0
+    (10, 2, 1, -1.0),
+    (10, 2, 1, float("nan")),
+    (10, 2, 1, float("inf")),
+    (2 ** 31, 2, 1, 0.1),  # M too large
+    (400_000_000, 2, 1, 0.1),  # symmetric layout beyond 2^31 slots
+])
+def test_create_rejects_bad_sizes(L, M, k, r, c):
+    knn = np.zeros((2, 2), np.int32)
+    st, h = _create(L, knn, M, k, r, c)
+    assert st == -1 and not h.value
+
+
+@pytest.mark.parametrize("field,value", [
+    ("opt", 3), ("opt", -1), ("a", -0.1), ("a", 1.5), ("a", float("nan")), ("b", 0.0),
+    ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
+    ("hub_threshold", 70000), ("reserved", 1),
+])
+def test_create_rejects_bad_params(L, field, value):
+    p = _lib.Params()
+    L.ivhd_default_params(ctypes.byref(p))
+    setattr(p, field, value)
+    knn = np.array([[1], [0], [0]], np.int32)
+    st, h = _create(L, knn, 3, 1, 1, 0.1, p)
+    assert st == -1 and not h.value
+
+
+def test_null_pointers_rejected(L):
+    h = ctypes.c_void_p()
+    assert L.ivhd_create(None, 3, 1, 1, 0.1, None, 0, ctypes.byref(h)) == -1
+    knn = np.array([[1], [0], [0]], np.int32)
+    assert L.ivhd_create(knn.ctypes.data, 3, 1, 1, 0.1, None, 0, None) == -1
+    assert L.ivhd_step(None, 1) == -1
+    assert L.ivhd_positions(None, None, 0) == -1
+    assert L.ivhd_forces(None, None, 0) == -1
+    assert L.ivhd_stress(None, None) == -1
+    assert L.ivhd_random_neighbors(None, None, 0) == -1
+    assert L.ivhd_set_positions(None, None, 0) == -1
+    assert L.ivhd_info(None, None) == -1
+    n = ctypes.c_size_t()
+    assert L.ivhd_state_size(None, ctypes.byref(n)) == -1
+    assert L.ivhd_get_state(None, None, 0) == -1
+    assert L.ivhd_set_state(None, None, 0) == -1
+    L.ivhd_destroy(None)  # no-op
+
+
+def test_knn_build_and_eval_reject_bad_args(L):
+    out = ctypes.c_double()
+    assert L.ivhd_knn_build(None, 0, 10, 4, 2, None, None) == -1
+    dummy = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert L.ivhd_knn_build(dummy, 0, 1, 4, 2, dummy, None) == -1     # M < 2
+    assert L.ivhd_knn_build(dummy, 0, 10, 0, 2, dummy, None) == -1    # N < 1
+    assert L.ivhd_knn_build(dummy, 0, 10, 4, 10, dummy, None) == -1   # k > M-1
+    assert L.ivhd_knn_build(dummy, 0, 1000, 4, 65, dummy, None) == -1  # k > 64
+    assert L.ivhd_knn_build(dummy, 2, 10, 4, 2, dummy, None) == -1    # dtype
+    assert L.ivhd_eval_qnx(dummy, 10, dummy, 0, dummy, 5, None, ctypes.byref(out), None) == -1
+    assert L.ivhd_eval_qnx(dummy, 10, dummy, 3, dummy, 0, None, ctypes.byref(out), None) == -1
+    assert L.ivhd_eval_cf(dummy, 10, dummy, 129, dummy, 5, ctypes.byref(out), None) == -1

@@ -1,0 +1,273 @@
+"""GPU path vs the FP64 oracle through the C ABI (``-m gpu``).
+
+Tolerances.  One step of forces and positions must agree within 1e-5
+relative, measured against the largest magnitude of the oracle array
+(the FP32 rounding of a vertex force is a few units of 2^-24 of the sum of
+its term magnitudes, far inside 1e-5).  Integer work (random neighbours, kNN
+ids, neighbour sets of the quality criteria, layout counters) must match
+exactly: every such decision is made in the same precision on both sides.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2303_05455_gb300 import ivhd, synth
+from paper_2303_05455_gb300._lib import IvhdError
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+OPT_ID = {"momentum": oracle.OPT_MOMENTUM, "nesterov": oracle.OPT_NESTEROV,
+          "adadelta": oracle.OPT_ADADELTA}
+
+
+def close(got, ref, rtol=RTOL):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert got.shape == ref.shape
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - ref).max() if ref.size else 0.0
+    scale = np.abs(ref).max() if ref.size else 0.0
+    assert err <= rtol * scale, f"max err {err:.3e} > {rtol:g} * {scale:.3e}"
+
+
+def graph_case(name):
+    if name == "gmm2k":
+        w = synth.WORKLOADS["gmm2k"]
+        X, _ = synth.workload_features(w)
+        return oracle.knn_f32(X, w.k), w.r, w.c
+    if name == "hubs5k":
+        return synth.random_knn_graph(5000, 5, 21, hub_frac=0.3, n_hubs=20), 2, 0.05
+    if name == "ragged37":
+        return synth.random_knn_graph(37, 3, 4), 1, 0.1
+    if name == "pair":
+        return np.array([[1], [0]], np.int32), 1, 0.1      # no eligible random neighbour
+    if name == "triangle":
+        return np.array([[1, 2], [0, 2], [0, 1]], np.int32), 2, 0.3
+    if name == "star":
+        M = 300                                            # vertex 0 has degree ~M
+        rng = np.random.default_rng(8)
+        g = np.empty((M, 3), np.int32)
+        g[0] = [1, 2, 3]
+        for i in range(1, M):
+            others = rng.choice(np.setdiff1d(np.arange(1, M), [i]), 2, replace=False)
+            g[i] = [0, *others]
+        return g, 1, 0.02
+    raise KeyError(name)
+
+
+CASES = ["gmm2k", "hubs5k", "ragged37", "pair", "triangle", "star"]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("seed", [0, 77])
+def test_random_neighbors_bit_exact(case, seed):
+    knn, r, c = graph_case(case)
+    emb = ivhd.Embedding(knn, r=r, c=c, seed=seed)
+    got = emb.random_neighbors()
+    ref, empty = oracle.random_neighbors(knn, r, seed)
+    assert np.array_equal(got, ref)
+    assert emb.info()["empty_rn"] == empty
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_init_positions_bit_exact(case):
+    knn, r, c = graph_case(case)
+    emb = ivhd.Embedding(knn, r=r, c=c, seed=123)
+    assert np.array_equal(emb.positions(host=True),
+                          oracle.init_positions(knn.shape[0], 123).astype(np.float32))
+
+
+@pytest.mark.parametrize("dedup", [False, True])
+@pytest.mark.parametrize("case", CASES)
+def test_layout_counts_match_term_list(case, dedup):
+    knn, r, c = graph_case(case)
+    emb = ivhd.Embedding(knn, r=r, c=c, seed=3, dedup_mutual=dedup)
+    rn, _ = oracle.random_neighbors(knn, r, 3)
+    terms = oracle.build_terms(knn, rn, dedup=dedup)
+    inf = emb.info()
+    assert inf["n_terms"] == terms.T
+    assert inf["nnz_sym"] == 2 * terms.T
+    deg = np.bincount(np.concatenate([terms.ti, terms.tj]), minlength=knn.shape[0])
+    assert inf["max_degree"] == deg.max()
+
+
+@pytest.mark.parametrize("hub_threshold", [0, 1, 65535])
+@pytest.mark.parametrize("dedup", [False, True])
+@pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
+@pytest.mark.parametrize("case", CASES)
+def test_one_step_and_ten_steps(case, opt, dedup, hub_threshold):
+    knn, r, c = graph_case(case)
+    a, b = 0.9, 0.01
+    emb = ivhd.Embedding(knn, r=r, c=c, opt=opt, a=a, b=b, seed=11, dedup_mutual=dedup,
+                         hub_threshold=hub_threshold)
+    rn, _ = oracle.random_neighbors(knn, r, 11)
+    terms = oracle.build_terms(knn, rn, dedup=dedup)
+    y0 = emb.positions(host=True).astype(np.float64)
+    close(emb.forces(host=True), oracle.forces(y0, terms, c))
+    st = oracle.State.fresh(y0)
+    emb.step(1)
+    oracle.step(st, terms, c, OPT_ID[opt], a=a, b=b)
+    close(emb.positions(host=True), st.Y)
+    emb.step(9)
+    oracle.run(st, terms, c, 9, OPT_ID[opt], a=a, b=b)
+    close(emb.positions(host=True), st.Y)
+    close(emb.forces(host=True), oracle.forces(st.Y, terms, c), rtol=1e-4)
+    assert emb.stress() == pytest.approx(oracle.stress(st.Y, terms, c), rel=1e-5)
+
+
+def test_given_positions_and_zero_distance_pairs():
+    # all vertices start at one point: every rn pair has d = 0 (zero force),
+    # nn forces vanish too; then a spread start through ivhd_set_positions
+    knn, r, c = graph_case("hubs5k")
+    M = knn.shape[0]
+    emb = ivhd.Embedding(knn, r=r, c=c, seed=2, init_uniform=False)
+    rn, _ = oracle.random_neighbors(knn, r, 2)
+    terms = oracle.build_terms(knn, rn)
+    assert np.all(emb.positions(host=True) == 0)
+    assert np.all(emb.forces(host=True) == 0)
+    y = synth.uniform_positions(M, 9, scale=3.0)
+    y[:100] = y[100]                                      # coincident points
+    emb.set_positions(y)
+    close(emb.forces(host=True), oracle.forces(y.astype(np.float64), terms, c))
+    yt = torch.from_numpy(y).cuda()
+    emb.set_positions(yt)
+    torch.cuda.synchronize()
+    close(emb.forces(host=True), oracle.forces(y.astype(np.float64), terms, c))
+
+
+def test_deterministic_bitwise():
+    knn, r, c = graph_case("hubs5k")
+    out = []
+    for _ in range(2):
+        emb = ivhd.Embedding(knn, r=r, c=c, seed=9)
+        emb.step(150)   # crosses the CUDA-graph path (64-step graphs) and the tail
+        out.append(emb.positions(host=True))
+    assert np.array_equal(out[0], out[1])
+
+
+def test_graph_replay_equals_single_launches():
+    knn, r, c = graph_case("gmm2k")
+    a = ivhd.Embedding(knn, r=r, c=c, seed=4)
+    b = ivhd.Embedding(knn, r=r, c=c, seed=4)
+    a.step(130)
+    for _ in range(130):
+        b.step(1)
+    assert np.array_equal(a.positions(host=True), b.positions(host=True))
+    assert a.info()["steps_done"] == 130 and a.info()["kernel_launches"] == 130
+
+
+def test_checkpoint_resume_bitwise_and_mismatch():
+    knn, r, c = graph_case("hubs5k")
+    ref = ivhd.Embedding(knn, r=r, c=c, opt="adadelta", seed=5)
+    ref.step(40)
+    state = ref.get_state()
+    ref.step(30)
+    y_ref = ref.positions(host=True)
+    other = ivhd.Embedding(knn, r=r, c=c, opt="adadelta", seed=5)
+    other.set_state(state)
+    assert other.info()["steps_done"] == 40
+    other.step(30)
+    assert np.array_equal(other.positions(host=True), y_ref)
+    wrong = ivhd.Embedding(knn, r=r, c=c, opt="adadelta", seed=6)
+    with pytest.raises(IvhdError) as e:
+        wrong.set_state(state)
+    assert e.value.status == -7
+
+
+def test_nonfinite_detected():
+    knn, r, c = graph_case("ragged37")
+    emb = ivhd.Embedding(knn, r=r, c=c)
+    y = synth.uniform_positions(37, 1)
+    y[5, 1] = np.nan
+    emb.set_positions(y)
+    with pytest.raises(IvhdError) as e:
+        emb.stress()
+    assert e.value.status == -5
+
+
+@pytest.mark.parametrize("bad", ["range", "negative", "self", "dup"])
+def test_invalid_graph_rejected_on_device(bad):
+    knn = synth.random_knn_graph(50, 3, 1)
+    if bad == "range":
+        knn[7, 1] = 50
+    elif bad == "negative":
+        knn[7, 1] = -1
+    elif bad == "self":
+        knn[7, 1] = 7
+    else:
+        knn[7, 1] = knn[7, 0]
+    for dev in (False, True):
+        src = torch.from_numpy(knn).cuda() if dev else knn
+        with pytest.raises(IvhdError) as e:
+            ivhd.Embedding(src, r=1, c=0.1)
+        assert e.value.status == -2
+
+
+# ------------------------------------------------------------------- kNN
+
+
+@pytest.mark.parametrize("M,N,k", [(1007, 50, 5), (300, 33, 1), (513, 100, 16), (129, 7, 64)])
+def test_knn_f32_bit_exact(M, N, k):
+    X, _ = synth.gaussian_mixture(M, N, 4, M + N)
+    got = ivhd.knn_build(torch.from_numpy(X).cuda(), k).cpu().numpy()
+    assert np.array_equal(got, oracle.knn_f32(X, k))
+
+
+def test_knn_f32_ties_to_lower_index():
+    # duplicated rows: equal distances must resolve to the lower index
+    X, _ = synth.gaussian_mixture(200, 8, 2, 3)
+    X[100:150] = X[:50]
+    got = ivhd.knn_build(torch.from_numpy(X).cuda(), 6).cpu().numpy()
+    assert np.array_equal(got, oracle.knn_f32(X, 6))
+
+
+@pytest.mark.parametrize("M,N,k", [(777, 784, 5), (260, 30, 3)])
+def test_knn_u8_bit_exact(M, N, k):
+    X, _ = synth.mnist_like(M, 5, N=N)
+    got = ivhd.knn_build(torch.from_numpy(X).cuda(), k).cpu().numpy()
+    assert np.array_equal(got, oracle.knn_u8(X, k))
+
+
+# --------------------------------------------------------------- quality
+
+
+def test_eval_qnx_cf_bit_exact():
+    M, k = 5000, 5
+    knn = synth.random_knn_graph(M, k, 12)
+    Y = synth.uniform_positions(M, 3)
+    Y[:500] = np.round(Y[:500] * 8) / 8   # many exact ties
+    rows = synth.sample_rows(M, 1200, 5)
+    q, low = ivhd.eval_qnx(torch.from_numpy(Y).cuda(), torch.from_numpy(knn).cuda(),
+                           torch.from_numpy(rows).cuda(), return_lowd=True)
+    q_ref, low_ref = oracle.qnx(Y, knn, rows, return_lowd=True)
+    assert np.array_equal(low.cpu().numpy(), low_ref)
+    assert q == q_ref
+    lab = (np.arange(M) % 7).astype(np.int32)
+    for nn in (2, 10, 100):
+        got = ivhd.eval_cf(torch.from_numpy(Y).cuda(), lab, nn, torch.from_numpy(rows).cuda())
+        assert got == oracle.cf(Y, lab, nn, rows)
+
+
+# ------------------------------------------------------------- full runs
+
+
+@pytest.mark.parametrize("opt", ["momentum", "adadelta"])
+def test_full_run_gmm2k_precision_matches_oracle(opt):
+    w = synth.WORKLOADS["gmm2k"]
+    X, labels = synth.workload_features(w)
+    knn = oracle.knn_f32(X, w.k)
+    emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=opt, a=w.a, b=w.b, seed=w.seed)
+    emb.step(w.n_iter)
+    Y = emb.positions(host=True)
+    rn, _ = oracle.random_neighbors(knn, w.r, w.seed)
+    terms = oracle.build_terms(knn, rn)
+    st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
+    oracle.run(st, terms, w.c, w.n_iter, OPT_ID[opt], a=w.a, b=w.b)
+    q_gpu = oracle.qnx(Y, knn)
+    q_ref = oracle.qnx(st.Y.astype(np.float32), knn)
+    assert abs(q_gpu - q_ref) <= 0.01, (q_gpu, q_ref)
+    E_gpu, E_ref = emb.stress(), oracle.stress(st.Y, terms, w.c)
+    assert abs(E_gpu - E_ref) <= 0.05 * E_ref, (E_gpu, E_ref)
+    assert q_gpu > 10 * w.k / (w.M - 1)   # far above a random embedding
