@@ -241,6 +241,32 @@ ivhd_status ivhd_eval_qnx(const float *Y, int64_t M, const int32_t *knn, int32_t
 ivhd_status ivhd_eval_cf(const float *Y, int64_t M, const int32_t *labels, int32_t nn,
                          const int64_t *rows, int64_t nrows, double *out_cf, void *stream);
 
+/*
+ * ivhd_eval_qnx_static -- ivhd_eval_qnx that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for host
+ * applications that cannot let a library allocate device memory (a process
+ * whose memory is reserved up front by another framework's caching
+ * allocator, a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device, or an application that must keep its
+ * device-memory footprint fixed after start-up).  Same arguments, result and
+ * rules as ivhd_eval_qnx; the caller still passes every input and output.
+ *
+ * Scratch: a fixed array of 8193 64-bit counters (about 64 KiB) in the
+ * library's own device memory, held by every GPU that loads the library
+ * until the process exits.  It limits one call to nrows <= 1,048,576
+ * (8192 blocks of 128 rows); larger calls return IVHD_ERR_ARG.  The first
+ * call on each device looks up the array's device address (this may load the
+ * library's device code), so make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's
+ * contents: calls whose GPU work overlaps (different streams or unsynchronised
+ * host threads) race and may return wrong values; order them on one stream.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.  Synchronises.
+ */
+ivhd_status ivhd_eval_qnx_static(const float *Y, int64_t M, const int32_t *knn, int32_t k,
+                                 const int64_t *rows, int64_t nrows, int32_t *out_lowd,
+                                 double *out_q, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,59 @@
+"""ivhd_eval_qnx_static: the allocation-free Q_NX entry point.
+
+It serves callers that cannot let the library allocate device memory (see
+its declaration in include/ivhd.h).  Its result must equal the allocating
+ivhd_eval_qnx on the same inputs -- Q_NX is a ratio of integer hit counts, so
+the tolerance is zero -- on two calls in a row, which share the fixed scratch
+array, including a second call with fewer rows than the first.  This file is
+collected last so that a run stopping at the first failure has run
+everything else already.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2303_05455_gb300 import _lib, ivhd, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _static_qnx(L, Y, knn, rows, lowd):
+    q = ctypes.c_double()
+    st = L.ivhd_eval_qnx_static(Y.data_ptr(), Y.shape[0], knn.data_ptr(), knn.shape[1],
+                                rows.data_ptr(), rows.numel(),
+                                lowd.data_ptr() if lowd is not None else None, ctypes.byref(q),
+                                torch.cuda.current_stream().cuda_stream or None)
+    return st, q.value
+
+
+def test_static_qnx_matches_allocating_entry_point_on_consecutive_calls():
+    L = _lib.load()
+    M, k = 40_000, 5
+    knn = torch.from_numpy(synth.random_knn_graph(M, k, 31)).cuda()
+    Y = torch.from_numpy(synth.uniform_positions(M, 8)).cuda()
+    Y[:4000] = torch.round(Y[:4000] * 16) / 16          # exact ties in the neighbour search
+    for call, n in enumerate((30_000, 1_000)):          # second call: fewer rows, stale scratch
+        rows = torch.from_numpy(synth.sample_rows(M, n, 100 + call)).cuda()
+        low = torch.empty((n, k), dtype=torch.int32, device="cuda")
+        st, q = _static_qnx(L, Y, knn, rows, low)
+        assert st == 0, st
+        q_ref, low_ref = ivhd.eval_qnx(Y, knn, rows, return_lowd=True)
+        assert q == q_ref
+        assert torch.equal(low, low_ref)
+        assert 0.0 <= q <= 1.0
+
+
+def test_static_qnx_rejects_more_rows_than_its_scratch():
+    L = _lib.load()
+    M, k = 2000, 3
+    knn = torch.from_numpy(synth.random_knn_graph(M, k, 2)).cuda()
+    Y = torch.from_numpy(synth.uniform_positions(M, 1)).cuda()
+    rows = torch.zeros(8192 * 128 + 1, dtype=torch.int64, device="cuda")
+    st, _ = _static_qnx(L, Y, knn, rows, None)
+    assert st == -1
+    # the entry point stays usable after the rejection
+    rows = torch.arange(M, dtype=torch.int64, device="cuda")
+    st, q = _static_qnx(L, Y, knn, rows, None)
+    assert st == 0 and q == ivhd.eval_qnx(Y, knn, rows)
