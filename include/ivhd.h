@@ -96,7 +96,7 @@ void ivhd_default_params(ivhd_params *p);
  *
  *   knn           M*k int32; host memory if knn_on_device == 0, else device.
  *                 Copied; the caller keeps ownership.
- *   M             number of vertices, 2 <= M < 2^31 - 1.
+ *   M             number of vertices, 2 <= M < 2^30.
  *   k             nearest neighbours per row, 1 <= k <= M - 1.
  *   r             random neighbours per vertex, r >= 0.  When fewer than r
  *                 unconnected vertices exist the missing slots stay empty.
@@ -163,7 +163,9 @@ typedef struct {
     int64_t M;
     int32_t k, r;
     int64_t n_terms;       /* undirected terms of Eq. 3.16 (nn + rn) */
-    int64_t nnz_sym;       /* symmetric adjacency entries gathered per step (2 per term) */
+    int64_t nnz_sym;       /* symmetric row entries gathered per step: 2 per term, except
+                              that a mutual kNN pair is one entry per endpoint (of weight 2
+                              when multiplicity is kept) */
     int64_t layout_slots;  /* id slots stored, including padding */
     int64_t n_hub;         /* vertices processed warp-per-vertex */
     int32_t max_degree;    /* largest symmetric degree */

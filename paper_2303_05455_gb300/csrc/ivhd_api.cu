@@ -129,7 +129,7 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
   if (!out) return IVHD_ERR_ARG;
   *out = nullptr;
   if (!knn) return IVHD_ERR_ARG;
-  if (M < 2 || M >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
+  if (M < 2 || M >= kMaxVertices) return IVHD_ERR_ARG;
   if (k < 1 || (int64_t)k > M - 1 || r < 0) return IVHD_ERR_ARG;
   if (!std::isfinite(c) || c <= 0.f) return IVHD_ERR_ARG;
   if ((int64_t)M * (int64_t)(k + r) * 2 >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;

@@ -4,7 +4,8 @@
 //   2. draw r random neighbours per vertex (Sec. 3.3.1 "generated ad hoc";
 //      Sec. 3.3.3: never a vertex connected to i), SplitMix64 draws
 //   3. count the symmetric degree of every vertex (each stress term of
-//      Eq. 3.16 appears in the rows of both endpoints)
+//      Eq. 3.16 appears in the rows of both endpoints; a mutual kNN pair is
+//      one entry per endpoint, of weight 2 when multiplicity is kept)
 //   4. order vertices by degree, descending (stable LSD radix sort), so that
 //      the 32 vertices of a warp have near-equal work -- the paper's IVHD-CUDA
 //      also sorts particles by connection count (Sec. 5.2)
@@ -81,38 +82,58 @@ __global__ void k_rn_sample(const int32_t* __restrict__ knn, int64_t M, int k, i
   if (got < r) atomicAdd(empty, (unsigned long long)(r - got));
 }
 
-// In-degree of every vertex: nn entries (i -> j) and kept rn entries.  With
-// dedup an nn entry is not mirrored when j already lists i (mutual pair).
+// In-degree of every vertex: nn entries (i -> j) and kept rn entries.  An nn
+// entry is not mirrored into row j when j already lists i (a mutual pair): the
+// out-entry of j stands for the pair, with weight 2 when multiplicity is kept.
+// *mutual counts the nn entries whose reverse entry exists.
 __global__ void k_count_in(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
-                           int64_t M, int k, int r, int dedup, int32_t* __restrict__ in_nn,
-                           int32_t* __restrict__ in_rn) {
+                           int64_t M, int k, int r, int32_t* __restrict__ in_nn,
+                           int32_t* __restrict__ in_rn, unsigned long long* mutual) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t n_nn = M * k;
+  bool mut = false;
   if (e < n_nn) {
     const int64_t i = e / k;
     const int32_t j = knn[e];
-    if (dedup && row_has(knn + (int64_t)j * k, k, (int32_t)i)) return;
-    atomicAdd(&in_nn[j], 1);
+    mut = row_has(knn + (int64_t)j * k, k, (int32_t)i);
+    if (!mut) atomicAdd(&in_nn[j], 1);
   } else if (e < n_nn + M * r) {
     const int32_t j = rn[e - n_nn];
     if (j >= 0) atomicAdd(&in_rn[j], 1);
   }
+  const unsigned b = __ballot_sync(0xffffffffu, mut);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(mutual, (unsigned long long)__popc(b));
 }
 
-// Degree and the descending-degree sort key; per-context totals.
+// Degree (stored row entries) and the descending-degree sort key; totals
+// are reduced per warp before the atomics.
 __global__ void k_degree(const int32_t* __restrict__ rc, const int32_t* __restrict__ in_nn,
                          const int32_t* __restrict__ in_rn, int64_t M, int k,
                          int32_t* __restrict__ deg, uint32_t* __restrict__ key,
                          int32_t* __restrict__ val, unsigned long long* sum_deg,
-                         int32_t* max_deg) {
+                         unsigned long long* sum_rc, int32_t* max_deg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const int32_t d = k + rc[i] + in_nn[i] + in_rn[i];
-  deg[i] = d;
-  key[i] = 0xFFFFu - (uint32_t)min(d, 0xFFFF);
-  val[i] = (int32_t)i;
-  atomicAdd(sum_deg, (unsigned long long)d);
-  atomicMax(max_deg, d);
+  int32_t d = 0, c = 0;
+  if (i < M) {
+    c = rc[i];
+    d = k + c + in_nn[i] + in_rn[i];
+    deg[i] = d;
+    key[i] = 0xFFFFu - (uint32_t)min(d, 0xFFFF);
+    val[i] = (int32_t)i;
+  }
+  unsigned long long sd = (unsigned long long)d, sc = (unsigned long long)c;
+  int32_t md = d;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sd += __shfl_down_sync(0xffffffffu, sd, o);
+    sc += __shfl_down_sync(0xffffffffu, sc, o);
+    md = max(md, __shfl_down_sync(0xffffffffu, md, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(sum_deg, sd);
+    atomicAdd(sum_rc, sc);
+    atomicMax(max_deg, md);
+  }
 }
 
 // ---- stable LSD radix sort, 8-bit digits, 1024 elements per block --------
@@ -219,17 +240,21 @@ __device__ __forceinline__ int64_t slot_addr(int64_t p, int t, int64_t n_hub,
   return (int64_t)slice_off[q >> 5] + ((int64_t)(t >> 2) * 32 + (q & 31)) * 4 + (t & 3);
 }
 
-// Out-entries of input vertex i: its k nn ids, then its kept rn ids (rn bit set).
+// Out-entries of input vertex i: its k nn ids (weight-2 bit on mutual pairs
+// when multiplicity is kept), then its kept rn ids (rn bit set).
 __global__ void k_fill_out(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
                            const int32_t* __restrict__ rc, const int32_t* __restrict__ inv,
-                           int64_t M, int k, int r, int64_t n_hub,
+                           int64_t M, int k, int r, int dedup, int64_t n_hub,
                            const int32_t* __restrict__ hub_off,
                            const int32_t* __restrict__ slice_off, uint32_t* __restrict__ ids) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int64_t p = inv[i];
-  for (int s = 0; s < k; ++s)
-    ids[slot_addr(p, s, n_hub, hub_off, slice_off)] = (uint32_t)inv[knn[i * k + s]];
+  for (int s = 0; s < k; ++s) {
+    const int32_t j = knn[i * k + s];
+    const bool w2 = !dedup && row_has(knn + (int64_t)j * k, k, (int32_t)i);
+    ids[slot_addr(p, s, n_hub, hub_off, slice_off)] = (uint32_t)inv[j] | (w2 ? kW2Bit : 0u);
+  }
   const int n = rc[i];
   for (int s = 0; s < n; ++s)
     ids[slot_addr(p, k + s, n_hub, hub_off, slice_off)] = (uint32_t)inv[rn[i * r + s]] | kRnBit;
@@ -238,7 +263,7 @@ __global__ void k_fill_out(const int32_t* __restrict__ knn, const int32_t* __res
 // In-entries: the mirror of every out-entry (i -> j) lands in row j.
 __global__ void k_fill_in(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
                           const int32_t* __restrict__ inv, const int32_t* __restrict__ outc_p,
-                          int64_t M, int k, int r, int dedup, int64_t n_hub,
+                          int64_t M, int k, int r, int64_t n_hub,
                           const int32_t* __restrict__ hub_off,
                           const int32_t* __restrict__ slice_off, int32_t* __restrict__ cursor,
                           uint32_t* __restrict__ ids) {
@@ -250,7 +275,7 @@ __global__ void k_fill_in(const int32_t* __restrict__ knn, const int32_t* __rest
   if (e < n_nn) {
     i = e / k;
     j = knn[e];
-    if (dedup && row_has(knn + (int64_t)j * k, k, (int32_t)i)) return;
+    if (row_has(knn + (int64_t)j * k, k, (int32_t)i)) return;  // mutual: held by j's out-entry
     bit = 0;
   } else if (e < n_nn + M * r) {
     i = (e - n_nn) / r;
@@ -404,6 +429,8 @@ struct HostTotals {
   int32_t max_deg;
   int32_t pad;
   unsigned long long sum_deg;
+  unsigned long long sum_rc;
+  unsigned long long mutual;
   unsigned long long empty;
   int64_t hub_total;
   int64_t sell_total;
@@ -462,10 +489,11 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   IVHD_TRY(cudaMemsetAsync(in_rn, 0, M * sizeof(int32_t), s));
   IVHD_TRY(cudaMemsetAsync(cursor, 0, M * sizeof(int32_t), s));
   const int64_t n_entries = M * (int64_t)(k + r);
-  k_count_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, M, k, r, dedup, in_nn, in_rn);
+  k_count_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, M, k, r, in_nn, in_rn,
+                                            &tot_d->mutual);
   ++ctx->setup_launches;
   k_degree<<<nblk(M), kB, 0, s>>>(rc, in_nn, in_rn, M, k, deg, key0, val0, &tot_d->sum_deg,
-                                  &tot_d->max_deg);
+                                  &tot_d->sum_rc, &tot_d->max_deg);
   ++ctx->setup_launches;
   IVHD_TRY(cudaGetLastError());
 
@@ -529,7 +557,8 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   ctx->n_slices = (M - h.n_hub + 31) / 32;
   ctx->n_slots = h.hub_total + h.sell_total;
   ctx->nnz_sym = (int64_t)h.sum_deg;
-  ctx->n_terms = ctx->nnz_sym / 2;
+  // stress terms: every kNN entry (a mutual pair once when deduplicated) plus kept rn draws
+  ctx->n_terms = M * (int64_t)k - (dedup ? (int64_t)(h.mutual / 2) : 0) + (int64_t)h.sum_rc;
   ctx->max_degree = h.max_deg;
   ctx->empty_rn = (int32_t)h.empty;
   if (ctx->n_slots >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
@@ -548,10 +577,10 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
                            cudaMemcpyDeviceToDevice, s));
   IVHD_TRY(cudaGetLastError());
 
-  k_fill_out<<<nblk(M), kB, 0, s>>>(ctx->knn, ctx->rn, rc, ctx->inv, M, k, r, ctx->n_hub,
+  k_fill_out<<<nblk(M), kB, 0, s>>>(ctx->knn, ctx->rn, rc, ctx->inv, M, k, r, dedup, ctx->n_hub,
                                     ctx->hub_off, ctx->slice_off, ctx->ids);
   ++ctx->setup_launches;
-  k_fill_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, ctx->inv, outc_p, M, k, r, dedup,
+  k_fill_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, ctx->inv, outc_p, M, k, r,
                                            ctx->n_hub, ctx->hub_off, ctx->slice_off, cursor,
                                            ctx->ids);
   ++ctx->setup_launches;

@@ -7,8 +7,10 @@
 //                         for Nesterov they hold the look-ahead point y + a v
 //   s1         float2[M]  velocity (momentum, Nesterov) or E[g^2] (Adadelta)
 //   s2         float2[M]  E[dx^2] (Adadelta only)
-//   ids        uint32[]   symmetric adjacency; entry = neighbour p-index,
-//                         bit 31 set for a random-neighbour term, 0xFFFFFFFF = padding
+//   ids        uint32[]   symmetric adjacency; entry = neighbour p-index (30 bits),
+//                         bit 31 set for a random-neighbour term, bit 30 set for
+//                         an nn entry of weight 2 (a mutual kNN pair counted with
+//                         multiplicity, gathered once), 0xFFFFFFFF = padding
 //   hub rows   p < n_hub: contiguous rows ids[hub_off[p] .. hub_off[p+1]),
 //                         lengths padded to a multiple of 4, one warp per row
 //   SELL rows  p >= n_hub: slices of 32 consecutive vertices; slice s starts at
@@ -25,9 +27,11 @@
 
 namespace ivhd {
 
-constexpr uint32_t kRnBit = 0x80000000u;
-constexpr uint32_t kIdxMask = 0x7FFFFFFFu;
+constexpr uint32_t kRnBit = 0x80000000u;  // random-neighbour term
+constexpr uint32_t kW2Bit = 0x40000000u;  // nn entry standing for a mutual pair (weight 2)
+constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
 constexpr uint32_t kPad = 0xFFFFFFFFu;
+constexpr int64_t kMaxVertices = (int64_t)1 << 30;
 constexpr int kDefaultHubThreshold = 128;
 constexpr int kStepBlock = 256;  // 8 warps
 constexpr int kWarpsPerBlock = kStepBlock / 32;
@@ -117,7 +121,7 @@ struct ivhd_ctx {
   cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
 
   // counters
-  int64_t n_terms = 0, nnz_sym = 0;
+  int64_t n_terms = 0, nnz_sym = 0;  // stress terms; stored (gathered) row entries
   int32_t max_degree = 0, empty_rn = 0;
   int64_t steps_done = 0, launches = 0, setup_launches = 0, aux_launches = 0;
 };

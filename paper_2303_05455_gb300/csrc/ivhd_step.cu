@@ -25,13 +25,14 @@ __device__ __forceinline__ float2 gather(const float2* __restrict__ y, uint32_t 
   return (e == kPad) ? self : __ldg(y + (e & kIdxMask));
 }
 
-// One term of the force on i.  nn: w = 1.  rn: w = c (1 - 1/d); w = 0 at d = 0.
-// Padding entries carry the rn bit and gather y_i itself, so d = 0, w = 0.
+// One term of the force on i.  nn: w = 1, or 2 for a mutual pair kept with
+// multiplicity.  rn: w = c (1 - 1/d); w = 0 at d = 0.  Padding entries carry
+// the rn bit and gather y_i itself, so d = 0, w = 0.
 __device__ __forceinline__ void force_term(uint32_t e, float2 yj, float2 yi, float c, float& fx,
                                            float& fy) {
   const float ux = yj.x - yi.x;
   const float uy = yj.y - yi.y;
-  float w = 1.f;
+  float w = (e & kW2Bit) ? 2.f : 1.f;
   if (e & kRnBit) {
     const float d2 = fmaf(uy, uy, ux * ux);
     w = (d2 > 0.f) ? c * (1.f - rsqrtf(d2)) : 0.f;
@@ -40,7 +41,7 @@ __device__ __forceinline__ void force_term(uint32_t e, float2 yj, float2 yi, flo
   fy = fmaf(w, uy, fy);
 }
 
-// One term of the stress: nn d^2, rn c (1 - d)^2; padding contributes nothing.
+// One term of the stress: nn w d^2 (w = 1 or 2), rn c (1 - d)^2; padding contributes nothing.
 __device__ __forceinline__ void stress_term(uint32_t e, float2 yj, float2 yi, float c, float& es) {
   if (e == kPad) return;
   const float ux = yj.x - yi.x;
@@ -50,7 +51,7 @@ __device__ __forceinline__ void stress_term(uint32_t e, float2 yj, float2 yi, fl
     const float t = 1.f - sqrtf(d2);
     es = fmaf(c * t, t, es);
   } else {
-    es += d2;
+    es = fmaf((e & kW2Bit) ? 2.f : 1.f, d2, es);
   }
 }
 
@@ -91,8 +92,12 @@ __device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const float
   }
 }
 
+#ifndef IVHD_STEP_MIN_BLOCKS
+#define IVHD_STEP_MIN_BLOCKS 1
+#endif
+
 template <int MODE>
-__global__ void __launch_bounds__(kStepBlock) k_step(const StepArgs A) {
+__global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float fx = 0.f, fy = 0.f;  // force, or (stress in fx)

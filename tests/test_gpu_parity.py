@@ -88,9 +88,21 @@ def test_layout_counts_match_term_list(case, dedup):
     terms = oracle.build_terms(knn, rn, dedup=dedup)
     inf = emb.info()
     assert inf["n_terms"] == terms.T
-    assert inf["nnz_sym"] == 2 * terms.T
-    deg = np.bincount(np.concatenate([terms.ti, terms.tj]), minlength=knn.shape[0])
+    # stored row entries: out-nn, kept rn, in-nn from non-mutual sources, in-rn
+    M, k = knn.shape
+    out_sets = [set(row) for row in knn.tolist()]
+    deg = np.full(M, k, np.int64) + (rn >= 0).sum(axis=1)
+    for i in range(M):
+        for j in knn[i]:
+            if i not in out_sets[j]:
+                deg[j] += 1
+        for j in rn[i]:
+            if j >= 0:
+                deg[j] += 1
+    assert inf["nnz_sym"] == deg.sum()
     assert inf["max_degree"] == deg.max()
+    mutual_pairs = sum(1 for i in range(M) for j in knn[i] if j < i and i in out_sets[j])
+    assert deg.sum() == 2 * terms.T - (0 if dedup else 2 * mutual_pairs)
 
 
 @pytest.mark.parametrize("hub_threshold", [0, 1, 65535])
