@@ -336,13 +336,18 @@ def run_ours(args):
     achieved = alg_bytes / launch_s / 1e9
     peaks = measured_peaks()
     tr = step_kernel_traffic()
+    gpeak = ivhd.probe_gather(M, 16_777_216, 20)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "peak_source": peaks["source"], "kernel": "k_step<momentum>",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "launch_us": launch_s * 1e6,
-                "gathers_per_s": nnz / launch_s}
+                "l2_gather": {
+                    "achieved": nnz / launch_s, "peak": gpeak, "unit": "gathers/s",
+                    "frac": (nnz / launch_s) / gpeak,
+                    "peak_source": "ivhd_probe_gather on this GPU: uniformly random float2 "
+                                   f"gathers from {M} elements, indices in registers"}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -244,6 +244,21 @@ ivhd_status ivhd_eval_cf(const float *Y, int64_t M, const int32_t *labels, int32
                          const int64_t *rows, int64_t nrows, double *out_cf, void *stream);
 
 /*
+ * Calibration of the gather roofline.  The force pass is dominated by reads of
+ * neighbour positions at data-dependent addresses (Sec. 5.2 notes that the
+ * IVHD-CUDA force step is limited by its scattered reads and writes).  This
+ * call measures how many uniformly random 8-byte float2 gathers per second the
+ * current GPU sustains from an array of n_positions elements (allocated and
+ * freed here), with indices generated in registers, over `repeats` timed
+ * launches of about n_gathers gathers each.  The step kernel, which also
+ * streams its neighbour ids and state, cannot gather faster.
+ * Constraints: 1 <= n_positions < 2^30, 16384 <= n_gathers <= 2^34,
+ * repeats >= 1.  Synchronises.  Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA.
+ */
+ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers, int32_t repeats,
+                              double *gathers_per_s, void *stream);
+
+/*
  * ivhd_eval_qnx_static -- ivhd_eval_qnx that allocates no device memory.
  *
  * The paper has no counterpart: this entry point exists for host

@@ -22,6 +22,7 @@ SYMBOLS = (
     "ivhd_forces", "ivhd_stress", "ivhd_random_neighbors", "ivhd_info", "ivhd_state_size",
     "ivhd_get_state", "ivhd_set_state", "ivhd_destroy", "ivhd_status_string", "ivhd_version",
     "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
+    "ivhd_probe_gather",
 )
 
 
@@ -106,6 +107,8 @@ def load(build_if_missing: bool = False):
     L.ivhd_eval_qnx_static.argtypes = [P, i64, P, i32, P, i64, P,
                                        ctypes.POINTER(ctypes.c_double), P]
     L.ivhd_eval_qnx_static.restype = i32
+    L.ivhd_probe_gather.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_double), P]
+    L.ivhd_probe_gather.restype = i32
     _lib = L
     return L
 

@@ -1,0 +1,90 @@
+// ivhd_probe.cu -- calibration of the random-gather roofline of the step kernel.
+//
+// The step kernel's cost is dominated by gathering neighbour positions
+// (8-byte float2 reads at data-dependent addresses), which the GPU serves one
+// 32-byte L2 sector per gather.  This probe measures the rate the GPU
+// sustains for uniformly random float2 gathers from an array of the same size
+// as the embedding, with the indices generated in registers (no index stream),
+// so it is an upper bound for the step kernel's gather rate.
+#include "ivhd_internal.cuh"
+
+namespace ivhd {
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbePerThread = 64;
+
+__global__ void __launch_bounds__(kProbeThreads) k_probe_gather(const float2* __restrict__ y,
+                                                                uint32_t M, uint32_t seed,
+                                                                float* __restrict__ out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t s = t * 2654435761u + seed;  // xorshift32 stream per thread
+  float ax = 0.f, ay = 0.f;
+  for (int g = 0; g < kProbePerThread; g += 8) {
+    uint32_t idx[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      s ^= s << 13;
+      s ^= s >> 17;
+      s ^= s << 5;
+      idx[q] = s % M;
+    }
+    float2 p[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) p[q] = __ldg(y + idx[q]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      ax += p[q].x;
+      ay += p[q].y;
+    }
+  }
+  out[t] = ax + ay;
+}
+
+__global__ void k_probe_fill(float2* y, uint32_t M) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) y[i] = make_float2((float)(i & 1023), (float)(i >> 10));
+}
+
+}  // namespace
+}  // namespace ivhd
+
+using namespace ivhd;
+
+extern "C" ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers, int32_t repeats,
+                                         double* gathers_per_s, void* stream) {
+  if (!gathers_per_s || n_positions < 1 || n_positions > kMaxVertices || repeats < 1 ||
+      n_gathers < kProbeThreads * kProbePerThread || n_gathers > ((int64_t)1 << 34))
+    return IVHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t threads = n_gathers / kProbePerThread;
+  const unsigned grid = (unsigned)(threads / kProbeThreads);
+  float2* y = nullptr;
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&y, (size_t)n_positions * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&out, (size_t)grid * kProbeThreads * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    const uint32_t M = (uint32_t)n_positions;
+    k_probe_fill<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(y, M);
+    for (int w = 0; w < 3; ++w) k_probe_gather<<<grid, kProbeThreads, 0, s>>>(y, M, 17u + w, out);
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < repeats; ++rep)
+      k_probe_gather<<<grid, kProbeThreads, 0, s>>>(y, M, 101u + rep, out);
+    cudaEventRecord(e1, s);
+    e = cudaGetLastError();
+  }
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (y) cudaFreeAsync(y, s);
+  if (out) cudaFreeAsync(out, s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  *gathers_per_s = (double)grid * kProbeThreads * kProbePerThread * repeats / (ms * 1e-3);
+  return IVHD_OK;
+}

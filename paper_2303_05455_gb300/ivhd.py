@@ -203,3 +203,13 @@ def eval_cf(Y: torch.Tensor, labels, nn: int, rows: torch.Tensor, stream=None) -
     check(L.ivhd_eval_cf(Y.data_ptr(), int(Y.shape[0]), lab.data_ptr(), int(nn), rows.data_ptr(),
                          rows.numel(), ctypes.byref(v), _stream_ptr(stream)), "ivhd_eval_cf")
     return v.value
+
+
+def probe_gather(n_positions: int, n_gathers: int = 16_777_216, repeats: int = 20,
+                 stream=None) -> float:
+    """Random float2 gathers per second the GPU sustains from n_positions elements."""
+    L = _lib.load()
+    v = ctypes.c_double()
+    check(L.ivhd_probe_gather(int(n_positions), int(n_gathers), int(repeats), ctypes.byref(v),
+                              _stream_ptr(stream)), "ivhd_probe_gather")
+    return v.value

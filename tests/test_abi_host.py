@@ -117,3 +117,7 @@ def test_knn_build_and_eval_reject_bad_args(L):
     assert L.ivhd_eval_qnx(dummy, 10, dummy, 0, dummy, 5, None, ctypes.byref(out), None) == -1
     assert L.ivhd_eval_qnx(dummy, 10, dummy, 3, dummy, 0, None, ctypes.byref(out), None) == -1
     assert L.ivhd_eval_cf(dummy, 10, dummy, 129, dummy, 5, ctypes.byref(out), None) == -1
+    assert L.ivhd_probe_gather(0, 1 << 20, 1, ctypes.byref(out), None) == -1
+    assert L.ivhd_probe_gather(1000, 100, 1, ctypes.byref(out), None) == -1
+    assert L.ivhd_probe_gather(1000, 1 << 20, 0, ctypes.byref(out), None) == -1
+    assert L.ivhd_probe_gather(1000, 1 << 20, 1, None, None) == -1

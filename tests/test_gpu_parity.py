@@ -286,3 +286,8 @@ def test_full_run_gmm2k_precision_matches_oracle(opt):
     assert abs(E_gpu - E_ref) <= 0.05 * E_ref, (E_gpu, E_ref)
     if opt == "momentum":  # Adadelta starts with sqrt(eps)-sized steps and is still far from converged
         assert q_gpu > 10 * w.k / (w.M - 1)   # far above a random embedding
+
+
+def test_probe_gather_rate_is_plausible():
+    rate = ivhd.probe_gather(1_400_000, 1 << 22, 3)
+    assert 1e9 < rate < 1e13
