@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU seconds of the oracle baseline sample")
+    ap.add_argument("--variants", default="f16,bf16",
+                    help="half-precision position formats also timed (comma list, or 'none')")
+    ap.add_argument("--qnx-rows", type=int, default=10000)
     return ap.parse_args()
 
 
@@ -146,6 +149,19 @@ def step_kernel_traffic():
     except (OSError, ValueError):
         pass
     return None
+
+
+def aggregate_ranks(total_s: float, kernel_ms: float, units: float, device) -> tuple:
+    """Whole-job figures over the ranks of the default process group: the max
+    of the timed seconds and of the kernel time, the sum of the units."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([total_s, kernel_ms, units], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(t[2])
 
 
 # ------------------------------------------------------------- oracle leg
@@ -250,9 +266,9 @@ def run_ours(args):
     out = torch.empty((w.M, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def one_embedding(knn_in, out_buf, evs=None):
+    def one_embedding(knn_in, out_buf, evs=None, pos_format="f32"):
         emb = ivhd.Embedding(knn_in, r=w.r, c=w.c, opt="momentum", a=w.a, b=w.b, seed=w.seed,
-                             stream=stream, device=dev)
+                             stream=stream, device=dev, pos_format=pos_format)
         if evs is not None:
             evs[0].record(stream)
         emb.step(n_iter)
@@ -296,17 +312,37 @@ def run_ours(args):
     units = terms * n_iter * args.steps
 
     if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([sum(step_ms) / 1e3, kms, float(units)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        total_s, total_units = float(mx[0]), float(tt[2])
-        kms = float(mx[1])
+        total_s, kms, total_units = aggregate_ranks(sum(step_ms) / 1e3, kms, float(units), dev)
     else:
         total_s, total_units = sum(step_ms) / 1e3, float(units)
     value = total_units / total_s
+
+    # kNN precision of the timed embedding (sampled rows, exact neighbour sets)
+    rows = torch.from_numpy(synth.sample_rows(w.M, args.qnx_rows, 12345)).to(dev)
+    qnx_f32 = ivhd.eval_qnx(out, knn, rows)
+
+    # half-precision gathered positions: same graph, same seed, same step
+    variants = {}
+    for fmt in [v for v in args.variants.split(",") if v and v != "none"]:
+        one_embedding(knn, out, pos_format=fmt)
+        vs, ve = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        vt = []
+        for s_ in range(args.steps):
+            flush.zero_()
+            vs.record(stream)
+            one_embedding(knn, out, vk[s_], pos_format=fmt)
+            ve.record(stream)
+            torch.cuda.synchronize()
+            vt.append(vs.elapsed_time(ve))
+        vms = statistics.mean(vt)
+        vkms = statistics.mean(a.elapsed_time(b) for a, b in vk)
+        q = ivhd.eval_qnx(out, knn, rows)
+        variants[fmt] = {"value": terms * n_iter / (vms / 1e3), "s_to_embed": vms / 1e3,
+                         "launch_us": 1e3 * vkms / n_iter, "qnx": q,
+                         "qnx_minus_f32": q - qnx_f32,
+                         "equal_precision": abs(q - qnx_f32) <= 0.01}
 
     # e2e through the public API from pinned host memory
     e2e = None
@@ -358,6 +394,9 @@ def run_ours(args):
         "kernel_edge_updates_per_s": terms * n_iter / (kms / 1e3),
         "terms": terms, "nnz_sym": nnz, "n_hub": info["n_hub"], "max_degree": info["max_degree"],
         "knn_build_s_untimed": knn_seconds,
+        "qnx": {"value": qnx_f32, "k": w.k, "rows": int(rows.numel()),
+                "what": "Q_NX(k) of the final embedding on sampled rows (input kNN edges recovered)"},
+        "half_precision": variants,
         "wall_s_timed_region": wall,
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }

@@ -65,6 +65,17 @@ typedef enum {
     IVHD_KNN_U8 = 1   /* uint8 features; exact integer squared distances */
 } ivhd_knn_dtype;
 
+/*
+ * Storage of the positions that the step kernel gathers from neighbours.
+ * With F16 / BF16 every vertex keeps an FP32 master position (and FP32
+ * optimiser state) for its own update, and a rounded copy (round to nearest
+ * even) that neighbours gather, halving the bytes per gather.  Differences
+ * y_j - y_i are taken between rounded copies (coincident points stay exactly
+ * coincident); forces accumulate in FP32.  ivhd_forces / ivhd_stress /
+ * ivhd_positions always use the FP32 master positions.
+ */
+typedef enum { IVHD_POS_F32 = 0, IVHD_POS_F16 = 1, IVHD_POS_BF16 = 2 } ivhd_pos_format;
+
 typedef struct {
     int32_t opt;          /* ivhd_opt; default IVHD_OPT_MOMENTUM */
     float a;              /* friction / momentum a in [0, 1]; default 0.9 */
@@ -78,7 +89,8 @@ typedef struct {
                              ivhd_set_positions; default 1 */
     int32_t hub_threshold;/* vertices with at least this many symmetric terms are
                              processed warp-per-vertex; 0 = library default (128) */
-    int32_t reserved;     /* must be 0 */
+    int32_t pos_format;   /* ivhd_pos_format of the positions the step kernel gathers;
+                             default IVHD_POS_F32 */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 

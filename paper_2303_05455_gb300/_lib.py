@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
         ("opt", ctypes.c_int32), ("a", ctypes.c_float), ("b", ctypes.c_float),
         ("rho", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64),
         ("dedup_mutual", ctypes.c_int32), ("init_uniform", ctypes.c_int32),
-        ("hub_threshold", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("hub_threshold", ctypes.c_int32), ("pos_format", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

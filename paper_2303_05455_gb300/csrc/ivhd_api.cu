@@ -33,7 +33,7 @@ bool params_ok(const ivhd_params& p) {
   if (!std::isfinite(p.rho) || p.rho <= 0.f || p.rho >= 1.f) return false;
   if (!std::isfinite(p.eps) || p.eps <= 0.f) return false;
   if (p.hub_threshold < 0 || p.hub_threshold > 65535) return false;
-  if (p.reserved != 0) return false;
+  if (p.pos_format < IVHD_POS_F32 || p.pos_format > IVHD_POS_BF16) return false;
   return true;
 }
 
@@ -42,8 +42,8 @@ void free_ctx(ivhd_ctx* ctx) {
   for (int q = 0; q < 2; ++q)
     if (ctx->graph_exec[q]) cudaGraphExecDestroy(ctx->graph_exec[q]);
   void* bufs[] = {ctx->knn, ctx->rn, ctx->perm, ctx->inv, ctx->ids, ctx->hub_off,
-                  ctx->slice_off, ctx->slice_w, ctx->y[0], ctx->y[1], ctx->s1, ctx->s2,
-                  ctx->partials, ctx->red_out, ctx->flag};
+                  ctx->slice_off, ctx->slice_w, ctx->y[0], ctx->y[1], ctx->yh[0], ctx->yh[1],
+                  ctx->s1, ctx->s2, ctx->partials, ctx->red_out, ctx->flag};
   for (void* b : bufs)
     if (b) cudaFreeAsync(b, s);
   cudaStreamSynchronize(s);
@@ -76,6 +76,7 @@ uint64_t fingerprint(const ivhd_ctx* ctx) {
   mix(&ctx->p.eps, sizeof(ctx->p.eps));
   mix(&ctx->p.seed, sizeof(ctx->p.seed));
   mix(&ctx->p.dedup_mutual, sizeof(ctx->p.dedup_mutual));
+  mix(&ctx->p.pos_format, sizeof(ctx->p.pos_format));
   mix(&ctx->nnz_sym, sizeof(ctx->nnz_sym));
   return h;
 }
@@ -104,7 +105,7 @@ void ivhd_default_params(ivhd_params* p) {
   p->dedup_mutual = 0;
   p->init_uniform = 1;
   p->hub_threshold = 0;
-  p->reserved = 0;
+  p->pos_format = IVHD_POS_F32;
   p->stream = nullptr;
 }
 
@@ -164,6 +165,10 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
   chk(dalloc(&ctx->y[1], M, s));
   chk(dalloc(&ctx->s1, M, s));
   if (p.opt == IVHD_OPT_ADADELTA) chk(dalloc(&ctx->s2, M, s));
+  if (p.pos_format != IVHD_POS_F32) {
+    chk(dalloc(&ctx->yh[0], M, s));
+    chk(dalloc(&ctx->yh[1], M, s));
+  }
   chk(dalloc(&ctx->red_out, 1, s));
   chk(dalloc(&ctx->flag, 1, s));
   if (e != cudaSuccess) {
@@ -189,6 +194,7 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
     chk(launch_init_positions(ctx));
   } else {
     chk(cudaMemsetAsync(ctx->y[0], 0, (size_t)M * sizeof(float2), s));
+    if (ctx->yh[0]) chk(cudaMemsetAsync(ctx->yh[0], 0, (size_t)M * sizeof(uint32_t), s));
     chk(cudaMemsetAsync(ctx->s1, 0, (size_t)M * sizeof(float2), s));
     if (ctx->s2) chk(cudaMemsetAsync(ctx->s2, 0, (size_t)M * sizeof(float2), s));
   }
@@ -399,6 +405,7 @@ ivhd_status ivhd_set_state(ivhd_ctx* ctx, const void* buf, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(ctx->y[ctx->cur], q, ab, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->s1, q + ab, ab, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && ctx->s2) e = cudaMemcpyAsync(ctx->s2, q + 2 * ab, ab, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_round_positions(ctx);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) ctx->steps_done = h.steps_done;
   return fail(ctx, e);

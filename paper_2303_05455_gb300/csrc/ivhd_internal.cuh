@@ -5,6 +5,8 @@
 //
 //   y[2]       float2[M]  positions, ping-pong (step reads y[cur], writes y[cur^1]);
 //                         for Nesterov they hold the look-ahead point y + a v
+//   yh[2]      uint32[M]  FP16x2 / BF16x2 copies of y that neighbours gather
+//                         (only with a half-precision position format)
 //   s1         float2[M]  velocity (momentum, Nesterov) or E[g^2] (Adadelta)
 //   s2         float2[M]  E[dx^2] (Adadelta only)
 //   ids        uint32[]   symmetric adjacency; entry = neighbour p-index (30 bits),
@@ -71,6 +73,8 @@ struct StepArgs {
   const int32_t* __restrict__ slice_w;
   const float2* __restrict__ y_in;
   float2* __restrict__ y_out;
+  const uint32_t* __restrict__ yh_in;  // rounded FP16 / BF16 copy gathered by neighbours
+  uint32_t* __restrict__ yh_out;
   float2* __restrict__ s1;
   float2* __restrict__ s2;
   const int32_t* __restrict__ perm;  // forces mode: scatter to input order
@@ -107,6 +111,7 @@ struct ivhd_ctx {
 
   // state
   float2* y[2] = {nullptr, nullptr};
+  uint32_t* yh[2] = {nullptr, nullptr};  // FP16 / BF16 gathered copies (pos_format != F32)
   int cur = 0;
   float2* s1 = nullptr;
   float2* s2 = nullptr;
@@ -138,6 +143,7 @@ cudaError_t launch_stress(ivhd_ctx* ctx);  // result in ctx->red_out[0], flag in
 cudaError_t launch_unpermute(ivhd_ctx* ctx, float2* out_input_order);
 cudaError_t launch_set_positions(ivhd_ctx* ctx, const float2* in_input_order);
 cudaError_t launch_init_positions(ivhd_ctx* ctx);
+cudaError_t launch_round_positions(ivhd_ctx* ctx);
 int step_grid(const ivhd_ctx* ctx);
 
 }  // namespace ivhd

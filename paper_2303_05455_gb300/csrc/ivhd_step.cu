@@ -17,12 +17,50 @@
 // Work split: SELL slices of 32 degree-sorted vertices, one thread per vertex
 // and one coalesced int4 id load per 4 neighbours; vertices of very high
 // degree ("hubs") get a warp each and a fixed-order butterfly reduction.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ivhd_internal.cuh"
 
 namespace ivhd {
 
-__device__ __forceinline__ float2 gather(const float2* __restrict__ y, uint32_t e, float2 self) {
-  return (e == kPad) ? self : __ldg(y + (e & kIdxMask));
+// Position of vertex idx as the neighbours see it: the FP32 array, or the
+// rounded FP16 / BF16 copy (one 32-bit word per vertex).
+template <int POS>
+__device__ __forceinline__ float2 load_pos(const StepArgs& A, uint32_t idx) {
+  if constexpr (POS == IVHD_POS_F32) {
+    return __ldg(A.y_in + idx);
+  } else {
+    const uint32_t w = __ldg(A.yh_in + idx);
+    if constexpr (POS == IVHD_POS_F16) {
+      __half2 h;
+      memcpy(&h, &w, 4);
+      return __half22float2(h);
+    } else {
+      __nv_bfloat162 h;
+      memcpy(&h, &w, 4);
+      return __bfloat1622float2(h);
+    }
+  }
+}
+
+// Round-to-nearest-even copy of a position in the gathered format.
+template <int POS>
+__device__ __forceinline__ uint32_t round_pos(float2 v) {
+  uint32_t w = 0;
+  if constexpr (POS == IVHD_POS_F16) {
+    const __half2 h = __floats2half2_rn(v.x, v.y);
+    memcpy(&w, &h, 4);
+  } else if constexpr (POS == IVHD_POS_BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    memcpy(&w, &h, 4);
+  }
+  return w;
+}
+
+template <int POS>
+__device__ __forceinline__ float2 gather(const StepArgs& A, uint32_t e, float2 self) {
+  return (e == kPad) ? self : load_pos<POS>(A, e & kIdxMask);
 }
 
 // One term of the force on i.  nn: w = 1, or 2 for a mutual pair kept with
@@ -55,12 +93,12 @@ __device__ __forceinline__ void stress_term(uint32_t e, float2 yj, float2 yi, fl
   }
 }
 
-template <int MODE>
-__device__ __forceinline__ void visit4(const int4 e, const float2* __restrict__ y, float2 yi,
-                                       float c, float& fx, float& fy) {
+template <int MODE, int POS>
+__device__ __forceinline__ void visit4(const int4 e, const StepArgs& A, float2 yi, float c,
+                                       float& fx, float& fy) {
   const uint32_t e0 = (uint32_t)e.x, e1 = (uint32_t)e.y, e2 = (uint32_t)e.z, e3 = (uint32_t)e.w;
-  const float2 g0 = gather(y, e0, yi), g1 = gather(y, e1, yi);
-  const float2 g2 = gather(y, e2, yi), g3 = gather(y, e3, yi);
+  const float2 g0 = gather<POS>(A, e0, yi), g1 = gather<POS>(A, e1, yi);
+  const float2 g2 = gather<POS>(A, e2, yi), g3 = gather<POS>(A, e3, yi);
   if (MODE == kStress) {
     stress_term(e0, g0, yi, c, fx);
     stress_term(e1, g1, yi, c, fx);
@@ -74,15 +112,15 @@ __device__ __forceinline__ void visit4(const int4 e, const float2* __restrict__ 
   }
 }
 
-template <int MODE>
-__device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const float2* __restrict__ y,
-                                       float2 yi, float c, float& fx, float& fy) {
+template <int MODE, int POS>
+__device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const StepArgs& A, float2 yi,
+                                       float c, float& fx, float& fy) {
   // all eight gathers are issued before any arithmetic (eight loads in flight per thread)
   const uint32_t e[8] = {(uint32_t)ea.x, (uint32_t)ea.y, (uint32_t)ea.z, (uint32_t)ea.w,
                          (uint32_t)eb.x, (uint32_t)eb.y, (uint32_t)eb.z, (uint32_t)eb.w};
   float2 g[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) g[q] = gather(y, e[q], yi);
+  for (int q = 0; q < 8; ++q) g[q] = gather<POS>(A, e[q], yi);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     if (MODE == kStress)
@@ -96,12 +134,16 @@ __device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const float
 #define IVHD_STEP_MIN_BLOCKS 1
 #endif
 
-template <int MODE>
+// MODE: optimiser epilogue (or forces / stress); POS: gathered position format.
+// yi is the vertex's own position in the gathered format (differences are taken
+// between equally rounded positions); ym is its FP32 master position.
+template <int MODE, int POS>
 __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float fx = 0.f, fy = 0.f;  // force, or (stress in fx)
   float2 yi = make_float2(0.f, 0.f);
+  float2 ym = make_float2(0.f, 0.f);
   int p = -1;
   bool own = false;
 
@@ -109,7 +151,8 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
     // hub rows: one warp per vertex, lanes stride over int4 groups
     p = (int)blockIdx.x * kWarpsPerBlock + wib;
     if (p < A.n_hub) {
-      yi = A.y_in[p];
+      ym = A.y_in[p];
+      yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(A, p);
       const int beg = A.hub_off[p], end = A.hub_off[p + 1];
       const int4* row = reinterpret_cast<const int4*>(A.ids + beg);
       const int ng = (end - beg) >> 2;
@@ -117,9 +160,9 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       for (; g + 32 < ng; g += 64) {
         const int4 ea = ld_stream_v4(row + g);
         const int4 eb = ld_stream_v4(row + g + 32);
-        visit8<MODE>(ea, eb, A.y_in, yi, A.c, fx, fy);
+        visit8<MODE, POS>(ea, eb, A, yi, A.c, fx, fy);
       }
-      if (g < ng) visit4<MODE>(ld_stream_v4(row + g), A.y_in, yi, A.c, fx, fy);
+      if (g < ng) visit4<MODE, POS>(ld_stream_v4(row + g), A, yi, A.c, fx, fy);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -133,16 +176,19 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
     if (s < A.n_slices) {
       p = A.n_hub + s * 32 + lane;
       const bool valid = p < A.M;
-      if (valid) yi = A.y_in[p];
+      if (valid) {
+        ym = A.y_in[p];
+        yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(A, p);
+      }
       const int4* base = reinterpret_cast<const int4*>(A.ids + A.slice_off[s]) + lane;
       const int W = A.slice_w[s];
       int g = 0;
       for (; g + 1 < W; g += 2) {
         const int4 ea = ld_stream_v4(base + g * 32);
         const int4 eb = ld_stream_v4(base + (g + 1) * 32);
-        visit8<MODE>(ea, eb, A.y_in, yi, A.c, fx, fy);
+        visit8<MODE, POS>(ea, eb, A, yi, A.c, fx, fy);
       }
-      if (g < W) visit4<MODE>(ld_stream_v4(base + g * 32), A.y_in, yi, A.c, fx, fy);
+      if (g < W) visit4<MODE, POS>(ld_stream_v4(base + g * 32), A, yi, A.c, fx, fy);
       own = valid;
     }
   }
@@ -154,7 +200,9 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       v.x = fmaf(A.a, v.x, A.b * fx);
       v.y = fmaf(A.a, v.y, A.b * fy);
       A.s1[p] = v;
-      A.y_out[p] = make_float2(yi.x + v.x, yi.y + v.y);
+      const float2 yn = make_float2(ym.x + v.x, ym.y + v.y);
+      A.y_out[p] = yn;
+      if (POS != IVHD_POS_F32) A.yh_out[p] = round_pos<POS>(yn);
     }
   } else if (MODE == kNesterov) {
     // state is the look-ahead point z = y + a v; F was taken at z.
@@ -166,7 +214,10 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       vn.y = fmaf(A.a, v.y, A.b * fy);
       A.s1[p] = vn;
       const float ap1 = 1.f + A.a;
-      A.y_out[p] = make_float2(yi.x + fmaf(ap1, vn.x, -A.a * v.x), yi.y + fmaf(ap1, vn.y, -A.a * v.y));
+      const float2 zn =
+          make_float2(ym.x + fmaf(ap1, vn.x, -A.a * v.x), ym.y + fmaf(ap1, vn.y, -A.a * v.y));
+      A.y_out[p] = zn;
+      if (POS != IVHD_POS_F32) A.yh_out[p] = round_pos<POS>(zn);
     }
   } else if (MODE == kAdadelta) {
     // Zeiler's Adadelta on g = -F: E[g^2] <- rho E[g^2] + (1-rho) g^2;
@@ -184,14 +235,16 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       ex.y = fmaf(A.rho, ex.y, omr * dy * dy);
       A.s1[p] = eg;
       A.s2[p] = ex;
-      A.y_out[p] = make_float2(yi.x + dx, yi.y + dy);
+      const float2 yn = make_float2(ym.x + dx, ym.y + dy);
+      A.y_out[p] = yn;
+      if (POS != IVHD_POS_F32) A.yh_out[p] = round_pos<POS>(yn);
     }
   } else if (MODE == kForces) {
     if (own) A.f_out[A.perm[p]] = make_float2(fx, fy);
   } else if (MODE == kStress) {
     __shared__ double red[kWarpsPerBlock];
     double v = own ? (double)fx : 0.0;
-    if (own && !(isfinite(yi.x) && isfinite(yi.y))) atomicOr(A.flag, 1);
+    if (own && !(isfinite(ym.x) && isfinite(ym.y))) atomicOr(A.flag, 1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0) red[wib] = v;
@@ -237,6 +290,23 @@ __global__ void k_unpermute(const float2* __restrict__ y, const float2* __restri
   out[perm[p]] = q;
 }
 
+// Rounded copy of the FP32 positions in the gathered format.
+__global__ void k_round_positions(const float2* __restrict__ y, int M, int pos,
+                                  uint32_t* __restrict__ yh) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= M) return;
+  yh[p] = (pos == IVHD_POS_F16) ? round_pos<IVHD_POS_F16>(y[p]) : round_pos<IVHD_POS_BF16>(y[p]);
+}
+
+cudaError_t launch_round_positions(ivhd_ctx* ctx) {
+  if (ctx->p.pos_format == IVHD_POS_F32) return cudaSuccess;
+  const int M = (int)ctx->M;
+  k_round_positions<<<(M + 255) / 256, 256, 0, ctx->stream>>>(ctx->y[ctx->cur], M, ctx->p.pos_format,
+                                                              ctx->yh[ctx->cur]);
+  ++ctx->aux_launches;
+  return cudaGetLastError();
+}
+
 // Positions from input order; optimiser state reset to zero (so z = y for Nesterov).
 __global__ void k_set_positions(const float2* __restrict__ in, const int32_t* __restrict__ perm,
                                 int M, float2* __restrict__ y, float2* __restrict__ s1,
@@ -271,6 +341,8 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   A.slice_w = ctx->slice_w;
   A.y_in = ctx->y[cur];
   A.y_out = ctx->y[cur ^ 1];
+  A.yh_in = ctx->yh[cur];
+  A.yh_out = ctx->yh[cur ^ 1];
   A.s1 = ctx->s1;
   A.s2 = ctx->s2;
   A.perm = ctx->perm;
@@ -294,13 +366,22 @@ int step_grid(const ivhd_ctx* ctx) {
   return (int)(nb_hub + nb_sell);
 }
 
+template <int POS>
+static void launch_opt(int opt, int grid, cudaStream_t s, const StepArgs& A) {
+  switch (opt) {
+    case IVHD_OPT_NESTEROV: k_step<kNesterov, POS><<<grid, kStepBlock, 0, s>>>(A); break;
+    case IVHD_OPT_ADADELTA: k_step<kAdadelta, POS><<<grid, kStepBlock, 0, s>>>(A); break;
+    default: k_step<kMomentum, POS><<<grid, kStepBlock, 0, s>>>(A); break;
+  }
+}
+
 cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s) {
   const StepArgs A = make_args(ctx, cur);
   const int grid = step_grid(ctx);
-  switch (ctx->p.opt) {
-    case IVHD_OPT_NESTEROV: k_step<kNesterov><<<grid, kStepBlock, 0, s>>>(A); break;
-    case IVHD_OPT_ADADELTA: k_step<kAdadelta><<<grid, kStepBlock, 0, s>>>(A); break;
-    default: k_step<kMomentum><<<grid, kStepBlock, 0, s>>>(A); break;
+  switch (ctx->p.pos_format) {
+    case IVHD_POS_F16: launch_opt<IVHD_POS_F16>(ctx->p.opt, grid, s, A); break;
+    case IVHD_POS_BF16: launch_opt<IVHD_POS_BF16>(ctx->p.opt, grid, s, A); break;
+    default: launch_opt<IVHD_POS_F32>(ctx->p.opt, grid, s, A); break;
   }
   return cudaGetLastError();
 }
@@ -331,7 +412,7 @@ static StepArgs eval_args(ivhd_ctx* ctx) {
 cudaError_t launch_forces(ivhd_ctx* ctx, float2* out) {
   StepArgs A = eval_args(ctx);
   A.f_out = out;
-  k_step<kForces><<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
+  k_step<kForces, IVHD_POS_F32><<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
   ++ctx->aux_launches;
   return cudaGetLastError();
 }
@@ -341,7 +422,7 @@ cudaError_t launch_stress(ivhd_ctx* ctx) {
   if (e != cudaSuccess) return e;
   StepArgs A = eval_args(ctx);
   const int grid = step_grid(ctx);
-  k_step<kStress><<<grid, kStepBlock, 0, ctx->stream>>>(A);
+  k_step<kStress, IVHD_POS_F32><<<grid, kStepBlock, 0, ctx->stream>>>(A);
   k_stress_final<<<1, 1024, 0, ctx->stream>>>(ctx->partials, grid, ctx->red_out);
   ctx->aux_launches += 2;
   return cudaGetLastError();
@@ -361,7 +442,8 @@ cudaError_t launch_set_positions(ivhd_ctx* ctx, const float2* in) {
   k_set_positions<<<(M + 255) / 256, 256, 0, ctx->stream>>>(in, ctx->perm, M, ctx->y[ctx->cur],
                                                             ctx->s1, ctx->s2);
   ++ctx->aux_launches;
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : launch_round_positions(ctx);
 }
 
 cudaError_t launch_init_positions(ivhd_ctx* ctx) {
@@ -369,7 +451,8 @@ cudaError_t launch_init_positions(ivhd_ctx* ctx) {
   k_init_positions<<<(M + 255) / 256, 256, 0, ctx->stream>>>(ctx->perm, M, ctx->p.seed,
                                                              ctx->y[ctx->cur], ctx->s1, ctx->s2);
   ++ctx->aux_launches;
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : launch_round_positions(ctx);
 }
 
 }  // namespace ivhd

@@ -22,6 +22,7 @@ from . import _lib
 from ._lib import IvhdError, Info, Params, check
 
 OPTS = {"momentum": 0, "nesterov": 1, "adadelta": 2}
+POS_FORMATS = {"f32": 0, "f16": 1, "bf16": 2}
 
 
 def _stream_ptr(stream) -> int | None:
@@ -46,7 +47,7 @@ class Embedding:
     def __init__(self, knn, r: int = 1, c: float = 0.01, *, opt: str = "momentum",
                  a: float = 0.9, b: float = 0.01, rho: float = 0.95, eps: float = 1e-6,
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
-                 hub_threshold: int = 0, stream=None, device=None):
+                 hub_threshold: int = 0, pos_format: str = "f32", stream=None, device=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -68,6 +69,7 @@ class Embedding:
         p.dedup_mutual = int(dedup_mutual)
         p.init_uniform = int(init_uniform)
         p.hub_threshold = int(hub_threshold)
+        p.pos_format = POS_FORMATS[pos_format]
         p.stream = self.stream.cuda_stream or None
         self.opt = opt
         self.params = p

@@ -75,7 +75,7 @@ def test_create_rejects_bad_sizes(L, M, k, r, c):
 @pytest.mark.parametrize("field,value", [
     ("opt", 3), ("opt", -1), ("a", -0.1), ("a", 1.5), ("a", float("nan")), ("b", 0.0),
     ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
-    ("hub_threshold", 70000), ("reserved", 1),
+    ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1),
 ])
 def test_create_rejects_bad_params(L, field, value):
     p = _lib.Params()
