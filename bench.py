@@ -253,7 +253,7 @@ def run_ours(args):
     n_iter = args.n_iter or w.n_iter
 
     # untimed set-up: data, exact kNN graph (replicas: every rank embeds its own copy)
-    X, _ = synth.workload_features(w)
+    X, labels = synth.workload_features(w)
     Xd = torch.from_numpy(X).to(dev)
     t = time.perf_counter()
     knn = ivhd.knn_build(Xd, w.k)
@@ -317,9 +317,27 @@ def run_ours(args):
         total_s, total_units = sum(step_ms) / 1e3, float(units)
     value = total_units / total_s
 
-    # kNN precision of the timed embedding (sampled rows, exact neighbour sets)
+    # kNN precision of the timed embedding (sampled rows, exact neighbour sets),
+    # class purity cf_nn, stress and finiteness of the final positions
     rows = torch.from_numpy(synth.sample_rows(w.M, args.qnx_rows, 12345)).to(dev)
-    qnx_f32 = ivhd.eval_qnx(out, knn, rows)
+    lab = torch.from_numpy(labels).to(dev)
+
+    def quality(pos_format="f32"):
+        emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt="momentum", a=w.a, b=w.b, seed=w.seed,
+                             stream=stream, device=dev, pos_format=pos_format)
+        emb.step(n_iter)
+        emb.positions(out=out)
+        try:
+            E, finite = emb.stress(), True
+        except ivhd.IvhdError:
+            E, finite = float("nan"), False
+        emb.close()
+        return {"qnx": ivhd.eval_qnx(out, knn, rows),
+                "cf": {str(nn): ivhd.eval_cf(out, lab, nn, rows) for nn in (2, 10, 100)},
+                "stress": E, "finite": finite}
+
+    q32 = quality()
+    qnx_f32 = q32["qnx"]
 
     # half-precision gathered positions: same graph, same seed, same step
     variants = {}
@@ -338,11 +356,12 @@ def run_ours(args):
             vt.append(vs.elapsed_time(ve))
         vms = statistics.mean(vt)
         vkms = statistics.mean(a.elapsed_time(b) for a, b in vk)
-        q = ivhd.eval_qnx(out, knn, rows)
+        qv = quality(fmt)
         variants[fmt] = {"value": terms * n_iter / (vms / 1e3), "s_to_embed": vms / 1e3,
-                         "launch_us": 1e3 * vkms / n_iter, "qnx": q,
-                         "qnx_minus_f32": q - qnx_f32,
-                         "equal_precision": abs(q - qnx_f32) <= 0.01}
+                         "launch_us": 1e3 * vkms / n_iter, "qnx": qv["qnx"], "cf": qv["cf"],
+                         "stress": qv["stress"], "finite": qv["finite"],
+                         "qnx_minus_f32": qv["qnx"] - qnx_f32,
+                         "equal_precision": abs(qv["qnx"] - qnx_f32) <= 0.01}
 
     # e2e through the public API from pinned host memory
     e2e = None
@@ -396,6 +415,7 @@ def run_ours(args):
         "knn_build_s_untimed": knn_seconds,
         "qnx": {"value": qnx_f32, "k": w.k, "rows": int(rows.numel()),
                 "what": "Q_NX(k) of the final embedding on sampled rows (input kNN edges recovered)"},
+        "quality_f32": q32,
         "half_precision": variants,
         "wall_s_timed_region": wall,
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,

@@ -76,6 +76,14 @@ typedef enum {
  */
 typedef enum { IVHD_POS_F32 = 0, IVHD_POS_F16 = 1, IVHD_POS_BF16 = 2 } ivhd_pos_format;
 
+/*
+ * Distance used by the stress and its forces.  L2 is the method (Eq. 3.16).
+ * L1 (d = |dx| + |dy|, gradient taken coordinate-wise with sign(0) = 0) is the
+ * late-stage variant of Sec. 3.4.1, which the paper applies for the last ~50
+ * steps to pull outliers into their clusters.  See ivhd_set_metric.
+ */
+typedef enum { IVHD_METRIC_L2 = 0, IVHD_METRIC_L1 = 1 } ivhd_metric;
+
 typedef struct {
     int32_t opt;          /* ivhd_opt; default IVHD_OPT_MOMENTUM */
     float a;              /* friction / momentum a in [0, 1]; default 0.9 */
@@ -91,6 +99,12 @@ typedef struct {
                              processed warp-per-vertex; 0 = library default (128) */
     int32_t pos_format;   /* ivhd_pos_format of the positions the step kernel gathers;
                              default IVHD_POS_F32 */
+    int32_t adaptive;     /* 1: self-adaptive b of Sec. 3.3.3 (momentum and Nesterov only);
+                             default 0 */
+    float tau;            /* adaptive b: a step whose kinetic-energy change dT satisfies
+                             |dT| > tau * T_old is rejected; default 0.5 */
+    float gamma1;         /* adaptive b: factor (> 1) applied to b when dT < 0; default 1.1 */
+    float gamma2;         /* adaptive b: factor (0, 1) applied to b when dT > 0; default 0.5 */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 
@@ -107,6 +121,8 @@ void ivhd_default_params(ivhd_params *p);
  * positions and optimiser state (velocity or Adadelta accumulators = 0).
  *
  *   knn           M*k int32; host memory if knn_on_device == 0, else device.
+ *                 -1 marks an absent entry (a vertex with fewer than k
+ *                 neighbours keeps those it has, Sec. 3.3.3).
  *                 Copied; the caller keeps ownership.
  *   M             number of vertices, 2 <= M < 2^30.
  *   k             nearest neighbours per row, 1 <= k <= M - 1.
@@ -202,6 +218,44 @@ ivhd_status ivhd_info(ivhd_ctx *ctx, ivhd_info_t *out);
 ivhd_status ivhd_state_size(ivhd_ctx *ctx, size_t *bytes);
 ivhd_status ivhd_get_state(ivhd_ctx *ctx, void *buf, size_t bytes);
 ivhd_status ivhd_set_state(ivhd_ctx *ctx, const void *buf, size_t bytes);
+
+/*
+ * Selects the distance of subsequent steps, forces and stress (ivhd_metric).
+ * The paper switches to L1 for the last steps of an embedding (Sec. 3.4.1).
+ * Host only; takes effect in stream order.  Errors: IVHD_ERR_ARG.
+ */
+ivhd_status ivhd_set_metric(ivhd_ctx *ctx, int32_t metric);
+
+/*
+ * Redraws the random neighbours (Sec. 3.3.1: rn "generated ad hoc during the
+ * embedding") and rebuilds the layout, keeping positions, optimiser state and
+ * step count.  Draw epoch e > 0 seeds every vertex stream with
+ * seed ^ mix(e) (mix = the SplitMix64 finaliser) instead of seed; e = 0
+ * reproduces the draw of ivhd_create.  Synchronises.
+ * Errors: IVHD_ERR_CUDA, IVHD_ERR_OOM, IVHD_ERR_STATE.
+ */
+ivhd_status ivhd_resample_random_neighbors(ivhd_ctx *ctx, uint64_t epoch);
+
+/*
+ * Reverse-neighbour mechanism (Sec. 3.4.2): keeps only the nn interactions
+ * (i -> j) of the calculation graph for which i is among the k_helper nearest
+ * neighbours of j in the helper graph (the paper's default helper has 4 nn
+ * neighbours per row), so that an interaction survives when the two particles
+ * are mutual neighbours or one is a reverse neighbour of the other.  Random
+ * neighbours are unchanged.  Rebuilds the layout keeping positions,
+ * optimiser state and step count; helper == NULL restores the full graph.
+ *   helper  M*k_helper int32 rows (-1 = absent), host or device per on_device.
+ * Synchronises.  Errors: IVHD_ERR_ARG, IVHD_ERR_INDEX, IVHD_ERR_CUDA, IVHD_ERR_OOM.
+ */
+ivhd_status ivhd_restrict_nn(ivhd_ctx *ctx, const int32_t *helper, int32_t k_helper,
+                             int32_t on_device);
+
+/*
+ * State of the self-adaptive b controller: the current b and the numbers of
+ * accepted and rejected steps.  Synchronises.  IVHD_ERR_ARG when the context
+ * was created without adaptive b.
+ */
+ivhd_status ivhd_adaptive_state(ivhd_ctx *ctx, float *b, int64_t *accepted, int64_t *rejected);
 
 /* Frees the context and its device memory (after its stream drains).  NULL is a no-op. */
 void ivhd_destroy(ivhd_ctx *ctx);

@@ -40,6 +40,19 @@ def _L():
         lib.ivo_splitmix64.restype = u64
         lib.ivo_random_neighbors.argtypes = [P, i64, i32, i32, u64, P]
         lib.ivo_random_neighbors.restype = i64
+        lib.ivo_random_neighbors_epoch.argtypes = [P, i64, i32, i32, u64, u64, P]
+        lib.ivo_random_neighbors_epoch.restype = i64
+        lib.ivo_restrict.argtypes = [P, P, i64, i32, i32, P]
+        lib.ivo_restrict.restype = None
+        lib.ivo_stress_l1.argtypes = [P, P, P, P, i64, dbl]
+        lib.ivo_stress_l1.restype = dbl
+        lib.ivo_forces_l1.argtypes = [P, i64, P, P, P, i64, dbl, P]
+        lib.ivo_forces_l1.restype = None
+        lib.ivo_step_l1.argtypes = [i32, P, P, i64, P, P, P, i64, dbl, dbl, dbl, P, P]
+        lib.ivo_step_l1.restype = None
+        lib.ivo_step_adaptive.argtypes = [i32, i32, P, P, i64, P, P, P, i64, dbl, dbl, P, dbl,
+                                          dbl, dbl, P, P, P, P]
+        lib.ivo_step_adaptive.restype = i32
         lib.ivo_init_positions.argtypes = [i64, u64, P]
         lib.ivo_init_positions.restype = None
         lib.ivo_build_terms.argtypes = [P, P, i64, i32, i32, i32, P, P, P]
@@ -76,13 +89,27 @@ def splitmix64(seed: int, t: int) -> int:
     return int(_L().ivo_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, t))
 
 
-def random_neighbors(knn, r: int, seed: int):
-    """Returns (rn int32 [M, r] with -1 for unfillable slots, number of -1 slots)."""
+def random_neighbors(knn, r: int, seed: int, epoch: int = 0):
+    """Returns (rn int32 [M, r] with -1 for unfillable slots, number of -1 slots).
+
+    epoch > 0 is a redraw with the seed replaced by seed ^ mix(epoch)."""
     knn = _c(knn, np.int32)
     M, k = knn.shape
-    rn = np.empty((M, r), dtype=np.int32)
-    empty = _L().ivo_random_neighbors(_p(knn), M, k, r, seed & 0xFFFFFFFFFFFFFFFF, _p(rn))
+    rn = np.empty((M, max(r, 1)), dtype=np.int32)[:, :r]
+    rn = np.ascontiguousarray(rn)
+    empty = _L().ivo_random_neighbors_epoch(_p(knn), M, k, r, seed & 0xFFFFFFFFFFFFFFFF,
+                                            epoch & 0xFFFFFFFFFFFFFFFF, _p(rn))
     return rn, int(empty)
+
+
+def restrict(knn, helper) -> np.ndarray:
+    """Reverse-neighbour restriction: keep (i, j) iff i is in helper row j, else -1."""
+    knn = _c(knn, np.int32)
+    helper = _c(helper, np.int32)
+    M, k = knn.shape
+    out = np.empty_like(knn)
+    _L().ivo_restrict(_p(knn), _p(helper), M, k, helper.shape[1], _p(out))
+    return out
 
 
 def init_positions(M: int, seed: int) -> np.ndarray:
@@ -116,15 +143,17 @@ def build_terms(knn, rn, dedup: bool = False) -> Terms:
     return Terms(ti[:T].copy(), tj[:T].copy(), kind[:T].copy(), M)
 
 
-def stress(Y, terms: Terms, c: float) -> float:
+def stress(Y, terms: Terms, c: float, metric: str = "l2") -> float:
     Y = _c(Y, np.float64)
-    return float(_L().ivo_stress(_p(Y), _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c))
+    fn = _L().ivo_stress_l1 if metric == "l1" else _L().ivo_stress
+    return float(fn(_p(Y), _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c))
 
 
-def forces(Y, terms: Terms, c: float) -> np.ndarray:
+def forces(Y, terms: Terms, c: float, metric: str = "l2") -> np.ndarray:
     Y = _c(Y, np.float64)
     F = np.empty_like(Y)
-    _L().ivo_forces(_p(Y), terms.M, _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c, _p(F))
+    fn = _L().ivo_forces_l1 if metric == "l1" else _L().ivo_forces
+    fn(_p(Y), terms.M, _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c, _p(F))
     return F
 
 
@@ -149,6 +178,32 @@ def step(state: State, terms: Terms, c: float, opt: int = OPT_MOMENTUM, a: float
     _L().ivo_step(opt, _p(state.Y), _p(state.S1), _p(state.S2), M, _p(terms.ti), _p(terms.tj),
                   _p(terms.kind), terms.T, c, a, b, rho, eps, _p(F), _p(W))
     return state
+
+
+def step_l1(state: State, terms: Terms, c: float, opt: int = OPT_MOMENTUM, a: float = 0.9,
+            b: float = 0.01) -> State:
+    """Momentum / Nesterov step with the L1 forces of the late stage."""
+    assert opt in (OPT_MOMENTUM, OPT_NESTEROV)
+    M = terms.M
+    F = np.empty((M, 2))
+    W = np.empty((M, 2))
+    _L().ivo_step_l1(opt, _p(state.Y), _p(state.S1), M, _p(terms.ti), _p(terms.tj),
+                     _p(terms.kind), terms.T, c, a, b, _p(F), _p(W))
+    return state
+
+
+def step_adaptive(state: State, terms: Terms, c: float, b_box: list, opt: int = OPT_MOMENTUM,
+                  a: float = 0.9, tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5,
+                  metric: str = "l2") -> bool:
+    """One attempt with self-adaptive b; b_box[0] holds b.  Returns True if accepted."""
+    M = terms.M
+    scratch = [np.empty((M, 2)) for _ in range(4)]
+    b = ctypes.c_double(b_box[0])
+    ok = _L().ivo_step_adaptive(opt, 1 if metric == "l1" else 0, _p(state.Y), _p(state.S1), M,
+                                _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c, a,
+                                ctypes.byref(b), tau, gamma1, gamma2, *[_p(x) for x in scratch])
+    b_box[0] = b.value
+    return bool(ok)
 
 
 def run(state: State, terms: Terms, c: float, n_iter: int, opt: int = OPT_MOMENTUM,

@@ -51,6 +51,18 @@
  *   R10 kNN ties are broken by the lower index; the squared distance that
  *       decides the set is the FP32 chain acc = fma(x_d - y_d, x_d - y_d, acc)
  *       over d = 0..N-1 for float data, exact integers for uint8 data.
+ *   R11 kNN rows may hold -1 for an absent entry (a vertex with fewer than
+ *       k neighbours keeps those it has, Sec. 3.3.3).
+ *   R12 A redraw of the random neighbours with epoch e > 0 replaces the seed
+ *       s by s ^ mix(e) (mix = the SplitMix64 finaliser).
+ *   R13 L1 late stage (Sec. 3.4.1): d = |dx| + |dy| in the stress; the force
+ *       is -1/2 of its gradient taken coordinate-wise with sign(0) = 0.
+ *   R14 Reverse-neighbour mechanism (Sec. 3.4.2): nn term (i, j) is kept iff
+ *       i is among the neighbours of j in the helper graph.
+ *   R15 Self-adaptive b (Sec. 3.3.3): dT = sum |v'|^2 - sum |v|^2 over the
+ *       candidate step; if |dT| > tau * sum |v|^2 (and sum |v|^2 > 0) the step
+ *       is rejected (positions and velocities unchanged) and b is multiplied
+ *       by gamma1 (dT < 0) or gamma2 (dT > 0); otherwise it is accepted.
  *
  * Random numbers: SplitMix64 (Steele, Lea, Flood, "Fast splittable
  * pseudorandom number generators", OOPSLA 2014), state advanced by the golden
@@ -116,6 +128,7 @@ int64_t ivo_random_neighbors(const int32_t *knn, int64_t M, int k, int r, uint64
                              int32_t *rn)
 {
     int64_t empty = 0;
+    if (r == 0) return 0;
     for (int64_t i = 0; i < M; ++i) {
         int32_t *row = rn + i * (int64_t)r;
         int got = 0;
@@ -135,6 +148,28 @@ int64_t ivo_random_neighbors(const int32_t *knn, int64_t M, int k, int r, uint64
         }
     }
     return empty;
+}
+
+/* Random neighbours of draw epoch e (R12); e = 0 is the first draw. */
+int64_t ivo_random_neighbors_epoch(const int32_t *knn, int64_t M, int k, int r, uint64_t seed,
+                                   uint64_t epoch, int32_t *rn)
+{
+    uint64_t s = epoch ? (seed ^ ivo_mix64(epoch)) : seed;
+    return ivo_random_neighbors(knn, M, k, r, s, rn);
+}
+
+/*
+ * Reverse-neighbour restriction (R14): out[i][s] = knn[i][s] when i appears in
+ * helper row knn[i][s], else -1.
+ */
+void ivo_restrict(const int32_t *knn, const int32_t *helper, int64_t M, int k, int kh,
+                  int32_t *out)
+{
+    for (int64_t i = 0; i < M; ++i)
+        for (int s = 0; s < k; ++s) {
+            int32_t j = knn[i * (int64_t)k + s];
+            out[i * (int64_t)k + s] = (j >= 0 && ivo_row_has(helper + (int64_t)j * kh, kh, i)) ? j : -1;
+        }
 }
 
 /*
@@ -167,6 +202,7 @@ int64_t ivo_build_terms(const int32_t *knn, const int32_t *rn, int64_t M, int k,
     for (int64_t i = 0; i < M; ++i) {
         for (int s = 0; s < k; ++s) {
             int64_t j = knn[i * (int64_t)k + s];
+            if (j < 0) continue;
             if (dedup && j < i && ivo_row_has(knn + j * (int64_t)k, k, i)) continue;
             ti[T] = i;
             tj[T] = j;
@@ -273,6 +309,98 @@ void ivo_step(int opt, double *Y, double *S1, double *S2, int64_t M, const int64
             S2[q] = rho * S2[q] + (1.0 - rho) * dx * dx;
             Y[q] += dx;
         }
+    }
+}
+
+static double ivo_sgn(double u) { return (double)((u > 0.0) - (u < 0.0)); }
+
+/* Stress with the L1 distance (R13). */
+double ivo_stress_l1(const double *Y, const int64_t *ti, const int64_t *tj, const int8_t *kind,
+                     int64_t T, double c)
+{
+    double E = 0.0;
+    for (int64_t t = 0; t < T; ++t) {
+        int64_t i = ti[t], j = tj[t];
+        double d = fabs(Y[2 * i] - Y[2 * j]) + fabs(Y[2 * i + 1] - Y[2 * j + 1]);
+        E += (kind[t] == 0) ? d * d : c * (1.0 - d) * (1.0 - d);
+    }
+    return E;
+}
+
+/*
+ * F = -1/2 grad of the L1 stress (R13).  With u = y_i - y_j and d = |u_x| + |u_y|:
+ * nn term: F_i -= d sign(u), F_j += d sign(u); rn term: g = c (1 - d) sign(u),
+ * F_i += g, F_j -= g.
+ */
+void ivo_forces_l1(const double *Y, int64_t M, const int64_t *ti, const int64_t *tj,
+                   const int8_t *kind, int64_t T, double c, double *F)
+{
+    memset(F, 0, sizeof(double) * 2 * (size_t)M);
+    for (int64_t t = 0; t < T; ++t) {
+        int64_t i = ti[t], j = tj[t];
+        double ux = Y[2 * i] - Y[2 * j], uy = Y[2 * i + 1] - Y[2 * j + 1];
+        double d = fabs(ux) + fabs(uy);
+        double s = (kind[t] == 0) ? -d : c * (1.0 - d);
+        double gx = s * ivo_sgn(ux), gy = s * ivo_sgn(uy);
+        F[2 * i] += gx;
+        F[2 * i + 1] += gy;
+        F[2 * j] -= gx;
+        F[2 * j + 1] -= gy;
+    }
+}
+
+/*
+ * One attempt of a momentum (opt 0) or Nesterov (opt 1) step with the
+ * self-adaptive b of R15, metric 0 = L2, 1 = L1.  Y, V are updated only when
+ * the step is accepted; *b is scaled when it is rejected.  Returns 1 when
+ * accepted, 0 when rejected.  F, W, Yn, Vn are caller scratch of 2*M doubles.
+ */
+int ivo_step_adaptive(int opt, int metric, double *Y, double *V, int64_t M, const int64_t *ti,
+                      const int64_t *tj, const int8_t *kind, int64_t T, double c, double a,
+                      double *b, double tau, double gamma1, double gamma2, double *F, double *W,
+                      double *Yn, double *Vn)
+{
+    int64_t n = 2 * M;
+    const double *at = Y;
+    if (opt == 1) {
+        for (int64_t q = 0; q < n; ++q) W[q] = Y[q] + a * V[q];
+        at = W;
+    }
+    if (metric == 1)
+        ivo_forces_l1(at, M, ti, tj, kind, T, c, F);
+    else
+        ivo_forces(at, M, ti, tj, kind, T, c, F);
+    double told = 0.0, tnew = 0.0;
+    for (int64_t q = 0; q < n; ++q) {
+        Vn[q] = a * V[q] + *b * F[q];
+        Yn[q] = Y[q] + Vn[q];
+        told += V[q] * V[q];
+        tnew += Vn[q] * Vn[q];
+    }
+    double dT = tnew - told;
+    if (told > 0.0 && fabs(dT) > tau * told) {
+        *b *= (dT < 0.0) ? gamma1 : gamma2;
+        return 0;
+    }
+    memcpy(Y, Yn, sizeof(double) * (size_t)n);
+    memcpy(V, Vn, sizeof(double) * (size_t)n);
+    return 1;
+}
+
+/* Momentum / Nesterov step with the L1 forces (R13); same state as ivo_step. */
+void ivo_step_l1(int opt, double *Y, double *V, int64_t M, const int64_t *ti, const int64_t *tj,
+                 const int8_t *kind, int64_t T, double c, double a, double b, double *F, double *W)
+{
+    int64_t n = 2 * M;
+    const double *at = Y;
+    if (opt == 1) {
+        for (int64_t q = 0; q < n; ++q) W[q] = Y[q] + a * V[q];
+        at = W;
+    }
+    ivo_forces_l1(at, M, ti, tj, kind, T, c, F);
+    for (int64_t q = 0; q < n; ++q) {
+        V[q] = a * V[q] + b * F[q];
+        Y[q] += V[q];
     }
 }
 

@@ -22,7 +22,8 @@ SYMBOLS = (
     "ivhd_forces", "ivhd_stress", "ivhd_random_neighbors", "ivhd_info", "ivhd_state_size",
     "ivhd_get_state", "ivhd_set_state", "ivhd_destroy", "ivhd_status_string", "ivhd_version",
     "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
-    "ivhd_probe_gather",
+    "ivhd_probe_gather", "ivhd_set_metric", "ivhd_resample_random_neighbors",
+    "ivhd_restrict_nn", "ivhd_adaptive_state",
 )
 
 
@@ -38,6 +39,8 @@ class Params(ctypes.Structure):
         ("rho", ctypes.c_float), ("eps", ctypes.c_float), ("seed", ctypes.c_uint64),
         ("dedup_mutual", ctypes.c_int32), ("init_uniform", ctypes.c_int32),
         ("hub_threshold", ctypes.c_int32), ("pos_format", ctypes.c_int32),
+        ("adaptive", ctypes.c_int32), ("tau", ctypes.c_float), ("gamma1", ctypes.c_float),
+        ("gamma2", ctypes.c_float),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -109,6 +112,15 @@ def load(build_if_missing: bool = False):
     L.ivhd_eval_qnx_static.restype = i32
     L.ivhd_probe_gather.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_double), P]
     L.ivhd_probe_gather.restype = i32
+    L.ivhd_set_metric.argtypes = [P, i32]
+    L.ivhd_set_metric.restype = i32
+    L.ivhd_resample_random_neighbors.argtypes = [P, u64]
+    L.ivhd_resample_random_neighbors.restype = i32
+    L.ivhd_restrict_nn.argtypes = [P, P, i32, i32]
+    L.ivhd_restrict_nn.restype = i32
+    L.ivhd_adaptive_state.argtypes = [P, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.ivhd_adaptive_state.restype = i32
     _lib = L
     return L
 

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ivhd_internal.cuh"
 
@@ -11,7 +12,7 @@ namespace {
 
 constexpr int kGraphSteps = 64;  // steps per captured CUDA graph (even: parity preserved)
 constexpr uint32_t kStateMagic = 0x44485649u;  // "IVHD"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 
 ivhd_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return IVHD_OK;
@@ -34,16 +35,43 @@ bool params_ok(const ivhd_params& p) {
   if (!std::isfinite(p.eps) || p.eps <= 0.f) return false;
   if (p.hub_threshold < 0 || p.hub_threshold > 65535) return false;
   if (p.pos_format < IVHD_POS_F32 || p.pos_format > IVHD_POS_BF16) return false;
+  if (p.adaptive != 0 && p.adaptive != 1) return false;
+  if (p.adaptive) {
+    if (p.opt == IVHD_OPT_ADADELTA) return false;
+    if (!std::isfinite(p.tau) || p.tau <= 0.f) return false;
+    if (!std::isfinite(p.gamma1) || p.gamma1 <= 1.f) return false;
+    if (!std::isfinite(p.gamma2) || p.gamma2 <= 0.f || p.gamma2 >= 1.f) return false;
+  }
   return true;
+}
+
+void drop_graphs(ivhd_ctx* ctx) {
+  for (auto& row : ctx->graph_exec)
+    for (auto& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+void free_layout(ivhd_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  void* bufs[] = {ctx->ids, ctx->hub_off, ctx->slice_off, ctx->slice_w, ctx->partials};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, s);
+  ctx->ids = nullptr;
+  ctx->hub_off = ctx->slice_off = ctx->slice_w = nullptr;
+  ctx->partials = nullptr;
 }
 
 void free_ctx(ivhd_ctx* ctx) {
   cudaStream_t s = ctx->stream;
-  for (int q = 0; q < 2; ++q)
-    if (ctx->graph_exec[q]) cudaGraphExecDestroy(ctx->graph_exec[q]);
-  void* bufs[] = {ctx->knn, ctx->rn, ctx->perm, ctx->inv, ctx->ids, ctx->hub_off,
-                  ctx->slice_off, ctx->slice_w, ctx->y[0], ctx->y[1], ctx->yh[0], ctx->yh[1],
-                  ctx->s1, ctx->s2, ctx->partials, ctx->red_out, ctx->flag};
+  drop_graphs(ctx);
+  free_layout(ctx);
+  void* bufs[] = {ctx->knn, ctx->knn_full, ctx->rn, ctx->perm, ctx->inv, ctx->y[0], ctx->y[1],
+                  ctx->yh[0], ctx->yh[1], ctx->vbuf[0], ctx->vbuf[1], ctx->s2, ctx->ctl,
+                  ctx->red_out, ctx->flag, ctx->seg_of, ctx->seg_lo, ctx->seg_n, ctx->seg_r,
+                  ctx->seg_seed};
   for (void* b : bufs)
     if (b) cudaFreeAsync(b, s);
   cudaStreamSynchronize(s);
@@ -53,6 +81,25 @@ void free_ctx(ivhd_ctx* ctx) {
 template <class T>
 cudaError_t dalloc(T** p, int64_t n, cudaStream_t s) {
   return cudaMallocAsync((void**)p, (size_t)(n > 0 ? n : 1) * sizeof(T), s);
+}
+
+// With self-adaptive b the current buffer is chosen on the device; host code
+// that touches the state first reads it back.
+cudaError_t sync_cur(ivhd_ctx* ctx) {
+  if (!ctx->ctl) return cudaSuccess;
+  AdaptCtl h{};
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->ctl, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return e;
+  ctx->cur = h.cur;
+  ctx->s1 = ctx->vbuf[h.cur];
+  return cudaSuccess;
+}
+
+// Partials for the stress (1 per block) and the adaptive controller (2 per block).
+cudaError_t alloc_partials(ivhd_ctx* ctx) {
+  ctx->n_partials = 2 * (int64_t)step_grid(ctx);
+  return dalloc(&ctx->partials, ctx->n_partials, ctx->stream);
 }
 
 // 64-bit FNV-1a over the quantities a checkpoint must agree on.
@@ -77,6 +124,7 @@ uint64_t fingerprint(const ivhd_ctx* ctx) {
   mix(&ctx->p.seed, sizeof(ctx->p.seed));
   mix(&ctx->p.dedup_mutual, sizeof(ctx->p.dedup_mutual));
   mix(&ctx->p.pos_format, sizeof(ctx->p.pos_format));
+  mix(&ctx->p.adaptive, sizeof(ctx->p.adaptive));
   mix(&ctx->nnz_sym, sizeof(ctx->nnz_sym));
   return h;
 }
@@ -87,7 +135,59 @@ struct StateHeader {
   int64_t M;
   int64_t steps_done;
   int32_t opt, n_arrays;
+  AdaptCtl ctl;
 };
+
+// Rebuilds the layout (after the graph or the random neighbours changed) and
+// carries positions and optimiser state across the new vertex order.
+ivhd_status rebuild_preserving_state(ivhd_ctx* ctx, bool draw_rn, uint64_t epoch) {
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  cudaError_t e = sync_cur(ctx);
+  if (e != cudaSuccess) return fail(ctx, e);
+  float2* save[3] = {nullptr, nullptr, nullptr};
+  float2* src[3] = {ctx->y[ctx->cur], ctx->s1, ctx->s2};
+  const int n = ctx->s2 ? 3 : 2;
+  for (int q = 0; q < n && e == cudaSuccess; ++q) {
+    e = dalloc(&save[q], M, s);
+    if (e == cudaSuccess) e = launch_to_input_order(ctx, src[q], save[q]);
+  }
+  ivhd_status st = IVHD_OK;
+  if (e == cudaSuccess) {
+    drop_graphs(ctx);
+    free_layout(ctx);
+    st = build_layout(ctx, draw_rn, epoch);
+  }
+  if (e == cudaSuccess && st == IVHD_OK) e = alloc_partials(ctx);
+  for (int q = 0; q < n && e == cudaSuccess && st == IVHD_OK; ++q)
+    e = launch_from_input_order(ctx, save[q], src[q]);
+  if (e == cudaSuccess && st == IVHD_OK) e = launch_round_positions(ctx);
+  for (int q = 0; q < n; ++q)
+    if (save[q]) cudaFreeAsync(save[q], s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, e);
+  if (st != IVHD_OK) ctx->poisoned = true;  // the layout is gone
+  return st;
+}
+
+// Keeps nn entry (i -> j) iff i is among helper[j] (Sec. 3.4.2 reading).
+__global__ void k_restrict(const int32_t* __restrict__ knn, const int32_t* __restrict__ helper,
+                           int64_t M, int k, int kh, int32_t* __restrict__ out,
+                           int32_t* __restrict__ err) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * k) return;
+  const int64_t i = e / k;
+  const int32_t j = knn[e];
+  int32_t keep = -1;
+  if (j >= 0) {
+    for (int t = 0; t < kh; ++t) {
+      const int32_t h = helper[(int64_t)j * kh + t];
+      if (h < -1 || (int64_t)h >= M) atomicOr(err, 1);
+      if (h == (int32_t)i) keep = j;
+    }
+  }
+  out[e] = keep;
+}
 
 }  // namespace
 
@@ -106,10 +206,14 @@ void ivhd_default_params(ivhd_params* p) {
   p->init_uniform = 1;
   p->hub_threshold = 0;
   p->pos_format = IVHD_POS_F32;
+  p->adaptive = 0;
+  p->tau = 0.5f;
+  p->gamma1 = 1.1f;
+  p->gamma2 = 0.5f;
   p->stream = nullptr;
 }
 
-int32_t ivhd_version(void) { return (0 << 16) | (1 << 8) | 0; }
+int32_t ivhd_version(void) { return (0 << 16) | (2 << 8) | 0; }
 
 const char* ivhd_status_string(ivhd_status s) {
   switch (s) {
@@ -124,6 +228,81 @@ const char* ivhd_status_string(ivhd_status s) {
   }
   return "unknown status";
 }
+
+}  // extern "C"
+
+namespace {
+
+// Allocates the per-vertex state of a context with M vertices.
+cudaError_t alloc_state(ivhd_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(dalloc(&ctx->rn, M * (int64_t)ctx->r, s));
+  chk(dalloc(&ctx->perm, M, s));
+  chk(dalloc(&ctx->inv, M, s));
+  chk(dalloc(&ctx->y[0], M, s));
+  chk(dalloc(&ctx->y[1], M, s));
+  chk(dalloc(&ctx->vbuf[0], M, s));
+  if (ctx->p.adaptive) {
+    chk(dalloc(&ctx->vbuf[1], M, s));
+    chk(dalloc(&ctx->ctl, 1, s));
+  }
+  if (ctx->p.opt == IVHD_OPT_ADADELTA) chk(dalloc(&ctx->s2, M, s));
+  if (ctx->p.pos_format != IVHD_POS_F32) {
+    chk(dalloc(&ctx->yh[0], M, s));
+    chk(dalloc(&ctx->yh[1], M, s));
+  }
+  chk(dalloc(&ctx->red_out, 1, s));
+  chk(dalloc(&ctx->flag, 1, s));
+  ctx->s1 = ctx->vbuf[0];
+  return e;
+}
+
+// Shared by the create entry points once the context holds its graph
+// (ctx->knn), segment tables and parameters: layout, positions, controller.
+ivhd_status finish_create(ivhd_ctx* ctx, ivhd_ctx** out) {
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  ivhd_status st = build_layout(ctx, true, 0);
+  if (st != IVHD_OK) {
+    free_ctx(ctx);
+    return st;
+  }
+  cudaError_t e = alloc_partials(ctx);
+  if (e == cudaSuccess) {
+    if (ctx->p.init_uniform) {
+      e = launch_init_positions(ctx);
+    } else {
+      e = cudaMemsetAsync(ctx->y[0], 0, (size_t)M * sizeof(float2), s);
+      if (e == cudaSuccess && ctx->yh[0])
+        e = cudaMemsetAsync(ctx->yh[0], 0, (size_t)M * sizeof(uint32_t), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctx->s1, 0, (size_t)M * sizeof(float2), s);
+      if (e == cudaSuccess && ctx->s2)
+        e = cudaMemsetAsync(ctx->s2, 0, (size_t)M * sizeof(float2), s);
+    }
+  }
+  if (e == cudaSuccess && ctx->ctl) {
+    AdaptCtl h{};
+    h.b = ctx->p.b;
+    e = cudaMemcpyAsync(ctx->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) {
+    st = cuda_status(e);
+    free_ctx(ctx);
+    return st;
+  }
+  *out = ctx;
+  return IVHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, float c,
                         const ivhd_params* p_in, int32_t knn_on_device, ivhd_ctx** out) {
@@ -153,58 +332,34 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
   cudaGetDevice(&ctx->device);
   cudaStream_t s = ctx->stream;
 
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = alloc_state(ctx);
   auto chk = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
   chk(dalloc(&ctx->knn, M * k, s));
-  chk(dalloc(&ctx->rn, M * (int64_t)r, s));
-  chk(dalloc(&ctx->perm, M, s));
-  chk(dalloc(&ctx->inv, M, s));
-  chk(dalloc(&ctx->y[0], M, s));
-  chk(dalloc(&ctx->y[1], M, s));
-  chk(dalloc(&ctx->s1, M, s));
-  if (p.opt == IVHD_OPT_ADADELTA) chk(dalloc(&ctx->s2, M, s));
-  if (p.pos_format != IVHD_POS_F32) {
-    chk(dalloc(&ctx->yh[0], M, s));
-    chk(dalloc(&ctx->yh[1], M, s));
+  // one segment: the whole graph
+  ctx->n_seg = 1;
+  chk(dalloc(&ctx->seg_lo, 1, s));
+  chk(dalloc(&ctx->seg_n, 1, s));
+  chk(dalloc(&ctx->seg_r, 1, s));
+  chk(dalloc(&ctx->seg_seed, 1, s));
+  if (e == cudaSuccess) {
+    const int64_t lo = 0;
+    chk(cudaMemcpyAsync(ctx->seg_lo, &lo, sizeof(lo), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->seg_n, &M, sizeof(M), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->seg_r, &r, sizeof(r), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->seg_seed, &p.seed, sizeof(p.seed), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->knn, knn, (size_t)(M * k) * sizeof(int32_t),
+                        knn_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    chk(cudaStreamSynchronize(s));  // the host scalars above live on this stack frame
   }
-  chk(dalloc(&ctx->red_out, 1, s));
-  chk(dalloc(&ctx->flag, 1, s));
   if (e != cudaSuccess) {
     ivhd_status st = cuda_status(e);
     free_ctx(ctx);
     return st;
   }
-  chk(cudaMemcpyAsync(ctx->knn, knn, (size_t)(M * k) * sizeof(int32_t),
-                      knn_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  if (e != cudaSuccess) {
-    ivhd_status st = cuda_status(e);
-    free_ctx(ctx);
-    return st;
-  }
-  ivhd_status st = build_layout(ctx);
-  if (st != IVHD_OK) {
-    free_ctx(ctx);
-    return st;
-  }
-  ctx->n_partials = step_grid(ctx);
-  chk(dalloc(&ctx->partials, ctx->n_partials, s));
-  if (p.init_uniform) {
-    chk(launch_init_positions(ctx));
-  } else {
-    chk(cudaMemsetAsync(ctx->y[0], 0, (size_t)M * sizeof(float2), s));
-    if (ctx->yh[0]) chk(cudaMemsetAsync(ctx->yh[0], 0, (size_t)M * sizeof(uint32_t), s));
-    chk(cudaMemsetAsync(ctx->s1, 0, (size_t)M * sizeof(float2), s));
-    if (ctx->s2) chk(cudaMemsetAsync(ctx->s2, 0, (size_t)M * sizeof(float2), s));
-  }
-  if (e != cudaSuccess) {
-    st = cuda_status(e);
-    free_ctx(ctx);
-    return st;
-  }
-  *out = ctx;
-  return IVHD_OK;
+  ctx->seg = SegTable{nullptr, ctx->seg_lo, ctx->seg_n, ctx->seg_r, ctx->seg_seed};
+  return finish_create(ctx, out);
 }
 
 void ivhd_destroy(ivhd_ctx* ctx) {
@@ -218,11 +373,11 @@ ivhd_status ivhd_set_positions(ivhd_ctx* ctx, const float* xy, int32_t on_device
   const int64_t M = ctx->M;
   const float2* src = (const float2*)xy;
   float2* tmp = nullptr;
-  cudaError_t e = cudaSuccess;
-  if (!on_device) {
+  cudaError_t e = sync_cur(ctx);
+  if (e == cudaSuccess && !on_device) {
     e = dalloc(&tmp, M, s);
-    if (e != cudaSuccess) return fail(ctx, e);
-    e = cudaMemcpyAsync(tmp, xy, (size_t)M * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp, xy, (size_t)M * sizeof(float2), cudaMemcpyHostToDevice, s);
     src = tmp;
   }
   if (e == cudaSuccess) e = launch_set_positions(ctx, src);
@@ -237,9 +392,14 @@ ivhd_status ivhd_step(ivhd_ctx* ctx, int64_t n_iter) {
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaSuccess;
   int64_t left = n_iter;
-  // whole graphs of kGraphSteps launches, then single launches for the rest
+  // with adaptive b the kernels pick their buffers on the device: one graph, no host flips
+  const bool flip = ctx->ctl == nullptr;
+  const int per_step = ctx->ctl ? 2 : 1;
+  const int par = flip ? ctx->cur : 0;
+  cudaGraphExec_t& gx = ctx->graph_exec[ctx->metric][par];
+  // whole graphs of kGraphSteps steps, then single launches for the rest
   if (left >= kGraphSteps) {
-    if (!ctx->graph_exec[ctx->cur]) {
+    if (!gx) {
       cudaStream_t cap = nullptr;
       e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
       if (e != cudaSuccess) return fail(ctx, e);
@@ -249,29 +409,29 @@ ivhd_status ivhd_step(ivhd_ctx* ctx, int64_t n_iter) {
         int cur = ctx->cur;
         for (int q = 0; q < kGraphSteps && e == cudaSuccess; ++q) {
           e = launch_step(ctx, cur, cap);
-          cur ^= 1;
+          if (flip) cur ^= 1;
         }
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
       }
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec[ctx->cur], g, 0);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
       if (g) cudaGraphDestroy(g);
       cudaStreamDestroy(cap);
       if (e != cudaSuccess) return fail(ctx, e);
     }
     while (left >= kGraphSteps) {
-      e = cudaGraphLaunch(ctx->graph_exec[ctx->cur], s);
+      e = cudaGraphLaunch(gx, s);
       if (e != cudaSuccess) return fail(ctx, e);
       left -= kGraphSteps;
-      ctx->launches += kGraphSteps;
+      ctx->launches += kGraphSteps * per_step;
       // kGraphSteps is even: the parity of cur is unchanged
     }
   }
   for (; left > 0; --left) {
     e = launch_step(ctx, ctx->cur, s);
     if (e != cudaSuccess) return fail(ctx, e);
-    ctx->cur ^= 1;
-    ctx->launches += 1;
+    if (flip) ctx->cur ^= 1;
+    ctx->launches += per_step;
   }
   ctx->steps_done += n_iter;
   return IVHD_OK;
@@ -282,11 +442,9 @@ ivhd_status ivhd_positions(ivhd_ctx* ctx, float* out, int32_t on_device) {
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
   const int64_t M = ctx->M;
-  cudaError_t e = cudaSuccess;
-  if (on_device) {
-    e = launch_unpermute(ctx, (float2*)out);
-    return fail(ctx, e);
-  }
+  cudaError_t e = sync_cur(ctx);
+  if (e != cudaSuccess) return fail(ctx, e);
+  if (on_device) return fail(ctx, launch_unpermute(ctx, (float2*)out));
   float2* tmp = nullptr;
   e = dalloc(&tmp, M, s);
   if (e == cudaSuccess) e = launch_unpermute(ctx, tmp);
@@ -302,7 +460,8 @@ ivhd_status ivhd_forces(ivhd_ctx* ctx, float* out, int32_t on_device) {
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
   const int64_t M = ctx->M;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = sync_cur(ctx);
+  if (e != cudaSuccess) return fail(ctx, e);
   if (on_device) return fail(ctx, launch_forces(ctx, (float2*)out));
   float2* tmp = nullptr;
   e = dalloc(&tmp, M, s);
@@ -318,7 +477,8 @@ ivhd_status ivhd_stress(ivhd_ctx* ctx, double* out) {
   if (!ctx || !out) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
-  cudaError_t e = launch_stress(ctx);
+  cudaError_t e = sync_cur(ctx);
+  if (e == cudaSuccess) e = launch_stress(ctx);
   int32_t flag = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, ctx->red_out, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, ctx->flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -357,6 +517,92 @@ ivhd_status ivhd_info(ivhd_ctx* ctx, ivhd_info_t* out) {
   return IVHD_OK;
 }
 
+ivhd_status ivhd_set_metric(ivhd_ctx* ctx, int32_t metric) {
+  if (!ctx || (metric != IVHD_METRIC_L2 && metric != IVHD_METRIC_L1)) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  ctx->metric = metric;
+  return IVHD_OK;
+}
+
+ivhd_status ivhd_resample_random_neighbors(ivhd_ctx* ctx, uint64_t epoch) {
+  if (!ctx) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  if (ctx->r == 0) return IVHD_OK;
+  return rebuild_preserving_state(ctx, true, epoch);
+}
+
+ivhd_status ivhd_restrict_nn(ivhd_ctx* ctx, const int32_t* helper, int32_t k_helper,
+                             int32_t on_device) {
+  if (!ctx) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  const int k = ctx->k;
+  cudaError_t e = cudaSuccess;
+  if (!helper) {  // restore the full graph
+    if (!ctx->knn_full) return IVHD_OK;
+    e = cudaMemcpyAsync(ctx->knn, ctx->knn_full, (size_t)(M * k) * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(ctx, e);
+    cudaFreeAsync(ctx->knn_full, s);
+    ctx->knn_full = nullptr;
+    return rebuild_preserving_state(ctx, false, 0);
+  }
+  if (k_helper < 1 || (int64_t)k_helper > M - 1) return IVHD_ERR_ARG;
+  if (!ctx->knn_full) {
+    e = dalloc(&ctx->knn_full, M * k, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->knn_full, ctx->knn, (size_t)(M * k) * sizeof(int32_t),
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(ctx, e);
+  }
+  int32_t* hd = nullptr;
+  int32_t* err = nullptr;
+  int32_t herr = 0;
+  const int32_t* hsrc = helper;
+  if (!on_device) {
+    e = dalloc(&hd, M * k_helper, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hd, helper, (size_t)(M * k_helper) * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s);
+    hsrc = hd;
+  }
+  if (e == cudaSuccess) e = dalloc(&err, 1, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) {
+    const int64_t n = M * k;
+    k_restrict<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->knn_full, hsrc, M, k, k_helper,
+                                                          ctx->knn, err);
+    ++ctx->aux_launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
+  if (hd) cudaFreeAsync(hd, s);
+  if (err) cudaFreeAsync(err, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, e);
+  if (herr) {  // bad helper ids: put the full graph back untouched
+    e = cudaMemcpyAsync(ctx->knn, ctx->knn_full, (size_t)(M * k) * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? IVHD_ERR_INDEX : fail(ctx, e);
+  }
+  return rebuild_preserving_state(ctx, false, 0);
+}
+
+ivhd_status ivhd_adaptive_state(ivhd_ctx* ctx, float* b, int64_t* accepted, int64_t* rejected) {
+  if (!ctx || !ctx->ctl) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  AdaptCtl h{};
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->ctl, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, e);
+  if (b) *b = h.b;
+  if (accepted) *accepted = h.accepted;
+  if (rejected) *rejected = h.rejected;
+  return IVHD_OK;
+}
+
 ivhd_status ivhd_state_size(ivhd_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return IVHD_ERR_ARG;
   const int n_arrays = ctx->s2 ? 3 : 2;
@@ -365,11 +611,15 @@ ivhd_status ivhd_state_size(ivhd_ctx* ctx, size_t* bytes) {
 }
 
 // The checkpoint stores the arrays in the internal (degree-sorted) order; the
-// fingerprint ties it to the same graph and parameters, so that order is the same.
+// fingerprint ties it to the same graph and parameters, so that order is the
+// same.  A context whose layout was rebuilt (resampled or restricted) must be
+// brought to the same layout before loading.
 ivhd_status ivhd_get_state(ivhd_ctx* ctx, void* buf, size_t bytes) {
   size_t need = 0;
   if (ivhd_state_size(ctx, &need) != IVHD_OK || !buf || bytes < need) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
+  cudaError_t e = sync_cur(ctx);
+  if (e != cudaSuccess) return fail(ctx, e);
   StateHeader h{};
   h.magic = kStateMagic;
   h.version = kStateVersion;
@@ -378,11 +628,16 @@ ivhd_status ivhd_get_state(ivhd_ctx* ctx, void* buf, size_t bytes) {
   h.steps_done = ctx->steps_done;
   h.opt = ctx->p.opt;
   h.n_arrays = ctx->s2 ? 3 : 2;
+  cudaStream_t s = ctx->stream;
+  if (ctx->ctl) {
+    e = cudaMemcpyAsync(&h.ctl, ctx->ctl, sizeof(h.ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, e);
+  }
   std::memcpy(buf, &h, sizeof(h));
   char* q = (char*)buf + sizeof(h);
   const size_t ab = (size_t)ctx->M * sizeof(float2);
-  cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaMemcpyAsync(q, ctx->y[ctx->cur], ab, cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(q, ctx->y[ctx->cur], ab, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(q + ab, ctx->s1, ab, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && ctx->s2) e = cudaMemcpyAsync(q + 2 * ab, ctx->s2, ab, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -399,10 +654,17 @@ ivhd_status ivhd_set_state(ivhd_ctx* ctx, const void* buf, size_t bytes) {
   if (h.magic != kStateMagic || h.version != kStateVersion || h.fingerprint != fingerprint(ctx) ||
       h.M != ctx->M || h.opt != ctx->p.opt || h.n_arrays != (ctx->s2 ? 3 : 2) || bytes < need)
     return IVHD_ERR_STATE;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (ctx->ctl) {
+    e = cudaMemcpyAsync(ctx->ctl, &h.ctl, sizeof(h.ctl), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = sync_cur(ctx);
+    if (e != cudaSuccess) return fail(ctx, e);
+  }
   const char* q = (const char*)buf + sizeof(h);
   const size_t ab = (size_t)ctx->M * sizeof(float2);
-  cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaMemcpyAsync(ctx->y[ctx->cur], q, ab, cudaMemcpyHostToDevice, s);
+  e = cudaMemcpyAsync(ctx->y[ctx->cur], q, ab, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->s1, q + ab, ab, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && ctx->s2) e = cudaMemcpyAsync(ctx->s2, q + 2 * ab, ab, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_round_positions(ctx);

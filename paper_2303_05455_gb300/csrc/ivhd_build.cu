@@ -1,8 +1,9 @@
 // ivhd_build.cu -- create-time set-up of one embedding context (all on the GPU).
 //
-//   1. validate the kNN rows (range, self loops, duplicates)
+//   1. validate the kNN rows (range, self loops, duplicates; -1 = absent entry)
 //   2. draw r random neighbours per vertex (Sec. 3.3.1 "generated ad hoc";
-//      Sec. 3.3.3: never a vertex connected to i), SplitMix64 draws
+//      Sec. 3.3.3: never a vertex connected to i), SplitMix64 draws, within the
+//      vertex's own embedding when several share the context
 //   3. count the symmetric degree of every vertex (each stress term of
 //      Eq. 3.16 appears in the rows of both endpoints; a mutual kNN pair is
 //      one entry per endpoint, of weight 2 when multiplicity is kept)
@@ -30,20 +31,32 @@ __device__ __forceinline__ bool row_has(const int32_t* row, int n, int32_t j) {
   return false;
 }
 
-// bit 0: id out of range, bit 1: self loop, bit 2: duplicate in a row
-__global__ void k_validate(const int32_t* __restrict__ knn, int64_t M, int k, int32_t* err) {
+// Row validation.  -1 marks an absent entry (a vertex with fewer than k
+// neighbours keeps all it has, Sec. 3.3.3).  err bit 0: id out of range,
+// bit 1: self loop, bit 2: duplicate in a row.  kv[i] = present entries.
+__global__ void k_validate(const int32_t* __restrict__ knn, int64_t M, int k, int32_t* err,
+                           int32_t* __restrict__ kv, unsigned long long* sum_kv) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const int32_t* row = knn + i * k;
-  int bad = 0;
-  for (int s = 0; s < k; ++s) {
-    const int32_t j = row[s];
-    if (j < 0 || (int64_t)j >= M) bad |= 1;
-    if ((int64_t)j == i) bad |= 2;
-    for (int t = 0; t < s; ++t)
-      if (row[t] == j) bad |= 4;
+  int n = 0;
+  if (i < M) {
+    const int32_t* row = knn + i * k;
+    int bad = 0;
+    for (int s = 0; s < k; ++s) {
+      const int32_t j = row[s];
+      if (j == -1) continue;
+      ++n;
+      if (j < 0 || (int64_t)j >= M) bad |= 1;
+      if ((int64_t)j == i) bad |= 2;
+      for (int t = 0; t < s; ++t)
+        if (row[t] == j) bad |= 4;
+    }
+    if (bad) atomicOr(err, bad);
+    kv[i] = n;
   }
-  if (bad) atomicOr(err, bad);
+  unsigned long long v = (unsigned long long)n;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(sum_kv, v);
 }
 
 __device__ __forceinline__ bool connected(const int32_t* __restrict__ knn, int k, int64_t i,
@@ -53,33 +66,64 @@ __device__ __forceinline__ bool connected(const int32_t* __restrict__ knn, int k
   return row_has(knn + j * k, k, (int32_t)i);
 }
 
-// Draw t of vertex i: x = output t of SplitMix64 seeded with
-// s_i = output i of SplitMix64 seeded with (seed ^ "rn_lists");
-// candidate floor(x * M / 2^64).  Kept unless connected to i or already kept;
-// after 64 r draws missing slots are filled by scanning 0..M-1; the rest
-// stay -1.
-__global__ void k_rn_sample(const int32_t* __restrict__ knn, int64_t M, int k, int r,
-                            uint64_t seed, int32_t* __restrict__ rn, int32_t* __restrict__ rc,
+// Segment of vertex i: the independent embedding it belongs to (one segment
+// unless several embeddings share the context).
+struct Seg {
+  int64_t lo, n;
+  int32_t r;
+  uint64_t seed;
+};
+__device__ __forceinline__ Seg seg_of(const SegTable& T, int64_t i) {
+  const int e = T.of ? T.of[i] : 0;
+  return Seg{T.lo[e], T.n[e], T.r[e], T.seed[e]};
+}
+
+// Random neighbours of vertex i in its segment [lo, lo + n) with local index
+// li = i - lo: draw t is x = output t of SplitMix64 seeded with s = output li
+// of SplitMix64 seeded with (seed ^ "rn_lists"); the candidate is
+// lo + floor(x * n / 2^64).  Kept unless connected to i or already kept;
+// after 64 r draws missing slots are filled by scanning the segment in order;
+// the rest stay -1.  Rows have r_max slots; slots past the segment's r are -1.
+__global__ void k_rn_sample(const int32_t* __restrict__ knn, int64_t M, int k, int r_max,
+                            SegTable T, int32_t* __restrict__ rn, int32_t* __restrict__ rc,
                             unsigned long long* empty) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
+  const Seg g = seg_of(T, i);
   const int32_t* rowi = knn + i * k;
-  int32_t* out = rn + i * r;
+  int32_t* out = rn + i * r_max;
   int got = 0;
-  const uint64_t si = sm64_out(seed ^ kDomainRn, (uint64_t)i);
-  const int64_t tmax = 64 * (int64_t)r;
-  for (int64_t t = 0; t < tmax && got < r; ++t) {
-    const int64_t j = (int64_t)__umul64hi(sm64_out(si, (uint64_t)t), (uint64_t)M);
+  const uint64_t si = sm64_out(g.seed ^ kDomainRn, (uint64_t)(i - g.lo));
+  const int64_t tmax = 64 * (int64_t)g.r;
+  for (int64_t t = 0; t < tmax && got < g.r; ++t) {
+    const int64_t j = g.lo + (int64_t)__umul64hi(sm64_out(si, (uint64_t)t), (uint64_t)g.n);
     if (connected(knn, k, i, rowi, j) || row_has(out, got, (int32_t)j)) continue;
     out[got++] = (int32_t)j;
   }
-  for (int64_t j = 0; j < M && got < r; ++j) {
+  for (int64_t j = g.lo; j < g.lo + g.n && got < g.r; ++j) {
     if (connected(knn, k, i, rowi, j) || row_has(out, got, (int32_t)j)) continue;
     out[got++] = (int32_t)j;
   }
-  for (int s = got; s < r; ++s) out[s] = -1;
+  for (int s = got; s < r_max; ++s) out[s] = -1;
   rc[i] = got;
-  if (got < r) atomicAdd(empty, (unsigned long long)(r - got));
+  if (got < g.r) atomicAdd(empty, (unsigned long long)(g.r - got));
+}
+
+// Seeds of a redraw: epoch e > 0 replaces seed s by s ^ mix(e) (e = 0 is the first draw).
+__global__ void k_reseed(const uint64_t* __restrict__ in, int n, uint64_t epoch,
+                         uint64_t* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = in[e] ^ sm64_mix(epoch);
+}
+
+// Kept random neighbours of an existing rn array (rebuild without redrawing).
+__global__ void k_rn_count(const int32_t* __restrict__ rn, int64_t M, int r,
+                           int32_t* __restrict__ rc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  int n = 0;
+  for (int s = 0; s < r; ++s) n += rn[i * r + s] >= 0;
+  rc[i] = n;
 }
 
 // In-degree of every vertex: nn entries (i -> j) and kept rn entries.  An nn
@@ -95,8 +139,10 @@ __global__ void k_count_in(const int32_t* __restrict__ knn, const int32_t* __res
   if (e < n_nn) {
     const int64_t i = e / k;
     const int32_t j = knn[e];
-    mut = row_has(knn + (int64_t)j * k, k, (int32_t)i);
-    if (!mut) atomicAdd(&in_nn[j], 1);
+    if (j >= 0) {
+      mut = row_has(knn + (int64_t)j * k, k, (int32_t)i);
+      if (!mut) atomicAdd(&in_nn[j], 1);
+    }
   } else if (e < n_nn + M * r) {
     const int32_t j = rn[e - n_nn];
     if (j >= 0) atomicAdd(&in_rn[j], 1);
@@ -107,16 +153,16 @@ __global__ void k_count_in(const int32_t* __restrict__ knn, const int32_t* __res
 
 // Degree (stored row entries) and the descending-degree sort key; totals
 // are reduced per warp before the atomics.
-__global__ void k_degree(const int32_t* __restrict__ rc, const int32_t* __restrict__ in_nn,
-                         const int32_t* __restrict__ in_rn, int64_t M, int k,
-                         int32_t* __restrict__ deg, uint32_t* __restrict__ key,
+__global__ void k_degree(const int32_t* __restrict__ kv, const int32_t* __restrict__ rc,
+                         const int32_t* __restrict__ in_nn, const int32_t* __restrict__ in_rn,
+                         int64_t M, int32_t* __restrict__ deg, uint32_t* __restrict__ key,
                          int32_t* __restrict__ val, unsigned long long* sum_deg,
                          unsigned long long* sum_rc, int32_t* max_deg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int32_t d = 0, c = 0;
   if (i < M) {
     c = rc[i];
-    d = k + c + in_nn[i] + in_rn[i];
+    d = kv[i] + c + in_nn[i] + in_rn[i];
     deg[i] = d;
     key[i] = 0xFFFFu - (uint32_t)min(d, 0xFFFF);
     val[i] = (int32_t)i;
@@ -192,16 +238,17 @@ __global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(
 // ---- layout sizing ---------------------------------------------------------
 
 __global__ void k_sorted_info(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg,
-                              const int32_t* __restrict__ rc, int64_t M, int k, int hub_thr,
-                              int32_t* __restrict__ inv, int32_t* __restrict__ deg_p,
-                              int32_t* __restrict__ outc_p, int32_t* n_hub) {
+                              const int32_t* __restrict__ kv, const int32_t* __restrict__ rc,
+                              int64_t M, int hub_thr, int32_t* __restrict__ inv,
+                              int32_t* __restrict__ deg_p, int32_t* __restrict__ outc_p,
+                              int32_t* n_hub) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= M) return;
   const int32_t i = perm[p];
   inv[i] = (int32_t)p;
   const int32_t d = deg[i];
   deg_p[p] = d;
-  outc_p[p] = k + rc[i];
+  outc_p[p] = kv[i] + rc[i];
   if (d >= hub_thr) atomicAdd(n_hub, 1);
 }
 
@@ -240,8 +287,8 @@ __device__ __forceinline__ int64_t slot_addr(int64_t p, int t, int64_t n_hub,
   return (int64_t)slice_off[q >> 5] + ((int64_t)(t >> 2) * 32 + (q & 31)) * 4 + (t & 3);
 }
 
-// Out-entries of input vertex i: its k nn ids (weight-2 bit on mutual pairs
-// when multiplicity is kept), then its kept rn ids (rn bit set).
+// Out-entries of input vertex i: its present nn ids (weight-2 bit on mutual
+// pairs when multiplicity is kept), then its kept rn ids (rn bit set).
 __global__ void k_fill_out(const int32_t* __restrict__ knn, const int32_t* __restrict__ rn,
                            const int32_t* __restrict__ rc, const int32_t* __restrict__ inv,
                            int64_t M, int k, int r, int dedup, int64_t n_hub,
@@ -250,14 +297,16 @@ __global__ void k_fill_out(const int32_t* __restrict__ knn, const int32_t* __res
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int64_t p = inv[i];
+  int t = 0;
   for (int s = 0; s < k; ++s) {
     const int32_t j = knn[i * k + s];
+    if (j < 0) continue;
     const bool w2 = !dedup && row_has(knn + (int64_t)j * k, k, (int32_t)i);
-    ids[slot_addr(p, s, n_hub, hub_off, slice_off)] = (uint32_t)inv[j] | (w2 ? kW2Bit : 0u);
+    ids[slot_addr(p, t++, n_hub, hub_off, slice_off)] = (uint32_t)inv[j] | (w2 ? kW2Bit : 0u);
   }
   const int n = rc[i];
   for (int s = 0; s < n; ++s)
-    ids[slot_addr(p, k + s, n_hub, hub_off, slice_off)] = (uint32_t)inv[rn[i * r + s]] | kRnBit;
+    ids[slot_addr(p, t + s, n_hub, hub_off, slice_off)] = (uint32_t)inv[rn[i * r + s]] | kRnBit;
 }
 
 // In-entries: the mirror of every out-entry (i -> j) lands in row j.
@@ -275,6 +324,7 @@ __global__ void k_fill_in(const int32_t* __restrict__ knn, const int32_t* __rest
   if (e < n_nn) {
     i = e / k;
     j = knn[e];
+    if (j < 0) return;
     if (row_has(knn + (int64_t)j * k, k, (int32_t)i)) return;  // mutual: held by j's out-entry
     bit = 0;
   } else if (e < n_nn + M * r) {
@@ -310,20 +360,29 @@ __global__ void k_sort_in_sell(const int32_t* __restrict__ deg_p, const int32_t*
   }
 }
 
-// Sorts the in-part of each hub row: warp per row, stable rank sort from a copy.
-__global__ void k_sort_in_hub(const int32_t* __restrict__ deg_p, const int32_t* __restrict__ outc_p,
-                              int64_t n_hub, const int32_t* __restrict__ hub_off,
-                              const uint32_t* __restrict__ copy, uint32_t* __restrict__ ids) {
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (p >= n_hub) return;
+// Sorts the in-part of each hub row: one block per row, stable rank sort of a
+// copy (in shared memory when it fits).
+constexpr int kHubSortSmem = 8192;
+__global__ void __launch_bounds__(256) k_sort_in_hub(const int32_t* __restrict__ deg_p,
+                                                     const int32_t* __restrict__ outc_p,
+                                                     const int32_t* __restrict__ hub_off,
+                                                     const uint32_t* __restrict__ copy,
+                                                     uint32_t* __restrict__ ids) {
+  __shared__ uint32_t sh[kHubSortSmem];
+  const int64_t p = blockIdx.x;
   const int64_t base = hub_off[p];
-  const int b = outc_p[p], n = deg_p[p];
-  for (int t = b + lane; t < n; t += 32) {
-    const uint32_t v = copy[base + t];
+  const int b = outc_p[p], n = deg_p[p], m = n - b;
+  const uint32_t* src = copy + base + b;
+  if (m <= kHubSortSmem) {
+    for (int t = threadIdx.x; t < m; t += blockDim.x) sh[t] = src[t];
+    __syncthreads();
+    src = sh;
+  }
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const uint32_t v = src[t];
     int rank = 0;
-    for (int u = b; u < n; ++u) {
-      const uint32_t w = copy[base + u];
+    for (int u = 0; u < m; ++u) {
+      const uint32_t w = src[u];
       rank += (w < v) || (w == v && u < t);
     }
     ids[base + b + rank] = v;
@@ -428,6 +487,7 @@ struct HostTotals {
   int32_t n_hub;
   int32_t max_deg;
   int32_t pad;
+  unsigned long long sum_kv;
   unsigned long long sum_deg;
   unsigned long long sum_rc;
   unsigned long long mutual;
@@ -443,7 +503,7 @@ struct HostTotals {
       return (e_ == cudaErrorMemoryAllocation) ? IVHD_ERR_OOM : IVHD_ERR_CUDA; \
   } while (0)
 
-ivhd_status build_layout(ivhd_ctx* ctx) {
+ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
   cudaStream_t s = ctx->stream;
   const int64_t M = ctx->M;
   const int k = ctx->k, r = ctx->r;
@@ -452,11 +512,12 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
 
   // totals block lives in device memory, read back twice
   HostTotals* tot_d = sc.get<HostTotals>(1);
+  int32_t* kv = sc.get<int32_t>(M);
   if (!sc.ok) return IVHD_ERR_OOM;
   IVHD_TRY(cudaMemsetAsync(tot_d, 0, sizeof(HostTotals), s));
 
   // 1. validation -- nothing below may index with an unchecked id
-  k_validate<<<nblk(M), kB, 0, s>>>(ctx->knn, M, k, &tot_d->err);
+  k_validate<<<nblk(M), kB, 0, s>>>(ctx->knn, M, k, &tot_d->err, kv, &tot_d->sum_kv);
   ++ctx->setup_launches;
   IVHD_TRY(cudaGetLastError());
   HostTotals h{};
@@ -464,7 +525,7 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   IVHD_TRY(cudaStreamSynchronize(s));
   if (h.err) return IVHD_ERR_INDEX;
 
-  // 2. random neighbours
+  // 2. random neighbours (drawn, or kept from the previous layout)
   int32_t* rc = sc.get<int32_t>(M);
   int32_t* in_nn = sc.get<int32_t>(M);
   int32_t* in_rn = sc.get<int32_t>(M);
@@ -476,11 +537,24 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   int32_t* outc_p = sc.get<int32_t>(M);
   int32_t* cursor = sc.get<int32_t>(M);
   if (!sc.ok) return IVHD_ERR_OOM;
-  if (r > 0) {
-    k_rn_sample<<<nblk(M), kB, 0, s>>>(ctx->knn, M, k, r, ctx->p.seed, ctx->rn, rc, &tot_d->empty);
+  if (r == 0) {
+    IVHD_TRY(cudaMemsetAsync(rc, 0, M * sizeof(int32_t), s));
+  } else if (draw_rn) {
+    SegTable T = ctx->seg;
+    // a redraw (epoch > 0) reseeds every segment's stream
+    uint64_t* seeds = nullptr;
+    if (rn_epoch) {
+      seeds = sc.get<uint64_t>(ctx->n_seg);
+      if (!sc.ok) return IVHD_ERR_OOM;
+      k_reseed<<<nblk(ctx->n_seg), kB, 0, s>>>(T.seed, ctx->n_seg, rn_epoch, seeds);
+      ++ctx->setup_launches;
+      T.seed = seeds;
+    }
+    k_rn_sample<<<nblk(M), kB, 0, s>>>(ctx->knn, M, k, r, T, ctx->rn, rc, &tot_d->empty);
     ++ctx->setup_launches;
   } else {
-    IVHD_TRY(cudaMemsetAsync(rc, 0, M * sizeof(int32_t), s));
+    k_rn_count<<<nblk(M), kB, 0, s>>>(ctx->rn, M, r, rc);
+    ++ctx->setup_launches;
   }
   IVHD_TRY(cudaGetLastError());
 
@@ -492,7 +566,7 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   k_count_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, M, k, r, in_nn, in_rn,
                                             &tot_d->mutual);
   ++ctx->setup_launches;
-  k_degree<<<nblk(M), kB, 0, s>>>(rc, in_nn, in_rn, M, k, deg, key0, val0, &tot_d->sum_deg,
+  k_degree<<<nblk(M), kB, 0, s>>>(kv, rc, in_nn, in_rn, M, deg, key0, val0, &tot_d->sum_deg,
                                   &tot_d->sum_rc, &tot_d->max_deg);
   ++ctx->setup_launches;
   IVHD_TRY(cudaGetLastError());
@@ -505,7 +579,6 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
     int64_t* c64 = sc.get<int64_t>(nc);
     int64_t* o64 = sc.get<int64_t>(nc + 1);
     int32_t* offs = sc.get<int32_t>(nc + 1);
-    if (!sc.ok) return IVHD_ERR_OOM;
     int32_t* val1 = sc.get<int32_t>(M);
     if (!sc.ok) return IVHD_ERR_OOM;
     // pass 0: (key0, val0) -> (key1, val1); pass 1: (key1, val1) -> (key0, perm)
@@ -516,21 +589,19 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
       uint32_t* kout = pass ? key0 : key1;
       int32_t* vout = pass ? ctx->perm : val1;
       k_radix_hist<<<nb, kRadixBlock, 0, s>>>(kin, M, shift, nb, counts);
-      ++ctx->setup_launches;
       k_widen<<<nblk(nc), kB, 0, s>>>(counts, c64, nc);
-      ++ctx->setup_launches;
+      ctx->setup_launches += 2;
       IVHD_TRY(cudaGetLastError());
       IVHD_TRY(scan_i64(c64, o64, nc, s, sc, &ctx->setup_launches));
       k_offsets_i32<<<nblk(nc + 1), kB, 0, s>>>(o64, nc, 0, offs);
-      ++ctx->setup_launches;
       k_radix_scatter<<<nb, kRadixBlock, 0, s>>>(kin, vin, kout, vout, M, shift, nb, offs);
-      ++ctx->setup_launches;
+      ctx->setup_launches += 2;
       IVHD_TRY(cudaGetLastError());
     }
   }
 
   // 5. sizes and offsets
-  k_sorted_info<<<nblk(M), kB, 0, s>>>(ctx->perm, deg, rc, M, k, ctx->hub_threshold, ctx->inv,
+  k_sorted_info<<<nblk(M), kB, 0, s>>>(ctx->perm, deg, kv, rc, M, ctx->hub_threshold, ctx->inv,
                                        deg_p, outc_p, &tot_d->n_hub);
   ++ctx->setup_launches;
   const int64_t max_slices = (M + 31) / 32;
@@ -557,10 +628,11 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   ctx->n_slices = (M - h.n_hub + 31) / 32;
   ctx->n_slots = h.hub_total + h.sell_total;
   ctx->nnz_sym = (int64_t)h.sum_deg;
-  // stress terms: every kNN entry (a mutual pair once when deduplicated) plus kept rn draws
-  ctx->n_terms = M * (int64_t)k - (dedup ? (int64_t)(h.mutual / 2) : 0) + (int64_t)h.sum_rc;
+  // stress terms: every present kNN entry (a mutual pair once when deduplicated)
+  // plus the kept rn draws
+  ctx->n_terms = (int64_t)h.sum_kv - (dedup ? (int64_t)(h.mutual / 2) : 0) + (int64_t)h.sum_rc;
   ctx->max_degree = h.max_deg;
-  ctx->empty_rn = (int32_t)h.empty;
+  if (draw_rn) ctx->empty_rn = (int32_t)h.empty;
   if (ctx->n_slots >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
 
   IVHD_TRY(cudaMallocAsync((void**)&ctx->ids, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
@@ -569,36 +641,36 @@ ivhd_status build_layout(ivhd_ctx* ctx) {
   IVHD_TRY(cudaMallocAsync((void**)&ctx->slice_w, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
   IVHD_TRY(cudaMemsetAsync(ctx->ids, 0xFF, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
   k_offsets_i32<<<nblk(ctx->n_hub + 1), kB, 0, s>>>(hub_o64, ctx->n_hub, 0, ctx->hub_off);
-  ++ctx->setup_launches;
   k_offsets_i32<<<nblk(ctx->n_slices + 1), kB, 0, s>>>(sl_o64, ctx->n_slices, h.hub_total,
                                                        ctx->slice_off);
-  ++ctx->setup_launches;
+  ctx->setup_launches += 2;
   IVHD_TRY(cudaMemcpyAsync(ctx->slice_w, slice_w, (size_t)ctx->n_slices * sizeof(int32_t),
                            cudaMemcpyDeviceToDevice, s));
   IVHD_TRY(cudaGetLastError());
 
   k_fill_out<<<nblk(M), kB, 0, s>>>(ctx->knn, ctx->rn, rc, ctx->inv, M, k, r, dedup, ctx->n_hub,
                                     ctx->hub_off, ctx->slice_off, ctx->ids);
-  ++ctx->setup_launches;
   k_fill_in<<<nblk(n_entries), kB, 0, s>>>(ctx->knn, ctx->rn, ctx->inv, outc_p, M, k, r,
                                            ctx->n_hub, ctx->hub_off, ctx->slice_off, cursor,
                                            ctx->ids);
-  ++ctx->setup_launches;
+  ctx->setup_launches += 2;
   IVHD_TRY(cudaGetLastError());
-  if (M - ctx->n_hub > 0)
+  if (M - ctx->n_hub > 0) {
     k_sort_in_sell<<<nblk(M - ctx->n_hub), kB, 0, s>>>(deg_p, outc_p, M, ctx->n_hub,
                                                         ctx->slice_off, ctx->ids);
     ++ctx->setup_launches;
+  }
   if (ctx->n_hub > 0) {
     uint32_t* copy = sc.get<uint32_t>(h.hub_total);
     if (!sc.ok) return IVHD_ERR_OOM;
     IVHD_TRY(cudaMemcpyAsync(copy, ctx->ids, (size_t)h.hub_total * sizeof(uint32_t),
                              cudaMemcpyDeviceToDevice, s));
-    k_sort_in_hub<<<nblk(ctx->n_hub * 32), kB, 0, s>>>(deg_p, outc_p, ctx->n_hub, ctx->hub_off,
-                                                       copy, ctx->ids);
+    k_sort_in_hub<<<(unsigned)ctx->n_hub, 256, 0, s>>>(deg_p, outc_p, ctx->hub_off, copy,
+                                                       ctx->ids);
     ++ctx->setup_launches;
   }
   IVHD_TRY(cudaGetLastError());
+  // the layout is complete once the stream reaches here; scratch frees follow in order
   return IVHD_OK;
 }
 

@@ -65,21 +65,44 @@ __device__ __forceinline__ int4 ld_stream_v4(const int4* p) {
   return v;
 }
 
-// Per-step arguments of the fused kernel (passed by value).
+// Independent embeddings sharing one context ("segments"): vertex i belongs to
+// segment of[i] (or 0 when of is null), which spans [lo, lo + n), draws r
+// random neighbours inside itself and seeds its streams with seed.
+struct SegTable {
+  const int32_t* of;
+  const int64_t* lo;
+  const int64_t* n;
+  const int32_t* r;
+  const uint64_t* seed;
+};
+
+// Device control word of the self-adaptive b scheme (Sec. 3.3.3).
+struct AdaptCtl {
+  int32_t cur;       // current ping-pong buffer
+  int32_t accepted;  // accepted steps
+  int32_t rejected;  // rejected steps
+  float b;           // current force scale
+  double last_dT;    // kinetic-energy change of the last attempted step
+};
+
+// Per-step arguments of the fused kernel (passed by value).  Buffers come in
+// ping-pong pairs: a step reads [cur] and writes [cur ^ 1]; velocities are
+// updated in place (v[0]) except with self-adaptive b, where they ping-pong too
+// and cur comes from the device control word.
 struct StepArgs {
   const uint32_t* __restrict__ ids;
   const int32_t* __restrict__ hub_off;
   const int32_t* __restrict__ slice_off;
   const int32_t* __restrict__ slice_w;
-  const float2* __restrict__ y_in;
-  float2* __restrict__ y_out;
-  const uint32_t* __restrict__ yh_in;  // rounded FP16 / BF16 copy gathered by neighbours
-  uint32_t* __restrict__ yh_out;
-  float2* __restrict__ s1;
+  float2* y[2];
+  uint32_t* yh[2];  // rounded FP16 / BF16 copies gathered by neighbours
+  float2* v[2];     // velocity or E[g^2]
   float2* __restrict__ s2;
+  int32_t cur;
+  AdaptCtl* ctl;
   const int32_t* __restrict__ perm;  // forces mode: scatter to input order
   float2* __restrict__ f_out;        // forces mode output
-  double* __restrict__ partials;     // stress mode: one double per block
+  double* __restrict__ partials;     // stress: one double per block; adaptive: two
   int32_t* __restrict__ flag;        // stress mode: non-finite flag
   int32_t M, n_hub, n_slices, nb_hub;
   float c, a, b, rho, eps;
@@ -98,8 +121,18 @@ struct ivhd_ctx {
   int hub_threshold = ivhd::kDefaultHubThreshold;
   bool poisoned = false;
 
+  // segments (independent embeddings) and their device tables
+  ivhd::SegTable seg{};
+  int32_t n_seg = 1;
+  int32_t* seg_of = nullptr;
+  int64_t* seg_lo = nullptr;
+  int64_t* seg_n = nullptr;
+  int32_t* seg_r = nullptr;
+  uint64_t* seg_seed = nullptr;
+
   // graph and layout
-  int32_t* knn = nullptr;   // M*k, input ids
+  int32_t* knn_full = nullptr;  // unrestricted kNN rows, kept while a restriction is active
+  int32_t* knn = nullptr;   // M*k, input ids, -1 = absent entry
   int32_t* rn = nullptr;    // M*r, input ids, -1 empty
   int32_t* perm = nullptr;  // p -> i
   int32_t* inv = nullptr;   // i -> p
@@ -113,8 +146,11 @@ struct ivhd_ctx {
   float2* y[2] = {nullptr, nullptr};
   uint32_t* yh[2] = {nullptr, nullptr};  // FP16 / BF16 gathered copies (pos_format != F32)
   int cur = 0;
-  float2* s1 = nullptr;
+  float2* vbuf[2] = {nullptr, nullptr};  // velocity / E[g^2]; [1] only with adaptive b
+  float2* s1 = nullptr;                  // = vbuf[cur] with adaptive b, else vbuf[0]
   float2* s2 = nullptr;
+  ivhd::AdaptCtl* ctl = nullptr;         // adaptive b only
+  int metric = IVHD_METRIC_L2;
 
   // scratch for reductions
   double* partials = nullptr;
@@ -122,8 +158,8 @@ struct ivhd_ctx {
   int32_t* flag = nullptr;
   int64_t n_partials = 0;
 
-  // CUDA graph of kGraphSteps steps, one per starting parity
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  // CUDA graphs of kGraphSteps steps, per metric and starting parity
+  cudaGraphExec_t graph_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 
   // counters
   int64_t n_terms = 0, nnz_sym = 0;  // stress terms; stored (gathered) row entries
@@ -133,8 +169,9 @@ struct ivhd_ctx {
 
 namespace ivhd {
 
-// ivhd_build.cu
-ivhd_status build_layout(ivhd_ctx* ctx);
+// ivhd_build.cu: builds the layout from ctx->knn (and ctx->rn unless draw_rn);
+// a redraw with epoch e > 0 reseeds the random-neighbour streams.
+ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch);
 
 // ivhd_step.cu
 cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s);
@@ -144,6 +181,8 @@ cudaError_t launch_unpermute(ivhd_ctx* ctx, float2* out_input_order);
 cudaError_t launch_set_positions(ivhd_ctx* ctx, const float2* in_input_order);
 cudaError_t launch_init_positions(ivhd_ctx* ctx);
 cudaError_t launch_round_positions(ivhd_ctx* ctx);
+cudaError_t launch_to_input_order(ivhd_ctx* ctx, const float2* a, float2* out);
+cudaError_t launch_from_input_order(ivhd_ctx* ctx, const float2* in, float2* a);
 int step_grid(const ivhd_ctx* ctx);
 
 }  // namespace ivhd

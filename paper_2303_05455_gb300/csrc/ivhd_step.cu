@@ -2,17 +2,27 @@
 //
 // For every vertex i (Sec. 3.3.1, Eq. 3.14 with F = -1/2 grad E of Eq. 3.16):
 //
-//     F_i = sum_{j in nn_sym(i)} (y_j - y_i)
+//     F_i = sum_{j in nn_sym(i)} w_ij (y_j - y_i)
 //         + c * sum_{k in rn_sym(i)} (1 - 1/d_ik) (y_k - y_i),   d_ik = |y_k - y_i|
 //
-// where nn_sym / rn_sym are the symmetrised neighbour multisets (every term of
-// the stress acts on both of its endpoints), followed in the same thread by
-// the optimiser update of Eq. 3.34 (momentum), or the Nesterov / Adadelta
-// forms of Sec. 3.3.2.  All forces of a step read y_in and all updates write
-// y_out (ping-pong), which is the synchronous scheme of the IVHD-CUDA
-// algorithm in Sec. 5.2 without its per-connection +/- slots and second pass:
-// each vertex gathers its neighbours' positions instead, so there are no
-// atomics and the summation order is fixed by the layout (deterministic).
+// where nn_sym / rn_sym are the symmetrised neighbour lists (every term of the
+// stress acts on both of its endpoints; w_ij = 2 for a mutual kNN pair kept
+// with multiplicity), followed in the same thread by the optimiser update of
+// Eq. 3.34 (momentum), or the Nesterov / Adadelta forms of Sec. 3.3.2.  All
+// forces of a step read y_in and all updates write y_out (ping-pong), which is
+// the synchronous scheme of the IVHD-CUDA algorithm in Sec. 5.2 without its
+// per-connection +/- slots and second pass: each vertex gathers its
+// neighbours' positions instead, so there are no atomics and the summation
+// order is fixed by the layout (deterministic).
+//
+// Variants selected by template parameters:
+//   POS     gathered position format (FP32, or FP16 / BF16 copies with an FP32
+//           master position for the vertex's own update)
+//   METRIC  L2 (the method) or L1 (Sec. 3.4.1: the l1 norm in the late
+//           stages of the embedding, for its "suction" of outliers)
+//   ADAPT   self-adaptive b (Sec. 3.3.3): velocities are ping-ponged, b and the
+//           current buffer come from a device control word, and every block
+//           reports its kinetic-energy sums for the controller kernel.
 //
 // Work split: SELL slices of 32 degree-sorted vertices, one thread per vertex
 // and one coalesced int4 id load per 4 neighbours; vertices of very high
@@ -27,11 +37,12 @@ namespace ivhd {
 // Position of vertex idx as the neighbours see it: the FP32 array, or the
 // rounded FP16 / BF16 copy (one 32-bit word per vertex).
 template <int POS>
-__device__ __forceinline__ float2 load_pos(const StepArgs& A, uint32_t idx) {
+__device__ __forceinline__ float2 load_pos(const float2* __restrict__ y,
+                                           const uint32_t* __restrict__ yh, uint32_t idx) {
   if constexpr (POS == IVHD_POS_F32) {
-    return __ldg(A.y_in + idx);
+    return __ldg(y + idx);
   } else {
-    const uint32_t w = __ldg(A.yh_in + idx);
+    const uint32_t w = __ldg(yh + idx);
     if constexpr (POS == IVHD_POS_F16) {
       __half2 h;
       memcpy(&h, &w, 4);
@@ -58,89 +69,134 @@ __device__ __forceinline__ uint32_t round_pos(float2 v) {
   return w;
 }
 
+struct Gsrc {
+  const float2* __restrict__ y;
+  const uint32_t* __restrict__ yh;
+};
+
 template <int POS>
-__device__ __forceinline__ float2 gather(const StepArgs& A, uint32_t e, float2 self) {
-  return (e == kPad) ? self : load_pos<POS>(A, e & kIdxMask);
+__device__ __forceinline__ float2 gather(const Gsrc& G, uint32_t e, float2 self) {
+  return (e == kPad) ? self : load_pos<POS>(G.y, G.yh, e & kIdxMask);
 }
 
-// One term of the force on i.  nn: w = 1, or 2 for a mutual pair kept with
-// multiplicity.  rn: w = c (1 - 1/d); w = 0 at d = 0.  Padding entries carry
-// the rn bit and gather y_i itself, so d = 0, w = 0.
+__device__ __forceinline__ float sgnf(float u) { return (float)((u > 0.f) - (u < 0.f)); }
+
+// One term of the force on i, u = y_j - y_i.
+// L2: nn w u (w = 1, or 2 for a mutual pair kept with multiplicity);
+//     rn c (1 - 1/d) u, zero at d = 0.
+// L1 (d = |u_x| + |u_y|, gradient taken coordinate-wise with sign(0) = 0):
+//     nn w d sign(u); rn -c (1 - d) sign(u).
+// Padding entries carry the rn bit and gather y_i itself: u = 0, no force.
+template <int METRIC>
 __device__ __forceinline__ void force_term(uint32_t e, float2 yj, float2 yi, float c, float& fx,
                                            float& fy) {
   const float ux = yj.x - yi.x;
   const float uy = yj.y - yi.y;
-  float w = (e & kW2Bit) ? 2.f : 1.f;
-  if (e & kRnBit) {
-    const float d2 = fmaf(uy, uy, ux * ux);
-    w = (d2 > 0.f) ? c * (1.f - rsqrtf(d2)) : 0.f;
+  if constexpr (METRIC == IVHD_METRIC_L2) {
+    float w = (e & kW2Bit) ? 2.f : 1.f;
+    if (e & kRnBit) {
+      const float d2 = fmaf(uy, uy, ux * ux);
+      w = (d2 > 0.f) ? c * (1.f - rsqrtf(d2)) : 0.f;
+    }
+    fx = fmaf(w, ux, fx);
+    fy = fmaf(w, uy, fy);
+  } else {
+    const float d = fabsf(ux) + fabsf(uy);
+    float s = ((e & kW2Bit) ? 2.f : 1.f) * d;
+    if (e & kRnBit) s = -c * (1.f - d);
+    fx = fmaf(s, sgnf(ux), fx);
+    fy = fmaf(s, sgnf(uy), fy);
   }
-  fx = fmaf(w, ux, fx);
-  fy = fmaf(w, uy, fy);
 }
 
-// One term of the stress: nn w d^2 (w = 1 or 2), rn c (1 - d)^2; padding contributes nothing.
+// One term of the stress: nn w d^2, rn c (1 - d)^2 (d in the active metric);
+// padding contributes nothing.
+template <int METRIC>
 __device__ __forceinline__ void stress_term(uint32_t e, float2 yj, float2 yi, float c, float& es) {
   if (e == kPad) return;
   const float ux = yj.x - yi.x;
   const float uy = yj.y - yi.y;
-  const float d2 = fmaf(uy, uy, ux * ux);
+  float d2, d;
+  if constexpr (METRIC == IVHD_METRIC_L2) {
+    d2 = fmaf(uy, uy, ux * ux);
+    d = sqrtf(d2);
+  } else {
+    d = fabsf(ux) + fabsf(uy);
+    d2 = d * d;
+  }
   if (e & kRnBit) {
-    const float t = 1.f - sqrtf(d2);
+    const float t = 1.f - d;
     es = fmaf(c * t, t, es);
   } else {
     es = fmaf((e & kW2Bit) ? 2.f : 1.f, d2, es);
   }
 }
 
-template <int MODE, int POS>
-__device__ __forceinline__ void visit4(const int4 e, const StepArgs& A, float2 yi, float c,
-                                       float& fx, float& fy) {
+template <int MODE, int POS, int METRIC>
+__device__ __forceinline__ void visit4(const int4 e, const Gsrc& G, float2 yi, float c, float& fx,
+                                       float& fy) {
   const uint32_t e0 = (uint32_t)e.x, e1 = (uint32_t)e.y, e2 = (uint32_t)e.z, e3 = (uint32_t)e.w;
-  const float2 g0 = gather<POS>(A, e0, yi), g1 = gather<POS>(A, e1, yi);
-  const float2 g2 = gather<POS>(A, e2, yi), g3 = gather<POS>(A, e3, yi);
+  const float2 g0 = gather<POS>(G, e0, yi), g1 = gather<POS>(G, e1, yi);
+  const float2 g2 = gather<POS>(G, e2, yi), g3 = gather<POS>(G, e3, yi);
   if (MODE == kStress) {
-    stress_term(e0, g0, yi, c, fx);
-    stress_term(e1, g1, yi, c, fx);
-    stress_term(e2, g2, yi, c, fx);
-    stress_term(e3, g3, yi, c, fx);
+    stress_term<METRIC>(e0, g0, yi, c, fx);
+    stress_term<METRIC>(e1, g1, yi, c, fx);
+    stress_term<METRIC>(e2, g2, yi, c, fx);
+    stress_term<METRIC>(e3, g3, yi, c, fx);
   } else {
-    force_term(e0, g0, yi, c, fx, fy);
-    force_term(e1, g1, yi, c, fx, fy);
-    force_term(e2, g2, yi, c, fx, fy);
-    force_term(e3, g3, yi, c, fx, fy);
+    force_term<METRIC>(e0, g0, yi, c, fx, fy);
+    force_term<METRIC>(e1, g1, yi, c, fx, fy);
+    force_term<METRIC>(e2, g2, yi, c, fx, fy);
+    force_term<METRIC>(e3, g3, yi, c, fx, fy);
   }
 }
 
-template <int MODE, int POS>
-__device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const StepArgs& A, float2 yi,
+template <int MODE, int POS, int METRIC>
+__device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const Gsrc& G, float2 yi,
                                        float c, float& fx, float& fy) {
   // all eight gathers are issued before any arithmetic (eight loads in flight per thread)
   const uint32_t e[8] = {(uint32_t)ea.x, (uint32_t)ea.y, (uint32_t)ea.z, (uint32_t)ea.w,
                          (uint32_t)eb.x, (uint32_t)eb.y, (uint32_t)eb.z, (uint32_t)eb.w};
   float2 g[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) g[q] = gather<POS>(A, e[q], yi);
+  for (int q = 0; q < 8; ++q) g[q] = gather<POS>(G, e[q], yi);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     if (MODE == kStress)
-      stress_term(e[q], g[q], yi, c, fx);
+      stress_term<METRIC>(e[q], g[q], yi, c, fx);
     else
-      force_term(e[q], g[q], yi, c, fx, fy);
+      force_term<METRIC>(e[q], g[q], yi, c, fx, fy);
   }
+}
+
+// Block sum of a per-thread double in a fixed order (warp tree, then warps in
+// order); the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();
+  return t;
 }
 
 #ifndef IVHD_STEP_MIN_BLOCKS
 #define IVHD_STEP_MIN_BLOCKS 1
 #endif
 
-// MODE: optimiser epilogue (or forces / stress); POS: gathered position format.
-// yi is the vertex's own position in the gathered format (differences are taken
-// between equally rounded positions); ym is its FP32 master position.
-template <int MODE, int POS>
+// MODE: optimiser epilogue (or forces / stress).  yi is the vertex's own
+// position in the gathered format (differences are taken between equally
+// rounded positions); ym is its FP32 master position.
+template <int MODE, int POS, int METRIC, bool ADAPT>
 __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  const int cur = ADAPT ? A.ctl->cur : A.cur;
+  const Gsrc G{A.y[cur], A.yh[cur]};
+  const float b = ADAPT ? A.ctl->b : A.b;
   float fx = 0.f, fy = 0.f;  // force, or (stress in fx)
   float2 yi = make_float2(0.f, 0.f);
   float2 ym = make_float2(0.f, 0.f);
@@ -151,8 +207,8 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
     // hub rows: one warp per vertex, lanes stride over int4 groups
     p = (int)blockIdx.x * kWarpsPerBlock + wib;
     if (p < A.n_hub) {
-      ym = A.y_in[p];
-      yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(A, p);
+      ym = G.y[p];
+      yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
       const int beg = A.hub_off[p], end = A.hub_off[p + 1];
       const int4* row = reinterpret_cast<const int4*>(A.ids + beg);
       const int ng = (end - beg) >> 2;
@@ -160,9 +216,9 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       for (; g + 32 < ng; g += 64) {
         const int4 ea = ld_stream_v4(row + g);
         const int4 eb = ld_stream_v4(row + g + 32);
-        visit8<MODE, POS>(ea, eb, A, yi, A.c, fx, fy);
+        visit8<MODE, POS, METRIC>(ea, eb, G, yi, A.c, fx, fy);
       }
-      if (g < ng) visit4<MODE, POS>(ld_stream_v4(row + g), A, yi, A.c, fx, fy);
+      if (g < ng) visit4<MODE, POS, METRIC>(ld_stream_v4(row + g), G, yi, A.c, fx, fy);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -177,8 +233,8 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       p = A.n_hub + s * 32 + lane;
       const bool valid = p < A.M;
       if (valid) {
-        ym = A.y_in[p];
-        yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(A, p);
+        ym = G.y[p];
+        yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
       }
       const int4* base = reinterpret_cast<const int4*>(A.ids + A.slice_off[s]) + lane;
       const int W = A.slice_w[s];
@@ -186,44 +242,59 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       for (; g + 1 < W; g += 2) {
         const int4 ea = ld_stream_v4(base + g * 32);
         const int4 eb = ld_stream_v4(base + (g + 1) * 32);
-        visit8<MODE, POS>(ea, eb, A, yi, A.c, fx, fy);
+        visit8<MODE, POS, METRIC>(ea, eb, G, yi, A.c, fx, fy);
       }
-      if (g < W) visit4<MODE, POS>(ld_stream_v4(base + g * 32), A, yi, A.c, fx, fy);
+      if (g < W) visit4<MODE, POS, METRIC>(ld_stream_v4(base + g * 32), G, yi, A.c, fx, fy);
       own = valid;
     }
   }
 
+  float2* __restrict__ y_out = A.y[cur ^ 1];
+  uint32_t* __restrict__ yh_out = A.yh[cur ^ 1];
+  const float2* __restrict__ v_in = A.v[ADAPT ? cur : 0];
+  float2* __restrict__ v_out = A.v[ADAPT ? (cur ^ 1) : 0];
+  double kin_new = 0.0, kin_old = 0.0;
+
   if (MODE == kMomentum) {
     // Eq. 3.34: v <- a v + b F ; y <- y + v
     if (own) {
-      float2 v = A.s1[p];
-      v.x = fmaf(A.a, v.x, A.b * fx);
-      v.y = fmaf(A.a, v.y, A.b * fy);
-      A.s1[p] = v;
-      const float2 yn = make_float2(ym.x + v.x, ym.y + v.y);
-      A.y_out[p] = yn;
-      if (POS != IVHD_POS_F32) A.yh_out[p] = round_pos<POS>(yn);
+      const float2 v = v_in[p];
+      float2 vn;
+      vn.x = fmaf(A.a, v.x, b * fx);
+      vn.y = fmaf(A.a, v.y, b * fy);
+      v_out[p] = vn;
+      const float2 yn = make_float2(ym.x + vn.x, ym.y + vn.y);
+      y_out[p] = yn;
+      if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
+      if (ADAPT) {
+        kin_new = (double)vn.x * vn.x + (double)vn.y * vn.y;
+        kin_old = (double)v.x * v.x + (double)v.y * v.y;
+      }
     }
   } else if (MODE == kNesterov) {
     // state is the look-ahead point z = y + a v; F was taken at z.
     // v' = a v + b F(z);  y' = y + v';  z' = y' + a v' = z - a v + (1 + a) v'
     if (own) {
-      const float2 v = A.s1[p];
+      const float2 v = v_in[p];
       float2 vn;
-      vn.x = fmaf(A.a, v.x, A.b * fx);
-      vn.y = fmaf(A.a, v.y, A.b * fy);
-      A.s1[p] = vn;
+      vn.x = fmaf(A.a, v.x, b * fx);
+      vn.y = fmaf(A.a, v.y, b * fy);
+      v_out[p] = vn;
       const float ap1 = 1.f + A.a;
       const float2 zn =
           make_float2(ym.x + fmaf(ap1, vn.x, -A.a * v.x), ym.y + fmaf(ap1, vn.y, -A.a * v.y));
-      A.y_out[p] = zn;
-      if (POS != IVHD_POS_F32) A.yh_out[p] = round_pos<POS>(zn);
+      y_out[p] = zn;
+      if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(zn);
+      if (ADAPT) {
+        kin_new = (double)vn.x * vn.x + (double)vn.y * vn.y;
+        kin_old = (double)v.x * v.x + (double)v.y * v.y;
+      }
     }
   } else if (MODE == kAdadelta) {
     // Zeiler's Adadelta on g = -F: E[g^2] <- rho E[g^2] + (1-rho) g^2;
     // dx = -sqrt(E[dx^2] + eps) / sqrt(E[g^2] + eps) g; E[dx^2] <- rho E[dx^2] + (1-rho) dx^2
     if (own) {
-      float2 eg = A.s1[p];
+      float2 eg = v_in[p];
       float2 ex = A.s2[p];
       const float omr = 1.f - A.rho;
       const float gx = -fx, gy = -fy;
@@ -233,26 +304,27 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
       const float dy = -(sqrtf(ex.y + A.eps) / sqrtf(eg.y + A.eps)) * gy;
       ex.x = fmaf(A.rho, ex.x, omr * dx * dx);
       ex.y = fmaf(A.rho, ex.y, omr * dy * dy);
-      A.s1[p] = eg;
+      v_out[p] = eg;
       A.s2[p] = ex;
       const float2 yn = make_float2(ym.x + dx, ym.y + dy);
-      A.y_out[p] = yn;
-      if (POS != IVHD_POS_F32) A.yh_out[p] = round_pos<POS>(yn);
+      y_out[p] = yn;
+      if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
     }
   } else if (MODE == kForces) {
     if (own) A.f_out[A.perm[p]] = make_float2(fx, fy);
   } else if (MODE == kStress) {
     __shared__ double red[kWarpsPerBlock];
-    double v = own ? (double)fx : 0.0;
     if (own && !(isfinite(ym.x) && isfinite(ym.y))) atomicOr(A.flag, 1);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wib] = v;
-    __syncthreads();
+    const double t = block_sum(own ? (double)fx : 0.0, red);
+    if (threadIdx.x == 0) A.partials[blockIdx.x] = t;
+  }
+  if (ADAPT) {
+    __shared__ double red2[kWarpsPerBlock];
+    const double tn = block_sum(kin_new, red2);
+    const double to = block_sum(kin_old, red2);
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kWarpsPerBlock; ++w) t += red[w];
-      A.partials[blockIdx.x] = t;
+      A.partials[2 * blockIdx.x] = tn;
+      A.partials[2 * blockIdx.x + 1] = to;
     }
   }
 }
@@ -264,14 +336,36 @@ __global__ void __launch_bounds__(1024) k_stress_final(const double* __restrict_
   __shared__ double sh[32];
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
+  const double t = block_sum(v, sh);
+  if (threadIdx.x == 0) out[0] = 0.5 * t;
+}
+
+// Self-adaptive b (Sec. 3.3.3): with T = sum |dr|^2 over all particles before
+// (T_old = |v|^2) and after (T_new = |v'|^2) the step, dT = T_new - T_old.
+// When |dT| > tau T_old the step is rejected (positions and velocities stay at
+// step n) and b is scaled by gamma1 > 1 (dT < 0) or gamma2 < 1 (dT > 0);
+// otherwise the step is accepted (the ping-pong buffers flip).
+__global__ void __launch_bounds__(1024) k_adapt(const double* __restrict__ partials, int nblocks,
+                                                float tau, float gamma1, float gamma2,
+                                                AdaptCtl* ctl) {
+  __shared__ double sh[32];
+  double tn = 0.0, to = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    tn += partials[2 * i];
+    to += partials[2 * i + 1];
+  }
+  tn = block_sum(tn, sh);
+  to = block_sum(to, sh);
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    out[0] = 0.5 * t;
+    const double dT = tn - to;
+    if (to > 0.0 && fabs(dT) > (double)tau * to) {
+      ctl->b *= (dT < 0.0) ? gamma1 : gamma2;
+      ctl->rejected += 1;
+    } else {
+      ctl->cur ^= 1;
+      ctl->accepted += 1;
+    }
+    ctl->last_dT = dT;
   }
 }
 
@@ -318,19 +412,47 @@ __global__ void k_set_positions(const float2* __restrict__ in, const int32_t* __
   if (s2) s2[p] = make_float2(0.f, 0.f);
 }
 
-// y0 ~ U(0,1)^2 per input vertex i = perm[p]: coordinate q is the top 24 bits
-// of output q of SplitMix64 seeded with s_i = output i of SplitMix64 seeded
-// with (seed ^ "init_pos"), times 2^-24 (exact in FP32).
-__global__ void k_init_positions(const int32_t* __restrict__ perm, int M, uint64_t seed,
+// y0 ~ U(0,1)^2 per input vertex i = perm[p] in its segment [lo, lo + n) with
+// local index li = i - lo: coordinate q is the top 24 bits of output q of
+// SplitMix64 seeded with s = output li of SplitMix64 seeded with
+// (seed ^ "init_pos"), times 2^-24 (exact in FP32).
+__global__ void k_init_positions(const int32_t* __restrict__ perm, int M, SegTable T,
                                  float2* __restrict__ y, float2* __restrict__ s1,
                                  float2* __restrict__ s2) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= M) return;
-  const uint64_t si = sm64_out(seed ^ kDomainInit, (uint64_t)perm[p]);
+  const int i = perm[p];
+  const int e = T.of ? T.of[i] : 0;
+  const uint64_t si = sm64_out(T.seed[e] ^ kDomainInit, (uint64_t)(i - T.lo[e]));
   const float sc = 1.0f / 16777216.0f;
   y[p] = make_float2((float)(sm64_out(si, 0) >> 40) * sc, (float)(sm64_out(si, 1) >> 40) * sc);
   s1[p] = make_float2(0.f, 0.f);
   if (s2) s2[p] = make_float2(0.f, 0.f);
+}
+
+// Optimiser state in input order (for a rebuild of the layout) and back.
+__global__ void k_to_input_order(const float2* __restrict__ a, const int32_t* __restrict__ perm,
+                                 int M, float2* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < M) out[perm[p]] = a[p];
+}
+__global__ void k_from_input_order(const float2* __restrict__ in, const int32_t* __restrict__ perm,
+                                   int M, float2* __restrict__ a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < M) a[p] = in[perm[p]];
+}
+
+cudaError_t launch_to_input_order(ivhd_ctx* ctx, const float2* a, float2* out) {
+  const int M = (int)ctx->M;
+  k_to_input_order<<<(M + 255) / 256, 256, 0, ctx->stream>>>(a, ctx->perm, M, out);
+  ++ctx->aux_launches;
+  return cudaGetLastError();
+}
+cudaError_t launch_from_input_order(ivhd_ctx* ctx, const float2* in, float2* a) {
+  const int M = (int)ctx->M;
+  k_from_input_order<<<(M + 255) / 256, 256, 0, ctx->stream>>>(in, ctx->perm, M, a);
+  ++ctx->aux_launches;
+  return cudaGetLastError();
 }
 
 static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
@@ -339,12 +461,15 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   A.hub_off = ctx->hub_off;
   A.slice_off = ctx->slice_off;
   A.slice_w = ctx->slice_w;
-  A.y_in = ctx->y[cur];
-  A.y_out = ctx->y[cur ^ 1];
-  A.yh_in = ctx->yh[cur];
-  A.yh_out = ctx->yh[cur ^ 1];
-  A.s1 = ctx->s1;
+  A.y[0] = ctx->y[0];
+  A.y[1] = ctx->y[1];
+  A.yh[0] = ctx->yh[0];
+  A.yh[1] = ctx->yh[1];
+  A.v[0] = ctx->vbuf[0];
+  A.v[1] = ctx->vbuf[1] ? ctx->vbuf[1] : ctx->vbuf[0];
   A.s2 = ctx->s2;
+  A.cur = cur;
+  A.ctl = ctx->ctl;
   A.perm = ctx->perm;
   A.partials = ctx->partials;
   A.flag = ctx->flag;
@@ -366,23 +491,52 @@ int step_grid(const ivhd_ctx* ctx) {
   return (int)(nb_hub + nb_sell);
 }
 
-template <int POS>
-static void launch_opt(int opt, int grid, cudaStream_t s, const StepArgs& A) {
+template <int MODE, int POS, int METRIC, bool ADAPT>
+static void launch1(int grid, cudaStream_t s, const StepArgs& A) {
+  k_step<MODE, POS, METRIC, ADAPT><<<grid, kStepBlock, 0, s>>>(A);
+}
+
+template <int POS, int METRIC>
+static void launch_opt(int opt, bool adapt, int grid, cudaStream_t s, const StepArgs& A) {
   switch (opt) {
-    case IVHD_OPT_NESTEROV: k_step<kNesterov, POS><<<grid, kStepBlock, 0, s>>>(A); break;
-    case IVHD_OPT_ADADELTA: k_step<kAdadelta, POS><<<grid, kStepBlock, 0, s>>>(A); break;
-    default: k_step<kMomentum, POS><<<grid, kStepBlock, 0, s>>>(A); break;
+    case IVHD_OPT_NESTEROV:
+      if (adapt)
+        launch1<kNesterov, POS, METRIC, true>(grid, s, A);
+      else
+        launch1<kNesterov, POS, METRIC, false>(grid, s, A);
+      break;
+    case IVHD_OPT_ADADELTA: launch1<kAdadelta, POS, METRIC, false>(grid, s, A); break;
+    default:
+      if (adapt)
+        launch1<kMomentum, POS, METRIC, true>(grid, s, A);
+      else
+        launch1<kMomentum, POS, METRIC, false>(grid, s, A);
+      break;
   }
 }
 
+template <int METRIC>
+static void launch_pos(const ivhd_ctx* ctx, bool adapt, int grid, cudaStream_t s,
+                       const StepArgs& A) {
+  switch (ctx->p.pos_format) {
+    case IVHD_POS_F16: launch_opt<IVHD_POS_F16, METRIC>(ctx->p.opt, adapt, grid, s, A); break;
+    case IVHD_POS_BF16: launch_opt<IVHD_POS_BF16, METRIC>(ctx->p.opt, adapt, grid, s, A); break;
+    default: launch_opt<IVHD_POS_F32, METRIC>(ctx->p.opt, adapt, grid, s, A); break;
+  }
+}
+
+// One step: the fused kernel, plus the controller kernel with self-adaptive b.
 cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s) {
   const StepArgs A = make_args(ctx, cur);
   const int grid = step_grid(ctx);
-  switch (ctx->p.pos_format) {
-    case IVHD_POS_F16: launch_opt<IVHD_POS_F16>(ctx->p.opt, grid, s, A); break;
-    case IVHD_POS_BF16: launch_opt<IVHD_POS_BF16>(ctx->p.opt, grid, s, A); break;
-    default: launch_opt<IVHD_POS_F32>(ctx->p.opt, grid, s, A); break;
-  }
+  const bool adapt = ctx->p.adaptive != 0;
+  if (ctx->metric == IVHD_METRIC_L1)
+    launch_pos<IVHD_METRIC_L1>(ctx, adapt, grid, s, A);
+  else
+    launch_pos<IVHD_METRIC_L2>(ctx, adapt, grid, s, A);
+  if (adapt)
+    k_adapt<<<1, 1024, 0, s>>>(ctx->partials, grid, ctx->p.tau, ctx->p.gamma1, ctx->p.gamma2,
+                               ctx->ctl);
   return cudaGetLastError();
 }
 
@@ -396,6 +550,8 @@ __global__ void k_lookback(const float2* __restrict__ z, const float2* __restric
   y[p] = make_float2(fmaf(-a, w.x, q.x), fmaf(-a, w.y, q.y));
 }
 
+// Arguments of the forces / stress evaluation at the FP32 positions y[cur]
+// (Nesterov: y = z - a v, written into y[cur ^ 1] and read from there).
 static StepArgs eval_args(ivhd_ctx* ctx) {
   StepArgs A = make_args(ctx, ctx->cur);
   if (ctx->p.opt == IVHD_OPT_NESTEROV) {
@@ -403,16 +559,20 @@ static StepArgs eval_args(ivhd_ctx* ctx) {
     k_lookback<<<(M + 255) / 256, 256, 0, ctx->stream>>>(ctx->y[ctx->cur], ctx->s1, M, ctx->p.a,
                                                          ctx->y[ctx->cur ^ 1]);
     ++ctx->aux_launches;
-    A.y_in = ctx->y[ctx->cur ^ 1];
+    A.cur = ctx->cur ^ 1;
   }
-  A.y_out = nullptr;
   return A;
 }
 
 cudaError_t launch_forces(ivhd_ctx* ctx, float2* out) {
   StepArgs A = eval_args(ctx);
   A.f_out = out;
-  k_step<kForces, IVHD_POS_F32><<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
+  if (ctx->metric == IVHD_METRIC_L1)
+    k_step<kForces, IVHD_POS_F32, IVHD_METRIC_L1, false>
+        <<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
+  else
+    k_step<kForces, IVHD_POS_F32, IVHD_METRIC_L2, false>
+        <<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
   ++ctx->aux_launches;
   return cudaGetLastError();
 }
@@ -422,7 +582,10 @@ cudaError_t launch_stress(ivhd_ctx* ctx) {
   if (e != cudaSuccess) return e;
   StepArgs A = eval_args(ctx);
   const int grid = step_grid(ctx);
-  k_step<kStress, IVHD_POS_F32><<<grid, kStepBlock, 0, ctx->stream>>>(A);
+  if (ctx->metric == IVHD_METRIC_L1)
+    k_step<kStress, IVHD_POS_F32, IVHD_METRIC_L1, false><<<grid, kStepBlock, 0, ctx->stream>>>(A);
+  else
+    k_step<kStress, IVHD_POS_F32, IVHD_METRIC_L2, false><<<grid, kStepBlock, 0, ctx->stream>>>(A);
   k_stress_final<<<1, 1024, 0, ctx->stream>>>(ctx->partials, grid, ctx->red_out);
   ctx->aux_launches += 2;
   return cudaGetLastError();
@@ -448,7 +611,7 @@ cudaError_t launch_set_positions(ivhd_ctx* ctx, const float2* in) {
 
 cudaError_t launch_init_positions(ivhd_ctx* ctx) {
   const int M = (int)ctx->M;
-  k_init_positions<<<(M + 255) / 256, 256, 0, ctx->stream>>>(ctx->perm, M, ctx->p.seed,
+  k_init_positions<<<(M + 255) / 256, 256, 0, ctx->stream>>>(ctx->perm, M, ctx->seg,
                                                              ctx->y[ctx->cur], ctx->s1, ctx->s2);
   ++ctx->aux_launches;
   cudaError_t e = cudaGetLastError();

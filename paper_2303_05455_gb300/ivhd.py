@@ -23,6 +23,7 @@ from ._lib import IvhdError, Info, Params, check
 
 OPTS = {"momentum": 0, "nesterov": 1, "adadelta": 2}
 POS_FORMATS = {"f32": 0, "f16": 1, "bf16": 2}
+METRICS = {"l2": 0, "l1": 1}
 
 
 def _stream_ptr(stream) -> int | None:
@@ -47,7 +48,9 @@ class Embedding:
     def __init__(self, knn, r: int = 1, c: float = 0.01, *, opt: str = "momentum",
                  a: float = 0.9, b: float = 0.01, rho: float = 0.95, eps: float = 1e-6,
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
-                 hub_threshold: int = 0, pos_format: str = "f32", stream=None, device=None):
+                 hub_threshold: int = 0, pos_format: str = "f32", adaptive: bool = False,
+                 tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, stream=None,
+                 device=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -70,6 +73,8 @@ class Embedding:
         p.init_uniform = int(init_uniform)
         p.hub_threshold = int(hub_threshold)
         p.pos_format = POS_FORMATS[pos_format]
+        p.adaptive = int(adaptive)
+        p.tau, p.gamma1, p.gamma2 = tau, gamma1, gamma2
         p.stream = self.stream.cuda_stream or None
         self.opt = opt
         self.params = p
@@ -147,6 +152,36 @@ class Embedding:
         inf = Info()
         check(self._L.ivhd_info(self._h, ctypes.byref(inf)), "ivhd_info")
         return {name: getattr(inf, name) for name, _ in Info._fields_}
+
+    def set_metric(self, metric: str):
+        """'l2' (the method) or 'l1' (the late-stage variant)."""
+        check(self._L.ivhd_set_metric(self._h, METRICS[metric]), "ivhd_set_metric")
+
+    def resample_random_neighbors(self, epoch: int):
+        check(self._L.ivhd_resample_random_neighbors(self._h, epoch & 0xFFFFFFFFFFFFFFFF),
+              "ivhd_resample_random_neighbors")
+
+    def restrict_nn(self, helper=None):
+        """Reverse-neighbour restriction with a helper kNN graph; None restores the graph."""
+        if helper is None:
+            check(self._L.ivhd_restrict_nn(self._h, None, 0, 0), "ivhd_restrict_nn")
+            return
+        if isinstance(helper, np.ndarray):
+            h = np.ascontiguousarray(helper, dtype=np.int32)
+            check(self._L.ivhd_restrict_nn(self._h, h.ctypes.data, h.shape[1], 0),
+                  "ivhd_restrict_nn")
+        else:
+            h = helper.to(dtype=torch.int32).contiguous()
+            check(self._L.ivhd_restrict_nn(self._h, h.data_ptr(), h.shape[1], int(h.is_cuda)),
+                  "ivhd_restrict_nn")
+
+    def adaptive_state(self) -> dict:
+        b = ctypes.c_float()
+        acc = ctypes.c_int64()
+        rej = ctypes.c_int64()
+        check(self._L.ivhd_adaptive_state(self._h, ctypes.byref(b), ctypes.byref(acc),
+                                          ctypes.byref(rej)), "ivhd_adaptive_state")
+        return {"b": b.value, "accepted": acc.value, "rejected": rej.value}
 
     def get_state(self) -> bytes:
         n = ctypes.c_size_t()

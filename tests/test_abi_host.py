@@ -37,11 +37,13 @@ def test_every_declared_symbol_is_exported(L):
 def test_params_struct_layout_and_defaults(L):
     p = _lib.Params()
     L.ivhd_default_params(ctypes.byref(p))
-    assert ctypes.sizeof(_lib.Params) == 56  # C layout: 20 B + pad, seed, 4 x int32, stream
+    assert ctypes.sizeof(_lib.Params) == 72  # C layout: 20 B + pad, seed, 5 x int32, 3 floats, stream
     assert (p.opt, p.init_uniform, p.dedup_mutual, p.hub_threshold) == (0, 1, 0, 0)
     assert p.a == pytest.approx(0.9) and p.b == pytest.approx(0.01)
     assert p.rho == pytest.approx(0.95) and p.eps == pytest.approx(1e-6)
-    assert L.ivhd_version() == (0 << 16) | (1 << 8)
+    assert L.ivhd_version() == (0 << 16) | (2 << 8)
+    assert p.adaptive == 0 and p.tau == pytest.approx(0.5)
+    assert p.gamma1 == pytest.approx(1.1) and p.gamma2 == pytest.approx(0.5)
     for s in (0, -1, -2, -3, -4, -5, -6, -7, 42):
         assert isinstance(L.ivhd_status_string(s), bytes)
 
@@ -75,7 +77,7 @@ def test_create_rejects_bad_sizes(L, M, k, r, c):
 @pytest.mark.parametrize("field,value", [
     ("opt", 3), ("opt", -1), ("a", -0.1), ("a", 1.5), ("a", float("nan")), ("b", 0.0),
     ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
-    ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1),
+    ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1), ("adaptive", 2),
 ])
 def test_create_rejects_bad_params(L, field, value):
     p = _lib.Params()
@@ -121,3 +123,25 @@ def test_knn_build_and_eval_reject_bad_args(L):
     assert L.ivhd_probe_gather(1000, 100, 1, ctypes.byref(out), None) == -1
     assert L.ivhd_probe_gather(1000, 1 << 20, 0, ctypes.byref(out), None) == -1
     assert L.ivhd_probe_gather(1000, 1 << 20, 1, None, None) == -1
+
+
+@pytest.mark.parametrize("opt,field,value", [
+    (2, "adaptive", 1),                      # adaptive b needs momentum or Nesterov
+    (0, "tau", 0.0), (0, "gamma1", 1.0), (0, "gamma2", 1.0), (0, "gamma2", 0.0),
+])
+def test_create_rejects_bad_adaptive_params(L, opt, field, value):
+    p = _lib.Params()
+    L.ivhd_default_params(ctypes.byref(p))
+    p.opt = opt
+    p.adaptive = 1
+    setattr(p, field, value)
+    knn = np.array([[1], [0], [0]], np.int32)
+    st, h = _create(L, knn, 3, 1, 1, 0.1, p)
+    assert st == -1 and not h.value
+
+
+def test_new_entry_points_reject_null(L):
+    assert L.ivhd_set_metric(None, 0) == -1
+    assert L.ivhd_resample_random_neighbors(None, 1) == -1
+    assert L.ivhd_restrict_nn(None, None, 0, 0) == -1
+    assert L.ivhd_adaptive_state(None, None, None, None) == -1

@@ -355,3 +355,101 @@ def test_cf_separated_and_mixed_labels():
     assert oracle.cf(Y, lab, 10) == 1.0
     lab_rand = rng.integers(0, 3, M).astype(np.int32)
     assert abs(oracle.cf(Y, lab_rand, 10) - 1 / 3) < 0.05
+
+
+# ------------------------------------------------- late-stage and paper variants
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_l1_force_is_half_negative_gradient(seed):
+    _, _, t, Y = _random_case(14, 3, 2, seed)
+    c = 0.2
+    F = oracle.forces(Y, t, c, metric="l1")
+    h = 1e-7  # random coordinates: no |u| kink within h of any term
+    G = np.zeros_like(Y)
+    for i in range(t.M):
+        for q in range(2):
+            Yp, Ym = Y.copy(), Y.copy()
+            Yp[i, q] += h
+            Ym[i, q] -= h
+            G[i, q] = (oracle.stress(Yp, t, c, "l1") - oracle.stress(Ym, t, c, "l1")) / (2 * h)
+    assert np.abs(F + 0.5 * G).max() <= 1e-6 * np.abs(F).max()
+
+
+def test_l1_symmetries_and_hand_value():
+    _, _, t, Y = _random_case(40, 3, 1, 6)
+    F = oracle.forces(Y, t, 0.1, metric="l1")
+    assert np.abs(F.sum(axis=0)).max() <= 1e-12 * np.abs(F).sum()
+    E = oracle.stress(Y, t, 0.1, "l1")
+    swap = np.array([[0.0, 1.0], [1.0, 0.0]])       # symmetries of the l1 ball
+    rot90 = np.array([[0.0, -1.0], [1.0, 0.0]])
+    for Q in (swap, rot90, -np.eye(2)):
+        assert oracle.stress(Y @ Q.T + 5.0, t, 0.1, "l1") == pytest.approx(E, rel=1e-12)
+        np.testing.assert_allclose(oracle.forces(Y @ Q.T, t, 0.1, "l1"), F @ Q.T, atol=1e-12)
+    # nn pair at (0,0)-(3,-4): d = 7, E = 49; force on 0 = d * sign(y_1 - y_0) = (7, -7)
+    tt = _terms([(0, 1, 0)], 2)
+    Yp = np.array([[0.0, 0.0], [3.0, -4.0]])
+    assert oracle.stress(Yp, tt, 0.1, "l1") == 49.0
+    np.testing.assert_array_equal(oracle.forces(Yp, tt, 0.1, "l1")[0], [7.0, -7.0])
+
+
+def test_redraw_epoch_is_a_first_draw_with_a_mixed_seed():
+    M, k, r, s = 500, 4, 2, 77
+    knn = synth.random_knn_graph(M, k, 9)
+    rn0, _ = oracle.random_neighbors(knn, r, s)
+    assert np.array_equal(oracle.random_neighbors(knn, r, s, epoch=0)[0], rn0)
+    gamma = 0x9E3779B97F4A7C15
+    for e in (1, 2, 12345):
+        mixed = oracle.splitmix64((e - gamma) % 2 ** 64, 0)   # = mix(e), pinned generator
+        rn_e, _ = oracle.random_neighbors(knn, r, s, epoch=e)
+        assert np.array_equal(rn_e, oracle.random_neighbors(knn, r, s ^ mixed)[0])
+        assert (rn_e != rn0).mean() > 0.9
+
+
+def test_absent_knn_entries():
+    knn = np.array([[1, -1], [0, 2], [-1, -1], [2, 0]], np.int32)
+    rn, _ = oracle.random_neighbors(knn, 1, 3)
+    # vertex 2 has no own nn but is connected to 1 and 3 through their rows
+    assert rn[2, 0] == 0
+    t = oracle.build_terms(knn, np.full((4, 0), -1, np.int32))
+    assert sorted(zip(t.ti.tolist(), t.tj.tolist())) == [(0, 1), (1, 0), (1, 2), (3, 0), (3, 2)]
+
+
+def test_reverse_neighbour_restriction():
+    knn = np.array([[1, 2], [0, 3], [3, 0], [2, 1]], np.int32)
+    helper = np.array([[1, 2, 3], [0, 2, 3], [3, 1, 0], [2, 1, 0]], np.int32)
+    out = oracle.restrict(knn, helper)
+    # (i, j) survives iff i is in helper[j]
+    want = [[j if (j >= 0 and i in helper[j]) else -1 for j in row] for i, row in enumerate(knn)]
+    assert out.tolist() == want
+    assert out.tolist() == [[1, 2], [0, 3], [3, 0], [2, 1]]
+    helper2 = np.array([[1, 3, 3], [0, 0, 0], [3, 3, 3], [2, 2, 2]], np.int32)
+    assert oracle.restrict(knn, helper2).tolist() == [[1, -1], [0, -1], [3, -1], [2, -1]]
+    assert np.array_equal(oracle.restrict(knn, np.tile(np.arange(4), (4, 1)).astype(np.int32)),
+                          knn)
+
+
+def test_adaptive_b_rule_on_a_single_pair():
+    # one nn pair (dedup): relative coordinate s, velocity w; F_0 - F_1 = -2 s
+    knn = np.array([[1], [0]], np.int32)
+    t = oracle.build_terms(knn, np.full((2, 0), -1, np.int32), dedup=True)
+    st = oracle.State.fresh(np.array([[0.0, 0.0], [1.0, 0.0]]))
+    box = [0.1]
+    a, tau, g1, g2 = 0.9, 0.5, 1.1, 0.5
+    assert oracle.step_adaptive(st, t, 0.01, box, a=a, tau=tau, gamma1=g1, gamma2=g2)  # T_old = 0
+    v1 = st.S1.copy()
+    np.testing.assert_allclose(v1, [[0.1, 0.0], [-0.1, 0.0]])
+    # second attempt: F0 = y1 - y0 = 0.8, v' = 0.9 * 0.1 + 0.1 * 0.8 = 0.17 per particle
+    # T_old = 2 * 0.01, T_new = 2 * 0.0289, dT / T_old = 1.89 > tau: rejected, b *= gamma2
+    y_before = st.Y.copy()
+    assert not oracle.step_adaptive(st, t, 0.01, box, a=a, tau=tau, gamma1=g1, gamma2=g2)
+    assert box[0] == pytest.approx(0.05)
+    np.testing.assert_array_equal(st.Y, y_before)
+    np.testing.assert_array_equal(st.S1, v1)
+    # third: v' = 0.09 + 0.05 * 0.8 = 0.13, dT / T_old = 0.69 > 0.5: rejected again -> b = 0.025
+    assert not oracle.step_adaptive(st, t, 0.01, box, a=a, tau=tau, gamma1=g1, gamma2=g2)
+    assert box[0] == pytest.approx(0.025)
+    # fourth: v' = 0.09 + 0.02 = 0.11, dT / T_old = 0.21 < 0.5: accepted
+    assert oracle.step_adaptive(st, t, 0.01, box, a=a, tau=tau, gamma1=g1, gamma2=g2)
+    np.testing.assert_allclose(st.S1[0], [0.11, 0.0])
+    np.testing.assert_allclose(st.Y[0], [0.21, 0.0])
