@@ -207,7 +207,7 @@ def test_invalid_graph_rejected_on_device(bad):
     if bad == "range":
         knn[7, 1] = 50
     elif bad == "negative":
-        knn[7, 1] = -1
+        knn[7, 1] = -2      # -1 is an absent entry, any other negative id is invalid
     elif bad == "self":
         knn[7, 1] = 7
     else:
