@@ -142,6 +142,44 @@ ivhd_status ivhd_create(const int32_t *knn, int64_t M, int32_t k, int32_t r, flo
                         const ivhd_params *p, int32_t knn_on_device, ivhd_ctx **out);
 
 /*
+ * Creates one context holding n_emb independent embeddings (for example
+ * several datasets, seeds or parameter sets of one sweep), so that every step
+ * of all of them is one kernel launch over the concatenated vertices.  The
+ * paper motivates many quick re-embeddings with different parameters
+ * (Sec. 3.4, interactive choice of nn, rn and c).  Embedding e has M_e[e]
+ * vertices, k_e[e] nearest neighbours per row, r_e[e] random neighbours
+ * (drawn inside embedding e only) and seed seed_e[e]; c and all parameters in
+ * p are shared.  Random neighbours and initial positions of embedding e are
+ * exactly those ivhd_create would draw for it alone with seed_e[e].
+ *
+ *   knn   the rows of all embeddings concatenated in order: M_e[e] rows of
+ *         k_e[e] local ids in [0, M_e[e]) (-1 = absent) for e = 0..n_emb-1;
+ *         host or device per knn_on_device.
+ *   M_e, k_e, r_e, seed_e   host arrays of n_emb entries.
+ * Positions, forces and the other per-vertex calls use the concatenated
+ * vertex order (embedding 0 first).  ivhd_stress sums all embeddings.
+ * Constraints: 1 <= n_emb <= 2^20, each M_e >= 2, 1 <= k_e <= M_e - 1,
+ * r_e >= 0, sum of M_e < 2^30.  Synchronises.  Errors as ivhd_create.
+ */
+ivhd_status ivhd_create_batch(const int32_t *knn, const int64_t *M_e, const int32_t *k_e,
+                              const int32_t *r_e, const uint64_t *seed_e, int32_t n_emb,
+                              float c, const ivhd_params *p, int32_t knn_on_device,
+                              ivhd_ctx **out);
+
+/*
+ * Launch-shape autotuner: times trial_steps steps for every pair of threads
+ * per block (128, 256, 512) and hub threshold (32, 64, 128, 256, 512: the
+ * degree from which a vertex gets a whole warp instead of one lane), starting
+ * each trial from the same state, then keeps the fastest pair and restores the
+ * state, so the embedding continues exactly as before the call (with the new
+ * layout's summation order).  Outputs (host, may be NULL): the chosen block
+ * size, hub threshold and microseconds per step.  Synchronises.
+ * Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA, IVHD_ERR_OOM, IVHD_ERR_STATE.
+ */
+ivhd_status ivhd_autotune(ivhd_ctx *ctx, int32_t trial_steps, int32_t *best_block,
+                          int32_t *best_hub_threshold, float *best_us_per_step);
+
+/*
  * Overwrites the positions with xy (M*2 float32, row-major, vertex order of
  * the input graph) and zeroes the optimiser state.  on_device selects the
  * memory space of xy.  Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA, IVHD_ERR_STATE.

@@ -23,7 +23,7 @@ SYMBOLS = (
     "ivhd_get_state", "ivhd_set_state", "ivhd_destroy", "ivhd_status_string", "ivhd_version",
     "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
     "ivhd_probe_gather", "ivhd_set_metric", "ivhd_resample_random_neighbors",
-    "ivhd_restrict_nn", "ivhd_adaptive_state",
+    "ivhd_restrict_nn", "ivhd_adaptive_state", "ivhd_create_batch", "ivhd_autotune",
 )
 
 
@@ -121,6 +121,12 @@ def load(build_if_missing: bool = False):
     L.ivhd_adaptive_state.argtypes = [P, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.ivhd_adaptive_state.restype = i32
+    L.ivhd_create_batch.argtypes = [P, P, P, P, P, i32, ctypes.c_float, ctypes.POINTER(Params),
+                                    i32, ctypes.POINTER(P)]
+    L.ivhd_create_batch.restype = i32
+    L.ivhd_autotune.argtypes = [P, i32, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+    L.ivhd_autotune.restype = i32
     _lib = L
     return L
 

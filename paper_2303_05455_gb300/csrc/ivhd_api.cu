@@ -179,14 +179,18 @@ __global__ void k_restrict(const int32_t* __restrict__ knn, const int32_t* __res
   const int64_t i = e / k;
   const int32_t j = knn[e];
   int32_t keep = -1;
-  if (j >= 0) {
-    for (int t = 0; t < kh; ++t) {
-      const int32_t h = helper[(int64_t)j * kh + t];
-      if (h < -1 || (int64_t)h >= M) atomicOr(err, 1);
-      if (h == (int32_t)i) keep = j;
-    }
+  if (j >= 0 && !*err) {
+    for (int t = 0; t < kh; ++t)
+      if (helper[(int64_t)j * kh + t] == (int32_t)i) keep = j;
   }
   out[e] = keep;
+}
+
+// Every helper id must be -1 or a vertex.
+__global__ void k_check_ids(const int32_t* __restrict__ a, int64_t n, int64_t M,
+                            int32_t* __restrict__ err) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n && (a[e] < -1 || (int64_t)a[e] >= M)) atomicOr(err, 1);
 }
 
 }  // namespace
@@ -570,10 +574,11 @@ ivhd_status ivhd_restrict_nn(ivhd_ctx* ctx, const int32_t* helper, int32_t k_hel
   if (e == cudaSuccess) e = dalloc(&err, 1, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
   if (e == cudaSuccess) {
-    const int64_t n = M * k;
+    const int64_t nh = M * k_helper, n = M * k;
+    k_check_ids<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(hsrc, nh, M, err);
     k_restrict<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->knn_full, hsrc, M, k, k_helper,
                                                           ctx->knn, err);
-    ++ctx->aux_launches;
+    ctx->aux_launches += 2;
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
@@ -674,3 +679,245 @@ ivhd_status ivhd_set_state(ivhd_ctx* ctx, const void* buf, size_t bytes) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Many independent embeddings in one context, and the launch-shape autotuner.
+
+namespace {
+
+// seg_of[g] = the embedding that owns global vertex g (binary search over lo).
+__global__ void k_seg_of(const int64_t* __restrict__ lo, int n_seg, int64_t M,
+                         int32_t* __restrict__ of) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= M) return;
+  int a = 0, b = n_seg - 1;
+  while (a < b) {
+    const int m = (a + b + 1) >> 1;
+    if (lo[m] <= g) a = m; else b = m - 1;
+  }
+  of[g] = a;
+}
+
+// Local kNN rows (k_e ids in [0, M_e), -1 absent) -> global rows of k_max ids.
+__global__ void k_globalize(const int32_t* __restrict__ local, const int64_t* __restrict__ row0,
+                            const int64_t* __restrict__ lo, const int64_t* __restrict__ n,
+                            const int32_t* __restrict__ ke, const int32_t* __restrict__ of,
+                            int64_t M, int k_max, int32_t* __restrict__ knn,
+                            int32_t* __restrict__ err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= M) return;
+  const int e = of[g];
+  const int64_t i = g - lo[e];
+  const int k = ke[e];
+  for (int s = 0; s < k_max; ++s) {
+    int32_t v = -1;
+    if (s < k) {
+      v = local[row0[e] + i * k + s];
+      if (v < -1 || (int64_t)v >= n[e]) {
+        atomicOr(err, 1);
+        v = -1;
+      }
+    }
+    knn[g * k_max + s] = v >= 0 ? (int32_t)(lo[e] + v) : -1;
+  }
+}
+
+}  // namespace
+
+extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
+                                         const int32_t* k_e, const int32_t* r_e,
+                                         const uint64_t* seed_e, int32_t n_emb, float c,
+                                         const ivhd_params* p_in, int32_t knn_on_device,
+                                         ivhd_ctx** out) {
+  if (!out) return IVHD_ERR_ARG;
+  *out = nullptr;
+  if (!knn || !M_e || !k_e || !r_e || !seed_e || n_emb < 1 || n_emb > (1 << 20))
+    return IVHD_ERR_ARG;
+  if (!std::isfinite(c) || c <= 0.f) return IVHD_ERR_ARG;
+  std::vector<int64_t> lo(n_emb), row0(n_emb), n(M_e, M_e + n_emb);
+  int64_t M = 0, entries = 0;
+  int k_max = 0, r_max = 0;
+  for (int e = 0; e < n_emb; ++e) {
+    if (M_e[e] < 2 || k_e[e] < 1 || (int64_t)k_e[e] > M_e[e] - 1 || r_e[e] < 0) return IVHD_ERR_ARG;
+    lo[e] = M;
+    row0[e] = entries;
+    M += M_e[e];
+    entries += M_e[e] * k_e[e];
+    k_max = k_e[e] > k_max ? k_e[e] : k_max;
+    r_max = r_e[e] > r_max ? r_e[e] : r_max;
+    if (M >= kMaxVertices) return IVHD_ERR_ARG;
+  }
+  if (M * (int64_t)(k_max + r_max) * 2 >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
+  ivhd_params p;
+  if (p_in)
+    p = *p_in;
+  else
+    ivhd_default_params(&p);
+  if (!params_ok(p)) return IVHD_ERR_ARG;
+
+  ivhd_ctx* ctx = new (std::nothrow) ivhd_ctx();
+  if (!ctx) return IVHD_ERR_OOM;
+  ctx->p = p;
+  ctx->M = M;
+  ctx->k = k_max;
+  ctx->r = r_max;
+  ctx->c = c;
+  ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : kDefaultHubThreshold;
+  ctx->stream = (cudaStream_t)p.stream;
+  cudaGetDevice(&ctx->device);
+  cudaStream_t s = ctx->stream;
+  ctx->n_seg = n_emb;
+
+  cudaError_t e = alloc_state(ctx);
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  int32_t* local = nullptr;
+  int64_t* row0_d = nullptr;
+  int32_t* err = nullptr;
+  int32_t herr = 0;
+  chk(dalloc(&ctx->knn, M * k_max, s));
+  chk(dalloc(&ctx->seg_of, M, s));
+  chk(dalloc(&ctx->seg_lo, n_emb, s));
+  chk(dalloc(&ctx->seg_n, n_emb, s));
+  chk(dalloc(&ctx->seg_r, n_emb, s));
+  chk(dalloc(&ctx->seg_seed, n_emb, s));
+  chk(dalloc(&row0_d, n_emb, s));
+  chk(dalloc(&err, 1, s));
+  if (!knn_on_device) chk(dalloc(&local, entries, s));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(ctx->seg_lo, lo.data(), n_emb * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->seg_n, n.data(), n_emb * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->seg_r, r_e, n_emb * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(ctx->seg_seed, seed_e, n_emb * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(row0_d, row0.data(), n_emb * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    chk(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    if (!knn_on_device)
+      chk(cudaMemcpyAsync(local, knn, (size_t)entries * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  int32_t* kd = nullptr;  // per-embedding k
+  chk(dalloc(&kd, n_emb, s));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(kd, k_e, n_emb * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const unsigned g = (unsigned)((M + 255) / 256);
+    k_seg_of<<<g, 256, 0, s>>>(ctx->seg_lo, n_emb, M, ctx->seg_of);
+    k_globalize<<<g, 256, 0, s>>>(knn_on_device ? knn : local, row0_d, ctx->seg_lo, ctx->seg_n, kd,
+                                  ctx->seg_of, M, k_max, ctx->knn, err);
+    ctx->setup_launches += 2;
+    chk(cudaGetLastError());
+    chk(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    chk(cudaStreamSynchronize(s));
+  }
+  if (local) cudaFreeAsync(local, s);
+  if (row0_d) cudaFreeAsync(row0_d, s);
+  if (err) cudaFreeAsync(err, s);
+  if (kd) cudaFreeAsync(kd, s);
+  if (e != cudaSuccess || herr) {
+    ivhd_status st = herr ? IVHD_ERR_INDEX : cuda_status(e);
+    free_ctx(ctx);
+    return st;
+  }
+  ctx->seg = SegTable{ctx->seg_of, ctx->seg_lo, ctx->seg_n, ctx->seg_r, ctx->seg_seed};
+  return finish_create(ctx, out);
+}
+
+extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t* best_block,
+                                     int32_t* best_hub_threshold, float* best_us_per_step) {
+  if (!ctx || trial_steps < 1) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  cudaError_t e = sync_cur(ctx);
+  if (e != cudaSuccess) return fail(ctx, e);
+  // the state in input order (layouts change between candidates) and the controller
+  float2* save[3] = {nullptr, nullptr, nullptr};
+  const int n = ctx->s2 ? 3 : 2;
+  AdaptCtl ctl_save{};
+  for (int q = 0; q < n && e == cudaSuccess; ++q) {
+    e = dalloc(&save[q], M, s);
+    float2* src = q == 0 ? ctx->y[ctx->cur] : (q == 1 ? ctx->s1 : ctx->s2);
+    if (e == cudaSuccess) e = launch_to_input_order(ctx, src, save[q]);
+  }
+  if (e == cudaSuccess && ctx->ctl)
+    e = cudaMemcpyAsync(&ctl_save, ctx->ctl, sizeof(ctl_save), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t x = cudaSuccess;
+    if (ctx->ctl) {
+      x = cudaMemcpyAsync(ctx->ctl, &ctl_save, sizeof(ctl_save), cudaMemcpyHostToDevice, s);
+      if (x == cudaSuccess) x = cudaStreamSynchronize(s);
+      if (x == cudaSuccess) x = sync_cur(ctx);
+    }
+    for (int q = 0; q < n && x == cudaSuccess; ++q) {
+      float2* dst = q == 0 ? ctx->y[ctx->cur] : (q == 1 ? ctx->s1 : ctx->s2);
+      x = launch_from_input_order(ctx, save[q], dst);
+    }
+    if (x == cudaSuccess) x = launch_round_positions(ctx);
+    return x;
+  };
+  const int blocks[3] = {128, 256, 512};
+  const int hubs[5] = {32, 64, 128, 256, 512};
+  float best = 1e30f;
+  int bb = ctx->block, bh = ctx->hub_threshold;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  ivhd_status st = IVHD_OK;
+  const int64_t steps_before = ctx->steps_done;
+  for (int hi = 0; hi < 5 && e == cudaSuccess && st == IVHD_OK; ++hi) {
+    ctx->hub_threshold = hubs[hi];
+    drop_graphs(ctx);
+    free_layout(ctx);
+    st = build_layout(ctx, false, 0);
+    for (int bi = 0; bi < 3 && e == cudaSuccess && st == IVHD_OK; ++bi) {
+      ctx->block = blocks[bi];
+      if (ctx->partials) cudaFreeAsync(ctx->partials, s);
+      ctx->partials = nullptr;
+      e = alloc_partials(ctx);
+      if (e == cudaSuccess) e = restore();
+      if (e == cudaSuccess) e = launch_step(ctx, ctx->ctl ? 0 : ctx->cur, s);  // warm-up
+      if (e == cudaSuccess && !ctx->ctl) ctx->cur ^= 1;
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int t = 0; t < trial_steps && e == cudaSuccess; ++t) {
+        e = launch_step(ctx, ctx->cur, s);
+        if (!ctx->ctl) ctx->cur ^= 1;
+        ctx->launches += ctx->ctl ? 2 : 1;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      const float us = 1e3f * ms / trial_steps;
+      if (e == cudaSuccess && us < best) {
+        best = us;
+        bb = blocks[bi];
+        bh = hubs[hi];
+      }
+    }
+  }
+  // settle on the winner with the original state
+  if (e == cudaSuccess && st == IVHD_OK) {
+    ctx->hub_threshold = bh;
+    ctx->block = bb;
+    drop_graphs(ctx);
+    free_layout(ctx);
+    st = build_layout(ctx, false, 0);
+    if (st == IVHD_OK) e = alloc_partials(ctx);
+    if (st == IVHD_OK && e == cudaSuccess) e = restore();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  ctx->steps_done = steps_before;
+  for (int q = 0; q < n; ++q)
+    if (save[q]) cudaFreeAsync(save[q], s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(ctx, e);
+  if (st != IVHD_OK) {
+    ctx->poisoned = true;
+    return st;
+  }
+  if (best_block) *best_block = bb;
+  if (best_hub_threshold) *best_hub_threshold = bh;
+  if (best_us_per_step) *best_us_per_step = best;
+  return IVHD_OK;
+}

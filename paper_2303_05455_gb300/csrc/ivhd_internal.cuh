@@ -35,8 +35,8 @@ constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
 constexpr uint32_t kPad = 0xFFFFFFFFu;
 constexpr int64_t kMaxVertices = (int64_t)1 << 30;
 constexpr int kDefaultHubThreshold = 128;
-constexpr int kStepBlock = 256;  // 8 warps
-constexpr int kWarpsPerBlock = kStepBlock / 32;
+constexpr int kStepBlock = 256;      // default threads per step block (8 warps)
+constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
 
 enum Mode { kMomentum = 0, kNesterov = 1, kAdadelta = 2, kForces = 3, kStress = 4 };
 
@@ -104,7 +104,7 @@ struct StepArgs {
   float2* __restrict__ f_out;        // forces mode output
   double* __restrict__ partials;     // stress: one double per block; adaptive: two
   int32_t* __restrict__ flag;        // stress mode: non-finite flag
-  int32_t M, n_hub, n_slices, nb_hub;
+  int32_t M, n_hub, n_slices, nb_hub, wpb;
   float c, a, b, rho, eps;
 };
 
@@ -119,6 +119,7 @@ struct ivhd_ctx {
   int32_t k = 0, r = 0;
   float c = 0.f;
   int hub_threshold = ivhd::kDefaultHubThreshold;
+  int block = ivhd::kStepBlock;
   bool poisoned = false;
 
   // segments (independent embeddings) and their device tables

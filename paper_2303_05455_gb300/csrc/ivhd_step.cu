@@ -191,7 +191,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // position in the gathered format (differences are taken between equally
 // rounded positions); ym is its FP32 master position.
 template <int MODE, int POS, int METRIC, bool ADAPT>
-__global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
+__global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int cur = ADAPT ? A.ctl->cur : A.cur;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
 
   if ((int)blockIdx.x < A.nb_hub) {
     // hub rows: one warp per vertex, lanes stride over int4 groups
-    p = (int)blockIdx.x * kWarpsPerBlock + wib;
+    p = (int)blockIdx.x * A.wpb + wib;
     if (p < A.n_hub) {
       ym = G.y[p];
       yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
     }
   } else {
     // SELL slice: one thread per vertex, one coalesced int4 per 4 neighbours
-    const int s = ((int)blockIdx.x - A.nb_hub) * kWarpsPerBlock + wib;
+    const int s = ((int)blockIdx.x - A.nb_hub) * A.wpb + wib;
     if (s < A.n_slices) {
       p = A.n_hub + s * 32 + lane;
       const bool valid = p < A.M;
@@ -313,13 +313,13 @@ __global__ void __launch_bounds__(kStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const
   } else if (MODE == kForces) {
     if (own) A.f_out[A.perm[p]] = make_float2(fx, fy);
   } else if (MODE == kStress) {
-    __shared__ double red[kWarpsPerBlock];
+    __shared__ double red[kMaxStepBlock / 32];
     if (own && !(isfinite(ym.x) && isfinite(ym.y))) atomicOr(A.flag, 1);
     const double t = block_sum(own ? (double)fx : 0.0, red);
     if (threadIdx.x == 0) A.partials[blockIdx.x] = t;
   }
   if (ADAPT) {
-    __shared__ double red2[kWarpsPerBlock];
+    __shared__ double red2[kMaxStepBlock / 32];
     const double tn = block_sum(kin_new, red2);
     const double to = block_sum(kin_old, red2);
     if (threadIdx.x == 0) {
@@ -476,7 +476,8 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   A.M = (int32_t)ctx->M;
   A.n_hub = (int32_t)ctx->n_hub;
   A.n_slices = (int32_t)ctx->n_slices;
-  A.nb_hub = (int32_t)((ctx->n_hub + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  A.wpb = ctx->block / 32;
+  A.nb_hub = (int32_t)((ctx->n_hub + A.wpb - 1) / A.wpb);
   A.c = ctx->c;
   A.a = ctx->p.a;
   A.b = ctx->p.b;
@@ -486,14 +487,15 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
 }
 
 int step_grid(const ivhd_ctx* ctx) {
-  const int64_t nb_hub = (ctx->n_hub + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const int64_t nb_sell = (ctx->n_slices + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int wpb = ctx->block / 32;
+  const int64_t nb_hub = (ctx->n_hub + wpb - 1) / wpb;
+  const int64_t nb_sell = (ctx->n_slices + wpb - 1) / wpb;
   return (int)(nb_hub + nb_sell);
 }
 
 template <int MODE, int POS, int METRIC, bool ADAPT>
 static void launch1(int grid, cudaStream_t s, const StepArgs& A) {
-  k_step<MODE, POS, METRIC, ADAPT><<<grid, kStepBlock, 0, s>>>(A);
+  k_step<MODE, POS, METRIC, ADAPT><<<grid, A.wpb * 32, 0, s>>>(A);
 }
 
 template <int POS, int METRIC>
@@ -569,10 +571,10 @@ cudaError_t launch_forces(ivhd_ctx* ctx, float2* out) {
   A.f_out = out;
   if (ctx->metric == IVHD_METRIC_L1)
     k_step<kForces, IVHD_POS_F32, IVHD_METRIC_L1, false>
-        <<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
+        <<<step_grid(ctx), ctx->block, 0, ctx->stream>>>(A);
   else
     k_step<kForces, IVHD_POS_F32, IVHD_METRIC_L2, false>
-        <<<step_grid(ctx), kStepBlock, 0, ctx->stream>>>(A);
+        <<<step_grid(ctx), ctx->block, 0, ctx->stream>>>(A);
   ++ctx->aux_launches;
   return cudaGetLastError();
 }
@@ -583,9 +585,9 @@ cudaError_t launch_stress(ivhd_ctx* ctx) {
   StepArgs A = eval_args(ctx);
   const int grid = step_grid(ctx);
   if (ctx->metric == IVHD_METRIC_L1)
-    k_step<kStress, IVHD_POS_F32, IVHD_METRIC_L1, false><<<grid, kStepBlock, 0, ctx->stream>>>(A);
+    k_step<kStress, IVHD_POS_F32, IVHD_METRIC_L1, false><<<grid, ctx->block, 0, ctx->stream>>>(A);
   else
-    k_step<kStress, IVHD_POS_F32, IVHD_METRIC_L2, false><<<grid, kStepBlock, 0, ctx->stream>>>(A);
+    k_step<kStress, IVHD_POS_F32, IVHD_METRIC_L2, false><<<grid, ctx->block, 0, ctx->stream>>>(A);
   k_stress_final<<<1, 1024, 0, ctx->stream>>>(ctx->partials, grid, ctx->red_out);
   ctx->aux_launches += 2;
   return cudaGetLastError();

@@ -50,7 +50,7 @@ class Embedding:
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
                  hub_threshold: int = 0, pos_format: str = "f32", adaptive: bool = False,
                  tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, stream=None,
-                 device=None):
+                 device=None, batch=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -60,9 +60,10 @@ class Embedding:
             knn_t = torch.from_numpy(np.ascontiguousarray(knn, dtype=np.int32))
         else:
             knn_t = knn.to(dtype=torch.int32).contiguous()
-        if knn_t.dim() != 2:
-            raise ValueError("knn must be [M, k]")
-        self.M, self.k = int(knn_t.shape[0]), int(knn_t.shape[1])
+        if batch is None:
+            if knn_t.dim() != 2:
+                raise ValueError("knn must be [M, k]")
+            self.M, self.k = int(knn_t.shape[0]), int(knn_t.shape[1])
         self.r, self.c = int(r), float(c)
         p = Params()
         self._L.ivhd_default_params(ctypes.byref(p))
@@ -80,8 +81,20 @@ class Embedding:
         self.params = p
         h = ctypes.c_void_p()
         on_dev = int(knn_t.is_cuda)
-        check(self._L.ivhd_create(knn_t.data_ptr(), self.M, self.k, self.r, self.c,
-                                  ctypes.byref(p), on_dev, ctypes.byref(h)), "ivhd_create")
+        if batch is None:
+            check(self._L.ivhd_create(knn_t.data_ptr(), self.M, self.k, self.r, self.c,
+                                      ctypes.byref(p), on_dev, ctypes.byref(h)), "ivhd_create")
+        else:
+            Ms = np.ascontiguousarray(batch["M"], dtype=np.int64)
+            ks = np.ascontiguousarray(batch["k"], dtype=np.int32)
+            rs = np.ascontiguousarray(batch["r"], dtype=np.int32)
+            seeds = np.ascontiguousarray(np.asarray(batch["seed"], dtype=np.uint64))
+            self.M, self.k, self.r = int(Ms.sum()), int(ks.max()), int(rs.max())
+            self.sizes = Ms
+            check(self._L.ivhd_create_batch(knn_t.data_ptr(), Ms.ctypes.data, ks.ctypes.data,
+                                            rs.ctypes.data, seeds.ctypes.data, len(Ms), self.c,
+                                            ctypes.byref(p), on_dev, ctypes.byref(h)),
+                  "ivhd_create_batch")
         self._h = h
 
     # -- lifetime ---------------------------------------------------------
@@ -174,6 +187,28 @@ class Embedding:
             h = helper.to(dtype=torch.int32).contiguous()
             check(self._L.ivhd_restrict_nn(self._h, h.data_ptr(), h.shape[1], int(h.is_cuda)),
                   "ivhd_restrict_nn")
+
+    @classmethod
+    def batch(cls, graphs, r, seeds, c: float = 0.01, **kw):
+        """One context for several independent embeddings.
+
+        graphs: list of int32 [M_e, k_e] local kNN rows; r, seeds: per-embedding
+        lists (or scalars).  Positions come back concatenated in list order."""
+        n = len(graphs)
+        rs = list(r) if np.ndim(r) else [int(r)] * n
+        sd = list(seeds) if np.ndim(seeds) else [int(seeds) + e for e in range(n)]
+        flat = np.concatenate([np.ascontiguousarray(g, dtype=np.int32).ravel() for g in graphs])
+        meta = {"M": [g.shape[0] for g in graphs], "k": [g.shape[1] for g in graphs], "r": rs,
+                "seed": sd}
+        return cls(flat, r=max(rs), c=c, batch=meta, **kw)
+
+    def autotune(self, trial_steps: int = 20) -> dict:
+        bb = ctypes.c_int32()
+        bh = ctypes.c_int32()
+        us = ctypes.c_float()
+        check(self._L.ivhd_autotune(self._h, int(trial_steps), ctypes.byref(bb), ctypes.byref(bh),
+                                    ctypes.byref(us)), "ivhd_autotune")
+        return {"block": bb.value, "hub_threshold": bh.value, "us_per_step": us.value}
 
     def adaptive_state(self) -> dict:
         b = ctypes.c_float()

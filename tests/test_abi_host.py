@@ -145,3 +145,14 @@ def test_new_entry_points_reject_null(L):
     assert L.ivhd_resample_random_neighbors(None, 1) == -1
     assert L.ivhd_restrict_nn(None, None, 0, 0) == -1
     assert L.ivhd_adaptive_state(None, None, None, None) == -1
+    assert L.ivhd_autotune(None, 5, None, None, None) == -1
+    h = ctypes.c_void_p()
+    M = np.array([10, 1], np.int64)           # an embedding with a single vertex
+    k = np.array([2, 1], np.int32)
+    r = np.array([1, 1], np.int32)
+    sd = np.array([0, 0], np.uint64)
+    knn = np.zeros(21, np.int32)
+    assert L.ivhd_create_batch(knn.ctypes.data, M.ctypes.data, k.ctypes.data, r.ctypes.data,
+                               sd.ctypes.data, 2, 0.1, None, 0, ctypes.byref(h)) == -1
+    assert L.ivhd_create_batch(knn.ctypes.data, M.ctypes.data, k.ctypes.data, r.ctypes.data,
+                               sd.ctypes.data, 0, 0.1, None, 0, ctypes.byref(h)) == -1
