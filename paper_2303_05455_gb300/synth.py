@@ -177,3 +177,19 @@ def sample_rows(M: int, n: int, seed: int) -> np.ndarray:
         return np.arange(M, dtype=np.int64)
     rng = _rng(seed)
     return np.sort(rng.choice(M, size=n, replace=False)).astype(np.int64)
+
+
+def batch_workload(seed: int = 64, n_emb: int = 64, m_lo: int = 5000, m_hi: int = 200000):
+    """Many independent embeddings of uneven size: M log-uniform in [m_lo, m_hi],
+    N = 64 Gaussian mixtures with 5-30 equal components, k in {2, 3, 5, 10},
+    r in {1, 2}.  Returns a list of dicts with X, labels, k, r, seed."""
+    rng = _rng(seed)
+    out = []
+    for e in range(n_emb):
+        M = int(round(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi)))))
+        comps = int(rng.integers(5, 31))
+        k = int(rng.choice([2, 3, 5, 10]))
+        r = int(rng.choice([1, 2]))
+        X, labels = gaussian_mixture(M, 64, comps, seed * 1000 + e)
+        out.append({"X": X, "labels": labels, "k": k, "r": r, "seed": seed * 1000 + e})
+    return out
