@@ -197,7 +197,12 @@ class Embedding:
         n = len(graphs)
         rs = list(r) if np.ndim(r) else [int(r)] * n
         sd = list(seeds) if np.ndim(seeds) else [int(seeds) + e for e in range(n)]
-        flat = np.concatenate([np.ascontiguousarray(g, dtype=np.int32).ravel() for g in graphs])
+        if all(isinstance(g, torch.Tensor) and g.is_cuda for g in graphs):
+            flat = torch.cat([g.to(torch.int32).reshape(-1) for g in graphs])
+        else:
+            flat = np.concatenate([np.ascontiguousarray(
+                g.cpu().numpy() if isinstance(g, torch.Tensor) else g, dtype=np.int32).ravel()
+                for g in graphs])
         meta = {"M": [g.shape[0] for g in graphs], "k": [g.shape[1] for g in graphs], "r": rs,
                 "seed": sd}
         return cls(flat, r=max(rs), c=c, batch=meta, **kw)

@@ -37,6 +37,7 @@ def main():
     out = {"workload": w.name, "n_iter": w.n_iter, "every": args.every, "curves": {}}
     for name, kw in runs.items():
         emb = ivhd.Embedding(knn, r=w.r, c=w.c, a=w.a, b=w.b, seed=w.seed, **kw)
+        info = emb.info()
         curve = [emb.stress()]
         done = 0
         while done < w.n_iter:
@@ -57,7 +58,7 @@ def main():
         emb.set_metric("l2")
         y = emb.positions()
         rec = {"stress": curve, "qnx": ivhd.eval_qnx(y, knn, rows),
-               "cf10": ivhd.eval_cf(y, labels, 10, rows)}
+               "cf10": ivhd.eval_cf(y, labels, 10, rows), "max_degree": info["max_degree"]}
         if kw.get("adaptive"):
             rec["adaptive"] = emb.adaptive_state()
         out["curves"][name] = rec
