@@ -363,6 +363,18 @@ ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers, int32_t re
                               double *gathers_per_s, void *stream);
 
 /*
+ * C = A B^T on the tensor cores (tcgen05, TMA-fed, FP32 accumulation): A is
+ * M x K and B is N x K, both BF16 row-major (device), C is M x N FP32
+ * row-major (device).  The building block of the dense layers of the learned
+ * warm start (an MLP mapping features to 2-D positions).  Constraints:
+ * K % 8 == 0, all pointers 16-byte aligned, dimensions < 2^30.  Synchronises.
+ * Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA, IVHD_ERR_TIMEOUT (a bounded
+ * device-side wait expired; the kernel returned without a result).
+ */
+ivhd_status ivhd_gemm_bf16_tn(const void *A, const void *B, float *C, int64_t M, int64_t N,
+                              int64_t K, void *stream);
+
+/*
  * ivhd_eval_qnx_static -- ivhd_eval_qnx that allocates no device memory.
  *
  * The paper has no counterpart: this entry point exists for host

@@ -24,6 +24,7 @@ SYMBOLS = (
     "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
     "ivhd_probe_gather", "ivhd_set_metric", "ivhd_resample_random_neighbors",
     "ivhd_restrict_nn", "ivhd_adaptive_state", "ivhd_create_batch", "ivhd_autotune",
+    "ivhd_gemm_bf16_tn",
 )
 
 
@@ -127,6 +128,8 @@ def load(build_if_missing: bool = False):
     L.ivhd_autotune.argtypes = [P, i32, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
     L.ivhd_autotune.restype = i32
+    L.ivhd_gemm_bf16_tn.argtypes = [P, P, P, i64, i64, i64, P]
+    L.ivhd_gemm_bf16_tn.restype = i32
     _lib = L
     return L
 

@@ -8,10 +8,10 @@ c = 0.01, a = 0.9, b = 0.001, 1,000 momentum steps each.  The kNN graphs are
 built on the GPU before anything is timed.  Timed, with CUDA events:
 
 * one-by-one: for each embedding ivhd_create + 1,000 steps + positions, FP32;
-* batched: one ivhd_create_batch with BF16 gathered positions + 1,000 steps
-  (one launch per step for all embeddings) + positions, after the
-  launch-shape autotuner picked block size and hub threshold (autotune time
-  reported separately).
+* batched: one ivhd_create_batch + the launch-shape autotuner (block size and
+  hub threshold) + 1,000 steps (one launch per step for all embeddings) +
+  positions, for BF16, FP16 and FP32 gathered positions; the same without the
+  autotuner is reported beside it.
 
 Prints one JSON line with both throughputs (edge-updates/s), the speed-up and
 the kNN precision Q_NX(k) of every embedding under both runs.
@@ -33,7 +33,7 @@ def main():
     ap.add_argument("--n-emb", type=int, default=64)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--qnx-rows", type=int, default=2000)
-    ap.add_argument("--pos-format", default="bf16")
+    ap.add_argument("--formats", default="bf16,f16,f32")
     args = ap.parse_args()
     c, a, b = 0.01, 0.9, 0.001
     work = synth.batch_workload(n_emb=args.n_emb)
@@ -66,52 +66,60 @@ def main():
     one_by_one()  # warm-up (module load, graph instantiation paths)
     (pos1, terms), t_one = timed(one_by_one)
 
-    # batched, autotuned
-    def create():
-        return ivhd.Embedding.batch([g for g in graphs], r=[w["r"] for w in work],
-                                    seeds=[w["seed"] for w in work], c=c, a=a, b=b,
-                                    pos_format=args.pos_format)
-
-    emb0 = create()
-    t = time.perf_counter()
-    tuned = emb0.autotune(trial_steps=20)
-    tune_s = time.perf_counter() - t
-    emb0.close()
-
-    def batched():
-        emb = create()
-        if tuned["block"] != 256 or tuned["hub_threshold"] != 128:
-            emb.autotune(trial_steps=20)
-        emb.step(args.steps)
-        y = emb.positions()
-        n = emb.info()["n_terms"]
-        emb.close()
-        return y, n
-
-    batched()
-    (ybat, terms_b), t_bat = timed(batched)
-    assert terms_b == terms
-
-    # equal kNN precision check per embedding
+    # batched, autotuned, per gathered-position format
     lo = np.concatenate([[0], np.cumsum([w["X"].shape[0] for w in work])])
-    dq = []
-    for e, (w, g) in enumerate(zip(work, graphs)):
-        rows = torch.from_numpy(synth.sample_rows(w["X"].shape[0], args.qnx_rows, e)).cuda()
-        q1 = ivhd.eval_qnx(pos1[e], g, rows)
-        q2 = ivhd.eval_qnx(ybat[lo[e]:lo[e + 1]].contiguous(), g, rows)
-        dq.append((q1, q2))
-    dqs = [q2 - q1 for q1, q2 in dq]
+    sampled = [torch.from_numpy(synth.sample_rows(w["X"].shape[0], args.qnx_rows, e)).cuda()
+               for e, w in enumerate(work)]
+    q_one = [ivhd.eval_qnx(pos1[e], g, sampled[e]) for e, g in enumerate(graphs)]
+    batched_runs = {}
+    for fmt in args.formats.split(","):
+        def create():
+            return ivhd.Embedding.batch([g for g in graphs], r=[w["r"] for w in work],
+                                        seeds=[w["seed"] for w in work], c=c, a=a, b=b,
+                                        pos_format=fmt)
+
+        emb0 = create()
+        t = time.perf_counter()
+        tuned = emb0.autotune(trial_steps=20)
+        tune_s = time.perf_counter() - t
+        emb0.close()
+
+        def batched():
+            emb = create()
+            emb.autotune(trial_steps=20)
+            emb.step(args.steps)
+            y = emb.positions()
+            n = emb.info()["n_terms"]
+            emb.close()
+            return y, n
+
+        def batched_untuned():
+            emb = create()
+            emb.step(args.steps)
+            y = emb.positions()
+            emb.close()
+            return y
+
+        batched()
+        (ybat, terms_b), t_bat = timed(batched)
+        _, t_plain = timed(batched_untuned)
+        assert terms_b == terms
+        dqs = [ivhd.eval_qnx(ybat[lo[e]:lo[e + 1]].contiguous(), g, sampled[e]) - q_one[e]
+               for e, g in enumerate(graphs)]
+        batched_runs[fmt] = {
+            "seconds_with_autotune": t_bat, "edge_updates_per_s": terms * args.steps / t_bat,
+            "seconds_default_shape": t_plain, "autotune": tuned, "autotune_seconds": tune_s,
+            "speedup_vs_one_by_one_f32": t_one / t_bat,
+            "qnx_delta_vs_one_by_one": {"max_abs": max(abs(d) for d in dqs),
+                                        "mean": float(np.mean(dqs))},
+            "equal_precision": max(abs(d) for d in dqs) <= 0.01}
+
     line = {
         "workload": "64 embeddings, M log-uniform [5e3, 2e5], N=64 GMM 5-30 comps, k {2,3,5,10}, r {1,2}",
         "n_emb": args.n_emb, "total_M": int(lo[-1]), "steps": args.steps, "terms": terms,
         "one_by_one_f32": {"seconds": t_one, "edge_updates_per_s": terms * args.steps / t_one},
-        "batched": {"pos_format": args.pos_format, "seconds": t_bat,
-                    "edge_updates_per_s": terms * args.steps / t_bat, "autotune": tuned,
-                    "autotune_seconds": tune_s},
-        "speedup": t_one / t_bat,
-        "qnx_delta": {"max_abs": max(abs(d) for d in dqs), "mean": float(np.mean(dqs)),
-                      "mean_qnx_f32": float(np.mean([q for q, _ in dq]))},
-        "equal_precision": max(abs(d) for d in dqs) <= 0.01,
+        "mean_qnx_one_by_one": float(np.mean(q_one)),
+        "batched": batched_runs,
         "knn_build_s_untimed": knn_s,
     }
     print(json.dumps(line), flush=True)

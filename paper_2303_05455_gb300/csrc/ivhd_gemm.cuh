@@ -1,0 +1,35 @@
+// ivhd_gemm.cuh -- tcgen05 BF16 GEMM with fused epilogues (see ivhd_gemm.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ivhd {
+
+enum GemmEpKind {
+  kEpStoreF32 = 0,   // out_f32 = C
+  kEpBiasGelu = 1,   // out_f32 = C + bias (pre-activation), out_bf16 = GELU(C + bias)
+  kEpGeluGrad = 2    // out_bf16 = C * GELU'(aux_f32)
+};
+
+struct GemmEpilogue {
+  int kind;
+  int64_t ld_out;  // row stride (elements) of out_f32 / out_bf16 / aux_f32
+  float* out_f32;
+  __nv_bfloat16* out_bf16;
+  const float* bias;
+  const float* aux_f32;
+};
+
+// C = A B^T for BF16 A (M x K, row stride lda) and B (N x K, row stride ldb),
+// FP32 accumulation on the tensor cores, epilogue ep.  K % 8 == 0, 16-byte
+// aligned operands.  err receives a non-zero flag if a bounded wait expired.
+cudaError_t gemm_bf16_tn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
+                         int M, int N, int K, const GemmEpilogue& ep, int32_t* err,
+                         cudaStream_t s);
+
+__device__ float gelu_dev(float x);
+__device__ float gelu_grad_dev(float x);
+
+}  // namespace ivhd

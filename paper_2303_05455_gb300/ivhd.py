@@ -290,3 +290,16 @@ def probe_gather(n_positions: int, n_gathers: int = 16_777_216, repeats: int = 2
     check(L.ivhd_probe_gather(int(n_positions), int(n_gathers), int(repeats), ctypes.byref(v),
                               _stream_ptr(stream)), "ivhd_probe_gather")
     return v.value
+
+
+def gemm_bf16_tn(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    """C = A @ B.T on the tensor cores: A [M, K], B [N, K] BF16 CUDA tensors -> FP32 [M, N]."""
+    L = _lib.load()
+    A = A.to(torch.bfloat16).contiguous()
+    B = B.to(torch.bfloat16).contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    check(L.ivhd_gemm_bf16_tn(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K,
+                              _stream_ptr(stream)), "ivhd_gemm_bf16_tn")
+    return C
