@@ -375,6 +375,56 @@ ivhd_status ivhd_gemm_bf16_tn(const void *A, const void *B, float *C, int64_t M,
                               int64_t K, void *stream);
 
 /*
+ * Learned warm start / out-of-sample placement.  The paper uses IVHD itself as
+ * an initial configuration for slower methods (Sec. 3.4) and reviews
+ * parametric maps from features to the embedding (parametric t-SNE and UMAP,
+ * Sec. 2); here a multilayer perceptron
+ *     x -> GELU(W1 x + b1) -> GELU(W2 h1 + b2) -> W3 h2 + b3      (n_in -> H -> H -> 2)
+ * is trained with the mean squared error to IVHD coordinates and Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected), then places new points
+ * or whole datasets before IVHD refines them.  FP32 master weights and Adam
+ * moments; the two wide layers run on the tensor cores (ivhd_gemm_bf16_tn)
+ * from BF16 copies with FP32 accumulation, bias + GELU fused in the epilogue.
+ *
+ * Parameters are one flat FP32 vector in the order W1 (H x n_in, row-major),
+ * b1 (H), W2 (H x H), b2 (H), W3 (2 x H), b3 (2); ivhd_mlp_num_params gives
+ * its length.  Inputs x are row-major (rows x n_in) device arrays of dtype
+ * 0 = BF16, 1 = uint8, 2 = FP32, multiplied by x_scale on load; targets are
+ * device FP32 rows x 2.  All calls are stream-ordered on `stream`.
+ * Constraints: n_in % 8 == 0, H % 16 == 0, batch sizes B % 8 == 0 with
+ * 8 <= B <= max_batch.  Errors: IVHD_ERR_ARG, IVHD_ERR_OOM, IVHD_ERR_CUDA,
+ * IVHD_ERR_TIMEOUT (a bounded wait in a GEMM expired), IVHD_ERR_STATE.
+ */
+typedef struct ivhd_mlp ivhd_mlp;
+
+ivhd_status ivhd_mlp_create(int32_t n_in, int32_t hidden, int32_t max_batch, void *stream,
+                            ivhd_mlp **out);
+void ivhd_mlp_destroy(ivhd_mlp *mlp);
+int64_t ivhd_mlp_num_params(ivhd_mlp *mlp);
+/* Loads all parameters (host or device) and resets the Adam state.  Synchronises. */
+ivhd_status ivhd_mlp_set_params(ivhd_mlp *mlp, const float *params, int32_t on_device);
+/* Copies the FP32 master parameters out.  Host output synchronises. */
+ivhd_status ivhd_mlp_get_params(ivhd_mlp *mlp, float *params, int32_t on_device);
+/*
+ * Loss (*loss, host, may be NULL) and gradients (grads: device, n_params
+ * FP32, may be NULL) of one batch, without updating.  Synchronises.
+ */
+ivhd_status ivhd_mlp_loss_grad(ivhd_mlp *mlp, const void *x, int32_t x_dtype, float x_scale,
+                               const float *targets, int32_t B, double *loss, float *grads);
+/*
+ * One Adam step on one batch with learning rate lr.  With loss != NULL the
+ * batch loss (before the update) is written and the call synchronises;
+ * otherwise it is fully asynchronous.
+ */
+ivhd_status ivhd_mlp_train_step(ivhd_mlp *mlp, const void *x, int32_t x_dtype, float x_scale,
+                                const float *targets, int32_t B, float lr, double *loss);
+/* y (device, n x 2 FP32) = the network applied to n rows of x.  Synchronises. */
+ivhd_status ivhd_mlp_forward(ivhd_mlp *mlp, const void *x, int32_t x_dtype, float x_scale,
+                             int64_t n, float *y);
+/* Kernels launched by this network so far. */
+int64_t ivhd_mlp_launches(ivhd_mlp *mlp);
+
+/*
  * ivhd_eval_qnx_static -- ivhd_eval_qnx that allocates no device memory.
  *
  * The paper has no counterpart: this entry point exists for host

@@ -24,7 +24,9 @@ SYMBOLS = (
     "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
     "ivhd_probe_gather", "ivhd_set_metric", "ivhd_resample_random_neighbors",
     "ivhd_restrict_nn", "ivhd_adaptive_state", "ivhd_create_batch", "ivhd_autotune",
-    "ivhd_gemm_bf16_tn",
+    "ivhd_gemm_bf16_tn", "ivhd_mlp_create", "ivhd_mlp_destroy", "ivhd_mlp_num_params",
+    "ivhd_mlp_set_params", "ivhd_mlp_get_params", "ivhd_mlp_loss_grad", "ivhd_mlp_train_step",
+    "ivhd_mlp_forward", "ivhd_mlp_launches",
 )
 
 
@@ -130,6 +132,26 @@ def load(build_if_missing: bool = False):
     L.ivhd_autotune.restype = i32
     L.ivhd_gemm_bf16_tn.argtypes = [P, P, P, i64, i64, i64, P]
     L.ivhd_gemm_bf16_tn.restype = i32
+    L.ivhd_mlp_create.argtypes = [i32, i32, i32, P, ctypes.POINTER(P)]
+    L.ivhd_mlp_create.restype = i32
+    L.ivhd_mlp_destroy.argtypes = [P]
+    L.ivhd_mlp_destroy.restype = None
+    L.ivhd_mlp_num_params.argtypes = [P]
+    L.ivhd_mlp_num_params.restype = i64
+    L.ivhd_mlp_set_params.argtypes = [P, P, i32]
+    L.ivhd_mlp_set_params.restype = i32
+    L.ivhd_mlp_get_params.argtypes = [P, P, i32]
+    L.ivhd_mlp_get_params.restype = i32
+    L.ivhd_mlp_loss_grad.argtypes = [P, P, i32, ctypes.c_float, P, i32,
+                                     ctypes.POINTER(ctypes.c_double), P]
+    L.ivhd_mlp_loss_grad.restype = i32
+    L.ivhd_mlp_train_step.argtypes = [P, P, i32, ctypes.c_float, P, i32, ctypes.c_float,
+                                      ctypes.POINTER(ctypes.c_double)]
+    L.ivhd_mlp_train_step.restype = i32
+    L.ivhd_mlp_forward.argtypes = [P, P, i32, ctypes.c_float, i64, P]
+    L.ivhd_mlp_forward.restype = i32
+    L.ivhd_mlp_launches.argtypes = [P]
+    L.ivhd_mlp_launches.restype = i64
     _lib = L
     return L
 

@@ -332,9 +332,6 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEp
 
 }  // namespace
 
-__device__ float gelu_dev(float x) { return gelu(x); }
-__device__ float gelu_grad_dev(float x) { return gelu_grad(x); }
-
 cudaError_t gemm_bf16_tn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
                          int M, int N, int K, const GemmEpilogue& ep, int32_t* err,
                          cudaStream_t s) {

@@ -29,7 +29,4 @@ cudaError_t gemm_bf16_tn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat1
                          int M, int N, int K, const GemmEpilogue& ep, int32_t* err,
                          cudaStream_t s);
 
-__device__ float gelu_dev(float x);
-__device__ float gelu_grad_dev(float x);
-
 }  // namespace ivhd

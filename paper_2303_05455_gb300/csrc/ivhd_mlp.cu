@@ -1,0 +1,471 @@
+// ivhd_mlp.cu -- the learned warm start: an MLP that maps features to 2-D positions.
+//
+//   x -> h1 = GELU(W1 x + b1) -> h2 = GELU(W2 h1 + b2) -> y = W3 h2 + b3
+//
+// trained with the mean squared error to IVHD embedding coordinates and Adam
+// (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Weights keep an FP32
+// master copy (and the Adam moments); the two wide layers run on the tensor
+// cores from BF16 copies with FP32 accumulation (ivhd_gemm.cu), with the bias
+// and GELU (forward) or GELU derivative (backward) fused into the GEMM
+// epilogue; the 2-wide output layer and the reductions over the batch run on
+// the CUDA cores in FP32 with fixed summation orders.  Everything on the
+// context stream; training steps need no host synchronisation.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <new>
+
+#include "ivhd_gemm.cuh"
+#include "ivhd_internal.cuh"
+
+struct ivhd_mlp {
+  int n_in = 0, hidden = 0, max_batch = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n_params = 0;
+  int64_t t = 0;          // Adam step counter
+  bool poisoned = false;
+  // parameters: FP32 master, Adam moments, gradients (flat: W1 b1 W2 b2 W3 b3)
+  float* w = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* g = nullptr;
+  // BF16 copies used by the tensor cores
+  __nv_bfloat16* w1 = nullptr;   // hidden x n_in
+  __nv_bfloat16* w2 = nullptr;   // hidden x hidden
+  __nv_bfloat16* w2t = nullptr;  // transposed W2
+  // workspace for one batch
+  __nv_bfloat16 *xb = nullptr, *xt = nullptr;
+  float *z1 = nullptr, *z2 = nullptr;
+  __nv_bfloat16 *h1 = nullptr, *h1t = nullptr, *h2 = nullptr;
+  __nv_bfloat16 *dz2 = nullptr, *dz2t = nullptr, *dz1 = nullptr, *dz1t = nullptr;
+  float *y = nullptr, *dy = nullptr;
+  double* loss_part = nullptr;
+  double* loss_out = nullptr;
+  int32_t* err = nullptr;
+  int64_t launches = 0;
+};
+
+namespace ivhd {
+namespace {
+
+constexpr int kLossBlocks = 256;
+
+// GELU'(x) = Phi(x) + x phi(x) for the exact GELU x Phi(x).
+__device__ __forceinline__ float gelu_grad_dev(float x) {
+  const float cdf = 0.5f * (1.f + erff(x * 0.70710678118654752f));
+  const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
+  return cdf + x * pdf;
+}
+
+struct Offs {
+  int64_t W1, b1, W2, b2, W3, b3, total;
+};
+Offs offsets(int n_in, int H) {
+  Offs o;
+  o.W1 = 0;
+  o.b1 = o.W1 + (int64_t)H * n_in;
+  o.W2 = o.b1 + H;
+  o.b2 = o.W2 + (int64_t)H * H;
+  o.W3 = o.b2 + H;
+  o.b3 = o.W3 + 2 * (int64_t)H;
+  o.total = o.b3 + 2;
+  return o;
+}
+
+inline unsigned nb(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+// Input rows to BF16: uint8 * scale, FP32, or BF16 as given.
+__global__ void k_convert_x(const void* __restrict__ x, int dtype, float scale, int64_t n,
+                            __nv_bfloat16* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  float v;
+  if (dtype == 1)
+    v = (float)((const uint8_t*)x)[e] * scale;
+  else if (dtype == 2)
+    v = ((const float*)x)[e] * scale;
+  else
+    v = __bfloat162float(((const __nv_bfloat16*)x)[e]) * scale;
+  out[e] = __float2bfloat16_rn(v);
+}
+
+// Tiled BF16 transpose: out[c][r] = in[r][c] for an R x C matrix.
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int R, int C,
+                                 __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    if (r < R && c < C) t[dy][threadIdx.x] = in[(int64_t)r * C + c];
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    if (r < R && c < C) out[(int64_t)c * R + r] = t[threadIdx.x][dy];
+  }
+}
+
+// y[b][j] = sum_i W3[j][i] h2[b][i] + b3[j], one warp per row, fixed lane order.
+__global__ void k_layer3(const __nv_bfloat16* __restrict__ h2, const float* __restrict__ W3,
+                         const float* __restrict__ b3, int B, int H, float* __restrict__ y) {
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= B) return;
+  float s0 = 0.f, s1 = 0.f;
+  for (int i = lane; i < H; i += 32) {
+    const float h = __bfloat162float(h2[(int64_t)row * H + i]);
+    s0 = fmaf(W3[i], h, s0);
+    s1 = fmaf(W3[H + i], h, s1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (lane == 0) {
+    y[2 * (int64_t)row] = s0 + b3[0];
+    y[2 * (int64_t)row + 1] = s1 + b3[1];
+  }
+}
+
+// dY = 2 (Y - T) / B; per-block partial sums of |Y - T|^2 (grid-stride, fixed order).
+__global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
+                                              const float* __restrict__ tgt, int B,
+                                              float* __restrict__ dy, double* __restrict__ part) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * (int64_t)B;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float d = y[e] - tgt[e];
+    dy[e] = 2.f * d / (float)B;
+    acc += (double)d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_loss_final(const double* __restrict__ part, int n, int B, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += part[i];
+    out[0] = t / B;
+  }
+}
+
+// dW3[j][i] = sum_b dY[b][j] h2[b][i], db3[j] = sum_b dY[b][j] (thread per output).
+__global__ void k_grad3(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h2, int B,
+                        int H, float* __restrict__ gW3, float* __restrict__ gb3) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < 2 * H) {
+    const int j = o / H, i = o % H;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s = fmaf(dy[2 * (int64_t)b + j], __bfloat162float(h2[(int64_t)b * H + i]), s);
+    gW3[o] = s;
+  } else if (o < 2 * H + 2) {
+    const int j = o - 2 * H;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += dy[2 * (int64_t)b + j];
+    gb3[j] = s;
+  }
+}
+
+// dZ2 = (dY W3) * GELU'(z2) in BF16.
+__global__ void k_dz2(const float* __restrict__ dy, const float* __restrict__ W3,
+                      const float* __restrict__ z2, int B, int H,
+                      __nv_bfloat16* __restrict__ dz2) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * H) return;
+  const int64_t b = e / H;
+  const int i = (int)(e % H);
+  const float dh = fmaf(dy[2 * b], W3[i], dy[2 * b + 1] * W3[H + i]);
+  dz2[e] = __float2bfloat16_rn(dh * gelu_grad_dev(z2[e]));
+}
+
+// Column sums (bias gradients) of a B x H BF16 matrix, thread per column.
+__global__ void k_colsum(const __nv_bfloat16* __restrict__ a, int B, int H, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += __bfloat162float(a[(int64_t)b * H + i]);
+  out[i] = s;
+}
+
+// Adam on the flat FP32 parameters (bias-corrected, Kingma and Ba).
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int64_t n, float lr, float c1, float c2) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float gi = g[e];
+  const float mi = fmaf(0.9f, m[e], 0.1f * gi);
+  const float vi = fmaf(0.999f, v[e], 0.001f * gi * gi);
+  m[e] = mi;
+  v[e] = vi;
+  w[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, int64_t n, __nv_bfloat16* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = __float2bfloat16_rn(a[e]);
+}
+
+cudaError_t transpose(const __nv_bfloat16* in, int R, int C, __nv_bfloat16* out, cudaStream_t s) {
+  dim3 grid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32)), block(32, 8);
+  k_transpose_bf16<<<grid, block, 0, s>>>(in, R, C, out);
+  return cudaGetLastError();
+}
+
+// BF16 copies of W1, W2 and the transposed W2 from the FP32 master.
+cudaError_t refresh_copies(ivhd_mlp* P) {
+  const Offs o = offsets(P->n_in, P->hidden);
+  const int H = P->hidden;
+  k_to_bf16<<<nb((int64_t)H * P->n_in), 256, 0, P->stream>>>(P->w + o.W1, (int64_t)H * P->n_in, P->w1);
+  k_to_bf16<<<nb((int64_t)H * H), 256, 0, P->stream>>>(P->w + o.W2, (int64_t)H * H, P->w2);
+  P->launches += 3;
+  return transpose(P->w2, H, H, P->w2t, P->stream);
+}
+
+// Forward pass of B rows already in P->xb: z1, h1, z2, h2, y.
+cudaError_t forward(ivhd_mlp* P, int B) {
+  const Offs o = offsets(P->n_in, P->hidden);
+  const int H = P->hidden;
+  GemmEpilogue e1{kEpBiasGelu, H, P->z1, P->h1, P->w + o.b1, nullptr};
+  cudaError_t e = gemm_bf16_tn(P->xb, P->n_in, P->w1, P->n_in, B, H, P->n_in, e1, P->err, P->stream);
+  GemmEpilogue e2{kEpBiasGelu, H, P->z2, P->h2, P->w + o.b2, nullptr};
+  if (e == cudaSuccess) e = gemm_bf16_tn(P->h1, H, P->w2, H, B, H, H, e2, P->err, P->stream);
+  if (e == cudaSuccess) {
+    k_layer3<<<nb((int64_t)B * 32), 256, 0, P->stream>>>(P->h2, P->w + o.W3, P->w + o.b3, B, H, P->y);
+    e = cudaGetLastError();
+  }
+  P->launches += 3;
+  return e;
+}
+
+// Loss and gradients of B rows (inputs in P->xb, targets tgt) into P->g.
+cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B) {
+  const Offs o = offsets(P->n_in, P->hidden);
+  const int H = P->hidden, n_in = P->n_in;
+  cudaStream_t s = P->stream;
+  cudaError_t e = forward(P, B);
+  if (e != cudaSuccess) return e;
+  k_loss<<<kLossBlocks, 256, 0, s>>>(P->y, tgt, B, P->dy, P->loss_part);
+  k_loss_final<<<1, 32, 0, s>>>(P->loss_part, kLossBlocks, B, P->loss_out);
+  k_grad3<<<nb(2 * (int64_t)H + 2), 256, 0, s>>>(P->dy, P->h2, B, H, P->g + o.W3, P->g + o.b3);
+  k_dz2<<<nb((int64_t)B * H), 256, 0, s>>>(P->dy, P->w + o.W3, P->z2, B, H, P->dz2);
+  k_colsum<<<nb(H), 256, 0, s>>>(P->dz2, B, H, P->g + o.b2);
+  P->launches += 5;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // dW2 = dZ2^T H1
+  if ((e = transpose(P->dz2, B, H, P->dz2t, s)) != cudaSuccess) return e;
+  if ((e = transpose(P->h1, B, H, P->h1t, s)) != cudaSuccess) return e;
+  GemmEpilogue gw2{kEpStoreF32, H, P->g + o.W2, nullptr, nullptr, nullptr};
+  if ((e = gemm_bf16_tn(P->dz2t, B, P->h1t, B, H, H, B, gw2, P->err, s)) != cudaSuccess) return e;
+  // dZ1 = (dZ2 W2) * GELU'(z1)
+  GemmEpilogue gz1{kEpGeluGrad, H, nullptr, P->dz1, nullptr, P->z1};
+  if ((e = gemm_bf16_tn(P->dz2, H, P->w2t, H, B, H, H, gz1, P->err, s)) != cudaSuccess) return e;
+  k_colsum<<<nb(H), 256, 0, s>>>(P->dz1, B, H, P->g + o.b1);
+  // dW1 = dZ1^T X
+  if ((e = transpose(P->dz1, B, H, P->dz1t, s)) != cudaSuccess) return e;
+  if ((e = transpose(P->xb, B, n_in, P->xt, s)) != cudaSuccess) return e;
+  GemmEpilogue gw1{kEpStoreF32, n_in, P->g + o.W1, nullptr, nullptr, nullptr};
+  e = gemm_bf16_tn(P->dz1t, B, P->xt, B, H, n_in, B, gw1, P->err, s);
+  P->launches += 8;
+  return e;
+}
+
+cudaError_t load_x(ivhd_mlp* P, const void* x, int dtype, float scale, int64_t rows) {
+  const int64_t n = rows * P->n_in;
+  k_convert_x<<<nb(n), 256, 0, P->stream>>>(x, dtype, scale, n, P->xb);
+  ++P->launches;
+  return cudaGetLastError();
+}
+
+ivhd_status mlp_fail(ivhd_mlp* P, cudaError_t e) {
+  if (e == cudaSuccess) return IVHD_OK;
+  if (e == cudaErrorMemoryAllocation) return IVHD_ERR_OOM;
+  if (e == cudaErrorInvalidValue) return IVHD_ERR_ARG;
+  P->poisoned = true;
+  return IVHD_ERR_CUDA;
+}
+
+// Timeouts of the GEMM's bounded waits, read back (synchronises).
+ivhd_status check_err(ivhd_mlp* P) {
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, P->err, sizeof(h), cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return mlp_fail(P, e);
+  if (h) {
+    P->poisoned = true;
+    return IVHD_ERR_TIMEOUT;
+  }
+  return IVHD_OK;
+}
+
+bool batch_ok(const ivhd_mlp* P, int64_t B) { return B >= 8 && B <= P->max_batch && B % 8 == 0; }
+
+}  // namespace
+}  // namespace ivhd
+
+using namespace ivhd;
+
+extern "C" {
+
+ivhd_status ivhd_mlp_create(int32_t n_in, int32_t hidden, int32_t max_batch, void* stream,
+                            ivhd_mlp** out) {
+  if (!out) return IVHD_ERR_ARG;
+  *out = nullptr;
+  if (n_in < 8 || n_in % 8 || n_in > 65536 || hidden < 16 || hidden % 16 || hidden > 4096 ||
+      max_batch < 8 || max_batch % 8 || max_batch > (1 << 20))
+    return IVHD_ERR_ARG;
+  ivhd_mlp* P = new (std::nothrow) ivhd_mlp();
+  if (!P) return IVHD_ERR_OOM;
+  P->n_in = n_in;
+  P->hidden = hidden;
+  P->max_batch = max_batch;
+  P->stream = (cudaStream_t)stream;
+  const Offs o = offsets(n_in, hidden);
+  P->n_params = o.total;
+  const int64_t B = max_batch, H = hidden;
+  cudaStream_t s = P->stream;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, int64_t n) {
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)p, (size_t)n * sizeof(**p), s);
+  };
+  A(&P->w, o.total);
+  A(&P->m, o.total);
+  A(&P->v, o.total);
+  A(&P->g, o.total);
+  A(&P->w1, H * n_in);
+  A(&P->w2, H * H);
+  A(&P->w2t, H * H);
+  A(&P->xb, B * n_in);
+  A(&P->xt, B * n_in);
+  A(&P->z1, B * H);
+  A(&P->z2, B * H);
+  A(&P->h1, B * H);
+  A(&P->h1t, B * H);
+  A(&P->h2, B * H);
+  A(&P->dz2, B * H);
+  A(&P->dz2t, B * H);
+  A(&P->dz1, B * H);
+  A(&P->dz1t, B * H);
+  A(&P->y, 2 * B);
+  A(&P->dy, 2 * B);
+  A(&P->loss_part, kLossBlocks);
+  A(&P->loss_out, 1);
+  A(&P->err, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->w, 0, o.total * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->m, 0, o.total * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->v, 0, o.total * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->err, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = refresh_copies(P);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    ivhd_mlp_destroy(P);
+    return e == cudaErrorMemoryAllocation ? IVHD_ERR_OOM : IVHD_ERR_CUDA;
+  }
+  *out = P;
+  return IVHD_OK;
+}
+
+void ivhd_mlp_destroy(ivhd_mlp* P) {
+  if (!P) return;
+  void* bufs[] = {P->w, P->m, P->v, P->g, P->w1, P->w2, P->w2t, P->xb, P->xt, P->z1, P->z2,
+                  P->h1, P->h1t, P->h2, P->dz2, P->dz2t, P->dz1, P->dz1t, P->y, P->dy,
+                  P->loss_part, P->loss_out, P->err};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, P->stream);
+  cudaStreamSynchronize(P->stream);
+  delete P;
+}
+
+int64_t ivhd_mlp_num_params(ivhd_mlp* P) { return P ? P->n_params : -1; }
+
+ivhd_status ivhd_mlp_set_params(ivhd_mlp* P, const float* params, int32_t on_device) {
+  if (!P || !params) return IVHD_ERR_ARG;
+  if (P->poisoned) return IVHD_ERR_STATE;
+  cudaStream_t s = P->stream;
+  const size_t bytes = (size_t)P->n_params * sizeof(float);
+  cudaError_t e = cudaMemcpyAsync(P->w, params, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->m, 0, bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->v, 0, bytes, s);
+  if (e == cudaSuccess) e = refresh_copies(P);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  P->t = 0;
+  return mlp_fail(P, e);
+}
+
+ivhd_status ivhd_mlp_get_params(ivhd_mlp* P, float* params, int32_t on_device) {
+  if (!P || !params) return IVHD_ERR_ARG;
+  if (P->poisoned) return IVHD_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(params, P->w, (size_t)P->n_params * sizeof(float),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  P->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(P->stream);
+  return mlp_fail(P, e);
+}
+
+ivhd_status ivhd_mlp_loss_grad(ivhd_mlp* P, const void* x, int32_t x_dtype, float x_scale,
+                               const float* targets, int32_t B, double* loss, float* grads) {
+  if (!P || !x || !targets || x_dtype < 0 || x_dtype > 2 || !batch_ok(P, B)) return IVHD_ERR_ARG;
+  if (P->poisoned) return IVHD_ERR_STATE;
+  cudaError_t e = load_x(P, x, x_dtype, x_scale, B);
+  if (e == cudaSuccess) e = loss_grad(P, targets, B);
+  if (e == cudaSuccess && grads)
+    e = cudaMemcpyAsync(grads, P->g, (size_t)P->n_params * sizeof(float), cudaMemcpyDeviceToDevice,
+                        P->stream);
+  if (e == cudaSuccess && loss)
+    e = cudaMemcpyAsync(loss, P->loss_out, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+  if (e != cudaSuccess) return mlp_fail(P, e);
+  return check_err(P);
+}
+
+ivhd_status ivhd_mlp_train_step(ivhd_mlp* P, const void* x, int32_t x_dtype, float x_scale,
+                                const float* targets, int32_t B, float lr, double* loss) {
+  if (!P || !x || !targets || x_dtype < 0 || x_dtype > 2 || !batch_ok(P, B) || !(lr > 0.f))
+    return IVHD_ERR_ARG;
+  if (P->poisoned) return IVHD_ERR_STATE;
+  cudaError_t e = load_x(P, x, x_dtype, x_scale, B);
+  if (e == cudaSuccess) e = loss_grad(P, targets, B);
+  if (e == cudaSuccess) {
+    P->t += 1;
+    const float c1 = 1.f - powf(0.9f, (float)P->t), c2 = 1.f - powf(0.999f, (float)P->t);
+    k_adam<<<nb(P->n_params), 256, 0, P->stream>>>(P->w, P->m, P->v, P->g, P->n_params, lr, c1, c2);
+    ++P->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = refresh_copies(P);
+  if (e == cudaSuccess && loss)
+    e = cudaMemcpyAsync(loss, P->loss_out, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+  if (e != cudaSuccess) return mlp_fail(P, e);
+  return loss ? check_err(P) : IVHD_OK;
+}
+
+ivhd_status ivhd_mlp_forward(ivhd_mlp* P, const void* x, int32_t x_dtype, float x_scale,
+                             int64_t n, float* y) {
+  if (!P || !x || !y || x_dtype < 0 || x_dtype > 2 || n < 1) return IVHD_ERR_ARG;
+  if (P->poisoned) return IVHD_ERR_STATE;
+  const size_t esz = x_dtype == 1 ? 1 : (x_dtype == 2 ? 4 : 2);
+  cudaError_t e = cudaSuccess;
+  for (int64_t r0 = 0; r0 < n && e == cudaSuccess; r0 += P->max_batch) {
+    const int64_t rows = (n - r0 < P->max_batch) ? n - r0 : P->max_batch;
+    e = load_x(P, (const char*)x + (size_t)r0 * P->n_in * esz, x_dtype, x_scale, rows);
+    if (e == cudaSuccess) e = forward(P, (int)rows);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(y + 2 * r0, P->y, (size_t)rows * 2 * sizeof(float),
+                          cudaMemcpyDeviceToDevice, P->stream);
+  }
+  if (e != cudaSuccess) return mlp_fail(P, e);
+  return check_err(P);
+}
+
+int64_t ivhd_mlp_launches(ivhd_mlp* P) { return P ? P->launches : -1; }
+
+}  // extern "C"

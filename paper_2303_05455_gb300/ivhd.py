@@ -303,3 +303,79 @@ def gemm_bf16_tn(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
     check(L.ivhd_gemm_bf16_tn(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K,
                               _stream_ptr(stream)), "ivhd_gemm_bf16_tn")
     return C
+
+
+_X_DTYPES = {torch.bfloat16: 0, torch.uint8: 1, torch.float32: 2}
+
+
+class MLP:
+    """The learned warm start (ivhd_mlp_*): n_in -> hidden -> hidden -> 2 with GELU."""
+
+    def __init__(self, n_in: int = 784, hidden: int = 512, max_batch: int = 4096, stream=None):
+        self._L = _lib.load()
+        self.n_in, self.hidden, self.max_batch = n_in, hidden, max_batch
+        h = ctypes.c_void_p()
+        check(self._L.ivhd_mlp_create(n_in, hidden, max_batch, _stream_ptr(stream),
+                                      ctypes.byref(h)), "ivhd_mlp_create")
+        self._h = h
+        self.n_params = int(self._L.ivhd_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.ivhd_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        if isinstance(flat, np.ndarray):
+            a = np.ascontiguousarray(flat, dtype=np.float32)
+            assert a.size == self.n_params
+            check(self._L.ivhd_mlp_set_params(self._h, a.ctypes.data, 0), "ivhd_mlp_set_params")
+        else:
+            t = flat.to(torch.float32).contiguous()
+            check(self._L.ivhd_mlp_set_params(self._h, t.data_ptr(), int(t.is_cuda)),
+                  "ivhd_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        check(self._L.ivhd_mlp_get_params(self._h, a.ctypes.data, 0), "ivhd_mlp_get_params")
+        return a
+
+    @staticmethod
+    def _x(x: torch.Tensor):
+        assert x.is_cuda and x.is_contiguous()
+        return x.data_ptr(), _X_DTYPES[x.dtype]
+
+    def loss_grad(self, x: torch.Tensor, t: torch.Tensor, x_scale: float = 1.0):
+        ptr, dt = self._x(x)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        loss = ctypes.c_double()
+        tt = t.to(torch.float32).contiguous()
+        check(self._L.ivhd_mlp_loss_grad(self._h, ptr, dt, x_scale, tt.data_ptr(), x.shape[0],
+                                         ctypes.byref(loss), g.data_ptr()), "ivhd_mlp_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x: torch.Tensor, t: torch.Tensor, lr: float = 1e-3, x_scale: float = 1.0,
+                   want_loss: bool = False):
+        ptr, dt = self._x(x)
+        tt = t if (t.dtype == torch.float32 and t.is_contiguous()) else t.to(torch.float32).contiguous()
+        loss = ctypes.c_double() if want_loss else None
+        check(self._L.ivhd_mlp_train_step(self._h, ptr, dt, x_scale, tt.data_ptr(), x.shape[0], lr,
+                                          ctypes.byref(loss) if loss is not None else None),
+              "ivhd_mlp_train_step")
+        return loss.value if loss is not None else None
+
+    def forward(self, x: torch.Tensor, x_scale: float = 1.0) -> torch.Tensor:
+        ptr, dt = self._x(x)
+        y = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+        check(self._L.ivhd_mlp_forward(self._h, ptr, dt, x_scale, x.shape[0], y.data_ptr()),
+              "ivhd_mlp_forward")
+        return y
+
+    def launches(self) -> int:
+        return int(self._L.ivhd_mlp_launches(self._h))

@@ -453,3 +453,54 @@ def test_adaptive_b_rule_on_a_single_pair():
     assert oracle.step_adaptive(st, t, 0.01, box, a=a, tau=tau, gamma1=g1, gamma2=g2)
     np.testing.assert_allclose(st.S1[0], [0.11, 0.0])
     np.testing.assert_allclose(st.Y[0], [0.21, 0.0])
+
+
+# ---------------------------------------------------------------- MLP oracle
+
+
+def test_mlp_bf16_rounding_values():
+    from oracle import mlp
+
+    x = np.array([1.0, 1.00390625, 1.005859375, 3.14159265, -2.0 ** -130, 65504.0])
+    # BF16 keeps 8 significant bits: 1 + 2^-8 is a tie between 1 and 1 + 2^-7 -> even (1.0)
+    want = np.array([1.0, 1.0, 1.0078125, 3.140625, -2.0 ** -130, 65536.0])
+    np.testing.assert_array_equal(mlp.bf16(x), want)
+
+
+def test_mlp_gradients_match_finite_differences():
+    from oracle import mlp
+
+    rng = np.random.default_rng(0)
+    p = mlp.init_params(7, 5, 2, 3)
+    p.b1 = rng.standard_normal(5) * 0.1
+    p.b2 = rng.standard_normal(5) * 0.1
+    X = rng.standard_normal((6, 7))
+    T = rng.standard_normal((6, 2))
+    L, g = mlp.loss_and_grads(p, X, T)
+    h = 1e-6
+    for n in p.names():
+        w = getattr(p, n)
+        num = np.zeros_like(w)
+        for idx in np.ndindex(w.shape):
+            q1, q2 = p.copy(), p.copy()
+            getattr(q1, n)[idx] += h
+            getattr(q2, n)[idx] -= h
+            num[idx] = (mlp.loss_and_grads(q1, X, T)[0] - mlp.loss_and_grads(q2, X, T)[0]) / (2 * h)
+        assert np.abs(num - g[n]).max() <= 1e-7 * max(1.0, np.abs(g[n]).max()), n
+
+
+def test_mlp_gelu_and_adam_closed_forms():
+    from oracle import mlp
+
+    assert mlp.gelu(0.0) == 0.0
+    assert mlp.gelu(1.0) == pytest.approx(0.8413447460685429)   # Phi(1)
+    assert mlp.gelu_grad(0.0) == pytest.approx(0.5)
+    # first Adam step moves every weight by lr * sign(g) (bias-corrected m / sqrt(v) = g / |g|)
+    p = mlp.init_params(3, 2, 2, 1)
+    g = {n: np.full_like(getattr(p, n), -0.3) for n in p.names()}
+    before = p.copy()
+    opt = mlp.Adam(lr=1e-3)
+    opt.step(p, g)
+    for n in p.names():
+        np.testing.assert_allclose(getattr(p, n) - getattr(before, n), 1e-3 * (0.3 / (0.3 + 1e-8)),
+                                   rtol=1e-12)
