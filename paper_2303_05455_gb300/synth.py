@@ -101,13 +101,18 @@ def gaussian_mixture(M: int, N: int, n_comp: int, seed: int, *, centre_std: floa
 
 
 def mnist_like(M: int, seed: int, *, N: int = 784, n_proto: int = 10, sigma: float = 40.0,
-               shuffle: bool = True):
+               shuffle: bool = True, noise_seed: int | None = None):
     """uint8 images: prototypes with i.i.d. U{0..255} pixels plus N(0, sigma^2) noise, clipped.
 
+    The prototypes come from ``seed``; the noise, the labels' order and the
+    shuffle from ``noise_seed`` (default: the same stream), so several sets can
+    share one distribution (training, held-out and arriving points).
     Returns ``(X uint8 [M, N], labels int32 [M])``.
     """
     rng = _rng(seed)
     protos = rng.integers(0, 256, size=(n_proto, N)).astype(np.float32)
+    if noise_seed is not None:
+        rng = _rng(noise_seed)
     labels = np.repeat(np.arange(n_proto, dtype=np.int32), -(-M // n_proto))[:M]
     X = np.empty((M, N), dtype=np.uint8)
     chunk = 8192
