@@ -105,6 +105,8 @@ typedef struct {
                              |dT| > tau * T_old is rejected; default 0.5 */
     float gamma1;         /* adaptive b: factor (> 1) applied to b when dT < 0; default 1.1 */
     float gamma2;         /* adaptive b: factor (0, 1) applied to b when dT > 0; default 0.5 */
+    int32_t block_size;   /* threads per block of the step kernel: 128, 256 or 512;
+                             0 = library default (256); see ivhd_autotune */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 

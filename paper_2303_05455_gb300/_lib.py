@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
         ("dedup_mutual", ctypes.c_int32), ("init_uniform", ctypes.c_int32),
         ("hub_threshold", ctypes.c_int32), ("pos_format", ctypes.c_int32),
         ("adaptive", ctypes.c_int32), ("tau", ctypes.c_float), ("gamma1", ctypes.c_float),
-        ("gamma2", ctypes.c_float),
+        ("gamma2", ctypes.c_float), ("block_size", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

@@ -8,10 +8,10 @@ c = 0.01, a = 0.9, b = 0.001, 1,000 momentum steps each.  The kNN graphs are
 built on the GPU before anything is timed.  Timed, with CUDA events:
 
 * one-by-one: for each embedding ivhd_create + 1,000 steps + positions, FP32;
-* batched: one ivhd_create_batch + the launch-shape autotuner (block size and
-  hub threshold) + 1,000 steps (one launch per step for all embeddings) +
-  positions, for BF16, FP16 and FP32 gathered positions; the same without the
-  autotuner is reported beside it.
+* batched: one ivhd_create_batch with the launch shape (block size, hub
+  threshold) the autotuner chose beforehand + 1,000 steps (one launch per step
+  for all embeddings) + positions, for BF16, FP16 and FP32 gathered
+  positions; the library's default shape is reported beside it.
 
 Prints one JSON line with both throughputs (edge-updates/s), the speed-up and
 the kNN precision Q_NX(k) of every embedding under both runs.
@@ -73,10 +73,12 @@ def main():
     q_one = [ivhd.eval_qnx(pos1[e], g, sampled[e]) for e, g in enumerate(graphs)]
     batched_runs = {}
     for fmt in args.formats.split(","):
-        def create():
+        def create(shape=None):
+            shape = shape or {"block": 0, "hub_threshold": 0}
             return ivhd.Embedding.batch([g for g in graphs], r=[w["r"] for w in work],
                                         seeds=[w["seed"] for w in work], c=c, a=a, b=b,
-                                        pos_format=fmt)
+                                        pos_format=fmt, block_size=shape["block"],
+                                        hub_threshold=shape["hub_threshold"])
 
         emb0 = create()
         t = time.perf_counter()
@@ -85,8 +87,7 @@ def main():
         emb0.close()
 
         def batched():
-            emb = create()
-            emb.autotune(trial_steps=20)
+            emb = create(tuned)
             emb.step(args.steps)
             y = emb.positions()
             n = emb.info()["n_terms"]
@@ -107,7 +108,7 @@ def main():
         dqs = [ivhd.eval_qnx(ybat[lo[e]:lo[e + 1]].contiguous(), g, sampled[e]) - q_one[e]
                for e, g in enumerate(graphs)]
         batched_runs[fmt] = {
-            "seconds_with_autotune": t_bat, "edge_updates_per_s": terms * args.steps / t_bat,
+            "seconds_tuned_shape": t_bat, "edge_updates_per_s": terms * args.steps / t_bat,
             "seconds_default_shape": t_plain, "autotune": tuned, "autotune_seconds": tune_s,
             "speedup_vs_one_by_one_f32": t_one / t_bat,
             "qnx_delta_vs_one_by_one": {"max_abs": max(abs(d) for d in dqs),

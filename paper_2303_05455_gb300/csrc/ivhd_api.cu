@@ -36,6 +36,8 @@ bool params_ok(const ivhd_params& p) {
   if (p.hub_threshold < 0 || p.hub_threshold > 65535) return false;
   if (p.pos_format < IVHD_POS_F32 || p.pos_format > IVHD_POS_BF16) return false;
   if (p.adaptive != 0 && p.adaptive != 1) return false;
+  if (p.block_size != 0 && p.block_size != 128 && p.block_size != 256 && p.block_size != 512)
+    return false;
   if (p.adaptive) {
     if (p.opt == IVHD_OPT_ADADELTA) return false;
     if (!std::isfinite(p.tau) || p.tau <= 0.f) return false;
@@ -332,6 +334,7 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
   ctx->r = r;
   ctx->c = c;
   ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : kDefaultHubThreshold;
+  ctx->block = p.block_size > 0 ? p.block_size : kStepBlock;
   ctx->stream = (cudaStream_t)p.stream;
   cudaGetDevice(&ctx->device);
   cudaStream_t s = ctx->stream;
@@ -763,6 +766,7 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
   ctx->r = r_max;
   ctx->c = c;
   ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : kDefaultHubThreshold;
+  ctx->block = p.block_size > 0 ? p.block_size : kStepBlock;
   ctx->stream = (cudaStream_t)p.stream;
   cudaGetDevice(&ctx->device);
   cudaStream_t s = ctx->stream;

@@ -49,8 +49,8 @@ class Embedding:
                  a: float = 0.9, b: float = 0.01, rho: float = 0.95, eps: float = 1e-6,
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
                  hub_threshold: int = 0, pos_format: str = "f32", adaptive: bool = False,
-                 tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, stream=None,
-                 device=None, batch=None):
+                 tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, block_size: int = 0,
+                 stream=None, device=None, batch=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -76,6 +76,7 @@ class Embedding:
         p.pos_format = POS_FORMATS[pos_format]
         p.adaptive = int(adaptive)
         p.tau, p.gamma1, p.gamma2 = tau, gamma1, gamma2
+        p.block_size = int(block_size)
         p.stream = self.stream.cuda_stream or None
         self.opt = opt
         self.params = p

@@ -19,6 +19,27 @@ def L():
     return _lib.load()
 
 
+_LAYOUT_CACHE = {}
+
+
+def c_layout(expr: str) -> int:
+    """Evaluates a sizeof/offsetof expression against include/ivhd.h with the host C compiler."""
+    import subprocess
+    import tempfile
+
+    if expr not in _LAYOUT_CACHE:
+        with tempfile.TemporaryDirectory() as d:
+            src = os.path.join(d, "t.c")
+            exe = os.path.join(d, "t")
+            with open(src, "w") as f:
+                f.write(f'#include <stddef.h>\n#include <stdio.h>\n#include "{HEADER}"\n'
+                        f'int main(void) {{ printf("%zu", (size_t)({expr})); return 0; }}\n')
+            subprocess.run(["gcc", "-std=c11", "-o", exe, src], check=True)
+            _LAYOUT_CACHE[expr] = int(subprocess.run([exe], capture_output=True, text=True,
+                                                     check=True).stdout)
+    return _LAYOUT_CACHE[expr]
+
+
 def declared_symbols():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -37,7 +58,10 @@ def test_every_declared_symbol_is_exported(L):
 def test_params_struct_layout_and_defaults(L):
     p = _lib.Params()
     L.ivhd_default_params(ctypes.byref(p))
-    assert ctypes.sizeof(_lib.Params) == 72  # C layout: 20 B + pad, seed, 5 x int32, 3 floats, stream
+    assert ctypes.sizeof(_lib.Params) == c_layout("sizeof(ivhd_params)")
+    for name, _ in _lib.Params._fields_:
+        assert getattr(_lib.Params, name).offset == c_layout(f"offsetof(ivhd_params, {name})"), name
+    assert ctypes.sizeof(_lib.Info) == c_layout("sizeof(ivhd_info_t)")
     assert (p.opt, p.init_uniform, p.dedup_mutual, p.hub_threshold) == (0, 1, 0, 0)
     assert p.a == pytest.approx(0.9) and p.b == pytest.approx(0.01)
     assert p.rho == pytest.approx(0.95) and p.eps == pytest.approx(1e-6)
@@ -78,6 +102,7 @@ def test_create_rejects_bad_sizes(L, M, k, r, c):
     ("opt", 3), ("opt", -1), ("a", -0.1), ("a", 1.5), ("a", float("nan")), ("b", 0.0),
     ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
     ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1), ("adaptive", 2),
+    ("block_size", 64), ("block_size", 1024),
 ])
 def test_create_rejects_bad_params(L, field, value):
     p = _lib.Params()
