@@ -195,7 +195,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
-  const int nk = (K + kBK - 1) / kBK;
+  // split-K: slice z of gridDim.z takes k-tiles [kt0, kt0 + nk)
+  const int nk_all = (K + kBK - 1) / kBK;
+  const int per = (nk_all + gridDim.z - 1) / gridDim.z;
+  const int kt0 = blockIdx.z * per;
+  const int nk = max(0, min(nk_all, kt0 + per) - kt0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -231,8 +235,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       unsigned char* sa = smem + s * GemmSmem<BN>::stage_bytes;
       unsigned char* sb = sa + GemmSmem<BN>::a_bytes;
       mbar_expect_tx(&full[s], GemmSmem<BN>::stage_bytes);
-      tma_load_2d(sa, &map_a, kt * kBK, m0, &full[s]);
-      tma_load_2d(sb, &map_b, kt * kBK, n0, &full[s]);
+      tma_load_2d(sa, &map_a, (kt0 + kt) * kBK, m0, &full[s]);
+      tma_load_2d(sb, &map_b, (kt0 + kt) * kBK, n0, &full[s]);
       *(volatile int*)issued = kt + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -267,11 +271,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (!aborted) {
     const int row = m0 + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    GemmEpilogue epz = ep;
+    if (gridDim.z > 1) epz.out_f32 += (int64_t)blockIdx.z * ep.split_stride;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
-      tmem_ld16(trow + c0, v);
-      if (row < M) ep_apply(ep, row, n0 + c0, N, v);
+      if (nk > 0) {
+        tmem_ld16(trow + c0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;  // an empty K slice contributes zero
+      }
+      if (row < M) ep_apply(epz, row, n0 + c0, N, v);
     }
   } else if (threadIdx.x == 0) {
     // drain copies still in flight before the shared memory goes away
@@ -320,12 +331,18 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
 
 template <int BN>
 cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEpilogue& ep, int M,
-                      int N, int K, int32_t* err, cudaStream_t s) {
+                      int N, int K, int splits, int32_t* err, cudaStream_t s) {
   const int smem = GemmSmem<BN>::total;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kBM - 1) / kBM));
+  static bool attr_set[64] = {};  // one attribute call per instantiation and device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kBM - 1) / kBM), (unsigned)splits);
   k_gemm_bf16_tn<BN><<<grid, kGemmThreads, smem, s>>>(ma, mb, ep, M, N, K, err);
   return cudaGetLastError();
 }
@@ -334,13 +351,30 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEp
 
 cudaError_t gemm_bf16_tn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
                          int M, int N, int K, const GemmEpilogue& ep, int32_t* err,
-                         cudaStream_t s) {
+                         cudaStream_t s, int splits) {
   const int BN = N <= 64 ? 64 : 128;
+  if (splits < 1 || (splits > 1 && ep.kind != kEpStoreF32)) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, K, lda, kBM)) return cudaErrorInvalidValue;
   if (!make_map(&mb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
-  if (BN == 64) return launch_bn<64>(ma, mb, ep, M, N, K, err, s);
-  return launch_bn<128>(ma, mb, ep, M, N, K, err, s);
+  if (BN == 64) return launch_bn<64>(ma, mb, ep, M, N, K, splits, err, s);
+  return launch_bn<128>(ma, mb, ep, M, N, K, splits, err, s);
+}
+
+// out[i] = sum_z part[z * stride + i] over `splits` slices in order (deterministic).
+__global__ void k_sum_slices(const float* __restrict__ part, int64_t n, int64_t stride, int splits,
+                             float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float t = 0.f;
+  for (int z = 0; z < splits; ++z) t += part[z * stride + i];
+  out[i] = t;
+}
+
+cudaError_t sum_slices(const float* part, int64_t n, int64_t stride, int splits, float* out,
+                       cudaStream_t s) {
+  k_sum_slices<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, n, stride, splits, out);
+  return cudaGetLastError();
 }
 
 }  // namespace ivhd
@@ -360,11 +394,12 @@ extern "C" ivhd_status ivhd_gemm_bf16_tn(const void* A, const void* B, float* C,
   e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
   GemmEpilogue ep{};
   ep.kind = kEpStoreF32;
+  ep.split_stride = 0;
   ep.out_f32 = C;
   ep.ld_out = N;
   if (e == cudaSuccess)
     e = gemm_bf16_tn((const __nv_bfloat16*)A, K, (const __nv_bfloat16*)B, K, (int)M, (int)N,
-                     (int)K, ep, err, s);
+                     (int)K, ep, err, s, 1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(err, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -39,6 +39,7 @@ struct ivhd_mlp {
   __nv_bfloat16 *h1 = nullptr, *h1t = nullptr, *h2 = nullptr;
   __nv_bfloat16 *dz2 = nullptr, *dz2t = nullptr, *dz1 = nullptr, *dz1t = nullptr;
   float *y = nullptr, *dy = nullptr;
+  float* part = nullptr;       // split-K slices and batch-chunk partial sums
   double* loss_part = nullptr;
   double* loss_out = nullptr;
   int32_t* err = nullptr;
@@ -49,6 +50,8 @@ namespace ivhd {
 namespace {
 
 constexpr int kLossBlocks = 256;
+constexpr int kSplitK = 8;       // K = batch products (weight gradients) are split 8 ways
+constexpr int kRowChunk = 64;    // rows per partial of the batch reductions
 
 // GELU'(x) = Phi(x) + x phi(x) for the exact GELU x Phi(x).
 __device__ __forceinline__ float gelu_grad_dev(float x) {
@@ -159,21 +162,44 @@ __global__ void k_loss_final(const double* __restrict__ part, int n, int B, doub
   }
 }
 
-// dW3[j][i] = sum_b dY[b][j] h2[b][i], db3[j] = sum_b dY[b][j] (thread per output).
-__global__ void k_grad3(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h2, int B,
-                        int H, float* __restrict__ gW3, float* __restrict__ gb3) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o < 2 * H) {
-    const int j = o / H, i = o % H;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s = fmaf(dy[2 * (int64_t)b + j], __bfloat162float(h2[(int64_t)b * H + i]), s);
-    gW3[o] = s;
-  } else if (o < 2 * H + 2) {
-    const int j = o - 2 * H;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s += dy[2 * (int64_t)b + j];
-    gb3[j] = s;
+// Partials of dW3[j][i] = sum_b dY[b][j] h2[b][i] and db3[j] = sum_b dY[b][j] over
+// chunks of kRowChunk rows: part[c][j][i] (i < H) and part[c][j][H] (bias).
+__global__ void k_grad3_part(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h2,
+                             int B, int H, float* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i > H) return;
+  const int r0 = c * kRowChunk, r1 = min(B, r0 + kRowChunk);
+  float s0 = 0.f, s1 = 0.f;
+  for (int b = r0; b < r1; ++b) {
+    const float h = (i < H) ? __bfloat162float(h2[(int64_t)b * H + i]) : 1.f;
+    s0 = fmaf(dy[2 * (int64_t)b], h, s0);
+    s1 = fmaf(dy[2 * (int64_t)b + 1], h, s1);
   }
+  part[((int64_t)c * 2 + 0) * (H + 1) + i] = s0;
+  part[((int64_t)c * 2 + 1) * (H + 1) + i] = s1;
+}
+
+// Partials of the column sums of a B x H BF16 matrix over chunks of kRowChunk rows.
+__global__ void k_colsum_part(const __nv_bfloat16* __restrict__ a, int B, int H,
+                              float* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= H) return;
+  const int r0 = c * kRowChunk, r1 = min(B, r0 + kRowChunk);
+  float s = 0.f;
+  for (int b = r0; b < r1; ++b) s += __bfloat162float(a[(int64_t)b * H + i]);
+  part[(int64_t)c * H + i] = s;
+}
+
+// out[q] = sum over chunks c (in order) of part[c * n + q].
+__global__ void k_chunk_sum(const float* __restrict__ part, int chunks, int n,
+                            float* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float t = 0.f;
+  for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * n + q];
+  out[q] = t;
 }
 
 // dZ2 = (dY W3) * GELU'(z2) in BF16.
@@ -188,13 +214,14 @@ __global__ void k_dz2(const float* __restrict__ dy, const float* __restrict__ W3
   dz2[e] = __float2bfloat16_rn(dh * gelu_grad_dev(z2[e]));
 }
 
-// Column sums (bias gradients) of a B x H BF16 matrix, thread per column.
-__global__ void k_colsum(const __nv_bfloat16* __restrict__ a, int B, int H, float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= H) return;
-  float s = 0.f;
-  for (int b = 0; b < B; ++b) s += __bfloat162float(a[(int64_t)b * H + i]);
-  out[i] = s;
+// Bias gradient: column sums of a B x H BF16 matrix, chunk partials then an ordered sum.
+cudaError_t colsum(ivhd_mlp* P, const __nv_bfloat16* a, int B, int H, float* out) {
+  const int chunks = (B + kRowChunk - 1) / kRowChunk;
+  k_colsum_part<<<dim3((unsigned)((H + 255) / 256), (unsigned)chunks), 256, 0, P->stream>>>(
+      a, B, H, P->part);
+  k_chunk_sum<<<(unsigned)((H + 255) / 256), 256, 0, P->stream>>>(P->part, chunks, H, out);
+  P->launches += 2;
+  return cudaGetLastError();
 }
 
 // Adam on the flat FP32 parameters (bias-corrected, Kingma and Ba).
@@ -235,9 +262,9 @@ cudaError_t refresh_copies(ivhd_mlp* P) {
 cudaError_t forward(ivhd_mlp* P, int B) {
   const Offs o = offsets(P->n_in, P->hidden);
   const int H = P->hidden;
-  GemmEpilogue e1{kEpBiasGelu, H, P->z1, P->h1, P->w + o.b1, nullptr};
+  GemmEpilogue e1{kEpBiasGelu, H, P->z1, P->h1, P->w + o.b1, nullptr, 0};
   cudaError_t e = gemm_bf16_tn(P->xb, P->n_in, P->w1, P->n_in, B, H, P->n_in, e1, P->err, P->stream);
-  GemmEpilogue e2{kEpBiasGelu, H, P->z2, P->h2, P->w + o.b2, nullptr};
+  GemmEpilogue e2{kEpBiasGelu, H, P->z2, P->h2, P->w + o.b2, nullptr, 0};
   if (e == cudaSuccess) e = gemm_bf16_tn(P->h1, H, P->w2, H, B, H, H, e2, P->err, P->stream);
   if (e == cudaSuccess) {
     k_layer3<<<nb((int64_t)B * 32), 256, 0, P->stream>>>(P->h2, P->w + o.W3, P->w + o.b3, B, H, P->y);
@@ -256,26 +283,46 @@ cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B) {
   if (e != cudaSuccess) return e;
   k_loss<<<kLossBlocks, 256, 0, s>>>(P->y, tgt, B, P->dy, P->loss_part);
   k_loss_final<<<1, 32, 0, s>>>(P->loss_part, kLossBlocks, B, P->loss_out);
-  k_grad3<<<nb(2 * (int64_t)H + 2), 256, 0, s>>>(P->dy, P->h2, B, H, P->g + o.W3, P->g + o.b3);
+  {
+    // dW3 (2 x H) and db3 (2): rows [j][0..H) of the (2, H + 1) chunk sums, bias in column H
+    const int chunks = (B + kRowChunk - 1) / kRowChunk;
+    k_grad3_part<<<dim3(nb(H + 1), (unsigned)chunks), 256, 0, s>>>(P->dy, P->h2, B, H, P->part);
+    float* sums = P->part + (int64_t)chunks * 2 * (H + 1);
+    k_chunk_sum<<<nb(2 * (int64_t)(H + 1)), 256, 0, s>>>(P->part, chunks, 2 * (H + 1), sums);
+    for (int j = 0; j < 2; ++j) {
+      e = cudaMemcpyAsync(P->g + o.W3 + (int64_t)j * H, sums + (int64_t)j * (H + 1),
+                          (size_t)H * sizeof(float), cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->g + o.b3 + j, sums + (int64_t)j * (H + 1) + H, sizeof(float),
+                            cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
   k_dz2<<<nb((int64_t)B * H), 256, 0, s>>>(P->dy, P->w + o.W3, P->z2, B, H, P->dz2);
-  k_colsum<<<nb(H), 256, 0, s>>>(P->dz2, B, H, P->g + o.b2);
   P->launches += 5;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = colsum(P, P->dz2, B, H, P->g + o.b2)) != cudaSuccess) return e;
   // dW2 = dZ2^T H1
   if ((e = transpose(P->dz2, B, H, P->dz2t, s)) != cudaSuccess) return e;
   if ((e = transpose(P->h1, B, H, P->h1t, s)) != cudaSuccess) return e;
-  GemmEpilogue gw2{kEpStoreF32, H, P->g + o.W2, nullptr, nullptr, nullptr};
-  if ((e = gemm_bf16_tn(P->dz2t, B, P->h1t, B, H, H, B, gw2, P->err, s)) != cudaSuccess) return e;
+  GemmEpilogue gw2{kEpStoreF32, H, P->part, nullptr, nullptr, nullptr, (int64_t)H * H};
+  if ((e = gemm_bf16_tn(P->dz2t, B, P->h1t, B, H, H, B, gw2, P->err, s, kSplitK)) != cudaSuccess)
+    return e;
+  if ((e = sum_slices(P->part, (int64_t)H * H, (int64_t)H * H, kSplitK, P->g + o.W2, s)) !=
+      cudaSuccess)
+    return e;
   // dZ1 = (dZ2 W2) * GELU'(z1)
-  GemmEpilogue gz1{kEpGeluGrad, H, nullptr, P->dz1, nullptr, P->z1};
+  GemmEpilogue gz1{kEpGeluGrad, H, nullptr, P->dz1, nullptr, P->z1, 0};
   if ((e = gemm_bf16_tn(P->dz2, H, P->w2t, H, B, H, H, gz1, P->err, s)) != cudaSuccess) return e;
-  k_colsum<<<nb(H), 256, 0, s>>>(P->dz1, B, H, P->g + o.b1);
+  if ((e = colsum(P, P->dz1, B, H, P->g + o.b1)) != cudaSuccess) return e;
   // dW1 = dZ1^T X
   if ((e = transpose(P->dz1, B, H, P->dz1t, s)) != cudaSuccess) return e;
   if ((e = transpose(P->xb, B, n_in, P->xt, s)) != cudaSuccess) return e;
-  GemmEpilogue gw1{kEpStoreF32, n_in, P->g + o.W1, nullptr, nullptr, nullptr};
-  e = gemm_bf16_tn(P->dz1t, B, P->xt, B, H, n_in, B, gw1, P->err, s);
-  P->launches += 8;
+  GemmEpilogue gw1{kEpStoreF32, n_in, P->part, nullptr, nullptr, nullptr, (int64_t)H * n_in};
+  if ((e = gemm_bf16_tn(P->dz1t, B, P->xt, B, H, n_in, B, gw1, P->err, s, kSplitK)) != cudaSuccess)
+    return e;
+  e = sum_slices(P->part, (int64_t)H * n_in, (int64_t)H * n_in, kSplitK, P->g + o.W1, s);
+  P->launches += 10;
   return e;
 }
 
@@ -357,6 +404,13 @@ ivhd_status ivhd_mlp_create(int32_t n_in, int32_t hidden, int32_t max_batch, voi
   A(&P->dz1t, B * H);
   A(&P->y, 2 * B);
   A(&P->dy, 2 * B);
+  {
+    // split-K slices of the largest weight gradient, or the batch-chunk partials
+    const int64_t chunks = (B + kRowChunk - 1) / kRowChunk;
+    const int64_t wide = H > n_in ? H : n_in;
+    const int64_t a1 = (int64_t)kSplitK * H * wide, a2 = (chunks + 1) * 2 * (H + 1);
+    A(&P->part, a1 > a2 ? a1 : a2);
+  }
   A(&P->loss_part, kLossBlocks);
   A(&P->loss_out, 1);
   A(&P->err, 1);
@@ -378,7 +432,7 @@ void ivhd_mlp_destroy(ivhd_mlp* P) {
   if (!P) return;
   void* bufs[] = {P->w, P->m, P->v, P->g, P->w1, P->w2, P->w2t, P->xb, P->xt, P->z1, P->z2,
                   P->h1, P->h1t, P->h2, P->dz2, P->dz2t, P->dz1, P->dz1t, P->y, P->dy,
-                  P->loss_part, P->loss_out, P->err};
+                  P->part, P->loss_part, P->loss_out, P->err};
   for (void* b : bufs)
     if (b) cudaFreeAsync(b, P->stream);
   cudaStreamSynchronize(P->stream);
