@@ -152,12 +152,18 @@ __global__ void k_count_in(const int32_t* __restrict__ knn, const int32_t* __res
 }
 
 // Degree (stored row entries) and the descending-degree sort key; totals
-// are reduced per warp before the atomics.
-__global__ void k_degree(const int32_t* __restrict__ kv, const int32_t* __restrict__ rc,
-                         const int32_t* __restrict__ in_nn, const int32_t* __restrict__ in_rn,
-                         int64_t M, int32_t* __restrict__ deg, uint32_t* __restrict__ key,
-                         int32_t* __restrict__ val, unsigned long long* sum_deg,
-                         unsigned long long* sum_rc, int32_t* max_deg) {
+// are reduced per block before one atomic per block and counter.
+__global__ void __launch_bounds__(256) k_degree(const int32_t* __restrict__ kv,
+                                                const int32_t* __restrict__ rc,
+                                                const int32_t* __restrict__ in_nn,
+                                                const int32_t* __restrict__ in_rn, int64_t M,
+                                                int32_t* __restrict__ deg,
+                                                uint32_t* __restrict__ key,
+                                                int32_t* __restrict__ val,
+                                                unsigned long long* sum_deg,
+                                                unsigned long long* sum_rc, int32_t* max_deg) {
+  __shared__ unsigned long long s_deg[8], s_rc[8];
+  __shared__ int32_t s_max[8];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int32_t d = 0, c = 0;
   if (i < M) {
@@ -167,17 +173,29 @@ __global__ void k_degree(const int32_t* __restrict__ kv, const int32_t* __restri
     key[i] = 0xFFFFu - (uint32_t)min(d, 0xFFFF);
     val[i] = (int32_t)i;
   }
-  unsigned long long sd = (unsigned long long)d, sc = (unsigned long long)c;
+  unsigned long long sd = (unsigned long long)d, sr = (unsigned long long)c;
   int32_t md = d;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     sd += __shfl_down_sync(0xffffffffu, sd, o);
-    sc += __shfl_down_sync(0xffffffffu, sc, o);
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
     md = max(md, __shfl_down_sync(0xffffffffu, md, o));
   }
+  const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
+    s_deg[w] = sd;
+    s_rc[w] = sr;
+    s_max[w] = md;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      sd += s_deg[q];
+      sr += s_rc[q];
+      md = max(md, s_max[q]);
+    }
     atomicAdd(sum_deg, sd);
-    atomicAdd(sum_rc, sc);
+    atomicAdd(sum_rc, sr);
     atomicMax(max_deg, md);
   }
 }
@@ -237,11 +255,18 @@ __global__ void __launch_bounds__(kRadixBlock) k_radix_scatter(
 
 // ---- layout sizing ---------------------------------------------------------
 
+// Rows of at most kShortRow in-entries are sorted in registers, longer ones
+// by a block in shared memory.
+constexpr int kShortRow = 32;
+
+// Per sorted position p: inverse permutation, degree, out-entry count; the
+// hub count, and n_long = the number of leading rows (degrees descend) of
+// degree above kShortRow, written by the one thread at the boundary.
 __global__ void k_sorted_info(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg,
                               const int32_t* __restrict__ kv, const int32_t* __restrict__ rc,
                               int64_t M, int hub_thr, int32_t* __restrict__ inv,
                               int32_t* __restrict__ deg_p, int32_t* __restrict__ outc_p,
-                              int32_t* n_hub) {
+                              int32_t* n_hub, int32_t* n_long) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= M) return;
   const int32_t i = perm[p];
@@ -250,6 +275,7 @@ __global__ void k_sorted_info(const int32_t* __restrict__ perm, const int32_t* _
   deg_p[p] = d;
   outc_p[p] = kv[i] + rc[i];
   if (d >= hub_thr) atomicAdd(n_hub, 1);
+  if (d > kShortRow && (p + 1 == M || deg[perm[p + 1]] <= kShortRow)) *n_long = (int32_t)(p + 1);
 }
 
 // Storage (in uint32 slots) of hub row p and of SELL slice s; 0 past the end.
@@ -340,52 +366,111 @@ __global__ void k_fill_in(const int32_t* __restrict__ knn, const int32_t* __rest
   ids[slot_addr(pj, slot, n_hub, hub_off, slice_off)] = (uint32_t)inv[i] | bit;
 }
 
-// Sorts the in-part of each SELL row (thread per row, insertion sort; rows are short).
-__global__ void k_sort_in_sell(const int32_t* __restrict__ deg_p, const int32_t* __restrict__ outc_p,
-                               int64_t M, int64_t n_hub, const int32_t* __restrict__ slice_off,
-                               uint32_t* __restrict__ ids) {
-  const int64_t p = n_hub + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= M) return;
-  const int b = outc_p[p], n = deg_p[p];
-  for (int t = b + 1; t < n; ++t) {
-    const uint32_t v = ids[slot_addr(p, t, n_hub, nullptr, slice_off)];
-    int u = t - 1;
-    while (u >= b) {
-      const uint32_t w = ids[slot_addr(p, u, n_hub, nullptr, slice_off)];
-      if (w <= v) break;
-      ids[slot_addr(p, u + 1, n_hub, nullptr, slice_off)] = w;
-      --u;
-    }
-    ids[slot_addr(p, u + 1, n_hub, nullptr, slice_off)] = v;
-  }
+// The in-part of every row (the mirrored entries, filled in arbitrary order
+// by k_fill_in) is sorted ascending so the layout, and with it every
+// summation order, is deterministic.  Values within a row are distinct
+// (one entry per source vertex and kind).
+
+// Compare-exchange of a bitonic network: ascending when up.
+__device__ __forceinline__ void bitonic_ce(uint32_t& x, uint32_t& y, bool up) {
+  const uint32_t lo = min(x, y), hi = max(x, y);
+  x = up ? lo : hi;
+  y = up ? hi : lo;
 }
 
-// Sorts the in-part of each hub row: one block per row, stable rank sort of a
-// copy (in shared memory when it fits).
-constexpr int kHubSortSmem = 8192;
-__global__ void __launch_bounds__(256) k_sort_in_hub(const int32_t* __restrict__ deg_p,
-                                                     const int32_t* __restrict__ outc_p,
-                                                     const int32_t* __restrict__ hub_off,
-                                                     const uint32_t* __restrict__ copy,
-                                                     uint32_t* __restrict__ ids) {
-  __shared__ uint32_t sh[kHubSortSmem];
-  const int64_t p = blockIdx.x;
-  const int64_t base = hub_off[p];
-  const int b = outc_p[p], n = deg_p[p], m = n - b;
-  const uint32_t* src = copy + base + b;
-  if (m <= kHubSortSmem) {
-    for (int t = threadIdx.x; t < m; t += blockDim.x) sh[t] = src[t];
-    __syncthreads();
-    src = sh;
+// Bitonic sort of N register values (N a power of two, fully unrolled).
+template <int N>
+__device__ __forceinline__ void bitonic_regs(uint32_t (&v)[kShortRow]) {
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) bitonic_ce(v[i], v[l], (i & k) == 0);
+      }
+}
+
+// SELL rows with at most kShortRow in-entries: thread per row, values in
+// registers; the network size is the warp's largest row rounded up.
+__global__ void __launch_bounds__(256) k_sort_in_short(const int32_t* __restrict__ deg_p,
+                                                       const int32_t* __restrict__ outc_p,
+                                                       int64_t M, int64_t n_hub,
+                                                       const int32_t* __restrict__ slice_off,
+                                                       uint32_t* __restrict__ ids) {
+  const int64_t p = n_hub + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int b = 0, m = 0;
+  if (p < M) {
+    b = outc_p[p];
+    m = deg_p[p] - b;
+    if (m > kShortRow) m = 0;  // sorted by k_sort_in_long
   }
-  for (int t = threadIdx.x; t < m; t += blockDim.x) {
-    const uint32_t v = src[t];
-    int rank = 0;
-    for (int u = 0; u < m; ++u) {
-      const uint32_t w = src[u];
-      rank += (w < v) || (w == v && u < t);
+  const int mw = __reduce_max_sync(0xffffffffu, m);
+  if (mw <= 1) return;
+  uint32_t v[kShortRow];
+#pragma unroll
+  for (int t = 0; t < kShortRow; ++t)
+    v[t] = (t < m) ? ids[slot_addr(p, b + t, n_hub, nullptr, slice_off)] : 0xFFFFFFFFu;
+  if (mw <= 4)
+    bitonic_regs<4>(v);
+  else if (mw <= 8)
+    bitonic_regs<8>(v);
+  else if (mw <= 16)
+    bitonic_regs<16>(v);
+  else
+    bitonic_regs<32>(v);
+#pragma unroll
+  for (int t = 0; t < kShortRow; ++t)
+    if (t < m) ids[slot_addr(p, b + t, n_hub, nullptr, slice_off)] = v[t];
+}
+
+// Hub rows, and SELL rows with more than kShortRow in-entries: one block per
+// row, bitonic sort in shared memory (rows up to kLongSortSmem entries), or a
+// stable rank sort that reads a copy of the layout (longer rows).
+constexpr int kLongSortSmem = 8192;
+__global__ void __launch_bounds__(256) k_sort_in_long(const int32_t* __restrict__ deg_p,
+                                                      const int32_t* __restrict__ outc_p,
+                                                      int64_t n_hub,
+                                                      const int32_t* __restrict__ hub_off,
+                                                      const int32_t* __restrict__ slice_off,
+                                                      const uint32_t* __restrict__ copy,
+                                                      uint32_t* __restrict__ ids) {
+  __shared__ uint32_t sh[kLongSortSmem];
+  const int64_t p = blockIdx.x;
+  const int b = outc_p[p], m = deg_p[p] - b;
+  if (m <= 1 || (p >= n_hub && m <= kShortRow)) return;
+  if (m <= kLongSortSmem) {
+    int n2 = 2;
+    while (n2 < m) n2 <<= 1;
+    for (int t = threadIdx.x; t < n2; t += blockDim.x)
+      sh[t] = (t < m) ? ids[slot_addr(p, b + t, n_hub, hub_off, slice_off)] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+          const int l = t ^ j;
+          if (l > t) {
+            uint32_t x = sh[t], y = sh[l];
+            bitonic_ce(x, y, (t & k) == 0);
+            sh[t] = x;
+            sh[l] = y;
+          }
+        }
+        __syncthreads();
+      }
+    for (int t = threadIdx.x; t < m; t += blockDim.x)
+      ids[slot_addr(p, b + t, n_hub, hub_off, slice_off)] = sh[t];
+  } else {
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+      const uint32_t v = copy[slot_addr(p, b + t, n_hub, hub_off, slice_off)];
+      int rank = 0;
+      for (int u = 0; u < m; ++u) {
+        const uint32_t w = copy[slot_addr(p, b + u, n_hub, hub_off, slice_off)];
+        rank += (w < v) || (w == v && u < t);
+      }
+      ids[slot_addr(p, b + rank, n_hub, hub_off, slice_off)] = v;
     }
-    ids[base + b + rank] = v;
   }
 }
 
@@ -486,7 +571,7 @@ struct HostTotals {
   int32_t err;
   int32_t n_hub;
   int32_t max_deg;
-  int32_t pad;
+  int32_t n_long;
   unsigned long long sum_kv;
   unsigned long long sum_deg;
   unsigned long long sum_rc;
@@ -602,7 +687,7 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
 
   // 5. sizes and offsets
   k_sorted_info<<<nblk(M), kB, 0, s>>>(ctx->perm, deg, kv, rc, M, ctx->hub_threshold, ctx->inv,
-                                       deg_p, outc_p, &tot_d->n_hub);
+                                       deg_p, outc_p, &tot_d->n_hub, &tot_d->n_long);
   ++ctx->setup_launches;
   const int64_t max_slices = (M + 31) / 32;
   int64_t* hub_sz = sc.get<int64_t>(M);
@@ -656,17 +741,22 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
   ctx->setup_launches += 2;
   IVHD_TRY(cudaGetLastError());
   if (M - ctx->n_hub > 0) {
-    k_sort_in_sell<<<nblk(M - ctx->n_hub), kB, 0, s>>>(deg_p, outc_p, M, ctx->n_hub,
-                                                        ctx->slice_off, ctx->ids);
+    k_sort_in_short<<<nblk(M - ctx->n_hub), 256, 0, s>>>(deg_p, outc_p, M, ctx->n_hub,
+                                                         ctx->slice_off, ctx->ids);
     ++ctx->setup_launches;
   }
-  if (ctx->n_hub > 0) {
-    uint32_t* copy = sc.get<uint32_t>(h.hub_total);
-    if (!sc.ok) return IVHD_ERR_OOM;
-    IVHD_TRY(cudaMemcpyAsync(copy, ctx->ids, (size_t)h.hub_total * sizeof(uint32_t),
-                             cudaMemcpyDeviceToDevice, s));
-    k_sort_in_hub<<<(unsigned)ctx->n_hub, 256, 0, s>>>(deg_p, outc_p, ctx->hub_off, copy,
-                                                       ctx->ids);
+  const int64_t n_long = ctx->n_hub > h.n_long ? ctx->n_hub : h.n_long;
+  if (n_long > 0) {
+    // rows longer than the shared-memory sort read a copy of the whole layout
+    uint32_t* copy = nullptr;
+    if (h.max_deg > kLongSortSmem) {
+      copy = sc.get<uint32_t>(ctx->n_slots);
+      if (!sc.ok) return IVHD_ERR_OOM;
+      IVHD_TRY(cudaMemcpyAsync(copy, ctx->ids, (size_t)ctx->n_slots * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, s));
+    }
+    k_sort_in_long<<<(unsigned)n_long, 256, 0, s>>>(deg_p, outc_p, ctx->n_hub, ctx->hub_off,
+                                                    ctx->slice_off, copy, ctx->ids);
     ++ctx->setup_launches;
   }
   IVHD_TRY(cudaGetLastError());
