@@ -342,6 +342,17 @@ class MLP:
             check(self._L.ivhd_mlp_set_params(self._h, t.data_ptr(), int(t.is_cuda)),
                   "ivhd_mlp_set_params")
 
+    def init_params(self, seed: int, out_scale: float = 0.1):
+        """He-uniform weights (U(-sqrt(6/fan_in), +sqrt(6/fan_in))), zero biases;
+        the output layer's weights scaled by out_scale.  Seeded numpy PCG64."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        parts = []
+        for fo, fi, sc in ((self.hidden, self.n_in, 1.0), (self.hidden, self.hidden, 1.0),
+                           (2, self.hidden, out_scale)):
+            lim = np.sqrt(6.0 / fi)
+            parts += [rng.uniform(-lim, lim, size=fo * fi) * sc, np.zeros(fo)]
+        self.set_params(np.concatenate(parts).astype(np.float32))
+
     def get_params(self) -> np.ndarray:
         a = np.empty(self.n_params, dtype=np.float32)
         check(self._L.ivhd_mlp_get_params(self._h, a.ctypes.data, 0), "ivhd_mlp_get_params")

@@ -1,0 +1,84 @@
+"""What the learned warm start gains over IVHD from a random start (``-m gpu``).
+
+A small instance of the warm-start workload: MNIST-shaped training points and
+their IVHD embedding teach the MLP (the library's tensor-core forward and
+backward kernels, Adam); the MLP then places a held-out set of the same
+distribution, and IVHD refines from that placement.  Against plain IVHD from
+the uniform random start on the same held-out kNN graph, the warm start must
+reach a lower stress with a tenth of the steps, and end at the same kNN
+precision (Q_NX(k) within 0.01) and class neighbourhood (cf_10 no worse than
+0.01 below) after the same number of steps.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2303_05455_gb300 import ivhd, synth
+
+pytestmark = pytest.mark.gpu
+
+K, R, C, A, B = 5, 1, 0.01, 0.9, 0.001
+N_TRAIN = N_HOLD = 40000
+STEPS = 1000
+
+
+def _curve(knn, lab, rows, init=None, seed=13):
+    e = ivhd.Embedding(knn, r=R, c=C, a=A, b=B, seed=seed, init_uniform=init is None)
+    if init is not None:
+        e.set_positions(init)
+    out = {}
+    done = 0
+    for st in (0, 50, 100, 200, STEPS):
+        e.step(st - done)
+        done = st
+        y = e.positions()
+        out[st] = {"stress": e.stress(), "qnx": ivhd.eval_qnx(y, knn, rows),
+                   "cf10": ivhd.eval_cf(y, lab, 10, rows)}
+    e.close()
+    return out
+
+
+def test_warm_start_gains_over_random_start():
+    dev = torch.device("cuda")
+    Xtr, _ = synth.mnist_like(N_TRAIN, 7, noise_seed=1)
+    Xtr_d = torch.from_numpy(Xtr).to(dev)
+    knn_tr = ivhd.knn_build(Xtr_d, K)
+    emb = ivhd.Embedding(knn_tr, r=R, c=C, a=A, b=B, seed=11)
+    emb.step(STEPS)
+    Ytr = emb.positions()
+    emb.close()
+    mu, sd = Ytr.mean(0), Ytr.std(0)
+    T = ((Ytr - mu) / sd).contiguous()
+
+    net = ivhd.MLP(784, 512, max_batch=4096)
+    net.init_params(5)
+    rng = np.random.Generator(np.random.PCG64(6))
+    bs = 4096
+    first = last = None
+    for ep in range(8):
+        perm = torch.from_numpy(rng.permutation(N_TRAIN)).to(dev)
+        Xs, Ts = Xtr_d[perm].contiguous(), T[perm].contiguous()
+        for bi in range(N_TRAIN // bs):
+            sl = slice(bi * bs, (bi + 1) * bs)
+            l = net.train_step(Xs[sl], Ts[sl], lr=1e-3, x_scale=1 / 255, want_loss=True)
+            first = l if first is None else first
+            last = l
+    assert last < 0.5 * first
+
+    Xh, Lh = synth.mnist_like(N_HOLD, 7, noise_seed=2)
+    Xh_d = torch.from_numpy(Xh).to(dev)
+    Yp = (net.forward(Xh_d, x_scale=1 / 255) * sd + mu).contiguous()
+    net.close()
+    knn_h = ivhd.knn_build(Xh_d, K)
+    rows = torch.from_numpy(synth.sample_rows(N_HOLD, 5000, 9)).to(dev)
+    lab = torch.from_numpy(Lh).to(dev)
+    plain = _curve(knn_h, lab, rows)
+    warm = _curve(knn_h, lab, rows, init=Yp)
+    print({"plain": plain, "warm": warm, "loss": (first, last)})
+    # a tenth of the steps reaches a lower stress than plain IVHD after all of them
+    assert warm[STEPS // 10]["stress"] < plain[STEPS]["stress"]
+    # the placement alone already keeps the classes apart as well as the full plain run
+    assert warm[0]["cf10"] >= plain[STEPS]["cf10"] - 0.01
+    # same kNN precision after the same number of steps
+    assert abs(warm[STEPS]["qnx"] - plain[STEPS]["qnx"]) <= 0.01
+    assert warm[STEPS]["cf10"] >= plain[STEPS]["cf10"] - 0.01
