@@ -311,16 +311,52 @@ int32_t ivhd_version(void);
  * paper's time_emb): for every row q of X, the k nearest other rows, nearest
  * first, ties broken by the lower index.  Float data are compared by the FP32
  * chain acc = fma(x_d - y_d, x_d - y_d, acc), d = 0..N-1; uint8 data by exact
- * integer squared distances.
+ * integer squared distances.  The result does not depend on the method.
  *
  *   X        device, M*N elements of `dtype` (ivhd_knn_dtype), row-major.
  *   out_knn  device, M*k int32.
  *   stream   cudaStream_t or NULL.
  * Constraints: 2 <= M < 2^31, 1 <= N <= 65536, 1 <= k <= min(M - 1, 64).
- * Asynchronous.  Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA.
+ * Uses the tensor-core method when it applies (ivhd_knn_build_ex).
+ * Synchronises.  Errors: IVHD_ERR_ARG, IVHD_ERR_OOM, IVHD_ERR_CUDA,
+ * IVHD_ERR_TIMEOUT (a bounded wait of the tensor-core kernel expired).
  */
 ivhd_status ivhd_knn_build(const void *X, int32_t dtype, int64_t M, int32_t N, int32_t k,
                            int32_t *out_knn, void *stream);
+
+typedef enum {
+    IVHD_KNN_AUTO = 0,          /* tensor cores when they apply, else CUDA cores */
+    IVHD_KNN_CUDA_CORES = 1,    /* FP32 chain (float) / dp4a (uint8) on every pair */
+    IVHD_KNN_TENSOR_CORES = 2   /* distance GEMM (tcgen05, BF16 operands, FP32 accumulate)
+                                   with the top-k fused into its epilogue */
+} ivhd_knn_method;
+
+typedef struct {
+    int32_t method;         /* the method that ran */
+    int64_t fallback_rows;  /* float data, tensor cores: rows whose candidate list could not
+                               be certified and were recomputed on the CUDA cores */
+    float max_rel_err;      /* float data, tensor cores: max |approximate - exact distance| /
+                               (|x_i|^2 + |x_j|^2) over all candidates */
+    float eps_coef;         /* the error bound per unit of |x_i|^2 + |x_j|^2 that the
+                               certificate assumes, 2^-13 + N 2^-19 */
+} ivhd_knn_stats_t;
+
+/*
+ * ivhd_knn_build with a choice of method and statistics (stats may be NULL).
+ * Tensor cores apply for k <= 32 and, for uint8 data, N <= 1024.  uint8: the
+ * GEMM on x - 128 in BF16 is exact (every partial sum is an integer below
+ * 2^24).  float: x = hi + lo + r with BF16 hi and lo; a GEMM over
+ * [hi, hi, lo] . [hi, lo, hi] gives distances dt within eps_coef (|x_i|^2 +
+ * |x_j|^2) of the exact ones and keeps per row the 32 smallest keys
+ * dt - eps_coef |x_j|^2; they are re-ranked by the exact FP32 chain, and a row
+ * is kept when its exact k-th distance lies below the 32nd key minus
+ * eps_coef |x_i|^2, so no vertex outside the list can be closer; other rows
+ * are recomputed by the CUDA-core method.  IVHD_ERR_ARG for
+ * IVHD_KNN_TENSOR_CORES outside its range.
+ */
+ivhd_status ivhd_knn_build_ex(const void *X, int32_t dtype, int64_t M, int32_t N, int32_t k,
+                              int32_t *out_knn, int32_t method, ivhd_knn_stats_t *stats,
+                              void *stream);
 
 /*
  * Neighbourhood preservation Q_NX(k) of Sec. 4.1 on sampled rows: for each

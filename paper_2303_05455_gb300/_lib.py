@@ -21,7 +21,7 @@ SYMBOLS = (
     "ivhd_default_params", "ivhd_create", "ivhd_set_positions", "ivhd_step", "ivhd_positions",
     "ivhd_forces", "ivhd_stress", "ivhd_random_neighbors", "ivhd_info", "ivhd_state_size",
     "ivhd_get_state", "ivhd_set_state", "ivhd_destroy", "ivhd_status_string", "ivhd_version",
-    "ivhd_knn_build", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
+    "ivhd_knn_build", "ivhd_knn_build_ex", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
     "ivhd_probe_gather", "ivhd_set_metric", "ivhd_resample_random_neighbors",
     "ivhd_restrict_nn", "ivhd_adaptive_state", "ivhd_create_batch", "ivhd_autotune",
     "ivhd_gemm_bf16_tn", "ivhd_mlp_create", "ivhd_mlp_destroy", "ivhd_mlp_num_params",
@@ -56,6 +56,13 @@ class Info(ctypes.Structure):
         ("max_degree", ctypes.c_int32), ("empty_rn", ctypes.c_int32),
         ("steps_done", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("setup_launches", ctypes.c_int64), ("aux_launches", ctypes.c_int64),
+    ]
+
+
+class KnnStats(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32), ("fallback_rows", ctypes.c_int64),
+        ("max_rel_err", ctypes.c_float), ("eps_coef", ctypes.c_float),
     ]
 
 
@@ -106,6 +113,8 @@ def load(build_if_missing: bool = False):
     L.ivhd_version.restype = i32
     L.ivhd_knn_build.argtypes = [P, i32, i64, i32, i32, P, P]
     L.ivhd_knn_build.restype = i32
+    L.ivhd_knn_build_ex.argtypes = [P, i32, i64, i32, i32, P, i32, P, P]
+    L.ivhd_knn_build_ex.restype = i32
     L.ivhd_eval_qnx.argtypes = [P, i64, P, i32, P, i64, P, ctypes.POINTER(ctypes.c_double), P]
     L.ivhd_eval_qnx.restype = i32
     L.ivhd_eval_cf.argtypes = [P, i64, P, i32, P, i64, ctypes.POINTER(ctypes.c_double), P]

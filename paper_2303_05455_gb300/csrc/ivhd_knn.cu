@@ -11,6 +11,7 @@
 // tile the 128x128 distances go through shared memory into a per-query sorted
 // list of the k best.
 #include "ivhd_internal.cuh"
+#include "ivhd_knn_tc.cuh"
 
 namespace ivhd {
 namespace {
@@ -56,8 +57,12 @@ __device__ __forceinline__ void merge_row(const D* row, int c0, int64_t M, int64
   }
 }
 
+// rows / n_rows (device, optional): the CTA's queries are entries q0 .. q0+127
+// of the list rows[0 .. *n_rows) instead of rows q0 .. q0+127.
 __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ X, int64_t M,
-                                                      int N, int k, int32_t* __restrict__ out) {
+                                                      int N, int k, int32_t* __restrict__ out,
+                                                      const int32_t* __restrict__ rows,
+                                                      const int32_t* __restrict__ n_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* Qs = reinterpret_cast<float*>(smem);                    // [kDK][kTQ + 4]
   float* Cs = Qs + kDK * (kTQ + 4);                              // [kDK][kTC + 4]
@@ -68,6 +73,9 @@ __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t q0 = (int64_t)blockIdx.x * kTQ;
+  const int64_t nq = rows ? (int64_t)*n_rows : M;
+  if (q0 >= nq) return;
+  auto qrow = [&](int64_t t) -> int64_t { return rows ? (int64_t)rows[t] : t; };
   int nlist = 0;  // used by threads tid < kTQ
 
   for (int64_t c0 = 0; c0 < M; c0 += kTC) {
@@ -81,9 +89,9 @@ __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ 
       // stage a [kDK x 128] slab of queries and candidates, transposed
       for (int e = tid; e < kDK * kTQ; e += kThreads) {
         const int row = e / kDK, dd = e % kDK;
-        const int64_t gq = q0 + row, gc = c0 + row;
+        const int64_t tq = q0 + row, gc = c0 + row;
         const int d = d0 + dd;
-        Qs[dd * (kTQ + 4) + row] = (gq < M && d < N) ? X[gq * N + d] : 0.f;
+        Qs[dd * (kTQ + 4) + row] = (tq < nq && d < N) ? X[qrow(tq) * N + d] : 0.f;
         Cs[dd * (kTC + 4) + row] = (gc < M && d < N) ? X[gc * N + d] : 0.f;
       }
       __syncthreads();
@@ -110,13 +118,13 @@ __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ 
 #pragma unroll
       for (int b = 0; b < 8; ++b) Dt[(ty * 8 + a) * kDStride + tx * 8 + b] = acc[a][b];
     __syncthreads();
-    if (tid < kTQ && q0 + tid < M)
-      merge_row<float>(Dt + tid * kDStride, (int)c0, M, q0 + tid, k, Ld + tid * k, Lj + tid * k,
-                       nlist);
+    if (tid < kTQ && q0 + tid < nq)
+      merge_row<float>(Dt + tid * kDStride, (int)c0, M, qrow(q0 + tid), k, Ld + tid * k,
+                       Lj + tid * k, nlist);
     __syncthreads();
   }
-  if (tid < kTQ && q0 + tid < M)
-    for (int s = 0; s < k; ++s) out[(q0 + tid) * k + s] = Lj[tid * k + s];
+  if (tid < kTQ && q0 + tid < nq)
+    for (int s = 0; s < k; ++s) out[qrow(q0 + tid) * k + s] = Lj[tid * k + s];
 }
 
 __global__ void k_norms_u8(const uint8_t* __restrict__ X, int64_t M, int N,
@@ -209,25 +217,30 @@ __global__ void __launch_bounds__(kThreads) k_knn_u8(const uint8_t* __restrict__
 }
 
 }  // namespace
-}  // namespace ivhd
 
-using namespace ivhd;
+cudaError_t knn_exact_rows_f32(const float* X, int64_t M, int32_t N, int32_t k,
+                               const int32_t* rows, const int32_t* n_rows, int32_t* out_knn,
+                               cudaStream_t s) {
+  const size_t sm = SmemLayout::total(k);
+  cudaError_t e = cudaFuncSetAttribute(k_knn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  // one CTA per 128 possible rows; CTAs past *n_rows return at once
+  k_knn_f32<<<(unsigned)((M + kTQ - 1) / kTQ), kThreads, sm, s>>>(X, M, N, k, out_knn, rows,
+                                                                  n_rows);
+  return cudaGetLastError();
+}
 
-extern "C" ivhd_status ivhd_knn_build(const void* X, int32_t dtype, int64_t M, int32_t N,
-                                      int32_t k, int32_t* out_knn, void* stream) {
-  if (!X || !out_knn) return IVHD_ERR_ARG;
-  if (M < 2 || M >= (int64_t)0x7FFFFFFF || N < 1 || N > 65536) return IVHD_ERR_ARG;
-  if (k < 1 || (int64_t)k > M - 1 || k > 64) return IVHD_ERR_ARG;
-  if (dtype != IVHD_KNN_F32 && dtype != IVHD_KNN_U8) return IVHD_ERR_ARG;
-  if (dtype == IVHD_KNN_U8 && (int64_t)N * 255 * 255 > 0x3FFFFFFF) return IVHD_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+// The CUDA-core build of every row (k <= 64).
+static ivhd_status knn_cuda_cores(const void* X, int32_t dtype, int64_t M, int32_t N, int32_t k,
+                                  int32_t* out_knn, cudaStream_t s) {
   const size_t sm = SmemLayout::total(k);
   const unsigned grid = (unsigned)((M + kTQ - 1) / kTQ);
   cudaError_t e;
   if (dtype == IVHD_KNN_F32) {
     e = cudaFuncSetAttribute(k_knn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return IVHD_ERR_CUDA;
-    k_knn_f32<<<grid, kThreads, sm, s>>>((const float*)X, M, N, k, out_knn);
+    k_knn_f32<<<grid, kThreads, sm, s>>>((const float*)X, M, N, k, out_knn, nullptr, nullptr);
     e = cudaGetLastError();
   } else {
     int32_t* nrm = nullptr;
@@ -241,5 +254,44 @@ extern "C" ivhd_status ivhd_knn_build(const void* X, int32_t dtype, int64_t M, i
     }
     cudaFreeAsync(nrm, s);
   }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? IVHD_OK : IVHD_ERR_CUDA;
+}
+
+}  // namespace ivhd
+
+using namespace ivhd;
+
+extern "C" ivhd_status ivhd_knn_build_ex(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                         int32_t k, int32_t* out_knn, int32_t method,
+                                         ivhd_knn_stats_t* stats, void* stream) {
+  if (!X || !out_knn) return IVHD_ERR_ARG;
+  if (M < 2 || M >= (int64_t)0x7FFFFFFF || N < 1 || N > 65536) return IVHD_ERR_ARG;
+  if (k < 1 || (int64_t)k > M - 1 || k > 64) return IVHD_ERR_ARG;
+  if (dtype != IVHD_KNN_F32 && dtype != IVHD_KNN_U8) return IVHD_ERR_ARG;
+  if (dtype == IVHD_KNN_U8 && (int64_t)N * 255 * 255 > 0x3FFFFFFF) return IVHD_ERR_ARG;
+  if (method < IVHD_KNN_AUTO || method > IVHD_KNN_TENSOR_CORES) return IVHD_ERR_ARG;
+  const bool tc_ok = knn_tc_supported(dtype, M, N, k);
+  if (method == IVHD_KNN_TENSOR_CORES && !tc_ok) return IVHD_ERR_ARG;
+  const bool use_tc = method == IVHD_KNN_TENSOR_CORES || (method == IVHD_KNN_AUTO && tc_ok);
+  cudaStream_t s = (cudaStream_t)stream;
+  ivhd_knn_stats_t st{};
+  st.method = use_tc ? IVHD_KNN_TENSOR_CORES : IVHD_KNN_CUDA_CORES;
+  ivhd_status r;
+  if (use_tc) {
+    KnnTcStats t{};
+    r = knn_tc_build(X, dtype, M, N, k, out_knn, s, &t);
+    st.fallback_rows = t.fallback_rows;
+    st.max_rel_err = t.max_rel_err;
+    st.eps_coef = t.eps_coef;
+  } else {
+    r = knn_cuda_cores(X, dtype, M, N, k, out_knn, s);
+  }
+  if (stats) *stats = st;
+  return r;
+}
+
+extern "C" ivhd_status ivhd_knn_build(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                      int32_t k, int32_t* out_knn, void* stream) {
+  return ivhd_knn_build_ex(X, dtype, M, N, k, out_knn, IVHD_KNN_AUTO, nullptr, stream);
 }

@@ -1,0 +1,544 @@
+// ivhd_knn_tc.cu -- kNN graph build (the set-up step of Sec. 5.1) on the
+// 5th-generation tensor cores: a distance GEMM with the top-k selection fused
+// into its epilogue.
+//
+// Squared distances come from the Gram matrix, |x_i - x_j|^2 = n_i + n_j - 2 <x_i, x_j>.
+//
+// uint8 data: the GEMM runs on x - 128 in BF16.  Every value in [-128, 127]
+//   is exact in BF16, every product (at most 2^14) is exact in FP32, and with
+//   N <= 1024 every partial sum stays below 2^24, so the tensor cores return
+//   <x_i, x_j> exactly whatever their summation order; with the norms of the
+//   shifted rows (exact int32) the distances are the exact integers and the
+//   fused top-k (ties to the lower index) is final.
+// FP32 data: x = hi + lo + r with hi = bf16(x), lo = bf16(x - hi) and
+//   |r| <= 2^-16 |x|; the GEMM over K = 3N of [hi, hi, lo] . [hi, lo, hi] gives
+//   <x_i, x_j> to about 2^-14 of sum_d |x_id x_jd|, so the approximate
+//   distance dt_ij is within eps (n_i + n_j) of the exact FP32-chain distance,
+//   eps = 2^-13 + N 2^-19 (the split, the FP32 accumulation of 3N products and
+//   the chain's own rounding, with a margin of several times).  The epilogue
+//   keeps, per row, the kList smallest keys kappa_j = dt_ij - eps n_j, each a
+//   lower bound of d_ij + eps n_i.  A re-rank pass recomputes the listed
+//   distances with the FP32 chain of the exact kernel, keeps the k best (ties to
+//   the lower index) and certifies the row: every vertex outside the list has
+//   kappa_j >= tau (the list's largest key), hence d_ij >= tau - eps n_i, so
+//   the row is final when its exact k-th distance is below tau - eps n_i.
+//   Other rows are recomputed by the exact CUDA-core kernel.
+//
+// One CTA owns 128 query rows (the 128 tensor-memory lanes) and sweeps all
+// candidates in tiles of 256 columns:
+//   warp 0, one lane   TMA producer: 128 x 64 query and 256 x 64 candidate
+//                      slices into a 4-stage ring (128-byte swizzle)
+//   warp 1, one lane   MMA issuer: tcgen05.mma M=128 N=256 K=16 into one of two
+//                      256-column accumulators in tensor memory (512 columns),
+//                      so the epilogue of tile t overlaps the MMAs of tile t+1
+//   warps 2-5          epilogue: thread = query row; tcgen05.ld of 32 columns at
+//                      a time, distance, compare with the row's list held in
+//                      registers
+// Every wait is bounded; a timeout sets an error flag and all roles stop.
+#include <climits>
+#include <cstring>
+#include <type_traits>
+
+#include "ivhd_internal.cuh"
+#include "ivhd_knn_tc.cuh"
+#include "ivhd_tc.cuh"
+
+namespace ivhd {
+namespace {
+
+using namespace tc;
+
+constexpr int kTM = 128;  // query rows per CTA
+constexpr int kTN = 256;  // candidate columns per accumulator tile
+constexpr int kTStages = 4;
+constexpr int kTcThreads = 192;
+
+struct KnnSmem {
+  static constexpr int a_bytes = kTM * kBK * 2;
+  static constexpr int b_bytes = kTN * kBK * 2;
+  static constexpr int stage_bytes = a_bytes + b_bytes;
+  static constexpr int bar_offset = kTStages * stage_bytes;
+  static constexpr int nrm_offset = bar_offset + 256;  // 4 warps x 32 column terms
+  static constexpr int total = nrm_offset + 512 + 1024;  // + alignment slack
+};
+
+template <class D>
+__device__ __forceinline__ bool better(D d, int j, D bd, int bj) {
+  return d < bd || (d == bd && j < bj);
+}
+
+// Inserts (d, j) into the ascending list (dl, jl) of kList entries, dropping the last.
+template <class D>
+__device__ __forceinline__ void list_insert(D d, int j, D (&dl)[kKnnList], int (&jl)[kKnnList]) {
+#pragma unroll
+  for (int q = 0; q < kKnnList; ++q) {
+    const bool b = better(d, j, dl[q], jl[q]);
+    const D td = dl[q];
+    const int tj = jl[q];
+    dl[q] = b ? d : td;
+    jl[q] = b ? j : tj;
+    d = b ? td : d;
+    j = b ? tj : j;
+  }
+}
+
+// Bounded wait that also stops when another role has given up.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort_flag) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+template <bool U8>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_knn_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+             const float* __restrict__ nrm_f, const int32_t* __restrict__ nrm_i, int M, int Kp,
+             int k, float eps_coef, int32_t* __restrict__ out_ids, float* __restrict__ out_d,
+             int32_t* __restrict__ err) {
+  using D = typename std::conditional<U8, int32_t, float>::type;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + KnnSmem::bar_offset);
+  uint64_t* empty = full + kTStages;
+  uint64_t* acc_full = empty + kTStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;     // [2]
+  uint64_t* done = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* issued = abort_flag + 1;
+  constexpr uint32_t kCols = 2 * kTN;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTM;
+  const int nk = Kp / kBK;
+  const int n_tiles = (M + kTN - 1) / kTN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);  // every epilogue thread arrives
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    *issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: the query slice (re-read from L2 for every tile) and the candidate slice
+      uint32_t g = 0;
+      for (int t = 0; t < n_tiles; ++t) {
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = (int)(g % kTStages);
+          if (g >= kTStages && !wait_or_abort(&empty[s], ((g / kTStages) - 1) & 1, abort_flag)) {
+            atomicOr(err, 1);
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + s * KnnSmem::stage_bytes;
+          unsigned char* sb = sa + KnnSmem::a_bytes;
+          mbar_expect_tx(&full[s], KnnSmem::stage_bytes);
+          tma_load_2d(sa, &map_a, kt * kBK, m0, &full[s]);
+          tma_load_2d(sb, &map_b, kt * kBK, t * kTN, &full[s]);
+          *issued = (int)(g + 1);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = instr_desc_bf16(kTM, kTN);
+      uint32_t g = 0;
+      bool ok = true;
+      for (int t = 0; t < n_tiles && ok; ++t) {
+        const int b = t & 1;
+        if (t >= 2 && !wait_or_abort(&acc_empty[b], ((t >> 1) - 1) & 1, abort_flag)) {
+          atomicOr(err, 2);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t dst = tmem + (uint32_t)(b * kTN);
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = (int)(g % kTStages);
+          if (!wait_or_abort(&full[s], (g / kTStages) & 1, abort_flag)) {
+            atomicOr(err, 4);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sa = smem_u32(smem + s * KnnSmem::stage_bytes);
+          const uint32_t sb = sa + KnnSmem::a_bytes;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            umma_bf16(dst, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc,
+                      (kt > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&acc_full[b]);
+      }
+      // every MMA issued above has finished before tensor memory is released
+      umma_commit(done);
+      if (!mbar_wait(done, 0)) atomicOr(err, 8);
+    }
+  } else {
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31.
+    // Keys: uint8, the exact distance; float, the lower-bound key
+    // kappa_j = dt_j - eps n_j = n_i + (1 - eps) n_j - 2 <x_i, x_j>~ (see the top).
+    // Columns arrive in increasing j, so a key equal to the list's last never
+    // enters (the earlier index wins the tie) and the test is a plain "<".
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    const int i = m0 + r;
+    D* nbuf = reinterpret_cast<D*>(smem + KnnSmem::nrm_offset) + quarter * 32;
+    const D kMaxKey = U8 ? (D)INT_MAX : (D)__int_as_float(0x7f800000);
+    D dl[kKnnList];
+    int jl[kKnnList];
+#pragma unroll
+    for (int q = 0; q < kKnnList; ++q) {
+      dl[q] = kMaxKey;
+      jl[q] = INT_MAX;
+    }
+    const D ni = (i < M) ? (U8 ? (D)nrm_i[i] : (D)nrm_f[i]) : (D)0;
+    const float col_scale = 1.f - eps_coef;
+    bool ok = true;
+    for (int t = 0; t < n_tiles; ++t) {
+      const int b = t & 1;
+      if (!wait_or_abort(&acc_full[b], (t >> 1) & 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN);
+      const int n0 = t * kTN;
+      for (int c0 = 0; c0 < kTN && n0 + c0 < M; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tbase + c0, v);
+        const int jb = n0 + c0;
+        // column terms of these 32 columns through a per-warp staging buffer
+        const int jc = jb + lane;
+        if constexpr (U8)
+          nbuf[lane] = (jc < M) ? nrm_i[jc] : 0;
+        else
+          nbuf[lane] = (jc < M) ? col_scale * nrm_f[jc] : 0.f;
+        __syncwarp();
+        D d[32];
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
+          D nj[4];
+          if constexpr (U8) {
+            const int4 w = *reinterpret_cast<const int4*>(nbuf + q);
+            nj[0] = w.x, nj[1] = w.y, nj[2] = w.z, nj[3] = w.w;
+          } else {
+            const float4 w = *reinterpret_cast<const float4*>(nbuf + q);
+            nj[0] = w.x, nj[1] = w.y, nj[2] = w.z, nj[3] = w.w;
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if constexpr (U8)
+              d[q + e] = ni + nj[e] - 2 * __float2int_rn(__uint_as_float(v[q + e]));
+            else
+              d[q + e] = fmaf(-2.f, __uint_as_float(v[q + e]), ni + nj[e]);
+          }
+        }
+        __syncwarp();
+        if (jb + 31 >= M || (jb <= i && i <= jb + 31)) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (jb + q >= M || jb + q == i) d[q] = kMaxKey;
+        }
+        D mn = d[0];
+#pragma unroll
+        for (int q = 1; q < 32; ++q) mn = min(mn, d[q]);
+        if (mn < dl[kKnnList - 1]) {
+          // rare after the first tiles: insert in column order
+          D tmp[32];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) tmp[q] = d[q];
+#pragma unroll 1
+          for (int q = 0; q < 32; ++q)
+            if (tmp[q] < dl[kKnnList - 1]) list_insert<D>(tmp[q], jb + q, dl, jl);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(&acc_empty[b]);
+    }
+    if (ok && i < M) {
+      if constexpr (U8) {
+#pragma unroll
+        for (int q = 0; q < kKnnList; ++q)
+          if (q < k) out_ids[(int64_t)i * k + q] = jl[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < kKnnList; ++q) {
+          out_ids[(int64_t)i * kKnnList + q] = jl[q];
+          out_d[(int64_t)i * kKnnList + q] = dl[q];
+        }
+      }
+    }
+    if (!ok && lane == 0) atomicOr(err, 16);
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) {
+    // drain copies still in flight before the shared memory goes away
+    const int iss = *issued;
+    for (int g = (iss > kTStages ? iss - kTStages : 0); g < iss; ++g)
+      mbar_wait(&full[g % kTStages], (g / kTStages) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+// ---- operand preparation ---------------------------------------------------
+
+// FP32: A = [hi | hi | lo], B = [hi | lo | hi] along K (3N, zero-padded to Kp).
+__global__ void k_prep_f32(const float* __restrict__ X, int64_t M, int N, int Kp,
+                           __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * Kp) return;
+  const int64_t i = e / Kp;
+  const int c = (int)(e - i * Kp);
+  const int seg = c / N, d = c - seg * N;
+  __nv_bfloat16 a = __float2bfloat16_rn(0.f), b = a;
+  if (seg < 3) {
+    const float x = X[i * N + d];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    a = (seg == 2) ? lo : hi;
+    b = (seg == 1) ? lo : hi;
+  }
+  A[e] = a;
+  B[e] = b;
+}
+
+// FP32 norms (FP64 sum, rounded once).
+__global__ void k_norms_f32(const float* __restrict__ X, int64_t M, int N, float* __restrict__ nrm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double s = 0.0;
+  for (int d = 0; d < N; ++d) {
+    const double x = X[i * N + d];
+    s += x * x;
+  }
+  nrm[i] = (float)s;
+}
+
+// uint8: A = B = x - 128 (zero-padded to Kp); norms of the shifted rows.
+__global__ void k_prep_u8(const uint8_t* __restrict__ X, int64_t M, int N, int Kp,
+                          __nv_bfloat16* __restrict__ A) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * Kp) return;
+  const int64_t i = e / Kp;
+  const int c = (int)(e - i * Kp);
+  A[e] = __float2bfloat16_rn(c < N ? (float)X[i * N + c] - 128.f : 0.f);
+}
+
+__global__ void k_norms_u8s(const uint8_t* __restrict__ X, int64_t M, int N,
+                            int32_t* __restrict__ nrm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  int32_t s = 0;
+  for (int d = 0; d < N; ++d) {
+    const int32_t v = (int32_t)X[i * N + d] - 128;
+    s += v * v;
+  }
+  nrm[i] = s;
+}
+
+// ---- FP32 re-rank and certificate (warp per row, lane = candidate) --------
+
+__device__ __forceinline__ void cas(float& d, int& j, int lane, int mask, bool up) {
+  const float od = __shfl_xor_sync(0xffffffffu, d, mask);
+  const int oj = __shfl_xor_sync(0xffffffffu, j, mask);
+  const bool lower = (lane & mask) == 0;
+  // the lower lane keeps the smaller pair when sorting up
+  const bool mine_better = better(d, j, od, oj);
+  const bool keep = (lower == up) ? mine_better : !mine_better;
+  if (!keep) {
+    d = od;
+    j = oj;
+  }
+}
+
+__global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
+                         const int32_t* __restrict__ cand, const float* __restrict__ key,
+                         const float* __restrict__ nrm, float eps_coef, int32_t* __restrict__ out,
+                         int32_t* __restrict__ fb_rows, int32_t* __restrict__ n_fb,
+                         int32_t* __restrict__ max_err_bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= M) return;
+  const int j0 = cand[i * kKnnList + lane];
+  const float kj = key[i * kKnnList + lane];
+  const float tau = __shfl_sync(0xffffffffu, kj, kKnnList - 1);
+  float d = __int_as_float(0x7f800000);
+  int j = INT_MAX;
+  float rel = 0.f;
+  if (j0 >= 0 && j0 < M) {
+    const float* xi = X + i * N;
+    const float* xj = X + (int64_t)j0 * N;
+    float acc = 0.f;
+    for (int q = 0; q < N; ++q) {
+      const float diff = __fsub_rn(xi[q], xj[q]);
+      acc = __fmaf_rn(diff, diff, acc);
+    }
+    d = acc;
+    j = j0;
+    // the approximate distance is the key plus eps n_j
+    rel = fabsf(fmaf(eps_coef, nrm[j0], kj) - acc) / fmaxf(nrm[i] + nrm[j0], 1e-30f);
+  }
+  // bitonic sort of the 32 (d, j) pairs, ascending
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1)
+#pragma unroll
+    for (int m = kk >> 1; m > 0; m >>= 1) cas(d, j, lane, m, (lane & kk) == 0);
+  float mrel = rel;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mrel = fmaxf(mrel, __shfl_xor_sync(0xffffffffu, mrel, o));
+  const float dk = __shfl_sync(0xffffffffu, d, k - 1);
+  const int jlast = __shfl_sync(0xffffffffu, j0, kKnnList - 1);
+  // a list that is not full, or that holds every other vertex, leaves nothing out;
+  // otherwise every vertex j outside it has an exact distance >= tau - eps n_i
+  const bool full_list = jlast >= 0 && jlast < M && (int64_t)M - 1 > kKnnList;
+  const bool certified = !full_list || dk < tau - eps_coef * nrm[i];
+  if (certified) {
+    if (lane < k) out[i * k + lane] = j;
+  } else if (lane == 0) {
+    fb_rows[atomicAdd(n_fb, 1)] = (int32_t)i;
+  }
+  if (lane == 0) atomicMax(max_err_bits, __float_as_int(mrel));
+}
+
+template <bool U8>
+cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float* nrm_f,
+                      const int32_t* nrm_i, int M, int Kp, int k, float eps_coef, int32_t* out_ids,
+                      float* out_d, int32_t* err, cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_knn_tc<U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         KnnSmem::total);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  const unsigned grid = (unsigned)((M + kTM - 1) / kTM);
+  k_knn_tc<U8><<<grid, kTcThreads, KnnSmem::total, s>>>(ma, mb, nrm_f, nrm_i, M, Kp, k, eps_coef,
+                                                         out_ids, out_d, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool knn_tc_supported(int32_t dtype, int64_t M, int32_t N, int32_t k) {
+  if (k < 1 || k > kKnnList || M < 2 || M > (1 << 30)) return false;
+  if (dtype == IVHD_KNN_U8) return N <= 1024;
+  return (int64_t)3 * N <= 65536;
+}
+
+// Device scratch freed on scope exit (stream-ordered).
+namespace {
+struct Bufs {
+  cudaStream_t s;
+  void* p[12] = {};
+  int n = 0;
+  bool ok = true;
+  explicit Bufs(cudaStream_t st) : s(st) {}
+  template <class T>
+  T* get(int64_t count) {
+    void* q = nullptr;
+    if (cudaMallocAsync(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s) != cudaSuccess) {
+      ok = false;
+      return nullptr;
+    }
+    p[n++] = q;
+    return (T*)q;
+  }
+  ~Bufs() {
+    for (int q = 0; q < n; ++q) cudaFreeAsync(p[q], s);
+  }
+};
+}  // namespace
+
+ivhd_status knn_tc_build(const void* X, int32_t dtype, int64_t M, int32_t N, int32_t k,
+                         int32_t* out_knn, cudaStream_t s, KnnTcStats* stats) {
+  const bool u8 = dtype == IVHD_KNN_U8;
+  const int Kp = (int)((((u8 ? (int64_t)N : 3 * (int64_t)N) + kBK - 1) / kBK) * kBK);
+  Bufs b(s);
+  __nv_bfloat16* A = b.get<__nv_bfloat16>(M * Kp);
+  __nv_bfloat16* B = u8 ? A : b.get<__nv_bfloat16>(M * Kp);
+  int32_t* err = b.get<int32_t>(8);  // err, n_fb, max-err bits
+  if (!b.ok) return IVHD_ERR_OOM;
+  cudaError_t e = cudaMemsetAsync(err, 0, 8 * sizeof(int32_t), s);
+  int32_t* n_fb = err + 1;
+  int32_t* maxerr_bits = err + 2;
+  const unsigned gprep = (unsigned)((M * Kp + 255) / 256);
+  const unsigned grow = (unsigned)((M + 255) / 256);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, Kp, Kp, kTM) || !make_map(&mb, B, M, Kp, Kp, kTN))
+    return IVHD_ERR_CUDA;
+  const float eps_coef = (float)(1.0 / 8192.0 + (double)N / 524288.0);
+  if (u8) {
+    int32_t* nrm = b.get<int32_t>(M);
+    if (!b.ok) return IVHD_ERR_OOM;
+    if (e == cudaSuccess) {
+      k_prep_u8<<<gprep, 256, 0, s>>>((const uint8_t*)X, M, N, Kp, A);
+      k_norms_u8s<<<grow, 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
+      e = launch_tc<true>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, out_knn, nullptr, err, s);
+    }
+  } else {
+    float* nrm = b.get<float>(M);
+    int32_t* cand = b.get<int32_t>(M * kKnnList);
+    float* cd = b.get<float>(M * kKnnList);
+    int32_t* fb = b.get<int32_t>(M);
+    if (!b.ok) return IVHD_ERR_OOM;
+    if (e == cudaSuccess) {
+      k_prep_f32<<<gprep, 256, 0, s>>>((const float*)X, M, N, Kp, A, B);
+      k_norms_f32<<<grow, 256, 0, s>>>((const float*)X, M, N, nrm);
+      e = launch_tc<false>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef, cand, cd, err, s);
+    }
+    if (e == cudaSuccess) {
+      k_rerank<<<(unsigned)((M + 7) / 8), 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd,
+                                                      nrm, eps_coef, out_knn, fb, n_fb,
+                                                      maxerr_bits);
+      e = cudaGetLastError();
+    }
+    // rows without a certificate: the exact CUDA-core kernel on just those rows
+    if (e == cudaSuccess) e = knn_exact_rows_f32((const float*)X, M, N, k, fb, n_fb, out_knn, s);
+  }
+  int32_t h[8] = {};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  if (stats) {
+    stats->fallback_rows = u8 ? 0 : h[1];
+    float mre = 0.f;
+    std::memcpy(&mre, &h[2], sizeof(mre));
+    stats->max_rel_err = u8 ? 0.f : mre;
+    stats->eps_coef = u8 ? 0.f : eps_coef;
+  }
+  return h[0] ? IVHD_ERR_TIMEOUT : IVHD_OK;
+}
+
+}  // namespace ivhd

@@ -236,8 +236,17 @@ class Embedding:
         check(self._L.ivhd_set_state(self._h, buf, len(state)), "ivhd_set_state")
 
 
-def knn_build(X: torch.Tensor, k: int, stream=None) -> torch.Tensor:
-    """Exact kNN graph of the rows of X (float32 or uint8 CUDA tensor) -> int32 [M, k]."""
+KNN_METHODS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
+
+
+def knn_build(X: torch.Tensor, k: int, stream=None, method: str = "auto",
+              return_stats: bool = False):
+    """Exact kNN graph of the rows of X (float32 or uint8 CUDA tensor) -> int32 [M, k].
+
+    method: "auto" (tensor cores when they apply), "cuda_cores" or "tensor_cores";
+    the graph is the same for every method.  return_stats adds a dict with the
+    method that ran, the rows recomputed after a failed certificate, and the
+    largest observed approximation error against the bound."""
     L = _lib.load()
     if not X.is_cuda:
         raise ValueError("knn_build expects a CUDA tensor")
@@ -250,8 +259,13 @@ def knn_build(X: torch.Tensor, k: int, stream=None) -> torch.Tensor:
         raise ValueError("X must be float32 or uint8")
     M, N = int(X.shape[0]), int(X.shape[1])
     out = torch.empty((M, k), dtype=torch.int32, device=X.device)
-    check(L.ivhd_knn_build(X.data_ptr(), dt, M, N, int(k), out.data_ptr(), _stream_ptr(stream)),
-          "ivhd_knn_build")
+    st = _lib.KnnStats()
+    check(L.ivhd_knn_build_ex(X.data_ptr(), dt, M, N, int(k), out.data_ptr(), KNN_METHODS[method],
+                              ctypes.byref(st), _stream_ptr(stream)), "ivhd_knn_build_ex")
+    if return_stats:
+        names = {v: n for n, v in KNN_METHODS.items()}
+        return out, {"method": names[st.method], "fallback_rows": st.fallback_rows,
+                     "max_rel_err": st.max_rel_err, "eps_coef": st.eps_coef}
     return out
 
 
