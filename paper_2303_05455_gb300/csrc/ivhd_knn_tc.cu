@@ -58,8 +58,8 @@ struct KnnSmem {
   static constexpr int b_bytes = kTN * kBK * 2;
   static constexpr int stage_bytes = a_bytes + b_bytes;
   static constexpr int bar_offset = kTStages * stage_bytes;
-  static constexpr int nrm_offset = bar_offset + 256;  // 4 warps x 32 column terms
-  static constexpr int total = nrm_offset + 512 + 1024;  // + alignment slack
+  static constexpr int nrm_offset = bar_offset + 256;  // 4 warps x 256 column terms
+  static constexpr int total = nrm_offset + 4 * kTN * 4 + 1024;  // + alignment slack
 };
 
 template <class D>
@@ -67,11 +67,11 @@ __device__ __forceinline__ bool better(D d, int j, D bd, int bj) {
   return d < bd || (d == bd && j < bj);
 }
 
-// Inserts (d, j) into the ascending list (dl, jl) of kList entries, dropping the last.
-template <class D>
-__device__ __forceinline__ void list_insert(D d, int j, D (&dl)[kKnnList], int (&jl)[kKnnList]) {
+// Inserts (d, j) into the ascending list (dl, jl) of L entries, dropping the last.
+template <class D, int L>
+__device__ __forceinline__ void list_insert(D d, int j, D (&dl)[L], int (&jl)[L]) {
 #pragma unroll
-  for (int q = 0; q < kKnnList; ++q) {
+  for (int q = 0; q < L; ++q) {
     const bool b = better(d, j, dl[q], jl[q]);
     const D td = dl[q];
     const int tj = jl[q];
@@ -93,7 +93,8 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
   return false;
 }
 
-template <bool U8>
+// U8: exact integer keys; L: list length (kKnnList for float, 8 or kKnnList for uint8).
+template <bool U8, int L>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_knn_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
              const float* __restrict__ nrm_f, const int32_t* __restrict__ nrm_i, int M, int Kp,
@@ -209,18 +210,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;
     const int i = m0 + r;
-    D* nbuf = reinterpret_cast<D*>(smem + KnnSmem::nrm_offset) + quarter * 32;
+    // the tile's 256 column terms, staged per warp; each lane prefetches its 8
+    // terms of the next tile into registers while the current one is processed
+    D* nbuf = reinterpret_cast<D*>(smem + KnnSmem::nrm_offset) + quarter * kTN;
+    constexpr int kPer = kTN / 32;
     const D kMaxKey = U8 ? (D)INT_MAX : (D)__int_as_float(0x7f800000);
-    D dl[kKnnList];
-    int jl[kKnnList];
+    const float col_scale = 1.f - eps_coef;
+    D pn[kPer];
+    auto fetch = [&](int t) {
 #pragma unroll
-    for (int q = 0; q < kKnnList; ++q) {
+      for (int e = 0; e < kPer; ++e) {
+        const int jc = t * kTN + e * 32 + lane;
+        if constexpr (U8)
+          pn[e] = (jc < M) ? nrm_i[jc] : 0;
+        else
+          pn[e] = (jc < M) ? col_scale * nrm_f[jc] : 0.f;
+      }
+    };
+    D dl[L];
+    int jl[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
       dl[q] = kMaxKey;
       jl[q] = INT_MAX;
     }
     const D ni = (i < M) ? (U8 ? (D)nrm_i[i] : (D)nrm_f[i]) : (D)0;
-    const float col_scale = 1.f - eps_coef;
     bool ok = true;
+    fetch(0);
     for (int t = 0; t < n_tiles; ++t) {
       const int b = t & 1;
       if (!wait_or_abort(&acc_full[b], (t >> 1) & 1, abort_flag)) {
@@ -228,28 +244,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) nbuf[e * 32 + lane] = pn[e];
+      __syncwarp();
+      if (t + 1 < n_tiles) fetch(t + 1);
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN);
       const int n0 = t * kTN;
-      for (int c0 = 0; c0 < kTN && n0 + c0 < M; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tbase + c0, v);
+      for (int c0 = 0; c0 < kTN && n0 + c0 < M; c0 += 64) {
+        uint32_t v[64];
+        tmem_ld32_nowait(tbase + c0, v);
+        tmem_ld32_nowait(tbase + c0 + 32, v + 32);
+        tmem_wait_ld();
         const int jb = n0 + c0;
-        // column terms of these 32 columns through a per-warp staging buffer
-        const int jc = jb + lane;
-        if constexpr (U8)
-          nbuf[lane] = (jc < M) ? nrm_i[jc] : 0;
-        else
-          nbuf[lane] = (jc < M) ? col_scale * nrm_f[jc] : 0.f;
-        __syncwarp();
-        D d[32];
+        D d[64];
 #pragma unroll
-        for (int q = 0; q < 32; q += 4) {
+        for (int q = 0; q < 64; q += 4) {
           D nj[4];
           if constexpr (U8) {
-            const int4 w = *reinterpret_cast<const int4*>(nbuf + q);
+            const int4 w = *reinterpret_cast<const int4*>(nbuf + c0 + q);
             nj[0] = w.x, nj[1] = w.y, nj[2] = w.z, nj[3] = w.w;
           } else {
-            const float4 w = *reinterpret_cast<const float4*>(nbuf + q);
+            const float4 w = *reinterpret_cast<const float4*>(nbuf + c0 + q);
             nj[0] = w.x, nj[1] = w.y, nj[2] = w.z, nj[3] = w.w;
           }
 #pragma unroll
@@ -260,23 +276,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               d[q + e] = fmaf(-2.f, __uint_as_float(v[q + e]), ni + nj[e]);
           }
         }
-        __syncwarp();
-        if (jb + 31 >= M || (jb <= i && i <= jb + 31)) {
+        if (jb + 63 >= M || (jb <= i && i <= jb + 63)) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
+          for (int q = 0; q < 64; ++q)
             if (jb + q >= M || jb + q == i) d[q] = kMaxKey;
         }
         D mn = d[0];
 #pragma unroll
-        for (int q = 1; q < 32; ++q) mn = min(mn, d[q]);
-        if (mn < dl[kKnnList - 1]) {
-          // rare after the first tiles: insert in column order
-          D tmp[32];
+        for (int q = 1; q < 64; ++q) mn = min(mn, d[q]);
+        if (mn < dl[L - 1]) {
+          // rare after the first tiles: visit the columns below the threshold in order
+          const D thr = dl[L - 1];
+          uint64_t mask = 0;
+          D tmp[64];
 #pragma unroll
-          for (int q = 0; q < 32; ++q) tmp[q] = d[q];
-#pragma unroll 1
-          for (int q = 0; q < 32; ++q)
-            if (tmp[q] < dl[kKnnList - 1]) list_insert<D>(tmp[q], jb + q, dl, jl);
+          for (int q = 0; q < 64; ++q) {
+            mask |= (uint64_t)(d[q] < thr) << q;
+            tmp[q] = d[q];
+          }
+          while (mask) {
+            const int q = __ffsll((long long)mask) - 1;
+            mask &= mask - 1;
+            if (tmp[q] < dl[L - 1]) list_insert<D, L>(tmp[q], jb + q, dl, jl);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -285,13 +307,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (ok && i < M) {
       if constexpr (U8) {
 #pragma unroll
-        for (int q = 0; q < kKnnList; ++q)
+        for (int q = 0; q < L; ++q)
           if (q < k) out_ids[(int64_t)i * k + q] = jl[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < kKnnList; ++q) {
-          out_ids[(int64_t)i * kKnnList + q] = jl[q];
-          out_d[(int64_t)i * kKnnList + q] = dl[q];
+        for (int q = 0; q < L; ++q) {
+          out_ids[(int64_t)i * L + q] = jl[q];
+          out_d[(int64_t)i * L + q] = dl[q];
         }
       }
     }
@@ -430,7 +452,7 @@ __global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
   if (lane == 0) atomicMax(max_err_bits, __float_as_int(mrel));
 }
 
-template <bool U8>
+template <bool U8, int L>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float* nrm_f,
                       const int32_t* nrm_i, int M, int Kp, int k, float eps_coef, int32_t* out_ids,
                       float* out_d, int32_t* err, cudaStream_t s) {
@@ -438,14 +460,15 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float*
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_knn_tc<U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_knn_tc<U8, L>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          KnnSmem::total);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   const unsigned grid = (unsigned)((M + kTM - 1) / kTM);
-  k_knn_tc<U8><<<grid, kTcThreads, KnnSmem::total, s>>>(ma, mb, nrm_f, nrm_i, M, Kp, k, eps_coef,
-                                                         out_ids, out_d, err);
+  k_knn_tc<U8, L><<<grid, kTcThreads, KnnSmem::total, s>>>(ma, mb, nrm_f, nrm_i, M, Kp, k,
+                                                            eps_coef, out_ids, out_d, err);
   return cudaGetLastError();
 }
 
@@ -505,7 +528,10 @@ ivhd_status knn_tc_build(const void* X, int32_t dtype, int64_t M, int32_t N, int
     if (e == cudaSuccess) {
       k_prep_u8<<<gprep, 256, 0, s>>>((const uint8_t*)X, M, N, Kp, A);
       k_norms_u8s<<<grow, 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
-      e = launch_tc<true>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, out_knn, nullptr, err, s);
+      e = (k <= 8) ? launch_tc<true, 8>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, out_knn, nullptr,
+                                        err, s)
+                   : launch_tc<true, kKnnList>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, out_knn,
+                                               nullptr, err, s);
     }
   } else {
     float* nrm = b.get<float>(M);
@@ -516,7 +542,8 @@ ivhd_status knn_tc_build(const void* X, int32_t dtype, int64_t M, int32_t N, int
     if (e == cudaSuccess) {
       k_prep_f32<<<gprep, 256, 0, s>>>((const float*)X, M, N, Kp, A, B);
       k_norms_f32<<<grow, 256, 0, s>>>((const float*)X, M, N, nrm);
-      e = launch_tc<false>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef, cand, cd, err, s);
+      e = launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef, cand, cd, err,
+                                     s);
     }
     if (e == cudaSuccess) {
       k_rerank<<<(unsigned)((M + 7) / 8), 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd,
