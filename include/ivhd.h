@@ -488,6 +488,25 @@ ivhd_status ivhd_eval_qnx_static(const float *Y, int64_t M, const int32_t *knn, 
                                  const int64_t *rows, int64_t nrows, int32_t *out_lowd,
                                  double *out_q, void *stream);
 
+/*
+ * Test support (the paper has no counterpart).
+ *
+ * ivhd_probe_wait_timeout runs, in one thread of one block, the bounded
+ * mbarrier wait that the tensor-core kernels use, on a barrier that nothing
+ * completes, for `polls` polls; returns IVHD_ERR_TIMEOUT (the expected result)
+ * without faulting or hanging, after which the library and the stream remain
+ * usable.  polls >= 1, else IVHD_ERR_ARG.  Synchronises.
+ *
+ * ivhd_test_fail_alloc(after): the next `after` device allocations made by the
+ * library succeed and the one after them fails with IVHD_ERR_OOM at the
+ * calling entry point (once; after < 0 switches the injection off).
+ * ivhd_test_live_allocs: device allocations made by the library and not yet
+ * released, to check that every error path frees what it took.  Process-wide.
+ */
+ivhd_status ivhd_probe_wait_timeout(int32_t polls, void *stream);
+void ivhd_test_fail_alloc(int64_t after);
+int64_t ivhd_test_live_allocs(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,8 @@ SYMBOLS = (
     "ivhd_restrict_nn", "ivhd_adaptive_state", "ivhd_create_batch", "ivhd_autotune",
     "ivhd_gemm_bf16_tn", "ivhd_mlp_create", "ivhd_mlp_destroy", "ivhd_mlp_num_params",
     "ivhd_mlp_set_params", "ivhd_mlp_get_params", "ivhd_mlp_loss_grad", "ivhd_mlp_train_step",
-    "ivhd_mlp_forward", "ivhd_mlp_launches",
+    "ivhd_mlp_forward", "ivhd_mlp_launches", "ivhd_probe_wait_timeout", "ivhd_test_fail_alloc",
+    "ivhd_test_live_allocs",
 )
 
 
@@ -115,6 +116,12 @@ def load(build_if_missing: bool = False):
     L.ivhd_knn_build.restype = i32
     L.ivhd_knn_build_ex.argtypes = [P, i32, i64, i32, i32, P, i32, P, P]
     L.ivhd_knn_build_ex.restype = i32
+    L.ivhd_probe_wait_timeout.argtypes = [i32, P]
+    L.ivhd_probe_wait_timeout.restype = i32
+    L.ivhd_test_fail_alloc.argtypes = [i64]
+    L.ivhd_test_fail_alloc.restype = None
+    L.ivhd_test_live_allocs.argtypes = []
+    L.ivhd_test_live_allocs.restype = i64
     L.ivhd_eval_qnx.argtypes = [P, i64, P, i32, P, i64, P, ctypes.POINTER(ctypes.c_double), P]
     L.ivhd_eval_qnx.restype = i32
     L.ivhd_eval_cf.argtypes = [P, i64, P, i32, P, i64, ctypes.POINTER(ctypes.c_double), P]

@@ -4,9 +4,49 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <atomic>
+
 #include "ivhd_internal.cuh"
 
+namespace ivhd {
+
+static std::atomic<int64_t> g_live_allocs{0};
+static std::atomic<int64_t> g_fail_after{-1};  // allocations to grant before one fails; -1 = off
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  int64_t f = g_fail_after.load();
+  while (f >= 0) {
+    if (f == 0) {
+      if (g_fail_after.compare_exchange_weak(f, -1)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+    } else if (g_fail_after.compare_exchange_weak(f, f - 1)) {
+      break;
+    }
+  }
+  const cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+cudaError_t dev_free(void* p, cudaStream_t s) {
+  if (!p) return cudaSuccess;
+  g_live_allocs.fetch_sub(1);
+  return cudaFreeAsync(p, s);
+}
+
+NvtxScope::NvtxScope(const char* name) { nvtxRangePushA(name); }
+NvtxScope::~NvtxScope() { nvtxRangePop(); }
+
+}  // namespace ivhd
+
 using namespace ivhd;
+
+extern "C" void ivhd_test_fail_alloc(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
+extern "C" int64_t ivhd_test_live_allocs(void) { return g_live_allocs.load(); }
 
 namespace {
 
@@ -60,7 +100,7 @@ void free_layout(ivhd_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   void* bufs[] = {ctx->ids, ctx->hub_off, ctx->slice_off, ctx->slice_w, ctx->partials};
   for (void* b : bufs)
-    if (b) cudaFreeAsync(b, s);
+    if (b) dev_free(b, s);
   ctx->ids = nullptr;
   ctx->hub_off = ctx->slice_off = ctx->slice_w = nullptr;
   ctx->partials = nullptr;
@@ -75,14 +115,14 @@ void free_ctx(ivhd_ctx* ctx) {
                   ctx->red_out, ctx->flag, ctx->seg_of, ctx->seg_lo, ctx->seg_n, ctx->seg_r,
                   ctx->seg_seed};
   for (void* b : bufs)
-    if (b) cudaFreeAsync(b, s);
+    if (b) dev_free(b, s);
   cudaStreamSynchronize(s);
   delete ctx;
 }
 
 template <class T>
 cudaError_t dalloc(T** p, int64_t n, cudaStream_t s) {
-  return cudaMallocAsync((void**)p, (size_t)(n > 0 ? n : 1) * sizeof(T), s);
+  return dev_alloc((void**)p, (size_t)(n > 0 ? n : 1) * sizeof(T), s);
 }
 
 // With self-adaptive b the current buffer is chosen on the device; host code
@@ -165,7 +205,7 @@ ivhd_status rebuild_preserving_state(ivhd_ctx* ctx, bool draw_rn, uint64_t epoch
     e = launch_from_input_order(ctx, save[q], src[q]);
   if (e == cudaSuccess && st == IVHD_OK) e = launch_round_positions(ctx);
   for (int q = 0; q < n; ++q)
-    if (save[q]) cudaFreeAsync(save[q], s);
+    if (save[q]) dev_free(save[q], s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, e);
   if (st != IVHD_OK) ctx->poisoned = true;  // the layout is gone
@@ -312,6 +352,7 @@ extern "C" {
 
 ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, float c,
                         const ivhd_params* p_in, int32_t knn_on_device, ivhd_ctx** out) {
+  NvtxScope nvtx_("ivhd_create");
   if (!out) return IVHD_ERR_ARG;
   *out = nullptr;
   if (!knn) return IVHD_ERR_ARG;
@@ -388,12 +429,13 @@ ivhd_status ivhd_set_positions(ivhd_ctx* ctx, const float* xy, int32_t on_device
     src = tmp;
   }
   if (e == cudaSuccess) e = launch_set_positions(ctx, src);
-  if (tmp) cudaFreeAsync(tmp, s);
+  if (tmp) dev_free(tmp, s);
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s);
   return fail(ctx, e);
 }
 
 ivhd_status ivhd_step(ivhd_ctx* ctx, int64_t n_iter) {
+  NvtxScope nvtx_("ivhd_step");
   if (!ctx || n_iter < 0) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
@@ -445,6 +487,7 @@ ivhd_status ivhd_step(ivhd_ctx* ctx, int64_t n_iter) {
 }
 
 ivhd_status ivhd_positions(ivhd_ctx* ctx, float* out, int32_t on_device) {
+  NvtxScope nvtx_("ivhd_positions");
   if (!ctx || !out) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
@@ -457,12 +500,13 @@ ivhd_status ivhd_positions(ivhd_ctx* ctx, float* out, int32_t on_device) {
   if (e == cudaSuccess) e = launch_unpermute(ctx, tmp);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, tmp, (size_t)M * sizeof(float2), cudaMemcpyDeviceToHost, s);
-  if (tmp) cudaFreeAsync(tmp, s);
+  if (tmp) dev_free(tmp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return fail(ctx, e);
 }
 
 ivhd_status ivhd_forces(ivhd_ctx* ctx, float* out, int32_t on_device) {
+  NvtxScope nvtx_("ivhd_forces");
   if (!ctx || !out) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
@@ -475,12 +519,13 @@ ivhd_status ivhd_forces(ivhd_ctx* ctx, float* out, int32_t on_device) {
   if (e == cudaSuccess) e = launch_forces(ctx, tmp);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, tmp, (size_t)M * sizeof(float2), cudaMemcpyDeviceToHost, s);
-  if (tmp) cudaFreeAsync(tmp, s);
+  if (tmp) dev_free(tmp, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return fail(ctx, e);
 }
 
 ivhd_status ivhd_stress(ivhd_ctx* ctx, double* out) {
+  NvtxScope nvtx_("ivhd_stress");
   if (!ctx || !out) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
@@ -551,7 +596,7 @@ ivhd_status ivhd_restrict_nn(ivhd_ctx* ctx, const int32_t* helper, int32_t k_hel
     e = cudaMemcpyAsync(ctx->knn, ctx->knn_full, (size_t)(M * k) * sizeof(int32_t),
                         cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(ctx, e);
-    cudaFreeAsync(ctx->knn_full, s);
+    dev_free(ctx->knn_full, s);
     ctx->knn_full = nullptr;
     return rebuild_preserving_state(ctx, false, 0);
   }
@@ -585,8 +630,8 @@ ivhd_status ivhd_restrict_nn(ivhd_ctx* ctx, const int32_t* helper, int32_t k_hel
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
-  if (hd) cudaFreeAsync(hd, s);
-  if (err) cudaFreeAsync(err, s);
+  if (hd) dev_free(hd, s);
+  if (err) dev_free(err, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, e);
   if (herr) {  // bad helper ids: put the full graph back untouched
@@ -732,6 +777,7 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
                                          const uint64_t* seed_e, int32_t n_emb, float c,
                                          const ivhd_params* p_in, int32_t knn_on_device,
                                          ivhd_ctx** out) {
+  NvtxScope nvtx_("ivhd_create_batch");
   if (!out) return IVHD_ERR_ARG;
   *out = nullptr;
   if (!knn || !M_e || !k_e || !r_e || !seed_e || n_emb < 1 || n_emb > (1 << 20))
@@ -812,10 +858,10 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
     chk(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s));
     chk(cudaStreamSynchronize(s));
   }
-  if (local) cudaFreeAsync(local, s);
-  if (row0_d) cudaFreeAsync(row0_d, s);
-  if (err) cudaFreeAsync(err, s);
-  if (kd) cudaFreeAsync(kd, s);
+  if (local) dev_free(local, s);
+  if (row0_d) dev_free(row0_d, s);
+  if (err) dev_free(err, s);
+  if (kd) dev_free(kd, s);
   if (e != cudaSuccess || herr) {
     ivhd_status st = herr ? IVHD_ERR_INDEX : cuda_status(e);
     free_ctx(ctx);
@@ -827,6 +873,7 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
 
 extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t* best_block,
                                      int32_t* best_hub_threshold, float* best_us_per_step) {
+  NvtxScope nvtx_("ivhd_autotune");
   if (!ctx || trial_steps < 1) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
@@ -875,7 +922,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
     st = build_layout(ctx, false, 0);
     for (int bi = 0; bi < 3 && e == cudaSuccess && st == IVHD_OK; ++bi) {
       ctx->block = blocks[bi];
-      if (ctx->partials) cudaFreeAsync(ctx->partials, s);
+      if (ctx->partials) dev_free(ctx->partials, s);
       ctx->partials = nullptr;
       e = alloc_partials(ctx);
       if (e == cudaSuccess) e = restore();
@@ -912,7 +959,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
   }
   ctx->steps_done = steps_before;
   for (int q = 0; q < n; ++q)
-    if (save[q]) cudaFreeAsync(save[q], s);
+    if (save[q]) dev_free(save[q], s);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail(ctx, e);

@@ -533,7 +533,7 @@ struct Scratch {
   template <class T>
   T* get(int64_t n) {
     void* q = nullptr;
-    if (cudaMallocAsync(&q, (size_t)(n > 0 ? n : 1) * sizeof(T), s) != cudaSuccess) {
+    if (dev_alloc(&q, (size_t)(n > 0 ? n : 1) * sizeof(T), s) != cudaSuccess) {
       ok = false;
       return nullptr;
     }
@@ -541,7 +541,7 @@ struct Scratch {
     return (T*)q;
   }
   ~Scratch() {
-    for (void* q : bufs) cudaFreeAsync(q, s);
+    for (void* q : bufs) dev_free(q, s);
   }
 };
 
@@ -720,10 +720,10 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
   if (draw_rn) ctx->empty_rn = (int32_t)h.empty;
   if (ctx->n_slots >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
 
-  IVHD_TRY(cudaMallocAsync((void**)&ctx->ids, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
-  IVHD_TRY(cudaMallocAsync((void**)&ctx->hub_off, (size_t)(ctx->n_hub + 1) * sizeof(int32_t), s));
-  IVHD_TRY(cudaMallocAsync((void**)&ctx->slice_off, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
-  IVHD_TRY(cudaMallocAsync((void**)&ctx->slice_w, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
+  IVHD_TRY(dev_alloc((void**)&ctx->ids, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
+  IVHD_TRY(dev_alloc((void**)&ctx->hub_off, (size_t)(ctx->n_hub + 1) * sizeof(int32_t), s));
+  IVHD_TRY(dev_alloc((void**)&ctx->slice_off, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
+  IVHD_TRY(dev_alloc((void**)&ctx->slice_w, (size_t)(ctx->n_slices + 1) * sizeof(int32_t), s));
   IVHD_TRY(cudaMemsetAsync(ctx->ids, 0xFF, (size_t)(ctx->n_slots + 4) * sizeof(uint32_t), s));
   k_offsets_i32<<<nblk(ctx->n_hub + 1), kB, 0, s>>>(hub_o64, ctx->n_hub, 0, ctx->hub_off);
   k_offsets_i32<<<nblk(ctx->n_slices + 1), kB, 0, s>>>(sl_o64, ctx->n_slices, h.hub_total,

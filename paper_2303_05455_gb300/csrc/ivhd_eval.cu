@@ -85,7 +85,7 @@ ivhd_status run_lowd(const float* Y, int64_t M, const int32_t* knn, const int32_
   cudaStream_t s = (cudaStream_t)stream;
   const size_t sm = (size_t)kEvalTile * sizeof(float2) + (size_t)kEvalThreads * kk * 8;
   unsigned long long* hits_d = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&hits_d, sizeof(unsigned long long), s);
+  cudaError_t e = dev_alloc((void**)&hits_d, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return IVHD_ERR_OOM;
   e = cudaMemsetAsync(hits_d, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess)
@@ -99,7 +99,7 @@ ivhd_status run_lowd(const float* Y, int64_t M, const int32_t* knn, const int32_
   unsigned long long hits = 0;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&hits, hits_d, sizeof(hits), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(hits_d, s);
+  dev_free(hits_d, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return IVHD_ERR_CUDA;
   *out = (double)hits / ((double)kk * (double)nrows);

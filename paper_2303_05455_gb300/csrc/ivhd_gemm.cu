@@ -293,7 +293,7 @@ extern "C" ivhd_status ivhd_gemm_bf16_tn(const void* A, const void* B, float* C,
   cudaStream_t s = (cudaStream_t)stream;
   int32_t* err = nullptr;
   int32_t herr = 0;
-  cudaError_t e = cudaMallocAsync((void**)&err, sizeof(int32_t), s);
+  cudaError_t e = dev_alloc((void**)&err, sizeof(int32_t), s);
   if (e != cudaSuccess) return IVHD_ERR_OOM;
   e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
   GemmEpilogue ep{};
@@ -305,7 +305,7 @@ extern "C" ivhd_status ivhd_gemm_bf16_tn(const void* A, const void* B, float* C,
     e = gemm_bf16_tn((const __nv_bfloat16*)A, K, (const __nv_bfloat16*)B, K, (int)M, (int)N,
                      (int)K, ep, err, s, 1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
-  cudaFreeAsync(err, s);
+  dev_free(err, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e == cudaErrorInvalidValue ? IVHD_ERR_ARG : IVHD_ERR_CUDA;
   return herr ? IVHD_ERR_TIMEOUT : IVHD_OK;

@@ -29,6 +29,22 @@
 
 namespace ivhd {
 
+// Every device allocation of the library goes through these two calls
+// (stream-ordered cudaMallocAsync / cudaFreeAsync).  They count the live
+// allocations, so tests can check that error paths free what they took, and
+// ivhd_test_fail_alloc can make one of them fail to exercise those paths.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+cudaError_t dev_free(void* p, cudaStream_t s);
+
+// Names the enclosing host scope in profiler timelines (NVTX range; a no-op
+// unless a tool is attached).
+struct NvtxScope {
+  explicit NvtxScope(const char* name);
+  ~NvtxScope();
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 constexpr uint32_t kRnBit = 0x80000000u;  // random-neighbour term
 constexpr uint32_t kW2Bit = 0x40000000u;  // nn entry standing for a mutual pair (weight 2)
 constexpr uint32_t kIdxMask = 0x3FFFFFFFu;

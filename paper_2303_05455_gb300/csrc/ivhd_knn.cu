@@ -244,7 +244,7 @@ static ivhd_status knn_cuda_cores(const void* X, int32_t dtype, int64_t M, int32
     e = cudaGetLastError();
   } else {
     int32_t* nrm = nullptr;
-    e = cudaMallocAsync((void**)&nrm, (size_t)M * sizeof(int32_t), s);
+    e = dev_alloc((void**)&nrm, (size_t)M * sizeof(int32_t), s);
     if (e != cudaSuccess) return IVHD_ERR_OOM;
     k_norms_u8<<<(unsigned)((M + 255) / 256), 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
     e = cudaFuncSetAttribute(k_knn_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -252,7 +252,7 @@ static ivhd_status knn_cuda_cores(const void* X, int32_t dtype, int64_t M, int32
       k_knn_u8<<<grid, kThreads, sm, s>>>((const uint8_t*)X, nrm, M, N, k, out_knn);
       e = cudaGetLastError();
     }
-    cudaFreeAsync(nrm, s);
+    dev_free(nrm, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? IVHD_OK : IVHD_ERR_CUDA;
@@ -265,6 +265,7 @@ using namespace ivhd;
 extern "C" ivhd_status ivhd_knn_build_ex(const void* X, int32_t dtype, int64_t M, int32_t N,
                                          int32_t k, int32_t* out_knn, int32_t method,
                                          ivhd_knn_stats_t* stats, void* stream) {
+  NvtxScope nvtx_("ivhd_knn_build");
   if (!X || !out_knn) return IVHD_ERR_ARG;
   if (M < 2 || M >= (int64_t)0x7FFFFFFF || N < 1 || N > 65536) return IVHD_ERR_ARG;
   if (k < 1 || (int64_t)k > M - 1 || k > 64) return IVHD_ERR_ARG;

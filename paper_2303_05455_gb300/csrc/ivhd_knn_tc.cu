@@ -491,7 +491,7 @@ struct Bufs {
   template <class T>
   T* get(int64_t count) {
     void* q = nullptr;
-    if (cudaMallocAsync(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s) != cudaSuccess) {
+    if (dev_alloc(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s) != cudaSuccess) {
       ok = false;
       return nullptr;
     }
@@ -499,7 +499,7 @@ struct Bufs {
     return (T*)q;
   }
   ~Bufs() {
-    for (int q = 0; q < n; ++q) cudaFreeAsync(p[q], s);
+    for (int q = 0; q < n; ++q) dev_free(p[q], s);
   }
 };
 }  // namespace

@@ -382,7 +382,7 @@ ivhd_status ivhd_mlp_create(int32_t n_in, int32_t hidden, int32_t max_batch, voi
   cudaStream_t s = P->stream;
   cudaError_t e = cudaSuccess;
   auto A = [&](auto** p, int64_t n) {
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)p, (size_t)n * sizeof(**p), s);
+    if (e == cudaSuccess) e = dev_alloc((void**)p, (size_t)n * sizeof(**p), s);
   };
   A(&P->w, o.total);
   A(&P->m, o.total);
@@ -434,7 +434,7 @@ void ivhd_mlp_destroy(ivhd_mlp* P) {
                   P->h1, P->h1t, P->h2, P->dz2, P->dz2t, P->dz1, P->dz1t, P->y, P->dy,
                   P->part, P->loss_part, P->loss_out, P->err};
   for (void* b : bufs)
-    if (b) cudaFreeAsync(b, P->stream);
+    if (b) dev_free(b, P->stream);
   cudaStreamSynchronize(P->stream);
   delete P;
 }
@@ -468,6 +468,7 @@ ivhd_status ivhd_mlp_get_params(ivhd_mlp* P, float* params, int32_t on_device) {
 
 ivhd_status ivhd_mlp_loss_grad(ivhd_mlp* P, const void* x, int32_t x_dtype, float x_scale,
                                const float* targets, int32_t B, double* loss, float* grads) {
+  NvtxScope nvtx_("ivhd_mlp_loss_grad");
   if (!P || !x || !targets || x_dtype < 0 || x_dtype > 2 || !batch_ok(P, B)) return IVHD_ERR_ARG;
   if (P->poisoned) return IVHD_ERR_STATE;
   cudaError_t e = load_x(P, x, x_dtype, x_scale, B);
@@ -483,6 +484,7 @@ ivhd_status ivhd_mlp_loss_grad(ivhd_mlp* P, const void* x, int32_t x_dtype, floa
 
 ivhd_status ivhd_mlp_train_step(ivhd_mlp* P, const void* x, int32_t x_dtype, float x_scale,
                                 const float* targets, int32_t B, float lr, double* loss) {
+  NvtxScope nvtx_("ivhd_mlp_train_step");
   if (!P || !x || !targets || x_dtype < 0 || x_dtype > 2 || !batch_ok(P, B) || !(lr > 0.f))
     return IVHD_ERR_ARG;
   if (P->poisoned) return IVHD_ERR_STATE;
@@ -504,6 +506,7 @@ ivhd_status ivhd_mlp_train_step(ivhd_mlp* P, const void* x, int32_t x_dtype, flo
 
 ivhd_status ivhd_mlp_forward(ivhd_mlp* P, const void* x, int32_t x_dtype, float x_scale,
                              int64_t n, float* y) {
+  NvtxScope nvtx_("ivhd_mlp_forward");
   if (!P || !x || !y || x_dtype < 0 || x_dtype > 2 || n < 1) return IVHD_ERR_ARG;
   if (P->poisoned) return IVHD_ERR_STATE;
   const size_t esz = x_dtype == 1 ? 1 : (x_dtype == 2 ? 4 : 2);

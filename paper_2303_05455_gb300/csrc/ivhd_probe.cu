@@ -7,6 +7,7 @@
 // as the embedding, with the indices generated in registers (no index stream),
 // so it is an upper bound for the step kernel's gather rate.
 #include "ivhd_internal.cuh"
+#include "ivhd_tc.cuh"
 
 namespace ivhd {
 namespace {
@@ -62,8 +63,8 @@ extern "C" ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers,
   float2* y = nullptr;
   float* out = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&y, (size_t)n_positions * sizeof(float2), s);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&out, (size_t)grid * kProbeThreads * sizeof(float), s);
+  cudaError_t e = dev_alloc((void**)&y, (size_t)n_positions * sizeof(float2), s);
+  if (e == cudaSuccess) e = dev_alloc((void**)&out, (size_t)grid * kProbeThreads * sizeof(float), s);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) {
@@ -79,12 +80,59 @@ extern "C" ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers,
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-  if (y) cudaFreeAsync(y, s);
-  if (out) cudaFreeAsync(out, s);
+  if (y) dev_free(y, s);
+  if (out) dev_free(out, s);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   if (e != cudaSuccess) return IVHD_ERR_CUDA;
   *gathers_per_s = (double)grid * kProbeThreads * kProbePerThread * repeats / (ms * 1e-3);
   return IVHD_OK;
+}
+
+// ---- bounded-wait check ------------------------------------------------------
+//
+// The tensor-core kernels wait on mbarriers with a bounded number of polls and
+// report a timeout through an error flag instead of hanging.  This kernel runs
+// the same bounded wait on an mbarrier that nothing ever completes, so a test
+// can watch the timeout path end cleanly with IVHD_ERR_TIMEOUT while the
+// context stays usable.
+namespace ivhd {
+namespace {
+
+__global__ void k_wait_unset(uint32_t polls, int32_t* timed_out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool done = false;
+    for (uint32_t it = 0; it < polls && !done; ++it) done = tc::mbar_try_wait(&bar, 0);
+    *timed_out = done ? 0 : 1;
+  }
+}
+
+}  // namespace
+}  // namespace ivhd
+
+extern "C" ivhd_status ivhd_probe_wait_timeout(int32_t polls, void* stream) {
+  if (polls < 1) return IVHD_ERR_ARG;
+  NvtxScope nvtx_("ivhd_probe_wait_timeout");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* flag = nullptr;
+  int32_t h = 0;
+  cudaError_t e = dev_alloc((void**)&flag, sizeof(int32_t), s);
+  if (e != cudaSuccess) return IVHD_ERR_OOM;
+  e = cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) {
+    k_wait_unset<<<1, 32, 0, s>>>((uint32_t)polls, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(h), cudaMemcpyDeviceToHost, s);
+  dev_free(flag, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  return h ? IVHD_ERR_TIMEOUT : IVHD_OK;
 }
