@@ -96,7 +96,9 @@ typedef struct {
     int32_t init_uniform; /* 1: y0 ~ U(0,1)^2 drawn from seed; 0: y0 = 0 until
                              ivhd_set_positions; default 1 */
     int32_t hub_threshold;/* vertices with at least this many symmetric terms are
-                             processed warp-per-vertex; 0 = library default (128) */
+                             processed warp-per-vertex; 0 = library default: the largest
+                             power of two not above 2 M (k + r) / 70,000, within
+                             [16, 256] (low for small, latency-bound graphs) */
     int32_t pos_format;   /* ivhd_pos_format of the positions the step kernel gathers;
                              default IVHD_POS_F32 */
     int32_t adaptive;     /* 1: self-adaptive b of Sec. 3.3.3 (momentum and Nesterov only);
@@ -106,7 +108,7 @@ typedef struct {
     float gamma1;         /* adaptive b: factor (> 1) applied to b when dT < 0; default 1.1 */
     float gamma2;         /* adaptive b: factor (0, 1) applied to b when dT > 0; default 0.5 */
     int32_t block_size;   /* threads per block of the step kernel: 128, 256 or 512;
-                             0 = library default (256); see ivhd_autotune */
+                             0 = library default (128); see ivhd_autotune */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 
@@ -170,7 +172,7 @@ ivhd_status ivhd_create_batch(const int32_t *knn, const int64_t *M_e, const int3
 
 /*
  * Launch-shape autotuner: times trial_steps steps for every pair of threads
- * per block (128, 256, 512) and hub threshold (32, 64, 128, 256, 512: the
+ * per block (128, 256, 512) and hub threshold (16, 32, 64, 128, 256, 512: the
  * degree from which a vertex gets a whole warp instead of one lane), starting
  * each trial from the same state, then keeps the fastest pair and restores the
  * state, so the embedding continues exactly as before the call (with the new

@@ -374,7 +374,8 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
   ctx->k = k;
   ctx->r = r;
   ctx->c = c;
-  ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : kDefaultHubThreshold;
+  ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold
+                                            : auto_hub_threshold(2 * M * (int64_t)(k + r));
   ctx->block = p.block_size > 0 ? p.block_size : kStepBlock;
   ctx->stream = (cudaStream_t)p.stream;
   cudaGetDevice(&ctx->device);
@@ -786,12 +787,14 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
   std::vector<int64_t> lo(n_emb), row0(n_emb), n(M_e, M_e + n_emb);
   int64_t M = 0, entries = 0;
   int k_max = 0, r_max = 0;
+  int64_t sym_entries = 0;  // 2 M_e (k_e + r_e) summed: the default hub threshold's input
   for (int e = 0; e < n_emb; ++e) {
     if (M_e[e] < 2 || k_e[e] < 1 || (int64_t)k_e[e] > M_e[e] - 1 || r_e[e] < 0) return IVHD_ERR_ARG;
     lo[e] = M;
     row0[e] = entries;
     M += M_e[e];
     entries += M_e[e] * k_e[e];
+    sym_entries += 2 * M_e[e] * (int64_t)(k_e[e] + r_e[e]);
     k_max = k_e[e] > k_max ? k_e[e] : k_max;
     r_max = r_e[e] > r_max ? r_e[e] : r_max;
     if (M >= kMaxVertices) return IVHD_ERR_ARG;
@@ -811,7 +814,7 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
   ctx->k = k_max;
   ctx->r = r_max;
   ctx->c = c;
-  ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : kDefaultHubThreshold;
+  ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : auto_hub_threshold(sym_entries);
   ctx->block = p.block_size > 0 ? p.block_size : kStepBlock;
   ctx->stream = (cudaStream_t)p.stream;
   cudaGetDevice(&ctx->device);
@@ -907,7 +910,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
     return x;
   };
   const int blocks[3] = {128, 256, 512};
-  const int hubs[5] = {32, 64, 128, 256, 512};
+  const int hubs[6] = {16, 32, 64, 128, 256, 512};
   float best = 1e30f;
   int bb = ctx->block, bh = ctx->hub_threshold;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -915,7 +918,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   ivhd_status st = IVHD_OK;
   const int64_t steps_before = ctx->steps_done;
-  for (int hi = 0; hi < 5 && e == cudaSuccess && st == IVHD_OK; ++hi) {
+  for (int hi = 0; hi < 6 && e == cudaSuccess && st == IVHD_OK; ++hi) {
     ctx->hub_threshold = hubs[hi];
     drop_graphs(ctx);
     free_layout(ctx);

@@ -51,7 +51,22 @@ constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
 constexpr uint32_t kPad = 0xFFFFFFFFu;
 constexpr int64_t kMaxVertices = (int64_t)1 << 30;
 constexpr int kDefaultHubThreshold = 128;
-constexpr int kStepBlock = 256;      // default threads per step block (8 warps)
+constexpr int kStepBlock = 128;      // default threads per step block (4 warps)
+
+// Default hub threshold for a graph with about `entries` symmetric row entries
+// (2 M (k + r) before mutual pairs merge): the largest power of two not above
+// entries / 70,000, within [16, 256].  A SELL slice of rows just below the
+// threshold is a chain of threshold / 8 dependent gather rounds for its warp;
+// small graphs finish in a few such chains, so a low threshold (short chains,
+// more warp-per-vertex rows) wins, while large graphs are throughput-bound and
+// lose lanes to short warp rows.  Measured best shapes: 2,000 and 70,000
+// vertices (k = 2 / 5, r = 1): 16; 1.4e6 vertices (k = 5, r = 1): 128; 64
+// embeddings with 3.7e6 vertices in total: 256.
+inline int auto_hub_threshold(int64_t entries) {
+  int h = 16;
+  while (h < 256 && (int64_t)(2 * h) * 70000 <= entries) h *= 2;
+  return h;
+}
 constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
 
 enum Mode { kMomentum = 0, kNesterov = 1, kAdadelta = 2, kForces = 3, kStress = 4 };
