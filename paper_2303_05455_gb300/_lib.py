@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
         ("hub_threshold", ctypes.c_int32), ("pos_format", ctypes.c_int32),
         ("adaptive", ctypes.c_int32), ("tau", ctypes.c_float), ("gamma1", ctypes.c_float),
         ("gamma2", ctypes.c_float), ("block_size", ctypes.c_int32),
-        ("stream", ctypes.c_void_p),
+        ("resident", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 

@@ -78,6 +78,7 @@ bool params_ok(const ivhd_params& p) {
   if (p.adaptive != 0 && p.adaptive != 1) return false;
   if (p.block_size != 0 && p.block_size != 128 && p.block_size != 256 && p.block_size != 512)
     return false;
+  if (p.resident != 0 && p.resident != -1) return false;
   if (p.adaptive) {
     if (p.opt == IVHD_OPT_ADADELTA) return false;
     if (!std::isfinite(p.tau) || p.tau <= 0.f) return false;
@@ -441,6 +442,15 @@ ivhd_status ivhd_step(ivhd_ctx* ctx, int64_t n_iter) {
   if (ctx->poisoned) return IVHD_ERR_STATE;
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaSuccess;
+  if (n_iter > 0 && !ctx->ctl && resident_mode(ctx) > 0) {
+    // the whole call in one single-block launch (state in shared memory)
+    e = launch_resident(ctx, n_iter, s);
+    if (e != cudaSuccess) return fail(ctx, e);
+    if (n_iter & 1) ctx->cur ^= 1;
+    ctx->launches += 1;
+    ctx->steps_done += n_iter;
+    return IVHD_OK;
+  }
   int64_t left = n_iter;
   // with adaptive b the kernels pick their buffers on the device: one graph, no host flips
   const bool flip = ctx->ctl == nullptr;

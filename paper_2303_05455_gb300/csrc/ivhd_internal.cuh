@@ -68,6 +68,7 @@ inline int auto_hub_threshold(int64_t entries) {
   return h;
 }
 constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
+constexpr int kResidentSmem = 200 * 1024;  // shared memory of the resident whole-run kernel
 
 enum Mode { kMomentum = 0, kNesterov = 1, kAdadelta = 2, kForces = 3, kStress = 4 };
 
@@ -207,6 +208,10 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch);
 
 // ivhd_step.cu
 cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s);
+// Resident whole-run kernel: all n_iter steps in one single-block launch for
+// embeddings whose state fits one SM (resident_mode > 0).
+int resident_mode(const ivhd_ctx* ctx);
+cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s);
 cudaError_t launch_forces(ivhd_ctx* ctx, float2* out_input_order);
 cudaError_t launch_stress(ivhd_ctx* ctx);  // result in ctx->red_out[0], flag in ctx->flag
 cudaError_t launch_unpermute(ivhd_ctx* ctx, float2* out_input_order);

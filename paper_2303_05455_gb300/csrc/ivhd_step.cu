@@ -198,6 +198,39 @@ __device__ __forceinline__ void visit8(const int4 ea, const int4 eb, const Gsrc&
   }
 }
 
+// Per-vertex optimiser updates (shared by the step kernel and the resident
+// whole-run kernel, so both produce the same bits).
+// Eq. 3.34: v <- a v + b F ; y <- y + v
+__device__ __forceinline__ void momentum_update(float a, float b, float fx, float fy, float2 ym,
+                                                float2 v, float2& vn, float2& yn) {
+  vn.x = fmaf(a, v.x, b * fx);
+  vn.y = fmaf(a, v.y, b * fy);
+  yn = make_float2(ym.x + vn.x, ym.y + vn.y);
+}
+// Nesterov: the state is the look-ahead point z = y + a v and F was taken at z.
+// v' = a v + b F(z);  y' = y + v';  z' = y' + a v' = z - a v + (1 + a) v'
+__device__ __forceinline__ void nesterov_update(float a, float b, float fx, float fy, float2 zm,
+                                                float2 v, float2& vn, float2& zn) {
+  vn.x = fmaf(a, v.x, b * fx);
+  vn.y = fmaf(a, v.y, b * fy);
+  const float ap1 = 1.f + a;
+  zn = make_float2(zm.x + fmaf(ap1, vn.x, -a * v.x), zm.y + fmaf(ap1, vn.y, -a * v.y));
+}
+// Zeiler's Adadelta on g = -F: E[g^2] <- rho E[g^2] + (1-rho) g^2;
+// dx = -sqrt(E[dx^2] + eps) / sqrt(E[g^2] + eps) g; E[dx^2] <- rho E[dx^2] + (1-rho) dx^2
+__device__ __forceinline__ void adadelta_update(float rho, float eps, float fx, float fy,
+                                                float2 ym, float2& eg, float2& ex, float2& yn) {
+  const float omr = 1.f - rho;
+  const float gx = -fx, gy = -fy;
+  eg.x = fmaf(rho, eg.x, omr * gx * gx);
+  eg.y = fmaf(rho, eg.y, omr * gy * gy);
+  const float dx = -(sqrtf(ex.x + eps) / sqrtf(eg.x + eps)) * gx;
+  const float dy = -(sqrtf(ex.y + eps) / sqrtf(eg.y + eps)) * gy;
+  ex.x = fmaf(rho, ex.x, omr * dx * dx);
+  ex.y = fmaf(rho, ex.y, omr * dy * dy);
+  yn = make_float2(ym.x + dx, ym.y + dy);
+}
+
 // Block sum of a per-thread double in a fixed order (warp tree, then warps in
 // order); the result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -287,14 +320,11 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
   double kin_new = 0.0, kin_old = 0.0;
 
   if (MODE == kMomentum) {
-    // Eq. 3.34: v <- a v + b F ; y <- y + v
     if (own) {
       const float2 v = v_in[p];
-      float2 vn;
-      vn.x = fmaf(A.a, v.x, b * fx);
-      vn.y = fmaf(A.a, v.y, b * fy);
+      float2 vn, yn;
+      momentum_update(A.a, b, fx, fy, ym, v, vn, yn);
       v_out[p] = vn;
-      const float2 yn = make_float2(ym.x + vn.x, ym.y + vn.y);
       y_out[p] = yn;
       if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
       if (ADAPT) {
@@ -303,17 +333,11 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       }
     }
   } else if (MODE == kNesterov) {
-    // state is the look-ahead point z = y + a v; F was taken at z.
-    // v' = a v + b F(z);  y' = y + v';  z' = y' + a v' = z - a v + (1 + a) v'
     if (own) {
       const float2 v = v_in[p];
-      float2 vn;
-      vn.x = fmaf(A.a, v.x, b * fx);
-      vn.y = fmaf(A.a, v.y, b * fy);
+      float2 vn, zn;
+      nesterov_update(A.a, b, fx, fy, ym, v, vn, zn);
       v_out[p] = vn;
-      const float ap1 = 1.f + A.a;
-      const float2 zn =
-          make_float2(ym.x + fmaf(ap1, vn.x, -A.a * v.x), ym.y + fmaf(ap1, vn.y, -A.a * v.y));
       y_out[p] = zn;
       if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(zn);
       if (ADAPT) {
@@ -322,22 +346,13 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       }
     }
   } else if (MODE == kAdadelta) {
-    // Zeiler's Adadelta on g = -F: E[g^2] <- rho E[g^2] + (1-rho) g^2;
-    // dx = -sqrt(E[dx^2] + eps) / sqrt(E[g^2] + eps) g; E[dx^2] <- rho E[dx^2] + (1-rho) dx^2
     if (own) {
       float2 eg = v_in[p];
       float2 ex = A.s2[p];
-      const float omr = 1.f - A.rho;
-      const float gx = -fx, gy = -fy;
-      eg.x = fmaf(A.rho, eg.x, omr * gx * gx);
-      eg.y = fmaf(A.rho, eg.y, omr * gy * gy);
-      const float dx = -(sqrtf(ex.x + A.eps) / sqrtf(eg.x + A.eps)) * gx;
-      const float dy = -(sqrtf(ex.y + A.eps) / sqrtf(eg.y + A.eps)) * gy;
-      ex.x = fmaf(A.rho, ex.x, omr * dx * dx);
-      ex.y = fmaf(A.rho, ex.y, omr * dy * dy);
+      float2 yn;
+      adadelta_update(A.rho, A.eps, fx, fy, ym, eg, ex, yn);
       v_out[p] = eg;
       A.s2[p] = ex;
-      const float2 yn = make_float2(ym.x + dx, ym.y + dy);
       y_out[p] = yn;
       if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
     }
@@ -357,6 +372,210 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       A.partials[2 * blockIdx.x] = tn;
       A.partials[2 * blockIdx.x + 1] = to;
     }
+  }
+}
+
+// ---- resident whole-run kernel -------------------------------------------------
+//
+// For an embedding whose positions (both ping-pong copies) and optimiser
+// state fit one SM's shared memory, one block of 1,024 threads runs every step
+// of an ivhd_step call: the steps of the synchronous scheme (Sec. 5.2) are
+// separated by __syncthreads instead of kernel launches, and every gather is a
+// shared-memory load.  The id rows are copied to shared memory too when they
+// fit, else read through L1.  The traversal (hub rows warp-per-vertex with the
+// same butterfly, SELL slices thread-per-vertex) and the arithmetic are those of
+// k_step, so the positions agree with the multi-launch path bit for bit.
+constexpr int kResidentThreads = 1024;
+
+template <int MODE, int METRIC>
+__device__ __forceinline__ void rvisit4(const int4 e, const float2* src, float2 yi, float c,
+                                        float& fx, float& fy) {
+  const uint32_t q[4] = {(uint32_t)e.x, (uint32_t)e.y, (uint32_t)e.z, (uint32_t)e.w};
+  float2 g[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) g[t] = (q[t] == kPad) ? yi : src[q[t] & kIdxMask];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) force_term<METRIC>(q[t], g[t], yi, c, fx, fy);
+}
+
+template <int MODE, int METRIC>
+__device__ __forceinline__ void rvisit8(const int4 ea, const int4 eb, const float2* src, float2 yi,
+                                        float c, float& fx, float& fy) {
+  const uint32_t q[8] = {(uint32_t)ea.x, (uint32_t)ea.y, (uint32_t)ea.z, (uint32_t)ea.w,
+                         (uint32_t)eb.x, (uint32_t)eb.y, (uint32_t)eb.z, (uint32_t)eb.w};
+  float2 g[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) g[t] = (q[t] == kPad) ? yi : src[q[t] & kIdxMask];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) force_term<METRIC>(q[t], g[t], yi, c, fx, fy);
+}
+
+template <int MODE, int METRIC, bool IDS_SMEM>
+__global__ void __launch_bounds__(kResidentThreads, 1)
+    k_resident(const StepArgs A, int64_t n_iter, int64_t n_slots) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  const int M = A.M, Mp = (A.M + 1) & ~1;  // even: every array starts 16-byte aligned
+  float2* ys0 = reinterpret_cast<float2*>(rsm);
+  float2* ys1 = ys0 + Mp;
+  float2* vs = ys1 + Mp;
+  float2* es = vs + Mp;  // Adadelta E[dx^2]
+  uint32_t* ids_s = reinterpret_cast<uint32_t*>(MODE == kAdadelta ? es + Mp : es);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
+
+  for (int p = threadIdx.x; p < M; p += blockDim.x) {
+    ys0[p] = A.y[A.cur][p];
+    vs[p] = A.v[0][p];
+    if (MODE == kAdadelta) es[p] = A.s2[p];
+  }
+  if (IDS_SMEM) {
+    const uint4* g = reinterpret_cast<const uint4*>(A.ids);
+    uint4* d = reinterpret_cast<uint4*>(ids_s);
+    for (int64_t q = threadIdx.x; q < n_slots / 4; q += blockDim.x) d[q] = g[q];
+  }
+  __syncthreads();
+  const uint32_t* ids = IDS_SMEM ? ids_s : A.ids;
+  const int n_items = A.n_hub + A.n_slices;
+
+  for (int64_t it = 0; it < n_iter; ++it) {
+    const float2* src = (it & 1) ? ys1 : ys0;
+    float2* dst = (it & 1) ? ys0 : ys1;
+    for (int item = warp; item < n_items; item += nwarps) {
+      float fx = 0.f, fy = 0.f;
+      float2 ym = make_float2(0.f, 0.f);
+      int p;
+      bool own;
+      if (item < A.n_hub) {
+        p = item;
+        ym = src[p];
+        const int beg = A.hub_off[p], end = A.hub_off[p + 1];
+        const int4* row = reinterpret_cast<const int4*>(ids + beg);
+        const int ng = (end - beg) >> 2;
+        int g = lane;
+        for (; g + 32 < ng; g += 64) rvisit8<MODE, METRIC>(row[g], row[g + 32], src, ym, A.c, fx, fy);
+        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, ym, A.c, fx, fy);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          fx += __shfl_xor_sync(0xffffffffu, fx, o);
+          fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        }
+        own = (lane == 0);
+      } else {
+        const int sl = item - A.n_hub;
+        p = A.n_hub + sl * 32 + lane;
+        own = p < M;
+        if (own) ym = src[p];
+        const int4* base = reinterpret_cast<const int4*>(ids + A.slice_off[sl]) + lane;
+        const int W = A.slice_w[sl];
+        int g = 0;
+        for (; g + 1 < W; g += 2)
+          rvisit8<MODE, METRIC>(base[g * 32], base[(g + 1) * 32], src, ym, A.c, fx, fy);
+        if (g < W) rvisit4<MODE, METRIC>(base[g * 32], src, ym, A.c, fx, fy);
+      }
+      if (!own) continue;
+      if (MODE == kMomentum) {
+        float2 vn, yn;
+        momentum_update(A.a, A.b, fx, fy, ym, vs[p], vn, yn);
+        vs[p] = vn;
+        dst[p] = yn;
+      } else if (MODE == kNesterov) {
+        float2 vn, zn;
+        nesterov_update(A.a, A.b, fx, fy, ym, vs[p], vn, zn);
+        vs[p] = vn;
+        dst[p] = zn;
+      } else {
+        float2 eg = vs[p], ex = es[p], yn;
+        adadelta_update(A.rho, A.eps, fx, fy, ym, eg, ex, yn);
+        vs[p] = eg;
+        es[p] = ex;
+        dst[p] = yn;
+      }
+    }
+    __syncthreads();
+  }
+  const float2* fin = (n_iter & 1) ? ys1 : ys0;
+  float2* yout = A.y[A.cur ^ (int)(n_iter & 1)];
+  for (int p = threadIdx.x; p < M; p += blockDim.x) {
+    yout[p] = fin[p];
+    A.v[0][p] = vs[p];
+    if (MODE == kAdadelta) A.s2[p] = es[p];
+  }
+}
+
+// Shared memory of the resident kernel with and without the id rows.
+static size_t resident_bytes(const ivhd_ctx* ctx, bool with_ids) {
+  const size_t Mp = (size_t)((ctx->M + 1) & ~1);
+  const size_t state = Mp * sizeof(float2) * (ctx->p.opt == IVHD_OPT_ADADELTA ? 4 : 3);
+  return state + (with_ids ? (size_t)ctx->n_slots * sizeof(uint32_t) : 0);
+}
+
+// 0: not eligible (adaptive b, half-precision gathers, or too large); 1: ids
+// read through L1; 2: ids in shared memory too.
+int resident_mode(const ivhd_ctx* ctx) {
+  if (ctx->p.resident < 0 || ctx->p.adaptive || ctx->p.pos_format != IVHD_POS_F32) return 0;
+  if (ctx->M > ((int64_t)1 << 20)) return 0;
+  if (resident_bytes(ctx, true) <= (size_t)kResidentSmem) return 2;
+  if (resident_bytes(ctx, false) <= (size_t)kResidentSmem) return 1;
+  return 0;
+}
+
+template <int MODE, int METRIC, bool IDS>
+static cudaError_t launch_res(const StepArgs& A, int64_t n_iter, int64_t n_slots, size_t smem,
+                              cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_resident<MODE, METRIC, IDS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  k_resident<MODE, METRIC, IDS><<<1, kResidentThreads, smem, s>>>(A, n_iter, n_slots);
+  return cudaGetLastError();
+}
+
+template <int MODE, int METRIC>
+static cudaError_t launch_res_ids(const StepArgs& A, int64_t n_iter, int64_t n_slots, int mode,
+                                  size_t smem, cudaStream_t s) {
+  return mode == 2 ? launch_res<MODE, METRIC, true>(A, n_iter, n_slots, smem, s)
+                   : launch_res<MODE, METRIC, false>(A, n_iter, n_slots, smem, s);
+}
+
+cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s) {
+  const int mode = resident_mode(ctx);
+  if (mode == 0) return cudaErrorInvalidValue;
+  StepArgs A{};
+  A.ids = ctx->ids;
+  A.hub_off = ctx->hub_off;
+  A.slice_off = ctx->slice_off;
+  A.slice_w = ctx->slice_w;
+  A.y[0] = ctx->y[0];
+  A.y[1] = ctx->y[1];
+  A.v[0] = ctx->vbuf[0];
+  A.s2 = ctx->s2;
+  A.cur = ctx->cur;
+  A.M = (int32_t)ctx->M;
+  A.n_hub = (int32_t)ctx->n_hub;
+  A.n_slices = (int32_t)ctx->n_slices;
+  A.c = ctx->c;
+  A.a = ctx->p.a;
+  A.b = ctx->p.b;
+  A.rho = ctx->p.rho;
+  A.eps = ctx->p.eps;
+  const size_t smem = resident_bytes(ctx, mode == 2);
+  const int64_t ns = ctx->n_slots;
+  const bool l1 = ctx->metric == IVHD_METRIC_L1;
+  switch (ctx->p.opt) {
+    case IVHD_OPT_NESTEROV:
+      return l1 ? launch_res_ids<kNesterov, IVHD_METRIC_L1>(A, n_iter, ns, mode, smem, s)
+                : launch_res_ids<kNesterov, IVHD_METRIC_L2>(A, n_iter, ns, mode, smem, s);
+    case IVHD_OPT_ADADELTA:
+      return l1 ? launch_res_ids<kAdadelta, IVHD_METRIC_L1>(A, n_iter, ns, mode, smem, s)
+                : launch_res_ids<kAdadelta, IVHD_METRIC_L2>(A, n_iter, ns, mode, smem, s);
+    default:
+      return l1 ? launch_res_ids<kMomentum, IVHD_METRIC_L1>(A, n_iter, ns, mode, smem, s)
+                : launch_res_ids<kMomentum, IVHD_METRIC_L2>(A, n_iter, ns, mode, smem, s);
   }
 }
 

@@ -1,0 +1,67 @@
+"""Resident whole-run kernel vs one launch per step (``-m gpu``).
+
+Small embeddings run all steps of an ivhd_step call in one single-block
+launch with positions and optimiser state in shared memory (and the id rows
+too when they fit).  Its traversal and arithmetic are those of the step
+kernel, so positions and optimiser state must agree bit for bit with the
+multi-launch path, for every optimiser and both metrics, with the id rows in
+shared memory (2,000-vertex mixture) and read through L1 (5,000-vertex hub
+graph).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_05455_gb300 import ivhd, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def graphs():
+    w = synth.WORKLOADS["gmm2k"]
+    X, _ = synth.workload_features(w)
+    return {"gmm2k": (oracle.knn_f32(X, w.k), w.r, w.c),
+            "hubs5k": (synth.random_knn_graph(5000, 5, 21, hub_frac=0.3, n_hubs=20), 2, 0.05),
+            "pair": (np.array([[1], [0]], np.int32), 1, 0.1),
+            "ragged37": (synth.random_knn_graph(37, 3, 4), 1, 0.1)}
+
+
+GRAPHS = graphs()
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_resident_equals_multi_launch_bitwise(name, opt, metric):
+    knn, r, c = GRAPHS[name]
+    runs = []
+    for resident in (True, False):
+        e = ivhd.Embedding(knn, r=r, c=c, opt=opt, b=0.002, seed=9, resident=resident)
+        if metric == "l1":
+            e.set_metric("l1")
+        out = []
+        for n in (1, 7, 64, 130):
+            e.step(n)
+            out.append(e.positions(host=True))
+        st = e.get_state()
+        runs.append((out, st, e.info()))
+        e.close()
+    (pa, sa, ia), (pb, sb, ib) = runs
+    for x, y in zip(pa, pb):
+        assert np.array_equal(x, y)
+    assert sa == sb
+    assert ia["steps_done"] == ib["steps_done"] == 202
+    assert ia["kernel_launches"] == 4 and ib["kernel_launches"] == 202
+
+
+def test_resident_not_used_when_state_does_not_fit():
+    knn = synth.random_knn_graph(20000, 5, 3)
+    e = ivhd.Embedding(knn, r=1, c=0.01, seed=1)
+    e.step(10)
+    assert e.info()["kernel_launches"] == 10
+    e.close()
+    small = synth.random_knn_graph(4000, 5, 4)
+    e = ivhd.Embedding(small, r=1, c=0.01, seed=1, adaptive=True)  # adaptive b: multi-launch
+    e.step(10)
+    assert e.info()["kernel_launches"] == 20  # step kernel + controller per step
+    e.close()
