@@ -256,6 +256,10 @@ template <int MODE, int POS, int METRIC, bool ADAPT>
 __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  // launched as a programmatic dependent of the previous step: wait until that
+  // grid has completed and its writes are visible before reading any state
+  // (a no-op for a launch without that attribute)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int cur = ADAPT ? A.ctl->cur : A.cur;
   uint64_t keep;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
@@ -313,6 +317,9 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
     }
   }
 
+  // this block's gathers are done: the next step's grid may start launching
+  // (its blocks wait for this grid's completion before reading anything)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   float2* __restrict__ y_out = A.y[cur ^ 1];
   uint32_t* __restrict__ yh_out = A.yh[cur ^ 1];
   const float2* __restrict__ v_in = A.v[ADAPT ? cur : 0];
@@ -745,7 +752,19 @@ int step_grid(const ivhd_ctx* ctx) {
 
 template <int MODE, int POS, int METRIC, bool ADAPT>
 static void launch1(int grid, cudaStream_t s, const StepArgs& A) {
-  k_step<MODE, POS, METRIC, ADAPT><<<grid, A.wpb * 32, 0, s>>>(A);
+  // programmatic dependent launch: the next step's blocks start while this
+  // step's last wave drains (0.5 % at 1.4e6 vertices, 5 % at 2,000)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)(A.wpb * 32));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_step<MODE, POS, METRIC, ADAPT>, A);
 }
 
 template <int POS, int METRIC>
