@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gmm1p4m", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--opt", default="momentum", choices=["momentum", "nesterov", "adadelta"],
+                    help="optimiser of the step (Sec. 3.3.2 / 3.3.3)")
     ap.add_argument("--n-iter", type=int, default=None, help="iterations per embedding")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -67,10 +69,10 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
-def workload_config(w: synth.Workload, n_iter: int) -> dict:
+def workload_config(w: synth.Workload, n_iter: int, opt: str = "momentum") -> dict:
     return {
         "workload": w.name, "M": w.M, "N": w.N, "features": w.dtype, "k": w.k, "r": w.r,
-        "c": w.c, "n_iter": n_iter, "optimizer": "momentum", "a": w.a, "b": w.b,
+        "c": w.c, "n_iter": n_iter, "optimizer": opt, "a": w.a, "b": w.b,
         "terms": "multiplicity (mutual kNN pairs give two nn terms)",
         "step": "ivhd_create + n_iter fused steps + positions read-back (one embedding)",
         "knn_graph": "exact, built on the GPU before the timed region (untimed)",
@@ -167,7 +169,10 @@ def aggregate_ranks(total_s: float, kernel_ms: float, units: float, device) -> t
 # ------------------------------------------------------------- oracle leg
 
 
-def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200):
+ORACLE_OPT = {"momentum": 0, "nesterov": 1, "adadelta": 2}
+
+
+def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200, opt: str = "momentum"):
     """Times the FP64 oracle's step loop on a graph of the workload's shape.
 
     The graph comes from the input generators (a kNN-shaped graph with hubs,
@@ -183,16 +188,18 @@ def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200):
     st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
     setup = time.perf_counter() - t0
     t = time.perf_counter()
-    oracle.run(st, terms, w.c, 1, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    oracle.run(st, terms, w.c, 1, ORACLE_OPT[opt], a=w.a, b=w.b)
     one = max(time.perf_counter() - t, 1e-6)
     iters = int(max(1, min(max_iters, target_s / one)))
     t = time.perf_counter()
-    oracle.run(st, terms, w.c, iters, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    oracle.run(st, terms, w.c, iters, ORACLE_OPT[opt], a=w.a, b=w.b)
     dt = time.perf_counter() - t
     return terms.T * iters / dt, iters, dt, terms.T, setup
 
 
 def run_reference(args):
+    if not hasattr(args, "opt"):
+        args.opt = "momentum"
     rank, _, world = dist_env()
     if rank != 0:
         return 0
@@ -205,15 +212,15 @@ def run_reference(args):
     terms = oracle.build_terms(knn, rn)
     st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
     t = time.perf_counter()
-    oracle.run(st, terms, w.c, 1, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    oracle.run(st, terms, w.c, 1, ORACLE_OPT[args.opt], a=w.a, b=w.b)
     one = max(time.perf_counter() - t, 1e-6)
     per_step = int(max(1, min(n_iter, 6.0 / one)))   # ~6 s of oracle work per step
     for _ in range(args.warmup):
-        oracle.run(st, terms, w.c, per_step, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+        oracle.run(st, terms, w.c, per_step, ORACLE_OPT[args.opt], a=w.a, b=w.b)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        oracle.run(st, terms, w.c, per_step, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+        oracle.run(st, terms, w.c, per_step, ORACLE_OPT[args.opt], a=w.a, b=w.b)
         times.append(time.perf_counter() - t)
     ms = 1e3 * statistics.mean(times)
     value = terms.T * per_step / (ms / 1e3)
@@ -223,7 +230,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {**workload_config(w, n_iter), "iterations_per_step": per_step},
+        "data": "synthetic", "config": {**workload_config(w, n_iter, args.opt),
+                                         "iterations_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -267,7 +275,7 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def one_embedding(knn_in, out_buf, evs=None, pos_format="f32"):
-        emb = ivhd.Embedding(knn_in, r=w.r, c=w.c, opt="momentum", a=w.a, b=w.b, seed=w.seed,
+        emb = ivhd.Embedding(knn_in, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b, seed=w.seed,
                              stream=stream, device=dev, pos_format=pos_format)
         if evs is not None:
             evs[0].record(stream)
@@ -323,7 +331,7 @@ def run_ours(args):
     lab = torch.from_numpy(labels).to(dev)
 
     def quality(pos_format="f32"):
-        emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt="momentum", a=w.a, b=w.b, seed=w.seed,
+        emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b, seed=w.seed,
                              stream=stream, device=dev, pos_format=pos_format)
         emb.step(n_iter)
         emb.positions(out=out)
@@ -386,7 +394,9 @@ def run_ours(args):
     M = w.M
     nnz = info["nnz_sym"]
     n_slices = (M - info["n_hub"] + 31) // 32
-    alg_bytes = 32 * M + 4 * nnz + 8 * n_slices + 4 * (info["n_hub"] + 1)
+    # per vertex: y, v read + y', v' written (Adadelta: + E[dx^2] read and written)
+    state_bytes = 48 if args.opt == "adadelta" else 32
+    alg_bytes = state_bytes * M + 4 * nnz + 8 * n_slices + 4 * (info["n_hub"] + 1)
     launch_s = kms / 1e3 / n_iter
     achieved = alg_bytes / launch_s / 1e9
     peaks = measured_peaks()
@@ -395,7 +405,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "peak_source": peaks["source"], "kernel": "k_step<momentum>",
+                "peak_source": peaks["source"], "kernel": f"k_step<{args.opt}>",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "launch_us": launch_s * 1e6,
                 "l2_gather": {
@@ -408,7 +418,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**workload_config(w, n_iter), "parallelism": "replicas" if world > 1 else "single"},
+        "config": {**workload_config(w, n_iter, args.opt),
+                   "parallelism": "replicas" if world > 1 else "single"},
         "s_to_embed": ms / 1e3,
         "kernel_edge_updates_per_s": terms * n_iter / (kms / 1e3),
         "terms": terms, "nnz_sym": nnz, "n_hub": info["n_hub"], "max_degree": info["max_degree"],
@@ -421,10 +432,10 @@ def run_ours(args):
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, iters, dt, T, setup = oracle_sample(w, args.cpu_seconds)
+        v, iters, dt, T, setup = oracle_sample(w, args.cpu_seconds, opt=args.opt)
         line["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{iters} of {n_iter} momentum iterations (FP64, single thread) on a "
+            "sample": f"{iters} of {n_iter} {args.opt} iterations (FP64, single thread) on a "
                       f"{w.M} x {w.k} kNN-shaped graph with r={w.r} ({T} terms), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)

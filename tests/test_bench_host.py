@@ -59,9 +59,10 @@ def test_reference_arm_line_on_small_workload(capsys, monkeypatch):
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
     ns = argparse.Namespace(impl="reference", workload="gmm2k", n_iter=50, steps=2, warmup=1,
-                            gpus=1)
+                            gpus=1, opt="adadelta")
     assert bench.run_reference(ns) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["config"]["optimizer"] == "adadelta"
