@@ -231,6 +231,22 @@ __device__ __forceinline__ void adadelta_update(float rho, float eps, float fx, 
   yn = make_float2(ym.x + dx, ym.y + dy);
 }
 
+// Block sum of a per-thread float in a fixed order (warp tree, then warps in
+// order); the result is valid in thread 0.  The kinetic energies of the
+// adaptive-b controller use it: FP64 arithmetic is slow on this GPU, and the
+// per-block FP32 sums (<= 512 terms) are added across blocks in FP64.
+__device__ __forceinline__ float block_sum_f32(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
 // Block sum of a per-thread double in a fixed order (warp tree, then warps in
 // order); the result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -324,7 +340,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
   uint32_t* __restrict__ yh_out = A.yh[cur ^ 1];
   const float2* __restrict__ v_in = A.v[ADAPT ? cur : 0];
   float2* __restrict__ v_out = A.v[ADAPT ? (cur ^ 1) : 0];
-  double kin_new = 0.0, kin_old = 0.0;
+  float kin_new = 0.f, kin_old = 0.f;  // |v'|^2, |v|^2 (FP32; blocks sum them in a fixed order)
 
   if (MODE == kMomentum) {
     if (own) {
@@ -335,8 +351,8 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       y_out[p] = yn;
       if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
       if (ADAPT) {
-        kin_new = (double)vn.x * vn.x + (double)vn.y * vn.y;
-        kin_old = (double)v.x * v.x + (double)v.y * v.y;
+        kin_new = fmaf(vn.y, vn.y, vn.x * vn.x);
+        kin_old = fmaf(v.y, v.y, v.x * v.x);
       }
     }
   } else if (MODE == kNesterov) {
@@ -348,8 +364,8 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       y_out[p] = zn;
       if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(zn);
       if (ADAPT) {
-        kin_new = (double)vn.x * vn.x + (double)vn.y * vn.y;
-        kin_old = (double)v.x * v.x + (double)v.y * v.y;
+        kin_new = fmaf(vn.y, vn.y, vn.x * vn.x);
+        kin_old = fmaf(v.y, v.y, v.x * v.x);
       }
     }
   } else if (MODE == kAdadelta) {
@@ -372,9 +388,9 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
     if (threadIdx.x == 0) A.partials[blockIdx.x] = t;
   }
   if (ADAPT) {
-    __shared__ double red2[kMaxStepBlock / 32];
-    const double tn = block_sum(kin_new, red2);
-    const double to = block_sum(kin_old, red2);
+    __shared__ float red2[kMaxStepBlock / 32];
+    const double tn = (double)block_sum_f32(kin_new, red2);
+    const double to = (double)block_sum_f32(kin_old, red2);
     if (threadIdx.x == 0) {
       A.partials[2 * blockIdx.x] = tn;
       A.partials[2 * blockIdx.x + 1] = to;
@@ -605,11 +621,27 @@ __global__ void __launch_bounds__(1024) k_stress_final(const double* __restrict_
 __global__ void __launch_bounds__(1024) k_adapt(const double* __restrict__ partials, int nblocks,
                                                 float tau, float gamma1, float gamma2,
                                                 AdaptCtl* ctl) {
+  // launched as a programmatic dependent of the step: wait for its partials,
+  // then let the next step's blocks launch (they wait for this grid to finish)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   __shared__ double sh[32];
   double tn = 0.0, to = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    tn += partials[2 * i];
-    to += partials[2 * i + 1];
+  // four independent loads in flight per thread; the summation order is fixed
+  const int stride = (int)blockDim.x;
+  for (int i = threadIdx.x; i < nblocks; i += 4 * stride) {
+    double a[4], c[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = i + q * stride;
+      a[q] = (j < nblocks) ? partials[2 * j] : 0.0;
+      c[q] = (j < nblocks) ? partials[2 * j + 1] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      tn += a[q];
+      to += c[q];
+    }
   }
   tn = block_sum(tn, sh);
   to = block_sum(to, sh);
@@ -805,9 +837,19 @@ cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s) {
     launch_pos<IVHD_METRIC_L1>(ctx, adapt, grid, s, A);
   else
     launch_pos<IVHD_METRIC_L2>(ctx, adapt, grid, s, A);
-  if (adapt)
-    k_adapt<<<1, 1024, 0, s>>>(ctx->partials, grid, ctx->p.tau, ctx->p.gamma1, ctx->p.gamma2,
-                               ctx->ctl);
+  if (adapt) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(1024);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_adapt, (const double*)ctx->partials, grid, ctx->p.tau,
+                       ctx->p.gamma1, ctx->p.gamma2, ctx->ctl);
+  }
   return cudaGetLastError();
 }
 
