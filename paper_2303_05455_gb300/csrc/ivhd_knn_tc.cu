@@ -51,15 +51,16 @@ using namespace tc;
 constexpr int kTM = 128;  // query rows per CTA
 constexpr int kTN = 256;  // candidate columns per accumulator tile
 constexpr int kTStages = 4;
-constexpr int kTcThreads = 192;
+constexpr int kEpiWarps = 8;  // two warpgroups: each reads one 128-column half of a tile
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 
 struct KnnSmem {
   static constexpr int a_bytes = kTM * kBK * 2;
   static constexpr int b_bytes = kTN * kBK * 2;
   static constexpr int stage_bytes = a_bytes + b_bytes;
   static constexpr int bar_offset = kTStages * stage_bytes;
-  static constexpr int nrm_offset = bar_offset + 256;  // 4 warps x 256 column terms
-  static constexpr int total = nrm_offset + 4 * kTN * 4 + 1024;  // + alignment slack
+  static constexpr int nrm_offset = bar_offset + 256;  // 8 warps x 128 column terms
+  static constexpr int total = nrm_offset + kEpiWarps * (kTN / 2) * 4 + 1024;  // + slack
 };
 
 template <class D>
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);  // every epilogue thread arrives
+      mbar_init(&acc_empty[b], 32 * kEpiWarps);  // every epilogue thread arrives
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -202,25 +203,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!mbar_wait(done, 0)) atomicOr(err, 8);
     }
   } else {
-    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31.
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31
+    // (its row quarter) of one 128-column half of each tile: warps 2-5 the
+    // first half, warps 6-9 the second, so every row has one list per half.
     // Keys: uint8, the exact distance; float, the lower-bound key
     // kappa_j = dt_j - eps n_j = n_i + (1 - eps) n_j - 2 <x_i, x_j>~ (see the top).
     // Columns arrive in increasing j, so a key equal to the list's last never
     // enters (the earlier index wins the tie) and the test is a plain "<".
+    constexpr int kHalf = kTN / 2;
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int r = quarter * 32 + lane;
     const int i = m0 + r;
-    // the tile's 256 column terms, staged per warp; each lane prefetches its 8
-    // terms of the next tile into registers while the current one is processed
-    D* nbuf = reinterpret_cast<D*>(smem + KnnSmem::nrm_offset) + quarter * kTN;
-    constexpr int kPer = kTN / 32;
+    // the half-tile's 128 column terms, staged per warp; each lane prefetches
+    // its 4 terms of the next tile into registers while the current one is processed
+    D* nbuf = reinterpret_cast<D*>(smem + KnnSmem::nrm_offset) + (warp - 2) * kHalf;
+    constexpr int kPer = kHalf / 32;
     const D kMaxKey = U8 ? (D)INT_MAX : (D)__int_as_float(0x7f800000);
     const float col_scale = 1.f - eps_coef;
     D pn[kPer];
     auto fetch = [&](int t) {
 #pragma unroll
       for (int e = 0; e < kPer; ++e) {
-        const int jc = t * kTN + e * 32 + lane;
+        const int jc = t * kTN + half * kHalf + e * 32 + lane;
         if constexpr (U8)
           pn[e] = (jc < M) ? nrm_i[jc] : 0;
         else
@@ -249,17 +254,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int e = 0; e < kPer; ++e) nbuf[e * 32 + lane] = pn[e];
       __syncwarp();
       if (t + 1 < n_tiles) fetch(t + 1);
-      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN);
-      const int n0 = t * kTN;
-      for (int c0 = 0; c0 < kTN && n0 + c0 < M; c0 += 64) {
-        uint32_t v[64];
-        tmem_ld32_nowait(tbase + c0, v);
-        tmem_ld32_nowait(tbase + c0 + 32, v + 32);
-        tmem_wait_ld();
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN + half * kHalf);
+      const int n0 = t * kTN + half * kHalf;
+      for (int c0 = 0; c0 < kHalf && n0 + c0 < M; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tbase + c0, v);
         const int jb = n0 + c0;
-        D d[64];
+        D d[32];
 #pragma unroll
-        for (int q = 0; q < 64; q += 4) {
+        for (int q = 0; q < 32; q += 4) {
           D nj[4];
           if constexpr (U8) {
             const int4 w = *reinterpret_cast<const int4*>(nbuf + c0 + q);
@@ -276,26 +279,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               d[q + e] = fmaf(-2.f, __uint_as_float(v[q + e]), ni + nj[e]);
           }
         }
-        if (jb + 63 >= M || (jb <= i && i <= jb + 63)) {
+        if (jb + 31 >= M || (jb <= i && i <= jb + 31)) {
 #pragma unroll
-          for (int q = 0; q < 64; ++q)
+          for (int q = 0; q < 32; ++q)
             if (jb + q >= M || jb + q == i) d[q] = kMaxKey;
         }
         D mn = d[0];
 #pragma unroll
-        for (int q = 1; q < 64; ++q) mn = min(mn, d[q]);
+        for (int q = 1; q < 32; ++q) mn = min(mn, d[q]);
         if (mn < dl[L - 1]) {
           // rare after the first tiles: visit the columns below the threshold in order
           const D thr = dl[L - 1];
-          uint64_t mask = 0;
-          D tmp[64];
+          uint32_t mask = 0;
+          D tmp[32];
 #pragma unroll
-          for (int q = 0; q < 64; ++q) {
-            mask |= (uint64_t)(d[q] < thr) << q;
+          for (int q = 0; q < 32; ++q) {
+            mask |= (uint32_t)(d[q] < thr) << q;
             tmp[q] = d[q];
           }
           while (mask) {
-            const int q = __ffsll((long long)mask) - 1;
+            const int q = __ffs((int)mask) - 1;
             mask &= mask - 1;
             if (tmp[q] < dl[L - 1]) list_insert<D, L>(tmp[q], jb + q, dl, jl);
           }
@@ -305,16 +308,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_arrive(&acc_empty[b]);
     }
     if (ok && i < M) {
-      if constexpr (U8) {
+      // the row's list for this half: out_ids / out_key [(i * 2 + half) * L + q]
+      const int64_t o = ((int64_t)i * 2 + half) * L;
 #pragma unroll
-        for (int q = 0; q < L; ++q)
-          if (q < k) out_ids[(int64_t)i * k + q] = jl[q];
-      } else {
-#pragma unroll
-        for (int q = 0; q < L; ++q) {
-          out_ids[(int64_t)i * L + q] = jl[q];
-          out_d[(int64_t)i * L + q] = dl[q];
-        }
+      for (int q = 0; q < L; ++q) {
+        out_ids[o + q] = jl[q];
+        if constexpr (U8)
+          reinterpret_cast<int32_t*>(out_d)[o + q] = dl[q];
+        else
+          out_d[o + q] = dl[q];
       }
     }
     if (!ok && lane == 0) atomicOr(err, 16);
@@ -403,53 +405,115 @@ __device__ __forceinline__ void cas(float& d, int& j, int lane, int mask, bool u
   }
 }
 
+// Exact FP32-chain distance of rows i and j (the order of the exact kernel).
+__device__ __forceinline__ float chain_dist(const float* __restrict__ xi,
+                                            const float* __restrict__ xj, int N) {
+  float acc = 0.f;
+  for (int q = 0; q < N; ++q) {
+    const float diff = __fsub_rn(xi[q], xj[q]);
+    acc = __fmaf_rn(diff, diff, acc);
+  }
+  return acc;
+}
+
+// Bitonic sort of one (d, j) pair per lane across the warp, ascending.
+__device__ __forceinline__ void warp_sort(float& d, int& j, int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1)
+#pragma unroll
+    for (int m = kk >> 1; m > 0; m >>= 1) cas(d, j, lane, m, (lane & kk) == 0);
+}
+
+// Warp per row: the two half-tile lists (32 candidates each, lane = entry)
+// are re-ranked by the exact FP32 chain, merged, and certified.  A half whose
+// list is full bounds every vertex it left out by its largest key tau_h
+// (d_ij >= tau_h - eps n_i); a half whose list is not full left nothing out.
+template <int L>
 __global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
                          const int32_t* __restrict__ cand, const float* __restrict__ key,
                          const float* __restrict__ nrm, float eps_coef, int32_t* __restrict__ out,
                          int32_t* __restrict__ fb_rows, int32_t* __restrict__ n_fb,
                          int32_t* __restrict__ max_err_bits) {
+  static_assert(L == 16 || L == 32, "half lists of 16 or 32 entries");
+  constexpr int kHalves = 32 / L;  // halves that one warp pass covers (lane = entry)
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= M) return;
-  const int j0 = cand[i * kKnnList + lane];
-  const float kj = key[i * kKnnList + lane];
-  const float tau = __shfl_sync(0xffffffffu, kj, kKnnList - 1);
-  float d = __int_as_float(0x7f800000);
-  int j = INT_MAX;
+  const float* xi = X + i * N;
+  float dh[2 / kHalves];
+  int jh[2 / kHalves];
+  float tau = __int_as_float(0x7f800000);
   float rel = 0.f;
-  if (j0 >= 0 && j0 < M) {
-    const float* xi = X + i * N;
-    const float* xj = X + (int64_t)j0 * N;
-    float acc = 0.f;
-    for (int q = 0; q < N; ++q) {
-      const float diff = __fsub_rn(xi[q], xj[q]);
-      acc = __fmaf_rn(diff, diff, acc);
+#pragma unroll
+  for (int pass = 0; pass < 2 / kHalves; ++pass) {
+    // L = 32: pass h reads half h; L = 16: one pass, lanes 0-15 half 0, 16-31 half 1
+    const int h = (L == 32) ? pass : (lane >> 4);
+    const int64_t o = (i * 2 + h) * L + (lane & (L - 1));
+    const int j0 = cand[o];
+    const float kj = key[o];
+    float d = __int_as_float(0x7f800000);
+    int j = INT_MAX;
+    if (j0 >= 0 && j0 < M) {
+      d = chain_dist(xi, X + (int64_t)j0 * N, N);
+      j = j0;
+      // the approximate distance is the key plus eps n_j
+      rel = fmaxf(rel, fabsf(fmaf(eps_coef, nrm[j0], kj) - d) / fmaxf(nrm[i] + nrm[j0], 1e-30f));
     }
-    d = acc;
-    j = j0;
-    // the approximate distance is the key plus eps n_j
-    rel = fabsf(fmaf(eps_coef, nrm[j0], kj) - acc) / fmaxf(nrm[i] + nrm[j0], 1e-30f);
+#pragma unroll
+    for (int hh = 0; hh < kHalves; ++hh) {
+      // the last entry of each half list present in this pass
+      const int last = hh * L + L - 1;
+      const int jlast = __shfl_sync(0xffffffffu, j0, last);
+      const float klast = __shfl_sync(0xffffffffu, kj, last);
+      if (jlast >= 0 && jlast < M) tau = fminf(tau, klast);
+    }
+    warp_sort(d, j, lane);
+    dh[pass] = d;
+    jh[pass] = j;
   }
-  // bitonic sort of the 32 (d, j) pairs, ascending
+  float d = dh[0];
+  int j = jh[0];
+  if constexpr (L == 32) {
+    // merge: the 32 smallest of both sorted halves form a bitonic sequence
+    // (half 0 ascending against half 1 reversed); a bitonic merge sorts it
+    const float rd = __shfl_sync(0xffffffffu, dh[2 / kHalves - 1], 31 - lane);
+    const int rj = __shfl_sync(0xffffffffu, jh[2 / kHalves - 1], 31 - lane);
+    if (better(rd, rj, d, j)) {
+      d = rd;
+      j = rj;
+    }
 #pragma unroll
-  for (int kk = 2; kk <= 32; kk <<= 1)
-#pragma unroll
-    for (int m = kk >> 1; m > 0; m >>= 1) cas(d, j, lane, m, (lane & kk) == 0);
+    for (int m = 16; m > 0; m >>= 1) cas(d, j, lane, m, true);
+  }
   float mrel = rel;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mrel = fmaxf(mrel, __shfl_xor_sync(0xffffffffu, mrel, o));
   const float dk = __shfl_sync(0xffffffffu, d, k - 1);
-  const int jlast = __shfl_sync(0xffffffffu, j0, kKnnList - 1);
-  // a list that is not full, or that holds every other vertex, leaves nothing out;
-  // otherwise every vertex j outside it has an exact distance >= tau - eps n_i
-  const bool full_list = jlast >= 0 && jlast < M && (int64_t)M - 1 > kKnnList;
-  const bool certified = !full_list || dk < tau - eps_coef * nrm[i];
+  const bool certified = dk < tau - eps_coef * nrm[i];
   if (certified) {
     if (lane < k) out[i * k + lane] = j;
   } else if (lane == 0) {
     fb_rows[atomicAdd(n_fb, 1)] = (int32_t)i;
   }
   if (lane == 0) atomicMax(max_err_bits, __float_as_int(mrel));
+}
+
+// uint8: the two exact half lists of each row (ascending by (distance, index))
+// merged into the k nearest.
+template <int L>
+__global__ void k_merge_u8(const int32_t* __restrict__ ids, const int32_t* __restrict__ keys,
+                           int64_t M, int k, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const int32_t* ja = ids + i * 2 * L;
+  const int32_t* da = keys + i * 2 * L;
+  const int32_t* jb = ja + L;
+  const int32_t* db = da + L;
+  int a = 0, c = 0;
+  for (int q = 0; q < k; ++q) {
+    const bool take_a = c >= L || (a < L && better(da[a], ja[a], db[c], jb[c]));
+    out[i * k + q] = take_a ? ja[a++] : jb[c++];
+  }
 }
 
 template <bool U8, int L>
@@ -523,32 +587,49 @@ ivhd_status knn_tc_build(const void* X, int32_t dtype, int64_t M, int32_t N, int
     return IVHD_ERR_CUDA;
   const float eps_coef = (float)(1.0 / 8192.0 + (double)N / 524288.0);
   if (u8) {
+    const int L = (k <= 8) ? 8 : kKnnList;
     int32_t* nrm = b.get<int32_t>(M);
+    int32_t* lids = b.get<int32_t>(M * 2 * L);
+    int32_t* lkeys = b.get<int32_t>(M * 2 * L);
     if (!b.ok) return IVHD_ERR_OOM;
     if (e == cudaSuccess) {
       k_prep_u8<<<gprep, 256, 0, s>>>((const uint8_t*)X, M, N, Kp, A);
       k_norms_u8s<<<grow, 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
-      e = (k <= 8) ? launch_tc<true, 8>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, out_knn, nullptr,
-                                        err, s)
-                   : launch_tc<true, kKnnList>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, out_knn,
-                                               nullptr, err, s);
+      e = (L == 8) ? launch_tc<true, 8>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, lids,
+                                        (float*)lkeys, err, s)
+                   : launch_tc<true, kKnnList>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, lids,
+                                               (float*)lkeys, err, s);
+    }
+    if (e == cudaSuccess) {
+      if (L == 8)
+        k_merge_u8<8><<<grow, 256, 0, s>>>(lids, lkeys, M, k, out_knn);
+      else
+        k_merge_u8<kKnnList><<<grow, 256, 0, s>>>(lids, lkeys, M, k, out_knn);
+      e = cudaGetLastError();
     }
   } else {
     float* nrm = b.get<float>(M);
-    int32_t* cand = b.get<int32_t>(M * kKnnList);
-    float* cd = b.get<float>(M * kKnnList);
+    const int L = (k <= 8) ? 16 : kKnnList;  // candidates per row and half
+    int32_t* cand = b.get<int32_t>(M * 2 * L);
+    float* cd = b.get<float>(M * 2 * L);
     int32_t* fb = b.get<int32_t>(M);
     if (!b.ok) return IVHD_ERR_OOM;
     if (e == cudaSuccess) {
       k_prep_f32<<<gprep, 256, 0, s>>>((const float*)X, M, N, Kp, A, B);
       k_norms_f32<<<grow, 256, 0, s>>>((const float*)X, M, N, nrm);
-      e = launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef, cand, cd, err,
-                                     s);
+      e = (L == 16) ? launch_tc<false, 16>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef, cand,
+                                           cd, err, s)
+                    : launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef,
+                                                 cand, cd, err, s);
     }
     if (e == cudaSuccess) {
-      k_rerank<<<(unsigned)((M + 7) / 8), 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd,
-                                                      nrm, eps_coef, out_knn, fb, n_fb,
-                                                      maxerr_bits);
+      const unsigned g8 = (unsigned)((M + 7) / 8);
+      if (L == 16)
+        k_rerank<16><<<g8, 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd, nrm, eps_coef,
+                                        out_knn, fb, n_fb, maxerr_bits);
+      else
+        k_rerank<kKnnList><<<g8, 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd, nrm,
+                                              eps_coef, out_knn, fb, n_fb, maxerr_bits);
       e = cudaGetLastError();
     }
     // rows without a certificate: the exact CUDA-core kernel on just those rows

@@ -153,6 +153,25 @@ class Embedding:
         check(self._L.ivhd_forces(self._h, out.data_ptr(), 1), "ivhd_forces")
         return out
 
+    def warm_start(self, xy) -> bool:
+        """Starts from the placement xy (M x 2, e.g. the warm-start network's
+        output) when its stress is finite and below that of the current
+        positions (the seeded uniform start right after create); otherwise keeps
+        the current positions, so plain IVHD is the placement's fallback.  Both
+        stresses are evaluated on the GPU (ivhd_stress).  Zeroes the optimiser
+        state either way.  Returns whether the placement was taken."""
+        y0 = self.positions().clone()
+        e0 = self.stress()
+        self.set_positions(xy)
+        try:
+            e1 = self.stress()
+        except IvhdError:
+            e1 = float("inf")
+        if e1 < e0:
+            return True
+        self.set_positions(y0)
+        return False
+
     def stress(self) -> float:
         v = ctypes.c_double()
         check(self._L.ivhd_stress(self._h, ctypes.byref(v)), "ivhd_stress")

@@ -74,6 +74,19 @@ def test_warm_start_gains_over_random_start():
     lab = torch.from_numpy(Lh).to(dev)
     plain = _curve(knn_h, lab, rows)
     warm = _curve(knn_h, lab, rows, init=Yp)
+    # plain IVHD is the placement's fallback: a good placement is taken, a
+    # non-finite or far worse one leaves the seeded uniform start in place
+    e = ivhd.Embedding(knn_h, r=R, c=C, a=A, b=B, seed=13)
+    y_uniform = e.positions(host=True)
+    bad = Yp.clone()
+    bad[7, 0] = float("nan")
+    assert not e.warm_start(bad)
+    assert np.array_equal(e.positions(host=True), y_uniform)
+    assert not e.warm_start(Yp * 1e4)
+    assert np.array_equal(e.positions(host=True), y_uniform)
+    assert e.warm_start(Yp)
+    assert np.allclose(e.positions(host=True), Yp.cpu().numpy())
+    e.close()
     print({"plain": plain, "warm": warm, "loss": (first, last)})
     # a tenth of the steps reaches a lower stress than plain IVHD after all of them
     assert warm[STEPS // 10]["stress"] < plain[STEPS]["stress"]
