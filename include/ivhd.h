@@ -109,11 +109,13 @@ typedef struct {
     float gamma2;         /* adaptive b: factor (0, 1) applied to b when dT > 0; default 0.5 */
     int32_t block_size;   /* threads per block of the step kernel: 128, 256 or 512;
                              0 = library default (128); see ivhd_autotune */
-    int32_t resident;     /* 0: an embedding whose positions and optimiser state fit one
+    int32_t resident;     /* 1: an embedding whose positions and optimiser state fit one
                              SM's shared memory (about 8,000 vertices; FP32 gathers, no
                              adaptive b) runs all steps of an ivhd_step call in one
                              single-block launch, with the same results bit for bit;
-                             -1: always one launch per step; default 0 */
+                             0: one launch per step (default; the single block is bound
+                             by one SM's instruction rate and only breaks even at
+                             ~2,000 vertices) */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 

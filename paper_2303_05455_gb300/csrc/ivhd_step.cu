@@ -408,6 +408,9 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
 // fit, else read through L1.  The traversal (hub rows warp-per-vertex with the
 // same butterfly, SELL slices thread-per-vertex) and the arithmetic are those of
 // k_step, so the positions agree with the multi-launch path bit for bit.
+// Opt-in (ivhd_params.resident = 1): measured, one SM's instruction rate bounds
+// it (2,000 vertices: 3.38 us per step against 3.43 for one launch per step;
+// 5,000-8,000 vertices with hubs: 10-29 us against 3.3-4.5).
 constexpr int kResidentThreads = 1024;
 
 template <int MODE, int METRIC>
@@ -535,7 +538,7 @@ static size_t resident_bytes(const ivhd_ctx* ctx, bool with_ids) {
 // 0: not eligible (adaptive b, half-precision gathers, or too large); 1: ids
 // read through L1; 2: ids in shared memory too.
 int resident_mode(const ivhd_ctx* ctx) {
-  if (ctx->p.resident < 0 || ctx->p.adaptive || ctx->p.pos_format != IVHD_POS_F32) return 0;
+  if (ctx->p.resident != 1 || ctx->p.adaptive || ctx->p.pos_format != IVHD_POS_F32) return 0;
   if (ctx->M > ((int64_t)1 << 20)) return 0;
   if (resident_bytes(ctx, true) <= (size_t)kResidentSmem) return 2;
   if (resident_bytes(ctx, false) <= (size_t)kResidentSmem) return 1;

@@ -54,14 +54,18 @@ def test_resident_equals_multi_launch_bitwise(name, opt, metric):
     assert ia["kernel_launches"] == 4 and ib["kernel_launches"] == 202
 
 
-def test_resident_not_used_when_state_does_not_fit():
+def test_resident_not_used_when_state_does_not_fit_or_not_asked():
     knn = synth.random_knn_graph(20000, 5, 3)
-    e = ivhd.Embedding(knn, r=1, c=0.01, seed=1)
+    e = ivhd.Embedding(knn, r=1, c=0.01, seed=1, resident=True)
     e.step(10)
     assert e.info()["kernel_launches"] == 10
     e.close()
     small = synth.random_knn_graph(4000, 5, 4)
-    e = ivhd.Embedding(small, r=1, c=0.01, seed=1, adaptive=True)  # adaptive b: multi-launch
+    e = ivhd.Embedding(small, r=1, c=0.01, seed=1)  # default: one launch per step
+    e.step(10)
+    assert e.info()["kernel_launches"] == 10
+    e.close()
+    e = ivhd.Embedding(small, r=1, c=0.01, seed=1, resident=True, adaptive=True)
     e.step(10)
     assert e.info()["kernel_launches"] == 20  # step kernel + controller per step
     e.close()
