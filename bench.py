@@ -327,7 +327,11 @@ def run_ours(args):
 
     # kNN precision of the timed embedding (sampled rows, exact neighbour sets),
     # class purity cf_nn, stress and finiteness of the final positions
-    rows = torch.from_numpy(synth.sample_rows(w.M, args.qnx_rows, 12345)).to(dev)
+    # Q_NX / cf over every vertex up to 1e5 vertices, else over a seeded sample
+    if w.M <= 100_000:
+        rows = torch.arange(w.M, dtype=torch.int64, device=dev)
+    else:
+        rows = torch.from_numpy(synth.sample_rows(w.M, args.qnx_rows, 12345)).to(dev)
     lab = torch.from_numpy(labels).to(dev)
 
     def quality(pos_format="f32"):
