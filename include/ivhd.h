@@ -109,13 +109,15 @@ typedef struct {
     float gamma2;         /* adaptive b: factor (0, 1) applied to b when dT > 0; default 0.5 */
     int32_t block_size;   /* threads per block of the step kernel: 128, 256 or 512;
                              0 = library default (128); see ivhd_autotune */
-    int32_t resident;     /* 1: an embedding whose positions and optimiser state fit one
-                             SM's shared memory (about 8,000 vertices; FP32 gathers, no
-                             adaptive b) runs all steps of an ivhd_step call in one
-                             single-block launch, with the same results bit for bit;
-                             0: one launch per step (default; the single block is bound
-                             by one SM's instruction rate and only breaks even at
-                             ~2,000 vertices) */
+    int32_t resident;     /* whole ivhd_step calls in one launch, for small embeddings whose
+                             positions and optimiser state fit an SM's shared memory
+                             (about 8,000 vertices; FP32 gathers, no adaptive b), with
+                             results equal to one launch per step bit for bit:
+                             2: a cluster of 8 blocks, each with a full copy of the
+                             positions, updated through distributed shared memory;
+                             1: a single block; 0 (default): the cluster for graphs of at
+                             most 40,000 stored entries, where it is faster, else one
+                             launch per step; -1: always one launch per step */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 

@@ -78,7 +78,7 @@ bool params_ok(const ivhd_params& p) {
   if (p.adaptive != 0 && p.adaptive != 1) return false;
   if (p.block_size != 0 && p.block_size != 128 && p.block_size != 256 && p.block_size != 512)
     return false;
-  if (p.resident != 0 && p.resident != 1) return false;
+  if (p.resident < -1 || p.resident > 2) return false;
   if (p.adaptive) {
     if (p.opt == IVHD_OPT_ADADELTA) return false;
     if (!std::isfinite(p.tau) || p.tau <= 0.f) return false;

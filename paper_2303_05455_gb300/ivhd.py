@@ -50,7 +50,7 @@ class Embedding:
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
                  hub_threshold: int = 0, pos_format: str = "f32", adaptive: bool = False,
                  tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, block_size: int = 0,
-                 resident: bool = False, stream=None, device=None, batch=None):
+                 resident=None, stream=None, device=None, batch=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -77,7 +77,9 @@ class Embedding:
         p.adaptive = int(adaptive)
         p.tau, p.gamma1, p.gamma2 = tau, gamma1, gamma2
         p.block_size = int(block_size)
-        p.resident = 1 if resident else 0
+        # resident: None (automatic), False (one launch per step), True (one block),
+        # "cluster" (8-block cluster)
+        p.resident = {None: 0, False: -1, True: 1, "cluster": 2}[resident]
         p.stream = self.stream.cuda_stream or None
         self.opt = opt
         self.params = p

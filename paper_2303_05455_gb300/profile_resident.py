@@ -30,7 +30,7 @@ def main():
     s = torch.cuda.current_stream()
     for rep in range(args.reps):
         out = {"rep": rep}
-        for resident in (True, False):
+        for resident in (True, "cluster", False):
             emb = ivhd.Embedding(knn, r=w.r, c=w.c, a=w.a, b=w.b, seed=w.seed, opt=args.opt,
                                  resident=resident)
             emb.step(16)
@@ -39,8 +39,8 @@ def main():
             emb.step(args.steps)
             e1.record(s)
             torch.cuda.synchronize()
-            out["resident_us" if resident else "multi_launch_us"] = 1e3 * e0.elapsed_time(e1) / args.steps
-            out["n_hub" if resident else "_"] = emb.info()["n_hub"]
+            key = {True: "resident_us", "cluster": "cluster_us", False: "multi_launch_us"}[resident]
+            out[key] = 1e3 * e0.elapsed_time(e1) / args.steps
             emb.close()
         print(json.dumps(out), flush=True)
 

@@ -102,7 +102,7 @@ def test_create_rejects_bad_sizes(L, M, k, r, c):
     ("opt", 3), ("opt", -1), ("a", -0.1), ("a", 1.5), ("a", float("nan")), ("b", 0.0),
     ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
     ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1), ("adaptive", 2),
-    ("block_size", 64), ("block_size", 1024), ("resident", 2), ("resident", -1),
+    ("block_size", 64), ("block_size", 1024), ("resident", 3), ("resident", -2),
 ])
 def test_create_rejects_bad_params(L, field, value):
     p = _lib.Params()

@@ -163,8 +163,8 @@ def test_deterministic_bitwise():
 
 def test_graph_replay_equals_single_launches():
     knn, r, c = graph_case("gmm2k")
-    a = ivhd.Embedding(knn, r=r, c=c, seed=4)
-    b = ivhd.Embedding(knn, r=r, c=c, seed=4)
+    a = ivhd.Embedding(knn, r=r, c=c, seed=4, resident=False)
+    b = ivhd.Embedding(knn, r=r, c=c, seed=4, resident=False)
     a.step(130)
     for _ in range(130):
         b.step(1)

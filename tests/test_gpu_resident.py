@@ -29,13 +29,14 @@ def graphs():
 GRAPHS = graphs()
 
 
+@pytest.mark.parametrize("kind", [True, "cluster"])
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 @pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
 @pytest.mark.parametrize("metric", ["l2", "l1"])
-def test_resident_equals_multi_launch_bitwise(name, opt, metric):
+def test_resident_equals_multi_launch_bitwise(name, opt, metric, kind):
     knn, r, c = GRAPHS[name]
     runs = []
-    for resident in (True, False):
+    for resident in (kind, False):
         e = ivhd.Embedding(knn, r=r, c=c, opt=opt, b=0.002, seed=9, resident=resident)
         if metric == "l1":
             e.set_metric("l1")
@@ -60,8 +61,17 @@ def test_resident_not_used_when_state_does_not_fit_or_not_asked():
     e.step(10)
     assert e.info()["kernel_launches"] == 10
     e.close()
-    small = synth.random_knn_graph(4000, 5, 4)
-    e = ivhd.Embedding(small, r=1, c=0.01, seed=1)  # default: one launch per step
+    small = synth.random_knn_graph(4000, 5, 4)  # ~46k entries: above the automatic limit
+    e = ivhd.Embedding(small, r=1, c=0.01, seed=1)
+    e.step(10)
+    assert e.info()["nnz_sym"] > 40000 and e.info()["kernel_launches"] == 10
+    e.close()
+    tiny = synth.random_knn_graph(1000, 3, 4)  # automatic: the cluster kernel
+    e = ivhd.Embedding(tiny, r=1, c=0.01, seed=1)
+    e.step(10)
+    assert e.info()["kernel_launches"] == 1
+    e.close()
+    e = ivhd.Embedding(tiny, r=1, c=0.01, seed=1, resident=False)
     e.step(10)
     assert e.info()["kernel_launches"] == 10
     e.close()
