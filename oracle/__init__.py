@@ -14,6 +14,8 @@ the readings taken where the paper is ambiguous):
 * ``stress``, ``forces`` -- E and F = -1/2 grad E.
 * ``step`` / ``run``   -- momentum (force-directed), Nesterov, Adadelta.
 * ``knn_f32`` / ``knn_u8`` -- exact brute-force kNN.
+* ``knn_query``, ``place_nn`` -- kNN of new points in a base set and their
+  placement at the mean embedding of those neighbours (Progressive UMAP).
 * ``qnx``, ``cf``      -- Q_NX(k) and neighbour hit cf_nn.
 """
 from __future__ import annotations
@@ -69,6 +71,12 @@ def _L():
         lib.ivo_knn_f32.restype = i32
         lib.ivo_knn_u8.argtypes = [P, i64, i32, i32, P, i64, P]
         lib.ivo_knn_u8.restype = i32
+        lib.ivo_knn_query_f32.argtypes = [P, i64, P, i64, i32, i32, P]
+        lib.ivo_knn_query_f32.restype = i32
+        lib.ivo_knn_query_u8.argtypes = [P, i64, P, i64, i32, i32, P]
+        lib.ivo_knn_query_u8.restype = i32
+        lib.ivo_place_nn.argtypes = [P, P, i64, i32, P]
+        lib.ivo_place_nn.restype = None
         lib.ivo_qnx.argtypes = [P, i64, P, i32, P, i64, P]
         lib.ivo_qnx.restype = dbl
         lib.ivo_cf.argtypes = [P, i64, P, i32, P, i64]
@@ -234,6 +242,30 @@ def knn_u8(X, k: int, rows=None) -> np.ndarray:
     out = np.empty((n, k), dtype=np.int32)
     if _L().ivo_knn_u8(_p(X), M, N, k, _p(rows_a), n, _p(out)) != 0:
         raise ValueError("oracle knn: need 1 <= k <= M-1")
+    return out
+
+
+def knn_query(Q, X, k: int) -> np.ndarray:
+    """The k base rows of X nearest to each query row of Q (float32 or uint8)."""
+    u8 = np.asarray(X).dtype == np.uint8
+    Q = _c(Q, np.uint8 if u8 else np.float32)
+    X = _c(X, np.uint8 if u8 else np.float32)
+    (Mq, N), M = Q.shape, X.shape[0]
+    assert X.shape[1] == N
+    out = np.empty((Mq, k), dtype=np.int32)
+    fn = _L().ivo_knn_query_u8 if u8 else _L().ivo_knn_query_f32
+    if fn(_p(Q), Mq, _p(X), M, N, k, _p(out)) != 0:
+        raise ValueError("oracle knn_query: need 1 <= k <= M")
+    return out
+
+
+def place_nn(Y, ids) -> np.ndarray:
+    """y_q = mean of Y over the base neighbours ids[q] (FP64)."""
+    Y = _c(Y, np.float32)
+    ids = _c(ids, np.int32)
+    n, k = ids.shape
+    out = np.empty((n, 2), dtype=np.float64)
+    _L().ivo_place_nn(_p(Y), _p(ids), n, k, _p(out))
     return out
 
 

@@ -22,6 +22,8 @@
  *     IVHD-CUDA scheme (Algorithm in Sec. 5.2)
  *   - neighbourhood preservation Q_NX(k)                Sec. 4.1 (rank criteria)
  *   - neighbour hit cf_nn                               Sec. 4.1, Eq. 4.4
+ *   - placement of new points at the embedding of their
+ *     nearest base neighbour(s)                        Sec. 2.4.3 (Progressive UMAP)
  *
  * READINGS where the paper is silent, garbled or inconsistent:
  *   R1  d_ij is the Euclidean norm ||y_i - y_j||_2 (Sec. 3.3 prints a square
@@ -512,6 +514,82 @@ int ivo_knn_u8(const uint8_t *X, int64_t M, int N, int k, const int64_t *rows, i
     }
     free(bd);
     return 0;
+}
+
+/*
+ * Exact kNN of query rows against a separate base set: the nearest-neighbour
+ * search of the Progressive UMAP placement (Sec. 2.4.3, Progressive UMAP
+ * scheme), made exact.  For each of the Mq queries, the k base rows nearest by
+ * the same FP32 sequential squared distance as ivo_knn_f32 (uint8: the exact
+ * integer distance), ascending, ties by lower index.  No row is excluded: a
+ * query equal to a base row finds it at distance 0.  out is Mq x k.
+ */
+int ivo_knn_query_f32(const float *Q, int64_t Mq, const float *X, int64_t M, int N, int k,
+                      int32_t *out)
+{
+    if (k < 1 || k > M) return -1;
+    float *bd = (float *)malloc(sizeof(float) * (size_t)k);
+    if (!bd) return -1;
+    for (int64_t q = 0; q < Mq; ++q) {
+        int32_t *bj = out + q * (int64_t)k;
+        int n = 0;
+        const float *xq = Q + q * (int64_t)N;
+        for (int64_t j = 0; j < M; ++j) {
+            const float *xj = X + j * (int64_t)N;
+            float acc = 0.0f;
+            for (int d = 0; d < N; ++d) {
+                float diff = xq[d] - xj[d];
+                acc = fmaf(diff, diff, acc);
+            }
+            ivo_topk_insert_f(bd, bj, &n, k, acc, (int32_t)j);
+        }
+    }
+    free(bd);
+    return 0;
+}
+
+int ivo_knn_query_u8(const uint8_t *Q, int64_t Mq, const uint8_t *X, int64_t M, int N, int k,
+                     int32_t *out)
+{
+    if (k < 1 || k > M) return -1;
+    int64_t *bd = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    if (!bd) return -1;
+    for (int64_t q = 0; q < Mq; ++q) {
+        int32_t *bj = out + q * (int64_t)k;
+        int n = 0;
+        const uint8_t *xq = Q + q * (int64_t)N;
+        for (int64_t j = 0; j < M; ++j) {
+            const uint8_t *xj = X + j * (int64_t)N;
+            int64_t acc = 0;
+            for (int d = 0; d < N; ++d) {
+                int64_t diff = (int64_t)xq[d] - (int64_t)xj[d];
+                acc += diff * diff;
+            }
+            ivo_topk_insert_i(bd, bj, &n, k, acc, (int32_t)j);
+        }
+    }
+    free(bd);
+    return 0;
+}
+
+/*
+ * Placement of new points from the embedding Y of their base neighbours:
+ * y_q = (1/k) sum_s Y[ids[q][s]] in FP64.  k = 1 is the Progressive UMAP
+ * initialisation (a new point starts at the embedding of its nearest
+ * neighbour, Sec. 2.4.3).  out is n x 2.
+ */
+void ivo_place_nn(const float *Y, const int32_t *ids, int64_t n, int k, double *out)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        double sx = 0.0, sy = 0.0;
+        for (int s = 0; s < k; ++s) {
+            int64_t j = ids[q * (int64_t)k + s];
+            sx += (double)Y[2 * j];
+            sy += (double)Y[2 * j + 1];
+        }
+        out[2 * q] = sx / k;
+        out[2 * q + 1] = sy / k;
+    }
 }
 
 /* The FP32 2-D squared distance that decides low-dimensional neighbours (R9). */

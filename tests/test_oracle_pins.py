@@ -504,3 +504,56 @@ def test_mlp_gelu_and_adam_closed_forms():
     for n in p.names():
         np.testing.assert_allclose(getattr(p, n) - getattr(before, n), 1e-3 * (0.3 / (0.3 + 1e-8)),
                                    rtol=1e-12)
+
+
+# ---------------------------------------------------------------- new points
+
+
+def test_knn_query_on_a_line_textbook():
+    # base points 0, 2, 4, ..., 38 on a line; a query at 5 is 1 from 4 and 6,
+    # then 3 from 2 and 8: ties go to the lower index; a query on a base
+    # point finds it first (nothing is excluded).
+    X = (np.arange(20, dtype=np.float32) * 2)[:, None]
+    Q = np.array([[5.0], [0.0], [38.5], [-7.0]], np.float32)
+    out = oracle.knn_query(Q, X, 4)
+    assert out[0].tolist() == [2, 3, 1, 4]
+    assert out[1].tolist() == [0, 1, 2, 3]
+    assert out[2].tolist() == [19, 18, 17, 16]
+    assert out[3].tolist() == [0, 1, 2, 3]
+    Xu = (np.arange(20) * 2).astype(np.uint8)[:, None]
+    Qu = np.array([[5], [0], [38], [1]], np.uint8)
+    assert oracle.knn_query(Qu, Xu, 3).tolist() == [[2, 3, 1], [0, 1, 2], [19, 18, 17],
+                                                   [0, 1, 2]]
+
+
+def test_knn_query_matches_float64_brute_force_and_integer_lexsort():
+    Z, _ = synth.gaussian_mixture(490, 16, 4, 7)
+    X, Q = Z[:400], Z[400:]
+    out = oracle.knn_query(Q, X, 5)
+    D = ((Q.astype(np.float64)[:, None, :] - X.astype(np.float64)[None, :, :]) ** 2).sum(-1)
+    ref = np.argsort(D, axis=1, kind="stable")[:, :5]
+    srt = np.sort(D, axis=1)
+    safe = (srt[:, 5] - srt[:, 4]) > 1e-3 * srt[:, 4]
+    assert safe.mean() > 0.9
+    for i in np.nonzero(safe)[0]:
+        assert set(out[i].tolist()) == set(ref[i].tolist())
+    Zu, _ = synth.mnist_like(370, 3, N=48)
+    Xu, Qu = Zu[:300], Zu[300:]
+    Du = ((Qu.astype(np.int64)[:, None, :] - Xu.astype(np.int64)[None, :, :]) ** 2).sum(-1)
+    order = np.lexsort((np.broadcast_to(np.arange(300), Du.shape), Du), axis=1)[:, :6]
+    assert np.array_equal(oracle.knn_query(Qu, Xu, 6), order)
+
+
+def test_knn_query_of_the_base_itself_is_self_then_the_knn_graph():
+    X, _ = synth.gaussian_mixture(250, 12, 3, 2)
+    q = oracle.knn_query(X, X, 5)
+    assert np.array_equal(q[:, 0], np.arange(250))
+    assert np.array_equal(q[:, 1:], oracle.knn_f32(X, 4))
+
+
+def test_place_nn_is_the_neighbour_mean():
+    Y = np.array([[0, 0], [2, 0], [0, 4], [6, 6]], np.float32)
+    ids = np.array([[0, 1], [1, 2], [3, 3], [2, 0]], np.int32)
+    assert oracle.place_nn(Y, ids).tolist() == [[1, 0], [1, 2], [6, 6], [0, 2]]
+    # k = 1 is the embedding of the nearest neighbour itself
+    assert oracle.place_nn(Y, ids[:, :1]).tolist() == Y[ids[:, 0]].tolist()
