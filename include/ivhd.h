@@ -370,6 +370,46 @@ ivhd_status ivhd_knn_build_ex(const void *X, int32_t dtype, int64_t M, int32_t N
                               void *stream);
 
 /*
+ * ivhd_knn_query -- the k nearest base rows of new points.
+ *
+ * The nearest-neighbour search with which Progressive UMAP places a point that
+ * arrives after the embedding was made (Sec. 2.4.3, Progressive UMAP scheme:
+ * a new point starts at the embedding of its nearest neighbour among the data
+ * seen so far), made exact.  out row q lists the k rows of the base set X
+ * nearest to query row q of Q, ascending by (distance, index), with the
+ * distances of ivhd_knn_build (FP32 chain for float data, exact integers for
+ * uint8).  No row is excluded: a query equal to a base row finds it at
+ * distance 0.
+ *   Q        device, Mq*N elements of `dtype`, row-major (the new points).
+ *   X        device, M*N elements of `dtype`, row-major (the base set).
+ *   out      device, Mq*k int32.
+ *   method, stats   as ivhd_knn_build_ex.
+ * 1 <= Mq < 2^31 - 1, 1 <= M < 2^31 - 1, 1 <= k <= min(M, 64), N as
+ * ivhd_knn_build; the tensor-core method needs M >= 2 and k <= 32.  Else
+ * IVHD_ERR_ARG.  Synchronises.
+ */
+ivhd_status ivhd_knn_query(const void *Q, int64_t Mq, const void *X, int64_t M, int32_t dtype,
+                           int32_t N, int32_t k, int32_t *out, int32_t method,
+                           ivhd_knn_stats_t *stats, void *stream);
+
+/*
+ * ivhd_place_nn -- place new points at the mean embedding of base neighbours.
+ *
+ * out[q] = (1/k) sum_s Y[ids[q][s]], the sum taken in FP32 in the order
+ * s = 0 .. k-1.  With the lists of ivhd_knn_query and k = 1 this is the
+ * Progressive UMAP initialisation of a new point (Sec. 2.4.3); k > 1 averages
+ * the embeddings of its k nearest base points.
+ *   Y     device, M*2 float32 (the embedding of the base set, input order).
+ *   ids   device, n*k int32, each in [0, M).
+ *   out   device, n*2 float32.
+ * M >= 1, n >= 0, 1 <= k <= 1024, else IVHD_ERR_ARG (ids and out may be NULL
+ * when n = 0, which does nothing); an id outside [0, M)
+ * returns IVHD_ERR_INDEX (rows holding one are left unwritten).  Synchronises.
+ */
+ivhd_status ivhd_place_nn(const float *Y, int64_t M, const int32_t *ids, int64_t n, int32_t k,
+                          float *out, void *stream);
+
+/*
  * Neighbourhood preservation Q_NX(k) of Sec. 4.1 on sampled rows: for each
  * row q in `rows`, the k nearest other points of y_q in the embedding (FP32
  * squared distance dx*dx rounded then fma(dy, dy, .), ties by lower index)
@@ -498,6 +538,38 @@ int64_t ivhd_mlp_launches(ivhd_mlp *mlp);
 ivhd_status ivhd_eval_qnx_static(const float *Y, int64_t M, const int32_t *knn, int32_t k,
                                  const int64_t *rows, int64_t nrows, int32_t *out_lowd,
                                  double *out_q, void *stream);
+
+/*
+ * ivhd_set_allocator -- take the library's device memory from the caller.
+ *
+ * The paper has no counterpart.  By default every device buffer of the
+ * library (context state, layouts, kNN and network scratch) comes from the
+ * stream-ordered pool (cudaMallocAsync / cudaFreeAsync on the call's stream).
+ * After this call, every later allocation calls alloc_fn instead, e.g. a
+ * framework's caching allocator, so that one pool serves both:
+ *
+ *   alloc_fn(bytes, stream, user): returns device memory of at least `bytes`
+ *     bytes on the current device, usable by work that the library then
+ *     enqueues on `stream` (a cudaStream_t; NULL = legacy default stream),
+ *     aligned to 256 bytes (as cudaMalloc is), or NULL when it cannot, which
+ *     the calling entry point reports as IVHD_ERR_OOM.  A pointer that is not
+ *     256-byte aligned is handed straight back to free_fn and treated as
+ *     NULL.
+ *   free_fn(ptr, bytes, stream, user): the library no longer needs ptr once
+ *     the work queued on `stream` so far has run; the allocator may hand the
+ *     block to later work on that stream at once (the contract of a
+ *     stream-ordered caching allocator) but to other streams only after that
+ *     work has finished.  `bytes` is the size that was asked for.
+ *
+ * Process-wide.  Both NULL restores the built-in pool; exactly one NULL is
+ * IVHD_ERR_ARG.  Each block is released through the allocator that made it,
+ * whatever the setting at release time.  The callbacks run on the calling
+ * host thread, never while a stream is being captured, and must not call
+ * back into the library.  Returns IVHD_OK.
+ */
+typedef void *(*ivhd_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*ivhd_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+ivhd_status ivhd_set_allocator(ivhd_alloc_fn alloc_fn, ivhd_free_fn free_fn, void *user);
 
 /*
  * Test support (the paper has no counterpart).

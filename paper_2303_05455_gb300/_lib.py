@@ -27,8 +27,13 @@ SYMBOLS = (
     "ivhd_gemm_bf16_tn", "ivhd_mlp_create", "ivhd_mlp_destroy", "ivhd_mlp_num_params",
     "ivhd_mlp_set_params", "ivhd_mlp_get_params", "ivhd_mlp_loss_grad", "ivhd_mlp_train_step",
     "ivhd_mlp_forward", "ivhd_mlp_launches", "ivhd_probe_wait_timeout", "ivhd_test_fail_alloc",
-    "ivhd_test_live_allocs",
+    "ivhd_test_live_allocs", "ivhd_set_allocator", "ivhd_knn_query", "ivhd_place_nn",
 )
+
+# callback types of ivhd_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                           ctypes.c_void_p)
 
 
 class IvhdError(RuntimeError):
@@ -116,12 +121,18 @@ def load(build_if_missing: bool = False):
     L.ivhd_knn_build.restype = i32
     L.ivhd_knn_build_ex.argtypes = [P, i32, i64, i32, i32, P, i32, P, P]
     L.ivhd_knn_build_ex.restype = i32
+    L.ivhd_knn_query.argtypes = [P, i64, P, i64, i32, i32, i32, P, i32, P, P]
+    L.ivhd_knn_query.restype = i32
+    L.ivhd_place_nn.argtypes = [P, i64, P, i64, i32, P, P]
+    L.ivhd_place_nn.restype = i32
     L.ivhd_probe_wait_timeout.argtypes = [i32, P]
     L.ivhd_probe_wait_timeout.restype = i32
     L.ivhd_test_fail_alloc.argtypes = [i64]
     L.ivhd_test_fail_alloc.restype = None
     L.ivhd_test_live_allocs.argtypes = []
     L.ivhd_test_live_allocs.restype = i64
+    L.ivhd_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
+    L.ivhd_set_allocator.restype = i32
     L.ivhd_eval_qnx.argtypes = [P, i64, P, i32, P, i64, P, ctypes.POINTER(ctypes.c_double), P]
     L.ivhd_eval_qnx.restype = i32
     L.ivhd_eval_cf.argtypes = [P, i64, P, i32, P, i64, ctypes.POINTER(ctypes.c_double), P]

@@ -7,6 +7,8 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 
 #include "ivhd_internal.cuh"
 
@@ -15,17 +17,64 @@ namespace ivhd {
 static std::atomic<int64_t> g_live_allocs{0};
 static std::atomic<int64_t> g_fail_after{-1};  // allocations to grant before one fails; -1 = off
 
-cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+// The caller's allocator (ivhd_set_allocator) and the blocks it handed out,
+// each with the free routine to return it to.  Never destroyed, so a context
+// released during process teardown still finds its blocks.
+struct UserAllocator {
+  ivhd_alloc_fn alloc = nullptr;
+  ivhd_free_fn release = nullptr;
+  void* user = nullptr;
+};
+struct UserBlock {
+  ivhd_free_fn release;
+  void* user;
+  size_t bytes;
+};
+static std::mutex& alloc_mutex() {
+  static std::mutex* m = new std::mutex;
+  return *m;
+}
+static UserAllocator g_user_alloc;  // guarded by alloc_mutex()
+static std::unordered_map<void*, UserBlock>& user_blocks() {
+  static auto* m = new std::unordered_map<void*, UserBlock>;
+  return *m;
+}
+
+static bool take_injected_failure() {
   int64_t f = g_fail_after.load();
   while (f >= 0) {
     if (f == 0) {
-      if (g_fail_after.compare_exchange_weak(f, -1)) {
-        *p = nullptr;
-        return cudaErrorMemoryAllocation;
-      }
+      if (g_fail_after.compare_exchange_weak(f, -1)) return true;
     } else if (g_fail_after.compare_exchange_weak(f, f - 1)) {
-      break;
+      return false;
     }
+  }
+  return false;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (take_injected_failure()) return cudaErrorMemoryAllocation;
+  UserAllocator ua;
+  {
+    std::lock_guard<std::mutex> lock(alloc_mutex());
+    ua = g_user_alloc;
+  }
+  if (ua.alloc) {
+    // the callback runs without the lock held, so it may take its own locks
+    void* q = ua.alloc(bytes, (void*)s, ua.user);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      ua.release(q, bytes, (void*)s, ua.user);
+      return cudaErrorMemoryAllocation;
+    }
+    {
+      std::lock_guard<std::mutex> lock(alloc_mutex());
+      user_blocks()[q] = UserBlock{ua.release, ua.user, bytes};
+    }
+    *p = q;
+    g_live_allocs.fetch_add(1);
+    return cudaSuccess;
   }
   const cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e == cudaSuccess) g_live_allocs.fetch_add(1);
@@ -35,6 +84,22 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
 cudaError_t dev_free(void* p, cudaStream_t s) {
   if (!p) return cudaSuccess;
   g_live_allocs.fetch_sub(1);
+  UserBlock b{};
+  bool from_user = false;
+  {
+    std::lock_guard<std::mutex> lock(alloc_mutex());
+    auto& m = user_blocks();
+    auto it = m.find(p);
+    if (it != m.end()) {
+      b = it->second;
+      m.erase(it);
+      from_user = true;
+    }
+  }
+  if (from_user) {
+    b.release(p, b.bytes, (void*)s, b.user);
+    return cudaSuccess;
+  }
   return cudaFreeAsync(p, s);
 }
 
@@ -44,6 +109,14 @@ NvtxScope::~NvtxScope() { nvtxRangePop(); }
 }  // namespace ivhd
 
 using namespace ivhd;
+
+extern "C" ivhd_status ivhd_set_allocator(ivhd_alloc_fn alloc_fn, ivhd_free_fn free_fn,
+                                          void* user) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return IVHD_ERR_ARG;
+  std::lock_guard<std::mutex> lock(alloc_mutex());
+  g_user_alloc = UserAllocator{alloc_fn, free_fn, alloc_fn ? user : nullptr};
+  return IVHD_OK;
+}
 
 extern "C" void ivhd_test_fail_alloc(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
 extern "C" int64_t ivhd_test_live_allocs(void) { return g_live_allocs.load(); }

@@ -30,7 +30,8 @@
 namespace ivhd {
 
 // Every device allocation of the library goes through these two calls
-// (stream-ordered cudaMallocAsync / cudaFreeAsync).  They count the live
+// (stream-ordered cudaMallocAsync / cudaFreeAsync, or the caller's allocator
+// set with ivhd_set_allocator).  They count the live
 // allocations, so tests can check that error paths free what they took, and
 // ivhd_test_fail_alloc can make one of them fail to exercise those paths.
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);

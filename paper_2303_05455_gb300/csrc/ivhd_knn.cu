@@ -10,6 +10,12 @@
 // candidates in tiles of 128 with an 8x8 register block per thread; after each
 // tile the 128x128 distances go through shared memory into a per-query sorted
 // list of the k best.
+//
+// The same search answers queries from a separate set of new points against
+// the embedded base set (ivhd_knn_query), and ivhd_place_nn puts each new
+// point at the mean embedding of its base neighbours: with k = 1 the
+// Progressive UMAP initialisation of a new point (Sec. 2.4.3), the comparator
+// of the learned placement.
 #include "ivhd_internal.cuh"
 #include "ivhd_knn_tc.cuh"
 
@@ -35,14 +41,15 @@ __device__ __forceinline__ bool better(D d, int j, D bd, int bj) {
   return d < bd || (d == bd && j < bj);
 }
 
-// Merge one 128-candidate row of the tile into query t's sorted list.
+// Merge one 128-candidate row of the tile into a query's sorted list; the
+// candidate `skip` (the query itself in a kNN graph, else -1) is left out.
 template <class D>
-__device__ __forceinline__ void merge_row(const D* row, int c0, int64_t M, int64_t q, int k,
+__device__ __forceinline__ void merge_row(const D* row, int c0, int64_t M, int64_t skip, int k,
                                           D* ld, int* lj, int& n) {
   for (int b = 0; b < kTC; ++b) {
     const int64_t j = c0 + b;
     if (j >= M) break;
-    if (j == q) continue;
+    if (j == skip) continue;
     const D d = row[b];
     if (n == k && !better(d, (int)j, ld[k - 1], lj[k - 1])) continue;
     int pos = (n < k) ? n : k - 1;
@@ -57,12 +64,13 @@ __device__ __forceinline__ void merge_row(const D* row, int c0, int64_t M, int64
   }
 }
 
+// Queries: the Mq rows of Q (Q = X and self = true for the kNN graph).
 // rows / n_rows (device, optional): the CTA's queries are entries q0 .. q0+127
 // of the list rows[0 .. *n_rows) instead of rows q0 .. q0+127.
-__global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ X, int64_t M,
-                                                      int N, int k, int32_t* __restrict__ out,
-                                                      const int32_t* __restrict__ rows,
-                                                      const int32_t* __restrict__ n_rows) {
+__global__ void __launch_bounds__(kThreads)
+    k_knn_f32(const float* __restrict__ Q, int64_t Mq, const float* __restrict__ X, int64_t M,
+              int N, int k, bool self, int32_t* __restrict__ out,
+              const int32_t* __restrict__ rows, const int32_t* __restrict__ n_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* Qs = reinterpret_cast<float*>(smem);                    // [kDK][kTQ + 4]
   float* Cs = Qs + kDK * (kTQ + 4);                              // [kDK][kTC + 4]
@@ -73,7 +81,7 @@ __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t q0 = (int64_t)blockIdx.x * kTQ;
-  const int64_t nq = rows ? (int64_t)*n_rows : M;
+  const int64_t nq = rows ? (int64_t)*n_rows : Mq;
   if (q0 >= nq) return;
   auto qrow = [&](int64_t t) -> int64_t { return rows ? (int64_t)rows[t] : t; };
   int nlist = 0;  // used by threads tid < kTQ
@@ -91,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ 
         const int row = e / kDK, dd = e % kDK;
         const int64_t tq = q0 + row, gc = c0 + row;
         const int d = d0 + dd;
-        Qs[dd * (kTQ + 4) + row] = (tq < nq && d < N) ? X[qrow(tq) * N + d] : 0.f;
+        Qs[dd * (kTQ + 4) + row] = (tq < nq && d < N) ? Q[qrow(tq) * N + d] : 0.f;
         Cs[dd * (kTC + 4) + row] = (gc < M && d < N) ? X[gc * N + d] : 0.f;
       }
       __syncthreads();
@@ -119,8 +127,8 @@ __global__ void __launch_bounds__(kThreads) k_knn_f32(const float* __restrict__ 
       for (int b = 0; b < 8; ++b) Dt[(ty * 8 + a) * kDStride + tx * 8 + b] = acc[a][b];
     __syncthreads();
     if (tid < kTQ && q0 + tid < nq)
-      merge_row<float>(Dt + tid * kDStride, (int)c0, M, qrow(q0 + tid), k, Ld + tid * k,
-                       Lj + tid * k, nlist);
+      merge_row<float>(Dt + tid * kDStride, (int)c0, M, self ? qrow(q0 + tid) : -1, k,
+                       Ld + tid * k, Lj + tid * k, nlist);
     __syncthreads();
   }
   if (tid < kTQ && q0 + tid < nq)
@@ -150,9 +158,10 @@ __device__ __forceinline__ uint32_t pack4(const uint8_t* __restrict__ X, int64_t
   return w;
 }
 
-__global__ void __launch_bounds__(kThreads) k_knn_u8(const uint8_t* __restrict__ X,
-                                                     const int32_t* __restrict__ nrm, int64_t M,
-                                                     int N, int k, int32_t* __restrict__ out) {
+__global__ void __launch_bounds__(kThreads)
+    k_knn_u8(const uint8_t* __restrict__ Q, const int32_t* __restrict__ qnrm, int64_t Mq,
+             const uint8_t* __restrict__ X, const int32_t* __restrict__ nrm, int64_t M, int N,
+             int k, bool self, int32_t* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* Qs = reinterpret_cast<uint32_t*>(smem);  // [kDK words][kTQ + 4]
   uint32_t* Cs = Qs + kDK * (kTQ + 4);
@@ -176,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_knn_u8(const uint8_t* __restrict__
       for (int e = tid; e < kDK * kTQ; e += kThreads) {
         const int row = e / kDK, ww = e % kDK;
         const int d = (w0 + ww) * 4;
-        Qs[ww * (kTQ + 4) + row] = (w0 + ww < nwords) ? pack4(X, q0 + row, M, N, d) : 0u;
+        Qs[ww * (kTQ + 4) + row] = (w0 + ww < nwords) ? pack4(Q, q0 + row, Mq, N, d) : 0u;
         Cs[ww * (kTC + 4) + row] = (w0 + ww < nwords) ? pack4(X, c0 + row, M, N, d) : 0u;
       }
       __syncthreads();
@@ -198,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_knn_u8(const uint8_t* __restrict__
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int64_t gq = q0 + ty * 8 + a;
-      const int32_t nq = (gq < M) ? nrm[gq] : 0;
+      const int32_t nq = (gq < Mq) ? qnrm[gq] : 0;
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
         const int64_t gc = c0 + tx * 8 + b;
@@ -207,92 +216,162 @@ __global__ void __launch_bounds__(kThreads) k_knn_u8(const uint8_t* __restrict__
       }
     }
     __syncthreads();
-    if (tid < kTQ && q0 + tid < M)
-      merge_row<int32_t>(Dt + tid * kDStride, (int)c0, M, q0 + tid, k, Ld + tid * k, Lj + tid * k,
-                         nlist);
+    if (tid < kTQ && q0 + tid < Mq)
+      merge_row<int32_t>(Dt + tid * kDStride, (int)c0, M, self ? q0 + tid : -1, k, Ld + tid * k,
+                         Lj + tid * k, nlist);
     __syncthreads();
   }
-  if (tid < kTQ && q0 + tid < M)
+  if (tid < kTQ && q0 + tid < Mq)
     for (int s = 0; s < k; ++s) out[(q0 + tid) * k + s] = Lj[tid * k + s];
+}
+
+// y_q = (1/k) sum_s Y[ids[q][s]], summed in FP32 in the order s = 0 .. k-1.
+// An id outside [0, M) raises *bad and leaves that row unwritten.
+__global__ void k_place_nn(const float2* __restrict__ Y, int64_t M, const int32_t* __restrict__ ids,
+                           int64_t n, int k, float2* __restrict__ out, int32_t* __restrict__ bad) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float sx = 0.f, sy = 0.f;
+  for (int s = 0; s < k; ++s) {
+    const int32_t j = ids[q * k + s];
+    if (j < 0 || (int64_t)j >= M) {
+      atomicOr(bad, 1);
+      return;
+    }
+    const float2 y = Y[j];
+    sx += y.x;
+    sy += y.y;
+  }
+  out[q] = make_float2(sx / (float)k, sy / (float)k);
 }
 
 }  // namespace
 
-cudaError_t knn_exact_rows_f32(const float* X, int64_t M, int32_t N, int32_t k,
-                               const int32_t* rows, const int32_t* n_rows, int32_t* out_knn,
-                               cudaStream_t s) {
-  const size_t sm = SmemLayout::total(k);
+cudaError_t knn_exact_rows_f32(const KnnProblem& P, const int32_t* rows, const int32_t* n_rows,
+                               int32_t* out_knn, cudaStream_t s) {
+  const size_t sm = SmemLayout::total(P.k);
   cudaError_t e = cudaFuncSetAttribute(k_knn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
   // one CTA per 128 possible rows; CTAs past *n_rows return at once
-  k_knn_f32<<<(unsigned)((M + kTQ - 1) / kTQ), kThreads, sm, s>>>(X, M, N, k, out_knn, rows,
-                                                                  n_rows);
+  k_knn_f32<<<(unsigned)((P.Mq + kTQ - 1) / kTQ), kThreads, sm, s>>>(
+      (const float*)P.Q, P.Mq, (const float*)P.X, P.M, P.N, P.k, P.self, out_knn, rows, n_rows);
   return cudaGetLastError();
 }
 
-// The CUDA-core build of every row (k <= 64).
-static ivhd_status knn_cuda_cores(const void* X, int32_t dtype, int64_t M, int32_t N, int32_t k,
-                                  int32_t* out_knn, cudaStream_t s) {
-  const size_t sm = SmemLayout::total(k);
-  const unsigned grid = (unsigned)((M + kTQ - 1) / kTQ);
+// The CUDA-core build of every query row (k <= 64).
+static ivhd_status knn_cuda_cores(const KnnProblem& P, int32_t* out_knn, cudaStream_t s) {
+  const size_t sm = SmemLayout::total(P.k);
+  const unsigned grid = (unsigned)((P.Mq + kTQ - 1) / kTQ);
   cudaError_t e;
-  if (dtype == IVHD_KNN_F32) {
-    e = cudaFuncSetAttribute(k_knn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return IVHD_ERR_CUDA;
-    k_knn_f32<<<grid, kThreads, sm, s>>>((const float*)X, M, N, k, out_knn, nullptr, nullptr);
-    e = cudaGetLastError();
+  if (P.dtype == IVHD_KNN_F32) {
+    e = knn_exact_rows_f32(P, nullptr, nullptr, out_knn, s);
   } else {
+    const uint8_t* X = (const uint8_t*)P.X;
+    const uint8_t* Q = (const uint8_t*)P.Q;
     int32_t* nrm = nullptr;
-    e = dev_alloc((void**)&nrm, (size_t)M * sizeof(int32_t), s);
-    if (e != cudaSuccess) return IVHD_ERR_OOM;
-    k_norms_u8<<<(unsigned)((M + 255) / 256), 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
+    int32_t* qnrm = nullptr;
+    e = dev_alloc((void**)&nrm, (size_t)P.M * sizeof(int32_t), s);
+    if (e == cudaSuccess && !P.self) e = dev_alloc((void**)&qnrm, (size_t)P.Mq * sizeof(int32_t), s);
+    if (e != cudaSuccess) {
+      dev_free(nrm, s);
+      return IVHD_ERR_OOM;
+    }
+    if (P.self) qnrm = nrm;
+    k_norms_u8<<<(unsigned)((P.M + 255) / 256), 256, 0, s>>>(X, P.M, P.N, nrm);
+    if (!P.self) k_norms_u8<<<(unsigned)((P.Mq + 255) / 256), 256, 0, s>>>(Q, P.Mq, P.N, qnrm);
     e = cudaFuncSetAttribute(k_knn_u8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) {
-      k_knn_u8<<<grid, kThreads, sm, s>>>((const uint8_t*)X, nrm, M, N, k, out_knn);
+      k_knn_u8<<<grid, kThreads, sm, s>>>(Q, qnrm, P.Mq, X, nrm, P.M, P.N, P.k, P.self, out_knn);
       e = cudaGetLastError();
     }
+    if (!P.self) dev_free(qnrm, s);
     dev_free(nrm, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? IVHD_OK : IVHD_ERR_CUDA;
 }
 
-}  // namespace ivhd
-
-using namespace ivhd;
-
-extern "C" ivhd_status ivhd_knn_build_ex(const void* X, int32_t dtype, int64_t M, int32_t N,
-                                         int32_t k, int32_t* out_knn, int32_t method,
-                                         ivhd_knn_stats_t* stats, void* stream) {
-  NvtxScope nvtx_("ivhd_knn_build");
-  if (!X || !out_knn) return IVHD_ERR_ARG;
-  if (M < 2 || M >= (int64_t)0x7FFFFFFF || N < 1 || N > 65536) return IVHD_ERR_ARG;
-  if (k < 1 || (int64_t)k > M - 1 || k > 64) return IVHD_ERR_ARG;
-  if (dtype != IVHD_KNN_F32 && dtype != IVHD_KNN_U8) return IVHD_ERR_ARG;
-  if (dtype == IVHD_KNN_U8 && (int64_t)N * 255 * 255 > 0x3FFFFFFF) return IVHD_ERR_ARG;
+// Method choice, tensor-core or CUDA-core run and statistics for one problem.
+static ivhd_status knn_run(const KnnProblem& P, int32_t* out, int32_t method,
+                           ivhd_knn_stats_t* stats, cudaStream_t s) {
   if (method < IVHD_KNN_AUTO || method > IVHD_KNN_TENSOR_CORES) return IVHD_ERR_ARG;
-  const bool tc_ok = knn_tc_supported(dtype, M, N, k);
+  const bool tc_ok = knn_tc_supported(P);
   if (method == IVHD_KNN_TENSOR_CORES && !tc_ok) return IVHD_ERR_ARG;
   const bool use_tc = method == IVHD_KNN_TENSOR_CORES || (method == IVHD_KNN_AUTO && tc_ok);
-  cudaStream_t s = (cudaStream_t)stream;
   ivhd_knn_stats_t st{};
   st.method = use_tc ? IVHD_KNN_TENSOR_CORES : IVHD_KNN_CUDA_CORES;
   ivhd_status r;
   if (use_tc) {
     KnnTcStats t{};
-    r = knn_tc_build(X, dtype, M, N, k, out_knn, s, &t);
+    r = knn_tc_build(P, out, s, &t);
     st.fallback_rows = t.fallback_rows;
     st.max_rel_err = t.max_rel_err;
     st.eps_coef = t.eps_coef;
   } else {
-    r = knn_cuda_cores(X, dtype, M, N, k, out_knn, s);
+    r = knn_cuda_cores(P, out, s);
   }
   if (stats) *stats = st;
   return r;
 }
 
+}  // namespace ivhd
+
+using namespace ivhd;
+
+// Argument rules shared by the graph build and the query (dtype, N, k against
+// the number of base rows that can be listed).
+static bool knn_args_ok(int32_t dtype, int64_t M, int32_t N, int32_t k, int64_t listable) {
+  if (M < 1 || M >= (int64_t)0x7FFFFFFF || N < 1 || N > 65536) return false;
+  if (k < 1 || (int64_t)k > listable || k > 64) return false;
+  if (dtype != IVHD_KNN_F32 && dtype != IVHD_KNN_U8) return false;
+  if (dtype == IVHD_KNN_U8 && (int64_t)N * 255 * 255 > 0x3FFFFFFF) return false;
+  return true;
+}
+
+extern "C" ivhd_status ivhd_knn_build_ex(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                         int32_t k, int32_t* out_knn, int32_t method,
+                                         ivhd_knn_stats_t* stats, void* stream) {
+  NvtxScope nvtx_("ivhd_knn_build");
+  if (!X || !out_knn || M < 2 || !knn_args_ok(dtype, M, N, k, M - 1)) return IVHD_ERR_ARG;
+  const KnnProblem P{X, M, X, M, dtype, N, k, true};
+  return knn_run(P, out_knn, method, stats, (cudaStream_t)stream);
+}
+
 extern "C" ivhd_status ivhd_knn_build(const void* X, int32_t dtype, int64_t M, int32_t N,
                                       int32_t k, int32_t* out_knn, void* stream) {
   return ivhd_knn_build_ex(X, dtype, M, N, k, out_knn, IVHD_KNN_AUTO, nullptr, stream);
+}
+
+extern "C" ivhd_status ivhd_knn_query(const void* Q, int64_t Mq, const void* X, int64_t M,
+                                      int32_t dtype, int32_t N, int32_t k, int32_t* out,
+                                      int32_t method, ivhd_knn_stats_t* stats, void* stream) {
+  NvtxScope nvtx_("ivhd_knn_query");
+  if (!Q || !X || !out || Mq < 1 || Mq >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
+  if (!knn_args_ok(dtype, M, N, k, M)) return IVHD_ERR_ARG;
+  const KnnProblem P{Q, Mq, X, M, dtype, N, k, false};
+  return knn_run(P, out, method, stats, (cudaStream_t)stream);
+}
+
+extern "C" ivhd_status ivhd_place_nn(const float* Y, int64_t M, const int32_t* ids, int64_t n,
+                                     int32_t k, float* out, void* stream) {
+  NvtxScope nvtx_("ivhd_place_nn");
+  if (!Y || M < 1 || n < 0 || k < 1 || k > 1024) return IVHD_ERR_ARG;
+  if (n == 0) return IVHD_OK;
+  if (!ids || !out) return IVHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* bad = nullptr;
+  if (dev_alloc((void**)&bad, sizeof(int32_t), s) != cudaSuccess) return IVHD_ERR_OOM;
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) {
+    k_place_nn<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float2*)Y, M, ids, n, k,
+                                                           (float2*)out, bad);
+    e = cudaGetLastError();
+  }
+  int32_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s);
+  dev_free(bad, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  return h ? IVHD_ERR_INDEX : IVHD_OK;
 }

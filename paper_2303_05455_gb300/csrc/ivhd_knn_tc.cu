@@ -24,6 +24,11 @@
 //   the row is final when its exact k-th distance is below tau - eps n_i.
 //   Other rows are recomputed by the exact CUDA-core kernel.
 //
+// Query rows are the rows of X itself for the kNN graph (a row never lists
+// itself), or a separate set of new points searched against X as the base set
+// (the nearest-neighbour placement of Progressive UMAP, Sec. 2.4.3); the
+// arithmetic and the certificate are the same, with n_i the query's norm.
+//
 // One CTA owns 128 query rows (the 128 tensor-memory lanes) and sweeps all
 // candidates in tiles of 256 columns:
 //   warp 0, one lane   TMA producer: 128 x 64 query and 256 x 64 candidate
@@ -98,9 +103,10 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
 template <bool U8, int L>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_knn_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-             const float* __restrict__ nrm_f, const int32_t* __restrict__ nrm_i, int M, int Kp,
-             int k, float eps_coef, int32_t* __restrict__ out_ids, float* __restrict__ out_d,
-             int32_t* __restrict__ err) {
+             const float* __restrict__ nrm_f, const int32_t* __restrict__ nrm_i,
+             const float* __restrict__ qnrm_f, const int32_t* __restrict__ qnrm_i, int Mq, int M,
+             int Kp, bool self, float eps_coef, int32_t* __restrict__ out_ids,
+             float* __restrict__ out_d, int32_t* __restrict__ err) {
   using D = typename std::conditional<U8, int32_t, float>::type;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -239,7 +245,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       dl[q] = kMaxKey;
       jl[q] = INT_MAX;
     }
-    const D ni = (i < M) ? (U8 ? (D)nrm_i[i] : (D)nrm_f[i]) : (D)0;
+    const D ni = (i < Mq) ? (U8 ? (D)qnrm_i[i] : (D)qnrm_f[i]) : (D)0;
+    const int iself = self ? i : -1;  // the column a row never lists (self-kNN only)
     bool ok = true;
     fetch(0);
     for (int t = 0; t < n_tiles; ++t) {
@@ -279,10 +286,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               d[q + e] = fmaf(-2.f, __uint_as_float(v[q + e]), ni + nj[e]);
           }
         }
-        if (jb + 31 >= M || (jb <= i && i <= jb + 31)) {
+        if (jb + 31 >= M || (jb <= iself && iself <= jb + 31)) {
 #pragma unroll
           for (int q = 0; q < 32; ++q)
-            if (jb + q >= M || jb + q == i) d[q] = kMaxKey;
+            if (jb + q >= M || jb + q == iself) d[q] = kMaxKey;
         }
         D mn = d[0];
 #pragma unroll
@@ -307,7 +314,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(&acc_empty[b]);
     }
-    if (ok && i < M) {
+    if (ok && i < Mq) {
       // the row's list for this half: out_ids / out_key [(i * 2 + half) * L + q]
       const int64_t o = ((int64_t)i * 2 + half) * L;
 #pragma unroll
@@ -336,7 +343,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---- operand preparation ---------------------------------------------------
 
-// FP32: A = [hi | hi | lo], B = [hi | lo | hi] along K (3N, zero-padded to Kp).
+// FP32: A = [hi | hi | lo], B = [hi | lo | hi] along K (3N, zero-padded to Kp);
+// either output may be null (queries fill A, the base set B).
 __global__ void k_prep_f32(const float* __restrict__ X, int64_t M, int N, int Kp,
                            __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -352,8 +360,8 @@ __global__ void k_prep_f32(const float* __restrict__ X, int64_t M, int N, int Kp
     a = (seg == 2) ? lo : hi;
     b = (seg == 1) ? lo : hi;
   }
-  A[e] = a;
-  B[e] = b;
+  if (A) A[e] = a;
+  if (B) B[e] = b;
 }
 
 // FP32 norms (FP64 sum, rounded once).
@@ -428,9 +436,11 @@ __device__ __forceinline__ void warp_sort(float& d, int& j, int lane) {
 // are re-ranked by the exact FP32 chain, merged, and certified.  A half whose
 // list is full bounds every vertex it left out by its largest key tau_h
 // (d_ij >= tau_h - eps n_i); a half whose list is not full left nothing out.
+// Q: the Mq query rows (X itself for the kNN graph), X: the M base rows.
 template <int L>
-__global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
-                         const int32_t* __restrict__ cand, const float* __restrict__ key,
+__global__ void k_rerank(const float* __restrict__ Q, int Mq, const float* __restrict__ X, int M,
+                         int N, int k, const int32_t* __restrict__ cand,
+                         const float* __restrict__ key, const float* __restrict__ qnrm,
                          const float* __restrict__ nrm, float eps_coef, int32_t* __restrict__ out,
                          int32_t* __restrict__ fb_rows, int32_t* __restrict__ n_fb,
                          int32_t* __restrict__ max_err_bits) {
@@ -438,8 +448,8 @@ __global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
   constexpr int kHalves = 32 / L;  // halves that one warp pass covers (lane = entry)
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= M) return;
-  const float* xi = X + i * N;
+  if (i >= Mq) return;
+  const float* xi = Q + i * N;
   float dh[2 / kHalves];
   int jh[2 / kHalves];
   float tau = __int_as_float(0x7f800000);
@@ -457,7 +467,7 @@ __global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
       d = chain_dist(xi, X + (int64_t)j0 * N, N);
       j = j0;
       // the approximate distance is the key plus eps n_j
-      rel = fmaxf(rel, fabsf(fmaf(eps_coef, nrm[j0], kj) - d) / fmaxf(nrm[i] + nrm[j0], 1e-30f));
+      rel = fmaxf(rel, fabsf(fmaf(eps_coef, nrm[j0], kj) - d) / fmaxf(qnrm[i] + nrm[j0], 1e-30f));
     }
 #pragma unroll
     for (int hh = 0; hh < kHalves; ++hh) {
@@ -489,7 +499,7 @@ __global__ void k_rerank(const float* __restrict__ X, int M, int N, int k,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mrel = fmaxf(mrel, __shfl_xor_sync(0xffffffffu, mrel, o));
   const float dk = __shfl_sync(0xffffffffu, d, k - 1);
-  const bool certified = dk < tau - eps_coef * nrm[i];
+  const bool certified = dk < tau - eps_coef * qnrm[i];
   if (certified) {
     if (lane < k) out[i * k + lane] = j;
   } else if (lane == 0) {
@@ -518,8 +528,9 @@ __global__ void k_merge_u8(const int32_t* __restrict__ ids, const int32_t* __res
 
 template <bool U8, int L>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float* nrm_f,
-                      const int32_t* nrm_i, int M, int Kp, int k, float eps_coef, int32_t* out_ids,
-                      float* out_d, int32_t* err, cudaStream_t s) {
+                      const int32_t* nrm_i, const float* qnrm_f, const int32_t* qnrm_i, int Mq,
+                      int M, int Kp, bool self, float eps_coef, int32_t* out_ids, float* out_d,
+                      int32_t* err, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -530,18 +541,19 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float*
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  const unsigned grid = (unsigned)((M + kTM - 1) / kTM);
-  k_knn_tc<U8, L><<<grid, kTcThreads, KnnSmem::total, s>>>(ma, mb, nrm_f, nrm_i, M, Kp, k,
-                                                            eps_coef, out_ids, out_d, err);
+  const unsigned grid = (unsigned)((Mq + kTM - 1) / kTM);
+  k_knn_tc<U8, L><<<grid, kTcThreads, KnnSmem::total, s>>>(
+      ma, mb, nrm_f, nrm_i, qnrm_f, qnrm_i, Mq, M, Kp, self, eps_coef, out_ids, out_d, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool knn_tc_supported(int32_t dtype, int64_t M, int32_t N, int32_t k) {
-  if (k < 1 || k > kKnnList || M < 2 || M > (1 << 30)) return false;
-  if (dtype == IVHD_KNN_U8) return N <= 1024;
-  return (int64_t)3 * N <= 65536;
+bool knn_tc_supported(const KnnProblem& P) {
+  if (P.k < 1 || P.k > kKnnList || P.M < 2 || P.M > (1 << 30) || P.Mq < 1 || P.Mq > (1 << 30))
+    return false;
+  if (P.dtype == IVHD_KNN_U8) return P.N <= 1024;
+  return (int64_t)3 * P.N <= 65536;
 }
 
 // Device scratch freed on scope exit (stream-ordered).
@@ -568,72 +580,91 @@ struct Bufs {
 };
 }  // namespace
 
-ivhd_status knn_tc_build(const void* X, int32_t dtype, int64_t M, int32_t N, int32_t k,
-                         int32_t* out_knn, cudaStream_t s, KnnTcStats* stats) {
-  const bool u8 = dtype == IVHD_KNN_U8;
+ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
+                         KnnTcStats* stats) {
+  const bool u8 = P.dtype == IVHD_KNN_U8;
+  const int64_t M = P.M, Mq = P.Mq;
+  const int N = P.N, k = P.k;
   const int Kp = (int)((((u8 ? (int64_t)N : 3 * (int64_t)N) + kBK - 1) / kBK) * kBK);
   Bufs b(s);
-  __nv_bfloat16* A = b.get<__nv_bfloat16>(M * Kp);
-  __nv_bfloat16* B = u8 ? A : b.get<__nv_bfloat16>(M * Kp);
+  // A: the query rows' operand, B: the base rows'; one array when they coincide (uint8 self)
+  __nv_bfloat16* B = b.get<__nv_bfloat16>(M * Kp);
+  __nv_bfloat16* A = (u8 && P.self) ? B : b.get<__nv_bfloat16>(Mq * Kp);
   int32_t* err = b.get<int32_t>(8);  // err, n_fb, max-err bits
   if (!b.ok) return IVHD_ERR_OOM;
   cudaError_t e = cudaMemsetAsync(err, 0, 8 * sizeof(int32_t), s);
   int32_t* n_fb = err + 1;
   int32_t* maxerr_bits = err + 2;
-  const unsigned gprep = (unsigned)((M * Kp + 255) / 256);
-  const unsigned grow = (unsigned)((M + 255) / 256);
+  auto blocks = [](int64_t n) { return (unsigned)((n + 255) / 256); };
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, M, Kp, Kp, kTM) || !make_map(&mb, B, M, Kp, Kp, kTN))
+  if (!make_map(&ma, A, Mq, Kp, Kp, kTM) || !make_map(&mb, B, M, Kp, Kp, kTN))
     return IVHD_ERR_CUDA;
   const float eps_coef = (float)(1.0 / 8192.0 + (double)N / 524288.0);
   if (u8) {
     const int L = (k <= 8) ? 8 : kKnnList;
     int32_t* nrm = b.get<int32_t>(M);
-    int32_t* lids = b.get<int32_t>(M * 2 * L);
-    int32_t* lkeys = b.get<int32_t>(M * 2 * L);
+    int32_t* qnrm = P.self ? nrm : b.get<int32_t>(Mq);
+    int32_t* lids = b.get<int32_t>(Mq * 2 * L);
+    int32_t* lkeys = b.get<int32_t>(Mq * 2 * L);
     if (!b.ok) return IVHD_ERR_OOM;
     if (e == cudaSuccess) {
-      k_prep_u8<<<gprep, 256, 0, s>>>((const uint8_t*)X, M, N, Kp, A);
-      k_norms_u8s<<<grow, 256, 0, s>>>((const uint8_t*)X, M, N, nrm);
-      e = (L == 8) ? launch_tc<true, 8>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, lids,
-                                        (float*)lkeys, err, s)
-                   : launch_tc<true, kKnnList>(ma, mb, nullptr, nrm, (int)M, Kp, k, 0.f, lids,
-                                               (float*)lkeys, err, s);
+      const uint8_t* X = (const uint8_t*)P.X;
+      const uint8_t* Q = (const uint8_t*)P.Q;
+      k_prep_u8<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, B);
+      k_norms_u8s<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
+      if (!P.self) {
+        k_prep_u8<<<blocks(Mq * Kp), 256, 0, s>>>(Q, Mq, N, Kp, A);
+        k_norms_u8s<<<blocks(Mq), 256, 0, s>>>(Q, Mq, N, qnrm);
+      }
+      e = (L == 8) ? launch_tc<true, 8>(ma, mb, nullptr, nrm, nullptr, qnrm, (int)Mq, (int)M, Kp,
+                                        P.self, 0.f, lids, (float*)lkeys, err, s)
+                   : launch_tc<true, kKnnList>(ma, mb, nullptr, nrm, nullptr, qnrm, (int)Mq,
+                                               (int)M, Kp, P.self, 0.f, lids, (float*)lkeys, err,
+                                               s);
     }
     if (e == cudaSuccess) {
       if (L == 8)
-        k_merge_u8<8><<<grow, 256, 0, s>>>(lids, lkeys, M, k, out_knn);
+        k_merge_u8<8><<<blocks(Mq), 256, 0, s>>>(lids, lkeys, Mq, k, out_knn);
       else
-        k_merge_u8<kKnnList><<<grow, 256, 0, s>>>(lids, lkeys, M, k, out_knn);
+        k_merge_u8<kKnnList><<<blocks(Mq), 256, 0, s>>>(lids, lkeys, Mq, k, out_knn);
       e = cudaGetLastError();
     }
   } else {
     float* nrm = b.get<float>(M);
+    float* qnrm = P.self ? nrm : b.get<float>(Mq);
     const int L = (k <= 8) ? 16 : kKnnList;  // candidates per row and half
-    int32_t* cand = b.get<int32_t>(M * 2 * L);
-    float* cd = b.get<float>(M * 2 * L);
-    int32_t* fb = b.get<int32_t>(M);
+    int32_t* cand = b.get<int32_t>(Mq * 2 * L);
+    float* cd = b.get<float>(Mq * 2 * L);
+    int32_t* fb = b.get<int32_t>(Mq);
     if (!b.ok) return IVHD_ERR_OOM;
+    const float* X = (const float*)P.X;
+    const float* Q = (const float*)P.Q;
     if (e == cudaSuccess) {
-      k_prep_f32<<<gprep, 256, 0, s>>>((const float*)X, M, N, Kp, A, B);
-      k_norms_f32<<<grow, 256, 0, s>>>((const float*)X, M, N, nrm);
-      e = (L == 16) ? launch_tc<false, 16>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef, cand,
-                                           cd, err, s)
-                    : launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, (int)M, Kp, k, eps_coef,
-                                                 cand, cd, err, s);
+      if (P.self) {
+        k_prep_f32<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, A, B);
+      } else {
+        k_prep_f32<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, nullptr, B);
+        k_prep_f32<<<blocks(Mq * Kp), 256, 0, s>>>(Q, Mq, N, Kp, A, nullptr);
+        k_norms_f32<<<blocks(Mq), 256, 0, s>>>(Q, Mq, N, qnrm);
+      }
+      k_norms_f32<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
+      e = (L == 16) ? launch_tc<false, 16>(ma, mb, nrm, nullptr, qnrm, nullptr, (int)Mq, (int)M,
+                                           Kp, P.self, eps_coef, cand, cd, err, s)
+                    : launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, qnrm, nullptr, (int)Mq,
+                                                 (int)M, Kp, P.self, eps_coef, cand, cd, err, s);
     }
     if (e == cudaSuccess) {
-      const unsigned g8 = (unsigned)((M + 7) / 8);
+      const unsigned g8 = (unsigned)((Mq + 7) / 8);
       if (L == 16)
-        k_rerank<16><<<g8, 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd, nrm, eps_coef,
-                                        out_knn, fb, n_fb, maxerr_bits);
+        k_rerank<16><<<g8, 256, 0, s>>>(Q, (int)Mq, X, (int)M, N, k, cand, cd, qnrm, nrm,
+                                        eps_coef, out_knn, fb, n_fb, maxerr_bits);
       else
-        k_rerank<kKnnList><<<g8, 256, 0, s>>>((const float*)X, (int)M, N, k, cand, cd, nrm,
+        k_rerank<kKnnList><<<g8, 256, 0, s>>>(Q, (int)Mq, X, (int)M, N, k, cand, cd, qnrm, nrm,
                                               eps_coef, out_knn, fb, n_fb, maxerr_bits);
       e = cudaGetLastError();
     }
     // rows without a certificate: the exact CUDA-core kernel on just those rows
-    if (e == cudaSuccess) e = knn_exact_rows_f32((const float*)X, M, N, k, fb, n_fb, out_knn, s);
+    if (e == cudaSuccess) e = knn_exact_rows_f32(P, fb, n_fb, out_knn, s);
   }
   int32_t h[8] = {};
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, s);

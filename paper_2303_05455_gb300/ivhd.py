@@ -13,6 +13,7 @@ plus ``knn_build`` (exact brute-force kNN graph) and ``eval_qnx`` / ``eval_cf``
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 
 import numpy as np
@@ -291,6 +292,43 @@ def knn_build(X: torch.Tensor, k: int, stream=None, method: str = "auto",
     return out
 
 
+def knn_query(Q: torch.Tensor, X: torch.Tensor, k: int, stream=None, method: str = "auto",
+              return_stats: bool = False):
+    """The k rows of the base set X nearest to each row of Q (ivhd_knn_query) -> int32 [Mq, k].
+
+    Same dtypes, distances, tie rule and methods as knn_build; nothing is excluded."""
+    L = _lib.load()
+    if not (Q.is_cuda and X.is_cuda) or Q.dtype != X.dtype or Q.shape[1] != X.shape[1]:
+        raise ValueError("knn_query expects CUDA tensors of one dtype and width")
+    dts = {torch.float32: 0, torch.uint8: 1}
+    if X.dtype not in dts:
+        raise ValueError("X must be float32 or uint8")
+    Q, X = Q.contiguous(), X.contiguous()
+    Mq, M, N = int(Q.shape[0]), int(X.shape[0]), int(X.shape[1])
+    out = torch.empty((Mq, k), dtype=torch.int32, device=X.device)
+    st = _lib.KnnStats()
+    check(L.ivhd_knn_query(Q.data_ptr(), Mq, X.data_ptr(), M, dts[X.dtype], N, int(k),
+                           out.data_ptr(), KNN_METHODS[method], ctypes.byref(st),
+                           _stream_ptr(stream)), "ivhd_knn_query")
+    if return_stats:
+        names = {v: n for n, v in KNN_METHODS.items()}
+        return out, {"method": names[st.method], "fallback_rows": st.fallback_rows,
+                     "max_rel_err": st.max_rel_err, "eps_coef": st.eps_coef}
+    return out
+
+
+def place_nn(Y: torch.Tensor, ids: torch.Tensor, stream=None) -> torch.Tensor:
+    """New points at the mean embedding of their base neighbours (ivhd_place_nn) -> [n, 2]."""
+    L = _lib.load()
+    Y = Y.to(torch.float32).contiguous()
+    ids = ids.to(device=Y.device, dtype=torch.int32).contiguous()
+    n, k = int(ids.shape[0]), int(ids.shape[1])
+    out = torch.empty((n, 2), dtype=torch.float32, device=Y.device)
+    check(L.ivhd_place_nn(Y.data_ptr(), int(Y.shape[0]), ids.data_ptr(), n, k, out.data_ptr(),
+                          _stream_ptr(stream)), "ivhd_place_nn")
+    return out
+
+
 def eval_qnx(Y: torch.Tensor, knn: torch.Tensor, rows: torch.Tensor, return_lowd: bool = False,
              stream=None):
     """Q_NX(k) on the sampled rows (Sec. 4.1); optionally the embedded neighbours found."""
@@ -327,6 +365,68 @@ def probe_gather(n_positions: int, n_gathers: int = 16_777_216, repeats: int = 2
     check(L.ivhd_probe_gather(int(n_positions), int(n_gathers), int(repeats), ctypes.byref(v),
                               _stream_ptr(stream)), "ivhd_probe_gather")
     return v.value
+
+
+# Every callback pair ever registered stays referenced: blocks keep the free
+# routine of the allocator that made them after the setting changes.
+_ALLOCATORS: list = []
+_FINALIZING = [False]
+
+
+def _stop_user_frees():
+    # blocks still held at interpreter exit are left to the process teardown
+    _FINALIZING[0] = True
+
+
+atexit.register(_stop_user_frees)
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """ivhd_set_allocator: take the library's device memory from ``alloc``.
+
+    ``alloc(nbytes, stream) -> int`` returns a device address (0 or an
+    exception = out of memory) usable on the ``cudaStream_t`` value
+    ``stream``; ``free(ptr, nbytes, stream)`` gives it back.  Both None
+    restores the library's own stream-ordered pool.
+    """
+    L = _lib.load()
+    if (alloc is None) != (free is None):
+        raise ValueError("set_allocator needs both alloc and free, or neither")
+    if alloc is None:
+        check(L.ivhd_set_allocator(ctypes.cast(None, _lib.ALLOC_FN),
+                                   ctypes.cast(None, _lib.FREE_FN), None), "ivhd_set_allocator")
+        return
+
+    def _alloc(nbytes, stream, _user):
+        try:
+            return int(alloc(int(nbytes), int(stream or 0))) or None
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, _user):
+        if _FINALIZING[0]:
+            return
+        try:
+            free(int(ptr), int(nbytes), int(stream or 0))
+        except Exception:
+            pass
+
+    cbs = (_lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free))
+    _ALLOCATORS.append(cbs)
+    check(L.ivhd_set_allocator(cbs[0], cbs[1], None), "ivhd_set_allocator")
+
+
+def use_torch_allocator(device=None) -> None:
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, dev, stream)
+
+    def free(ptr, _nbytes, _stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)
 
 
 def gemm_bf16_tn(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:

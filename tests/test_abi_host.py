@@ -181,3 +181,21 @@ def test_new_entry_points_reject_null(L):
                                sd.ctypes.data, 2, 0.1, None, 0, ctypes.byref(h)) == -1
     assert L.ivhd_create_batch(knn.ctypes.data, M.ctypes.data, k.ctypes.data, r.ctypes.data,
                                sd.ctypes.data, 0, 0.1, None, 0, ctypes.byref(h)) == -1
+
+
+def test_set_allocator_pairs_and_reset(L):
+    """Host logic of ivhd_set_allocator: alloc and free come in pairs, both
+    NULL restores the built-in pool; no callback runs without an allocation."""
+    calls = []
+    alloc = _lib.ALLOC_FN(lambda n, s, u: calls.append(n))
+    free = _lib.FREE_FN(lambda p, n, s, u: calls.append(p))
+    null_alloc = ctypes.cast(None, _lib.ALLOC_FN)
+    null_free = ctypes.cast(None, _lib.FREE_FN)
+    assert L.ivhd_set_allocator(alloc, null_free, None) == -1
+    assert L.ivhd_set_allocator(null_alloc, free, None) == -1
+    assert L.ivhd_set_allocator(alloc, free, None) == 0
+    assert L.ivhd_set_allocator(null_alloc, null_free, None) == 0
+    assert calls == []
+    with pytest.raises(ValueError):
+        from paper_2303_05455_gb300 import ivhd
+        ivhd.set_allocator(lambda n, s: 0)

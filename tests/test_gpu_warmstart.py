@@ -7,7 +7,10 @@ distribution, and IVHD refines from that placement.  Against plain IVHD from
 the uniform random start on the same held-out kNN graph, the warm start must
 reach a lower stress with a tenth of the steps, and end at the same kNN
 precision (Q_NX(k) within 0.01) and class neighbourhood (cf_10 no worse than
-0.01 below) after the same number of steps.
+0.01 below) after the same number of steps.  The nearest-neighbour placement
+(each held-out point at the embedding of its nearest training point, the
+Progressive UMAP initialisation of Sec. 2.4.3) is run beside it as the
+comparator.
 """
 import numpy as np
 import pytest
@@ -69,11 +72,15 @@ def test_warm_start_gains_over_random_start():
     Xh_d = torch.from_numpy(Xh).to(dev)
     Yp = (net.forward(Xh_d, x_scale=1 / 255) * sd + mu).contiguous()
     net.close()
+    # the comparator: each held-out point at the embedding of its nearest
+    # training point (Progressive UMAP initialisation)
+    Ynn = ivhd.place_nn(Ytr, ivhd.knn_query(Xh_d, Xtr_d, 1))
     knn_h = ivhd.knn_build(Xh_d, K)
     rows = torch.from_numpy(synth.sample_rows(N_HOLD, 5000, 9)).to(dev)
     lab = torch.from_numpy(Lh).to(dev)
     plain = _curve(knn_h, lab, rows)
     warm = _curve(knn_h, lab, rows, init=Yp)
+    nn = _curve(knn_h, lab, rows, init=Ynn)
     # plain IVHD is the placement's fallback: a good placement is taken, a
     # non-finite or far worse one leaves the seeded uniform start in place
     e = ivhd.Embedding(knn_h, r=R, c=C, a=A, b=B, seed=13)
@@ -87,7 +94,10 @@ def test_warm_start_gains_over_random_start():
     assert e.warm_start(Yp)
     assert np.allclose(e.positions(host=True), Yp.cpu().numpy())
     e.close()
-    print({"plain": plain, "warm": warm, "loss": (first, last)})
+    print({"plain": plain, "warm": warm, "nn_placement": nn, "loss": (first, last)})
+    # both placements start far below the uniform start and keep the classes apart
+    assert nn[0]["stress"] < 0.1 * plain[0]["stress"]
+    assert nn[0]["cf10"] >= plain[STEPS]["cf10"] - 0.01
     # a tenth of the steps reaches a lower stress than plain IVHD after all of them
     assert warm[STEPS // 10]["stress"] < plain[STEPS]["stress"]
     # the placement alone already keeps the classes apart as well as the full plain run
