@@ -13,7 +13,8 @@ timed region (untimed, as the paper's time_emb excludes the graph build).
 ``e2e`` repeats the step from pinned host memory (kNN upload and positions
 download inside the timed region).  ``roofline`` reports the fused step
 kernel against the measured HBM copy bandwidth.  ``cpu_baseline`` times the
-FP64 oracle on a bounded sample of the same workload.
+FP64 oracle on a bounded sample of the same workload on one core, and
+``cpu_baseline.all_cores`` the same loop on every host core.
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this
 project has) on the same metric; under torchrun only rank 0 runs it.
@@ -172,12 +173,23 @@ def aggregate_ranks(total_s: float, kernel_ms: float, units: float, device) -> t
 ORACLE_OPT = {"momentum": 0, "nesterov": 1, "adadelta": 2}
 
 
-def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200, opt: str = "momentum"):
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200, opt: str = "momentum",
+                  threads: int = 1):
     """Times the FP64 oracle's step loop on a graph of the workload's shape.
 
     The graph comes from the input generators (a kNN-shaped graph with hubs,
-    M x k), not from the GPU path.  Returns (edge-updates/s, iterations, seconds,
-    terms, setup seconds).
+    M x k), not from the GPU path.  The serial loop (oracle.run) is timed for
+    about target_s seconds, then, with threads > 1, the same loop on that many
+    host threads (oracle.run_threads) for about as long.  Returns a dict with
+    edge-updates/s, iterations and seconds of each, the term count and the
+    set-up seconds.
     """
     import oracle
 
@@ -186,15 +198,25 @@ def oracle_sample(w: synth.Workload, target_s: float, max_iters: int = 200, opt:
     rn, _ = oracle.random_neighbors(knn, w.r, w.seed)
     terms = oracle.build_terms(knn, rn)
     st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
-    setup = time.perf_counter() - t0
-    t = time.perf_counter()
-    oracle.run(st, terms, w.c, 1, ORACLE_OPT[opt], a=w.a, b=w.b)
-    one = max(time.perf_counter() - t, 1e-6)
-    iters = int(max(1, min(max_iters, target_s / one)))
-    t = time.perf_counter()
-    oracle.run(st, terms, w.c, iters, ORACLE_OPT[opt], a=w.a, b=w.b)
-    dt = time.perf_counter() - t
-    return terms.T * iters / dt, iters, dt, terms.T, setup
+    out = {"terms": terms.T, "setup_s": time.perf_counter() - t0}
+
+    def timed(fn):
+        t = time.perf_counter()
+        fn(st, terms, w.c, 1)
+        one = max(time.perf_counter() - t, 1e-6)
+        iters = int(max(1, min(max_iters, target_s / one)))
+        t = time.perf_counter()
+        fn(st, terms, w.c, iters)
+        dt = time.perf_counter() - t
+        return {"value": terms.T * iters / dt, "iters": iters, "seconds": dt}
+
+    out["serial"] = timed(lambda s_, t_, c_, n_: oracle.run(s_, t_, c_, n_, ORACLE_OPT[opt],
+                                                            a=w.a, b=w.b))
+    if threads > 1:
+        out["threads"] = timed(lambda s_, t_, c_, n_: oracle.run_threads(
+            s_, t_, c_, n_, ORACLE_OPT[opt], a=w.a, b=w.b, threads=threads))
+        out["threads"]["cores"] = threads
+    return out
 
 
 def run_reference(args):
@@ -436,11 +458,21 @@ def run_ours(args):
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, iters, dt, T, setup = oracle_sample(w, args.cpu_seconds, opt=args.opt)
+        nt = host_threads()
+        o = oracle_sample(w, args.cpu_seconds, opt=args.opt, threads=nt)
+        ser = o["serial"]
         line["cpu_baseline"] = {
-            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{iters} of {n_iter} {args.opt} iterations (FP64, single thread) on a "
-                      f"{w.M} x {w.k} kNN-shaped graph with r={w.r} ({T} terms), {dt:.1f} s"}
+            "value": ser["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ser['iters']} of {n_iter} {args.opt} iterations (FP64, single thread) "
+                      f"on a {w.M} x {w.k} kNN-shaped graph with r={w.r} ({o['terms']} terms), "
+                      f"{ser['seconds']:.1f} s"}
+        if "threads" in o:
+            th = o["threads"]
+            line["cpu_baseline"]["all_cores"] = {
+                "value": th["value"], "unit": UNIT, "cores": th["cores"], "kind": "oracle",
+                "sample": f"{th['iters']} iterations of the same loop on {th['cores']} host "
+                          f"threads (per-thread force sums added in thread order), "
+                          f"{th['seconds']:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

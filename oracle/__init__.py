@@ -13,6 +13,7 @@ the readings taken where the paper is ambiguous):
 * ``build_terms``      -- the nn / rn term list of the stress (Eq. 3.16).
 * ``stress``, ``forces`` -- E and F = -1/2 grad E.
 * ``step`` / ``run``   -- momentum (force-directed), Nesterov, Adadelta.
+* ``run_threads``      -- ``run`` on several host threads (CPU timing).
 * ``knn_f32`` / ``knn_u8`` -- exact brute-force kNN.
 * ``knn_query``, ``place_nn`` -- kNN of new points in a base set and their
   placement at the mean embedding of those neighbours (Progressive UMAP).
@@ -67,6 +68,9 @@ def _L():
         lib.ivo_step.restype = None
         lib.ivo_run.argtypes = [i32, P, P, P, i64, P, P, P, i64, dbl, dbl, dbl, dbl, dbl, i64]
         lib.ivo_run.restype = i32
+        lib.ivo_run_threads.argtypes = [i32, P, P, P, i64, P, P, P, i64, dbl, dbl, dbl, dbl, dbl,
+                                        i64, i32]
+        lib.ivo_run_threads.restype = i32
         lib.ivo_knn_f32.argtypes = [P, i64, i32, i32, P, i64, P]
         lib.ivo_knn_f32.restype = i32
         lib.ivo_knn_u8.argtypes = [P, i64, i32, i32, P, i64, P]
@@ -220,6 +224,18 @@ def run(state: State, terms: Terms, c: float, n_iter: int, opt: int = OPT_MOMENT
                       _p(terms.tj), _p(terms.kind), terms.T, c, a, b, rho, eps, n_iter)
     if rc != 0:
         raise MemoryError("oracle run")
+    return state
+
+
+def run_threads(state: State, terms: Terms, c: float, n_iter: int, opt: int = OPT_MOMENTUM,
+                a: float = 0.9, b: float = 0.01, rho: float = 0.95, eps: float = 1e-6,
+                threads: int = 1) -> State:
+    """run() on `threads` host threads: per-thread force sums added in thread order."""
+    rc = _L().ivo_run_threads(opt, _p(state.Y), _p(state.S1), _p(state.S2), terms.M,
+                              _p(terms.ti), _p(terms.tj), _p(terms.kind), terms.T, c, a, b, rho,
+                              eps, n_iter, int(threads))
+    if rc != 0:
+        raise MemoryError("oracle run_threads")
     return state
 
 

@@ -72,6 +72,7 @@
  * the generator seeded with s is mix(s + (t+1) * gamma).
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -423,6 +424,125 @@ int ivo_run(int opt, double *Y, double *S1, double *S2, int64_t M, const int64_t
     free(F);
     free(W);
     return 0;
+}
+
+/*
+ * ivo_run on n_threads host threads (the multi-core CPU timing of the same
+ * oracle; POSIX threads).  Every step runs the phases of ivo_step with the
+ * same arithmetic: thread t sums the forces of its contiguous share of the
+ * term list into its own buffer, then F = sum over t of those buffers, added
+ * in thread order for every coordinate, and each thread updates its share of
+ * the coordinates.  Only the order in which the terms' contributions are
+ * added differs from ivo_run; with one thread the result is bit for bit
+ * ivo_run's.  Returns 0, or -1 on OOM or a failed thread start.
+ */
+/* Start gate of the worker threads: 0 = wait, 1 = run, 2 = return at once. */
+typedef struct {
+    pthread_mutex_t mu;
+    pthread_cond_t cv;
+    int state;
+} ivo_gate;
+
+typedef struct {
+    int opt, t, nt;
+    double *Y, *S1, *S2, *F, *W, *Fp;
+    int64_t M, T, n_iter;
+    const int64_t *ti, *tj;
+    const int8_t *kind;
+    double c, a, b, rho, eps;
+    pthread_barrier_t *bar;
+    ivo_gate *gate;
+} ivo_thread_arg;
+
+static void *ivo_thread_main(void *p)
+{
+    ivo_thread_arg *A = (ivo_thread_arg *)p;
+    if (A->t > 0) {
+        pthread_mutex_lock(&A->gate->mu);
+        while (A->gate->state == 0) pthread_cond_wait(&A->gate->cv, &A->gate->mu);
+        int go = A->gate->state == 1;
+        pthread_mutex_unlock(&A->gate->mu);
+        if (!go) return NULL;
+    }
+    int64_t n = 2 * A->M;
+    int64_t q0 = n * A->t / A->nt, q1 = n * (A->t + 1) / A->nt;
+    int64_t t0 = A->T * A->t / A->nt, t1 = A->T * (A->t + 1) / A->nt;
+    double *Fmine = A->Fp + (size_t)A->t * (size_t)n;
+    for (int64_t it = 0; it < A->n_iter; ++it) {
+        const double *Yf = A->Y;
+        if (A->opt == 1) {
+            for (int64_t q = q0; q < q1; ++q) A->W[q] = A->Y[q] + A->a * A->S1[q];
+            pthread_barrier_wait(A->bar);
+            Yf = A->W;
+        }
+        ivo_forces(Yf, A->M, A->ti + t0, A->tj + t0, A->kind + t0, t1 - t0, A->c, Fmine);
+        pthread_barrier_wait(A->bar);
+        for (int64_t q = q0; q < q1; ++q) {
+            double f = 0.0;
+            for (int u = 0; u < A->nt; ++u) f += A->Fp[(size_t)u * (size_t)n + (size_t)q];
+            A->F[q] = f;
+        }
+        for (int64_t q = q0; q < q1; ++q) {
+            if (A->opt != 2) {
+                A->S1[q] = A->a * A->S1[q] + A->b * A->F[q];
+                A->Y[q] += A->S1[q];
+            } else {
+                double g = -A->F[q];
+                A->S1[q] = A->rho * A->S1[q] + (1.0 - A->rho) * g * g;
+                double dx = -sqrt(A->S2[q] + A->eps) / sqrt(A->S1[q] + A->eps) * g;
+                A->S2[q] = A->rho * A->S2[q] + (1.0 - A->rho) * dx * dx;
+                A->Y[q] += dx;
+            }
+        }
+        pthread_barrier_wait(A->bar);
+    }
+    return NULL;
+}
+
+int ivo_run_threads(int opt, double *Y, double *S1, double *S2, int64_t M, const int64_t *ti,
+                    const int64_t *tj, const int8_t *kind, int64_t T, double c, double a,
+                    double b, double rho, double eps, int64_t n_iter, int n_threads)
+{
+    if (n_threads < 1) return -1;
+    size_t n = 2 * (size_t)M;
+    double *F = (double *)malloc(sizeof(double) * n);
+    double *W = (double *)malloc(sizeof(double) * n);
+    double *Fp = (double *)malloc(sizeof(double) * n * (size_t)n_threads);
+    ivo_thread_arg *args = (ivo_thread_arg *)malloc(sizeof(ivo_thread_arg) * (size_t)n_threads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    ivo_gate gate = {PTHREAD_MUTEX_INITIALIZER, PTHREAD_COND_INITIALIZER, 0};
+    pthread_barrier_t bar;
+    int rc = -1, started = 0;
+    if (!F || !W || !Fp || !args || !th) goto out;
+    if (pthread_barrier_init(&bar, NULL, (unsigned)n_threads) != 0) goto out;
+    for (int t = 0; t < n_threads; ++t) {
+        ivo_thread_arg A = {opt, t, n_threads, Y, S1, S2, F, W, Fp, M, T, n_iter,
+                            ti, tj, kind, c, a, b, rho, eps, &bar, &gate};
+        args[t] = A;
+    }
+    /* share 0 runs on the calling thread; the others wait at the gate until
+       every thread has started, so a failed start stops them all */
+    for (int t = 1; t < n_threads; ++t) {
+        if (pthread_create(&th[t], NULL, ivo_thread_main, &args[t]) != 0) break;
+        ++started;
+    }
+    pthread_mutex_lock(&gate.mu);
+    gate.state = (started == n_threads - 1) ? 1 : 2;
+    pthread_cond_broadcast(&gate.cv);
+    pthread_mutex_unlock(&gate.mu);
+    if (gate.state == 1) {
+        ivo_thread_main(&args[0]);
+        rc = 0;
+    }
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&bar);
+out:
+    free(F);
+    free(W);
+    free(Fp);
+    free(args);
+    free(th);
+    return rc;
 }
 
 /* Insert (d, j) into a list of n best (ascending d, ties by lower j) of capacity k. */

@@ -557,3 +557,35 @@ def test_place_nn_is_the_neighbour_mean():
     assert oracle.place_nn(Y, ids).tolist() == [[1, 0], [1, 2], [6, 6], [0, 2]]
     # k = 1 is the embedding of the nearest neighbour itself
     assert oracle.place_nn(Y, ids[:, :1]).tolist() == Y[ids[:, 0]].tolist()
+
+
+# ---------------------------------------------------------------- threaded timing mode
+
+
+@pytest.mark.parametrize("opt", [oracle.OPT_MOMENTUM, oracle.OPT_NESTEROV, oracle.OPT_ADADELTA])
+def test_run_threads_matches_serial_run(opt):
+    _, _, t, Y = _random_case(400, 5, 1, 3)
+    ref = oracle.State.fresh(Y)
+    oracle.run(ref, t, 0.01, 20, opt, a=0.9, b=0.01)
+    one = oracle.State.fresh(Y)
+    oracle.run_threads(one, t, 0.01, 20, opt, a=0.9, b=0.01, threads=1)
+    assert np.array_equal(one.Y, ref.Y) and np.array_equal(one.S1, ref.S1)
+    for nt in (2, 3, 8):
+        st = oracle.State.fresh(Y)
+        oracle.run_threads(st, t, 0.01, 20, opt, a=0.9, b=0.01, threads=nt)
+        assert np.abs(st.Y - ref.Y).max() <= 1e-12 * np.abs(ref.Y).max()
+        assert np.abs(st.Y.mean(axis=0) - Y.mean(axis=0)).max() < 1e-12 or opt == 2
+
+
+def test_run_threads_single_pair_recurrence():
+    # two nn terms over five threads (three of them without a term) follow the
+    # closed-form 2x2 recurrence of the pair's separation
+    knn = np.array([[1], [0]], np.int32)
+    t = oracle.build_terms(knn, np.full((2, 0), -1, np.int32))
+    Y0 = np.array([[0.3, -0.2], [1.1, 0.5]])
+    st = oracle.State.fresh(Y0)
+    oracle.run_threads(st, t, 0.01, 37, oracle.OPT_MOMENTUM, a=0.9, b=0.01, threads=5)
+    s = st.Y[0] - st.Y[1]
+    for q in range(2):
+        want = _recurrence(Y0[0, q] - Y0[1, q], 0.0, 4.0, 0.9, 0.01, 37)[0]
+        assert s[q] == pytest.approx(want, abs=1e-12)
