@@ -587,6 +587,25 @@ ivhd_status ivhd_set_allocator(ivhd_alloc_fn alloc_fn, ivhd_free_fn free_fn, voi
  * released, to check that every error path frees what it took.  Process-wide.
  */
 ivhd_status ivhd_probe_wait_timeout(int32_t polls, void *stream);
+
+/*
+ * Checked builds (the library compiled with IVHD_CHECKED: build_lib with
+ * IVHD_CHECKED=1, loaded by the binding when that variable is set), the
+ * stand-in for a memory checker.  Every index the step kernels gather and
+ * every row extent they read from the layout is tested first; a bad one is
+ * counted and skipped, never dereferenced.
+ *
+ * ivhd_check_violations: *out = the number of such indices and rows met since
+ * the last reset (reset != 0 clears it), or -1 in a normal build.
+ * Process-wide; synchronises the device.
+ *
+ * ivhd_test_corrupt_layout: writes `value` into entry `slot` of the
+ * context's layout (0 <= slot < the layout's entries, ivhd_info), so that a
+ * test can check that the kernels report it.  Checked builds only: a normal
+ * build returns IVHD_ERR_ARG and changes nothing.  Synchronises.
+ */
+ivhd_status ivhd_check_violations(int64_t *out, int32_t reset);
+ivhd_status ivhd_test_corrupt_layout(ivhd_ctx *ctx, int64_t slot, uint32_t value);
 void ivhd_test_fail_alloc(int64_t after);
 int64_t ivhd_test_live_allocs(void);
 

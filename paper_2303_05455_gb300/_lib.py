@@ -28,6 +28,7 @@ SYMBOLS = (
     "ivhd_mlp_set_params", "ivhd_mlp_get_params", "ivhd_mlp_loss_grad", "ivhd_mlp_train_step",
     "ivhd_mlp_forward", "ivhd_mlp_launches", "ivhd_probe_wait_timeout", "ivhd_test_fail_alloc",
     "ivhd_test_live_allocs", "ivhd_set_allocator", "ivhd_knn_query", "ivhd_place_nn",
+    "ivhd_check_violations", "ivhd_test_corrupt_layout",
 )
 
 # callback types of ivhd_set_allocator
@@ -80,14 +81,16 @@ def lib_path() -> str:
 
 
 def load(build_if_missing: bool = False):
-    """Loads libivhd.so; raises if it is absent (no CPU fallback exists)."""
+    """Loads libivhd.so (libivhd_checked.so when IVHD_CHECKED is set); raises if
+    it is absent (no CPU fallback exists)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = build_lib.LIB
+    checked = os.environ.get("IVHD_CHECKED", "") not in ("", "0")
+    path = build_lib.LIB_CHECKED if checked else build_lib.LIB
     if not os.path.exists(path):
         if build_if_missing:
-            build_lib.build()
+            build_lib.build(checked=checked)
         else:
             raise RuntimeError(f"libivhd.so is not built ({path}); run __graft_entry__.build()")
     L = ctypes.CDLL(path)
@@ -121,6 +124,10 @@ def load(build_if_missing: bool = False):
     L.ivhd_knn_build.restype = i32
     L.ivhd_knn_build_ex.argtypes = [P, i32, i64, i32, i32, P, i32, P, P]
     L.ivhd_knn_build_ex.restype = i32
+    L.ivhd_check_violations.argtypes = [ctypes.POINTER(ctypes.c_int64), i32]
+    L.ivhd_check_violations.restype = i32
+    L.ivhd_test_corrupt_layout.argtypes = [P, i64, ctypes.c_uint32]
+    L.ivhd_test_corrupt_layout.restype = i32
     L.ivhd_knn_query.argtypes = [P, i64, P, i64, i32, i32, i32, P, i32, P, P]
     L.ivhd_knn_query.restype = i32
     L.ivhd_place_nn.argtypes = [P, i64, P, i64, i32, P, P]

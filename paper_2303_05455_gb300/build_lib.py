@@ -3,6 +3,11 @@
 Each ``csrc/*.cu`` compiles to an object in parallel, then nvcc links the
 shared library (static CUDA runtime, so the library carries no dependency on
 a particular ``libcudart.so``).  Output: ``paper_2303_05455_gb300/_build/libivhd.so``.
+
+``build(checked=True)`` (``IVHD_CHECKED=1 python -m paper_2303_05455_gb300.build_lib``)
+compiles the same sources with ``-DIVHD_CHECKED`` into ``_build/libivhd_checked.so``:
+the step kernels then test every gathered index and row extent before use
+and count what they skip (``ivhd_check_violations``).
 """
 from __future__ import annotations
 
@@ -16,6 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libivhd.so")
+LIB_CHECKED = os.path.join(BUILD, "libivhd_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -37,22 +43,26 @@ def _deps():
         os.path.join(HERE, "..", "include", "ivhd.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(checked):
+        return lib
+    obj_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_v else []
+    extra = (["-Xptxas", "-v"] if ptxas_v else []) + (["-DIVHD_CHECKED"] if checked else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -66,15 +76,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             if err:
                 print(err)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force=True, verbose=True, ptxas_v="-v" in sys.argv))
+    print(build(force=True, verbose=True, ptxas_v="-v" in sys.argv,
+                checked=os.environ.get("IVHD_CHECKED", "") not in ("", "0")))

@@ -138,6 +138,7 @@ struct StepArgs {
   double* __restrict__ partials;     // stress: one double per block; adaptive: two
   int32_t* __restrict__ flag;        // stress mode: non-finite flag
   int32_t M, n_hub, n_slices, nb_hub, wpb;
+  int64_t n_slots;  // layout entries (checked builds test row extents against it)
   float c, a, b, rho, eps;
 };
 

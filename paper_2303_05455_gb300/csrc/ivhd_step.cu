@@ -73,7 +73,31 @@ struct Gsrc {
   const float2* __restrict__ y;
   const uint32_t* __restrict__ yh;
   uint64_t keep;  // L2 cache policy "evict last" for the cold FP32 gathers
+  uint32_t M;     // positions (checked builds test every gathered index against it)
 };
+
+// Checked builds (compiled with IVHD_CHECKED, the stand-in for a memory
+// checker): every gathered index and every row extent read from the layout is
+// tested before use; a bad one is counted in g_check_violations and skipped
+// (the gather returns the vertex's own position, the row is treated as
+// empty), so a corrupt layout is reported instead of read out of bounds.  In
+// normal builds both tests are compile-time true.
+#ifdef IVHD_CHECKED
+__device__ unsigned long long g_check_violations = 0;
+__device__ __forceinline__ bool index_ok(uint32_t idx, uint32_t n) {
+  if (idx < n) return true;
+  atomicAdd(&g_check_violations, 1ull);
+  return false;
+}
+__device__ __forceinline__ bool row_ok(int64_t beg, int64_t end, int64_t n_slots) {
+  if (0 <= beg && beg <= end && end <= n_slots && (beg & 3) == 0) return true;
+  atomicAdd(&g_check_violations, 1ull);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool index_ok(uint32_t, uint32_t) { return true; }
+__device__ __forceinline__ constexpr bool row_ok(int64_t, int64_t, int64_t) { return true; }
+#endif
 
 // L1 policy of the FP32 gathers.  The layout orders vertices by degree, and a
 // vertex is gathered once per symmetric term, so the first vertices are the
@@ -100,11 +124,12 @@ __device__ __forceinline__ float2 load_f32_no_l1(const float2* y, uint32_t idx, 
 template <int POS>
 __device__ __forceinline__ float2 gather(const Gsrc& G, uint32_t e, float2 self) {
   if constexpr (POS == IVHD_POS_F32) {
-    if (e == kPad) return self;
+    if (e == kPad || !index_ok(e & kIdxMask, G.M)) return self;
     const uint32_t idx = e & kIdxMask;
     return (idx < kL1HotF32) ? __ldg(G.y + idx) : load_f32_no_l1(G.y, idx, G.keep);
   } else {
-    return (e == kPad) ? self : load_pos<POS>(G.y, G.yh, e & kIdxMask);
+    return (e == kPad || !index_ok(e & kIdxMask, G.M)) ? self
+                                                       : load_pos<POS>(G.y, G.yh, e & kIdxMask);
   }
 }
 
@@ -279,7 +304,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
   const int cur = ADAPT ? A.ctl->cur : A.cur;
   uint64_t keep;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
-  const Gsrc G{A.y[cur], A.yh[cur], keep};
+  const Gsrc G{A.y[cur], A.yh[cur], keep, (uint32_t)A.M};
   const float b = ADAPT ? A.ctl->b : A.b;
   float fx = 0.f, fy = 0.f;  // force, or (stress in fx)
   float2 yi = make_float2(0.f, 0.f);
@@ -295,7 +320,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
       const int beg = A.hub_off[p], end = A.hub_off[p + 1];
       const int4* row = reinterpret_cast<const int4*>(A.ids + beg);
-      const int ng = (end - beg) >> 2;
+      const int ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
       int g = lane;
       for (; g + 32 < ng; g += 64) {
         const int4 ea = ld_stream_v4(row + g);
@@ -321,7 +346,9 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
         yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
       }
       const int4* base = reinterpret_cast<const int4*>(A.ids + A.slice_off[s]) + lane;
-      const int W = A.slice_w[s];
+      const int W = row_ok(A.slice_off[s], A.slice_off[s] + (int64_t)A.slice_w[s] * 128, A.n_slots)
+                        ? A.slice_w[s]
+                        : 0;
       int g = 0;
       for (; g + 1 < W; g += 2) {
         const int4 ea = ld_stream_v4(base + g * 32);
@@ -414,24 +441,26 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
 constexpr int kResidentThreads = 1024;
 
 template <int MODE, int METRIC>
-__device__ __forceinline__ void rvisit4(const int4 e, const float2* src, float2 yi, float c,
-                                        float& fx, float& fy) {
+__device__ __forceinline__ void rvisit4(const int4 e, const float2* src, uint32_t M, float2 yi,
+                                        float c, float& fx, float& fy) {
   const uint32_t q[4] = {(uint32_t)e.x, (uint32_t)e.y, (uint32_t)e.z, (uint32_t)e.w};
   float2 g[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) g[t] = (q[t] == kPad) ? yi : src[q[t] & kIdxMask];
+  for (int t = 0; t < 4; ++t)
+    g[t] = (q[t] == kPad || !index_ok(q[t] & kIdxMask, M)) ? yi : src[q[t] & kIdxMask];
 #pragma unroll
   for (int t = 0; t < 4; ++t) force_term<METRIC>(q[t], g[t], yi, c, fx, fy);
 }
 
 template <int MODE, int METRIC>
-__device__ __forceinline__ void rvisit8(const int4 ea, const int4 eb, const float2* src, float2 yi,
-                                        float c, float& fx, float& fy) {
+__device__ __forceinline__ void rvisit8(const int4 ea, const int4 eb, const float2* src,
+                                        uint32_t M, float2 yi, float c, float& fx, float& fy) {
   const uint32_t q[8] = {(uint32_t)ea.x, (uint32_t)ea.y, (uint32_t)ea.z, (uint32_t)ea.w,
                          (uint32_t)eb.x, (uint32_t)eb.y, (uint32_t)eb.z, (uint32_t)eb.w};
   float2 g[8];
 #pragma unroll
-  for (int t = 0; t < 8; ++t) g[t] = (q[t] == kPad) ? yi : src[q[t] & kIdxMask];
+  for (int t = 0; t < 8; ++t)
+    g[t] = (q[t] == kPad || !index_ok(q[t] & kIdxMask, M)) ? yi : src[q[t] & kIdxMask];
 #pragma unroll
   for (int t = 0; t < 8; ++t) force_term<METRIC>(q[t], g[t], yi, c, fx, fy);
 }
@@ -476,10 +505,11 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
         ym = src[p];
         const int beg = A.hub_off[p], end = A.hub_off[p + 1];
         const int4* row = reinterpret_cast<const int4*>(ids + beg);
-        const int ng = (end - beg) >> 2;
+        const int ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
         int g = lane;
-        for (; g + 32 < ng; g += 64) rvisit8<MODE, METRIC>(row[g], row[g + 32], src, ym, A.c, fx, fy);
-        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, ym, A.c, fx, fy);
+        for (; g + 32 < ng; g += 64)
+          rvisit8<MODE, METRIC>(row[g], row[g + 32], src, (uint32_t)M, ym, A.c, fx, fy);
+        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, (uint32_t)M, ym, A.c, fx, fy);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -492,11 +522,15 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
         own = p < M;
         if (own) ym = src[p];
         const int4* base = reinterpret_cast<const int4*>(ids + A.slice_off[sl]) + lane;
-        const int W = A.slice_w[sl];
+        const int W =
+            row_ok(A.slice_off[sl], A.slice_off[sl] + (int64_t)A.slice_w[sl] * 128, A.n_slots)
+                ? A.slice_w[sl]
+                : 0;
         int g = 0;
         for (; g + 1 < W; g += 2)
-          rvisit8<MODE, METRIC>(base[g * 32], base[(g + 1) * 32], src, ym, A.c, fx, fy);
-        if (g < W) rvisit4<MODE, METRIC>(base[g * 32], src, ym, A.c, fx, fy);
+          rvisit8<MODE, METRIC>(base[g * 32], base[(g + 1) * 32], src, (uint32_t)M, ym, A.c, fx,
+                                fy);
+        if (g < W) rvisit4<MODE, METRIC>(base[g * 32], src, (uint32_t)M, ym, A.c, fx, fy);
       }
       if (!own) continue;
       if (MODE == kMomentum) {
@@ -603,10 +637,11 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_cluster(const StepArgs 
         ym = src[p];
         const int beg = A.hub_off[p], end = A.hub_off[p + 1];
         const int4* row = reinterpret_cast<const int4*>(A.ids + beg);
-        const int ng = (end - beg) >> 2;
+        const int ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
         int g = lane;
-        for (; g + 32 < ng; g += 64) rvisit8<MODE, METRIC>(row[g], row[g + 32], src, ym, A.c, fx, fy);
-        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, ym, A.c, fx, fy);
+        for (; g + 32 < ng; g += 64)
+          rvisit8<MODE, METRIC>(row[g], row[g + 32], src, (uint32_t)M, ym, A.c, fx, fy);
+        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, (uint32_t)M, ym, A.c, fx, fy);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -619,11 +654,15 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_cluster(const StepArgs 
         own = p < M;
         if (own) ym = src[p];
         const int4* base = reinterpret_cast<const int4*>(A.ids + A.slice_off[sl]) + lane;
-        const int W = A.slice_w[sl];
+        const int W =
+            row_ok(A.slice_off[sl], A.slice_off[sl] + (int64_t)A.slice_w[sl] * 128, A.n_slots)
+                ? A.slice_w[sl]
+                : 0;
         int g = 0;
         for (; g + 1 < W; g += 2)
-          rvisit8<MODE, METRIC>(base[g * 32], base[(g + 1) * 32], src, ym, A.c, fx, fy);
-        if (g < W) rvisit4<MODE, METRIC>(base[g * 32], src, ym, A.c, fx, fy);
+          rvisit8<MODE, METRIC>(base[g * 32], base[(g + 1) * 32], src, (uint32_t)M, ym, A.c, fx,
+                                fy);
+        if (g < W) rvisit4<MODE, METRIC>(base[g * 32], src, (uint32_t)M, ym, A.c, fx, fy);
       }
       if (!own) continue;
       float2 yn;
@@ -750,6 +789,7 @@ cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s) {
   A.M = (int32_t)ctx->M;
   A.n_hub = (int32_t)ctx->n_hub;
   A.n_slices = (int32_t)ctx->n_slices;
+  A.n_slots = ctx->n_slots;
   A.c = ctx->c;
   A.a = ctx->p.a;
   A.b = ctx->p.b;
@@ -947,6 +987,7 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   A.M = (int32_t)ctx->M;
   A.n_hub = (int32_t)ctx->n_hub;
   A.n_slices = (int32_t)ctx->n_slices;
+  A.n_slots = ctx->n_slots;
   A.wpb = ctx->block / 32;
   A.nb_hub = (int32_t)((ctx->n_hub + A.wpb - 1) / A.wpb);
   A.c = ctx->c;
@@ -1114,3 +1155,41 @@ cudaError_t launch_init_positions(ivhd_ctx* ctx) {
 }
 
 }  // namespace ivhd
+
+using namespace ivhd;
+
+extern "C" ivhd_status ivhd_check_violations(int64_t* out, int32_t reset) {
+  if (!out) return IVHD_ERR_ARG;
+#ifdef IVHD_CHECKED
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned long long v = 0;
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_check_violations, sizeof(v));
+  if (e == cudaSuccess && reset) {
+    const unsigned long long zero = 0;
+    e = cudaMemcpyToSymbol(g_check_violations, &zero, sizeof(zero));
+  }
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  *out = (int64_t)v;
+#else
+  (void)reset;
+  *out = -1;
+#endif
+  return IVHD_OK;
+}
+
+extern "C" ivhd_status ivhd_test_corrupt_layout(ivhd_ctx* ctx, int64_t slot, uint32_t value) {
+#ifdef IVHD_CHECKED
+  if (!ctx || slot < 0 || slot >= ctx->n_slots) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  cudaError_t e = cudaMemcpyAsync(ctx->ids + slot, &value, sizeof(value), cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return e == cudaSuccess ? IVHD_OK : IVHD_ERR_CUDA;
+#else
+  // only a build whose kernels test every index may hold a corrupt layout
+  (void)ctx;
+  (void)slot;
+  (void)value;
+  return IVHD_ERR_ARG;
+#endif
+}

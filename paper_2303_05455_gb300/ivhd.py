@@ -416,6 +416,15 @@ def set_allocator(alloc=None, free=None) -> None:
     check(L.ivhd_set_allocator(cbs[0], cbs[1], None), "ivhd_set_allocator")
 
 
+def check_violations(reset: bool = False) -> int:
+    """Out-of-range indices / rows the step kernels met and skipped (checked
+    builds, IVHD_CHECKED=1); -1 with the normal library."""
+    L = _lib.load()
+    v = ctypes.c_int64()
+    check(L.ivhd_check_violations(ctypes.byref(v), int(bool(reset))), "ivhd_check_violations")
+    return int(v.value)
+
+
 def use_torch_allocator(device=None) -> None:
     """Route the library's device allocations through PyTorch's caching allocator."""
     dev = torch.cuda.current_device() if device is None else torch.device(device).index

@@ -199,3 +199,12 @@ def test_set_allocator_pairs_and_reset(L):
     with pytest.raises(ValueError):
         from paper_2303_05455_gb300 import ivhd
         ivhd.set_allocator(lambda n, s: 0)
+
+
+@pytest.mark.skipif(os.environ.get("IVHD_CHECKED", "") not in ("", "0"),
+                    reason="the checked library counts violations")
+def test_normal_build_counts_no_violations_and_refuses_corruption(L):
+    v = ctypes.c_int64(7)
+    assert L.ivhd_check_violations(ctypes.byref(v), 0) == 0 and v.value == -1
+    assert L.ivhd_check_violations(None, 0) == -1
+    assert L.ivhd_test_corrupt_layout(None, 0, 0) == -1

@@ -161,6 +161,21 @@ def test_deterministic_bitwise():
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
+def test_bitwise_equal_across_block_sizes(opt):
+    # the layout (hub threshold) fixes every vertex's summation order; the
+    # block size only groups rows into blocks, so results must not move
+    knn, r, c = graph_case("hubs5k")
+    out = []
+    for bs in (128, 256, 512):
+        emb = ivhd.Embedding(knn, r=r, c=c, seed=9, opt=opt, block_size=bs, hub_threshold=32,
+                             resident=False)
+        emb.step(70)
+        out.append(emb.positions(host=True))
+        emb.close()
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
 def test_graph_replay_equals_single_launches():
     knn, r, c = graph_case("gmm2k")
     a = ivhd.Embedding(knn, r=r, c=c, seed=4, resident=False)
