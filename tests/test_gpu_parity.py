@@ -168,11 +168,12 @@ def test_bitwise_equal_across_block_sizes(opt):
     knn, r, c = graph_case("hubs5k")
     out = []
     for bs in (128, 256, 512):
-        emb = ivhd.Embedding(knn, r=r, c=c, seed=9, opt=opt, block_size=bs, hub_threshold=32,
-                             resident=False)
+        emb = ivhd.Embedding(knn, r=r, c=c, seed=9, opt=opt, b=0.002, block_size=bs,
+                             hub_threshold=32, resident=False)
         emb.step(70)
         out.append(emb.positions(host=True))
         emb.close()
+    assert np.all(np.isfinite(out[0]))
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
