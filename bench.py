@@ -22,6 +22,7 @@ project has) on the same metric; under torchrun only rank 0 runs it.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -45,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="gmm1p4m", choices=sorted(synth.WORKLOADS))
@@ -83,15 +84,23 @@ def workload_config(w: synth.Workload, n_iter: int, opt: str = "momentum") -> di
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region.
+
+    The sampler starts, and its first sample is awaited, before the timed
+    region opens, so that nvidia-smi's own start-up does not overlap the timed
+    work; a reader thread drains its output while it runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, first_sample_timeout: float = 10.0):
+        import threading
+
         self.proc = None
         self.gpu = gpu_index
+        self.lines = []
+        self._first = threading.Event()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -99,19 +108,33 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self._reader = threading.Thread(target=self._drain, daemon=True)
+        self._reader.start()
+        self._first.wait(first_sample_timeout)
+        self.n_before = len(self.lines)   # samples taken before the timed region
+
+    def _drain(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
+            self._first.set()
+        self._first.set()
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        self._reader.join(timeout=5)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        # the samples of the timed region (the last one before it opened included,
+        # so that a short region still has one)
+        for line in self.lines[max(0, self.n_before - 1):]:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -318,10 +341,12 @@ def run_ours(args):
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     launches = 0
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    gc.collect()
+    gc.disable()   # no collector pauses between the host calls of a timed embedding
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank) if rank == 0 else None
     wall0 = time.perf_counter()
     for s in range(args.steps):
         flush.zero_()
@@ -331,6 +356,7 @@ def run_ours(args):
         launches += info["setup_launches"] + info["kernel_launches"] + info["aux_launches"]
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    gc.enable()
     clk = clocks.stop() if clocks else None
     if world > 1:
         torch.distributed.barrier()

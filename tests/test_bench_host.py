@@ -66,3 +66,26 @@ def test_reference_arm_line_on_small_workload(capsys, monkeypatch):
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
     assert line["config"]["optimizer"] == "adadelta"
+
+
+def test_clock_sampler_parses_samples_and_reasons(tmp_path, monkeypatch):
+    # a stand-in for nvidia-smi that prints one CSV sample every 50 ms
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nwhile true; do\n"
+                    "echo '0, 1980, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Active'\n"
+                    "sleep 0.05\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    cs = bench.ClockSampler(0)
+    assert cs.lines, "the first sample is awaited before the timed region"
+    import time
+    time.sleep(0.3)
+    r = cs.stop()
+    assert r["sm_mhz"] == 1980.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"] and r["samples"] >= 3
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    r = bench.ClockSampler(0).stop()
+    assert r["sm_mhz"] is None and r["reasons"] == ["nvidia-smi unavailable"]
