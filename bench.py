@@ -465,6 +465,16 @@ def run_ours(args):
                     "frac": (nnz / launch_s) / gpeak,
                     "peak_source": "ivhd_probe_gather on this GPU: uniformly random float2 "
                                    f"gathers from {M} elements, indices in registers"}}
+    # the binding limit: t_min = max(HBM bytes / HBM peak, gathers / measured gather rate)
+    t_hbm = alg_bytes / (peaks["hbm_gbs"] * 1e9)
+    t_gather = nnz / gpeak
+    roofline["binding"] = {
+        "bound": "l2_gather" if t_gather >= t_hbm else "hbm",
+        "t_min_us": 1e6 * max(t_hbm, t_gather), "t_hbm_us": 1e6 * t_hbm,
+        "t_gather_us": 1e6 * t_gather, "frac": max(t_hbm, t_gather) / launch_s,
+        "what": "launch time against the larger of the two lower bounds: the streamed "
+                "bytes at the HBM copy peak, and the gathered entries at the measured "
+                "random-gather rate (each gather is one 32-byte L2 sector request)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
