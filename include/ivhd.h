@@ -308,7 +308,11 @@ ivhd_status ivhd_restrict_nn(ivhd_ctx *ctx, const int32_t *helper, int32_t k_hel
  */
 ivhd_status ivhd_adaptive_state(ivhd_ctx *ctx, float *b, int64_t *accepted, int64_t *rejected);
 
-/* Frees the context and its device memory (after its stream drains).  NULL is a no-op. */
+/*
+ * Frees the context and its device memory.  The memory is released in stream
+ * order, after the work already queued on the context's stream; the call does
+ * not wait for that work.  NULL is a no-op.
+ */
 void ivhd_destroy(ivhd_ctx *ctx);
 
 /* A static, human-readable name for a status.  Never NULL. */

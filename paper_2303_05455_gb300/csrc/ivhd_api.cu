@@ -180,9 +180,13 @@ void free_layout(ivhd_ctx* ctx) {
   ctx->partials = nullptr;
 }
 
+// The frees are stream-ordered: they take effect once the work already queued
+// on the context's stream has run, so destroy does not wait for it.  They are
+// queued before the graphs are destroyed, so that they are not held up behind
+// graph executions that are still in flight (an in-flight graph is released
+// when it completes).
 void free_ctx(ivhd_ctx* ctx) {
   cudaStream_t s = ctx->stream;
-  drop_graphs(ctx);
   free_layout(ctx);
   void* bufs[] = {ctx->knn, ctx->knn_full, ctx->rn, ctx->perm, ctx->inv, ctx->y[0], ctx->y[1],
                   ctx->yh[0], ctx->yh[1], ctx->vbuf[0], ctx->vbuf[1], ctx->s2, ctx->ctl,
@@ -190,7 +194,7 @@ void free_ctx(ivhd_ctx* ctx) {
                   ctx->seg_seed};
   for (void* b : bufs)
     if (b) dev_free(b, s);
-  cudaStreamSynchronize(s);
+  drop_graphs(ctx);
   delete ctx;
 }
 
