@@ -118,6 +118,12 @@ typedef struct {
                              1: a single block; 0 (default): the cluster for graphs of at
                              most 40,000 stored entries, where it is faster, else one
                              launch per step; -1: always one launch per step */
+    int32_t vertices_per_warp; /* warp-per-vertex rows of medium degree processed several
+                             to a warp: 1, 2, 4 or 8 rows per warp, each on 32 / that many
+                             lanes, for the rows below 512 / that many entries (longer rows
+                             keep a whole warp); 0 = library default: 4 for graphs of at most
+                             ~2e6 stored entries (latency-bound launches), else 1 (a whole
+                             warp per row); see ivhd_autotune */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 
@@ -180,17 +186,20 @@ ivhd_status ivhd_create_batch(const int32_t *knn, const int64_t *M_e, const int3
                               ivhd_ctx **out);
 
 /*
- * Launch-shape autotuner: times trial_steps steps for every pair of threads
- * per block (128, 256, 512) and hub threshold (16, 32, 64, 128, 256, 512: the
- * degree from which a vertex gets a whole warp instead of one lane), starting
- * each trial from the same state, then keeps the fastest pair and restores the
- * state, so the embedding continues exactly as before the call (with the new
- * layout's summation order).  Outputs (host, may be NULL): the chosen block
- * size, hub threshold and microseconds per step.  Synchronises.
- * Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA, IVHD_ERR_OOM, IVHD_ERR_STATE.
+ * Launch-shape autotuner: times trial_steps steps for every combination of
+ * threads per block (128, 256, 512), hub threshold (16, 32, 64, 128, 256, 512:
+ * the degree from which a vertex gets warp lanes instead of one lane) and
+ * vertices per warp (1, 2, 4, 8: how many rows of medium degree share a warp),
+ * starting each trial from the same state, then keeps the fastest and restores
+ * the state, so the embedding continues exactly as before the call (with the
+ * new layout's summation order).  Outputs (host, may be NULL): the chosen
+ * block size, hub threshold, vertices per warp and microseconds per step.
+ * Synchronises.  Errors: IVHD_ERR_ARG, IVHD_ERR_CUDA, IVHD_ERR_OOM,
+ * IVHD_ERR_STATE.
  */
 ivhd_status ivhd_autotune(ivhd_ctx *ctx, int32_t trial_steps, int32_t *best_block,
-                          int32_t *best_hub_threshold, float *best_us_per_step);
+                          int32_t *best_hub_threshold, int32_t *best_vertices_per_warp,
+                          float *best_us_per_step);
 
 /*
  * Overwrites the positions with xy (M*2 float32, row-major, vertex order of

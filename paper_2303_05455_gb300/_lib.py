@@ -51,7 +51,8 @@ class Params(ctypes.Structure):
         ("hub_threshold", ctypes.c_int32), ("pos_format", ctypes.c_int32),
         ("adaptive", ctypes.c_int32), ("tau", ctypes.c_float), ("gamma1", ctypes.c_float),
         ("gamma2", ctypes.c_float), ("block_size", ctypes.c_int32),
-        ("resident", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("resident", ctypes.c_int32), ("vertices_per_warp", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
     ]
 
 
@@ -162,7 +163,8 @@ def load(build_if_missing: bool = False):
                                     i32, ctypes.POINTER(P)]
     L.ivhd_create_batch.restype = i32
     L.ivhd_autotune.argtypes = [P, i32, ctypes.POINTER(ctypes.c_int32),
-                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]
+                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_float)]
     L.ivhd_autotune.restype = i32
     L.ivhd_gemm_bf16_tn.argtypes = [P, P, P, i64, i64, i64, P]
     L.ivhd_gemm_bf16_tn.restype = i32

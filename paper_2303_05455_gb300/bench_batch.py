@@ -9,7 +9,7 @@ built on the GPU before anything is timed.  Timed, with CUDA events:
 
 * one-by-one: for each embedding ivhd_create + 1,000 steps + positions, FP32;
 * batched: one ivhd_create_batch with the launch shape (block size, hub
-  threshold) the autotuner chose beforehand + 1,000 steps (one launch per step
+  threshold, vertices per warp) the autotuner chose beforehand + 1,000 steps (one launch per step
   for all embeddings) + positions, for BF16, FP16 and FP32 gathered
   positions; the library's default shape is reported beside it.
 
@@ -74,11 +74,12 @@ def main():
     batched_runs = {}
     for fmt in args.formats.split(","):
         def create(shape=None):
-            shape = shape or {"block": 0, "hub_threshold": 0}
+            shape = shape or {"block": 0, "hub_threshold": 0, "vertices_per_warp": 0}
             return ivhd.Embedding.batch([g for g in graphs], r=[w["r"] for w in work],
                                         seeds=[w["seed"] for w in work], c=c, a=a, b=b,
                                         pos_format=fmt, block_size=shape["block"],
-                                        hub_threshold=shape["hub_threshold"])
+                                        hub_threshold=shape["hub_threshold"],
+                                        vertices_per_warp=shape["vertices_per_warp"])
 
         emb0 = create()
         t = time.perf_counter()

@@ -152,6 +152,9 @@ bool params_ok(const ivhd_params& p) {
   if (p.block_size != 0 && p.block_size != 128 && p.block_size != 256 && p.block_size != 512)
     return false;
   if (p.resident < -1 || p.resident > 2) return false;
+  if (p.vertices_per_warp != 0 && p.vertices_per_warp != 1 && p.vertices_per_warp != 2 &&
+      p.vertices_per_warp != 4 && p.vertices_per_warp != 8)
+    return false;
   if (p.adaptive) {
     if (p.opt == IVHD_OPT_ADADELTA) return false;
     if (!std::isfinite(p.tau) || p.tau <= 0.f) return false;
@@ -455,6 +458,8 @@ ivhd_status ivhd_create(const int32_t* knn, int64_t M, int32_t k, int32_t r, flo
   ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold
                                             : auto_hub_threshold(2 * M * (int64_t)(k + r));
   ctx->block = p.block_size > 0 ? p.block_size : kStepBlock;
+  ctx->vpw = p.vertices_per_warp > 0 ? p.vertices_per_warp
+                                     : auto_vertices_per_warp(2 * M * (int64_t)(k + r));
   ctx->stream = (cudaStream_t)p.stream;
   cudaGetDevice(&ctx->device);
   cudaStream_t s = ctx->stream;
@@ -903,6 +908,7 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
   ctx->c = c;
   ctx->hub_threshold = p.hub_threshold > 0 ? p.hub_threshold : auto_hub_threshold(sym_entries);
   ctx->block = p.block_size > 0 ? p.block_size : kStepBlock;
+  ctx->vpw = p.vertices_per_warp > 0 ? p.vertices_per_warp : auto_vertices_per_warp(sym_entries);
   ctx->stream = (cudaStream_t)p.stream;
   cudaGetDevice(&ctx->device);
   cudaStream_t s = ctx->stream;
@@ -962,7 +968,8 @@ extern "C" ivhd_status ivhd_create_batch(const int32_t* knn, const int64_t* M_e,
 }
 
 extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t* best_block,
-                                     int32_t* best_hub_threshold, float* best_us_per_step) {
+                                     int32_t* best_hub_threshold,
+                                     int32_t* best_vertices_per_warp, float* best_us_per_step) {
   NvtxScope nvtx_("ivhd_autotune");
   if (!ctx || trial_steps < 1) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;
@@ -998,8 +1005,9 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
   };
   const int blocks[3] = {128, 256, 512};
   const int hubs[6] = {16, 32, 64, 128, 256, 512};
+  const int vpws[4] = {1, 2, 4, 8};
   float best = 1e30f;
-  int bb = ctx->block, bh = ctx->hub_threshold;
+  int bb = ctx->block, bh = ctx->hub_threshold, bv = ctx->vpw;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -1010,8 +1018,10 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
     drop_graphs(ctx);
     free_layout(ctx);
     st = build_layout(ctx, false, 0);
-    for (int bi = 0; bi < 3 && e == cudaSuccess && st == IVHD_OK; ++bi) {
+    for (int c = 0; c < 12 && e == cudaSuccess && st == IVHD_OK; ++c) {
+      const int bi = c / 4, vi = c % 4;
       ctx->block = blocks[bi];
+      ctx->vpw = vpws[vi];
       if (ctx->partials) dev_free(ctx->partials, s);
       ctx->partials = nullptr;
       e = alloc_partials(ctx);
@@ -1033,6 +1043,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
         best = us;
         bb = blocks[bi];
         bh = hubs[hi];
+        bv = vpws[vi];
       }
     }
   }
@@ -1040,6 +1051,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
   if (e == cudaSuccess && st == IVHD_OK) {
     ctx->hub_threshold = bh;
     ctx->block = bb;
+    ctx->vpw = bv;
     drop_graphs(ctx);
     free_layout(ctx);
     st = build_layout(ctx, false, 0);
@@ -1059,6 +1071,7 @@ extern "C" ivhd_status ivhd_autotune(ivhd_ctx* ctx, int32_t trial_steps, int32_t
   }
   if (best_block) *best_block = bb;
   if (best_hub_threshold) *best_hub_threshold = bh;
+  if (best_vertices_per_warp) *best_vertices_per_warp = bv;
   if (best_us_per_step) *best_us_per_step = best;
   return IVHD_OK;
 }

@@ -68,6 +68,11 @@ inline int auto_hub_threshold(int64_t entries) {
   while (h < 256 && (int64_t)(2 * h) * 70000 <= entries) h *= 2;
   return h;
 }
+// Rows of medium degree per warp in the warp-per-vertex region.  Small and
+// mid-size graphs finish a launch in one or two waves of short rows, and
+// packing the rows below 128 entries four to a warp (8 lanes each) shortens
+// the launch; large graphs are request-rate bound and keep a warp per row.
+inline int auto_vertices_per_warp(int64_t entries) { return entries <= 2000000 ? 4 : 1; }
 constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
 constexpr int kResidentSmem = 200 * 1024;  // shared memory of the resident whole-run kernel
 
@@ -138,6 +143,9 @@ struct StepArgs {
   double* __restrict__ partials;     // stress: one double per block; adaptive: two
   int32_t* __restrict__ flag;        // stress mode: non-finite flag
   int32_t M, n_hub, n_slices, nb_hub, wpb;
+  // warp-per-vertex rows: the first n_full take a whole warp each, the others
+  // share a warp, mid_g lanes per row; hub_warps warps cover all of them
+  int32_t n_full, mid_g, hub_warps;
   int64_t n_slots;  // layout entries (checked builds test row extents against it)
   float c, a, b, rho, eps;
 };
@@ -154,6 +162,7 @@ struct ivhd_ctx {
   float c = 0.f;
   int hub_threshold = ivhd::kDefaultHubThreshold;
   int block = ivhd::kStepBlock;
+  int vpw = 1;  // rows of medium degree per warp (1, 2, 4, 8)
   bool poisoned = false;
 
   // segments (independent embeddings) and their device tables
@@ -176,6 +185,7 @@ struct ivhd_ctx {
   int32_t* slice_off = nullptr;
   int32_t* slice_w = nullptr;
   int64_t n_slots = 0, n_hub = 0, n_slices = 0;
+  int64_t n_ge[3] = {0, 0, 0};  // rows with at least 256, 128, 64 entries (all hub rows)
 
   // state
   float2* y[2] = {nullptr, nullptr};

@@ -99,6 +99,32 @@ __device__ __forceinline__ constexpr bool index_ok(uint32_t, uint32_t) { return 
 __device__ __forceinline__ constexpr bool row_ok(int64_t, int64_t, int64_t) { return true; }
 #endif
 
+// Warp w of the warp-per-vertex region (the hub rows, in descending degree):
+// the first n_full rows take a whole warp each; the rest share a warp, mid_g
+// lanes per row (32 / mid_g rows per warp).  Lanes past the last row get a
+// row index >= n_hub.  With mid_g = 32 every row has its own warp.
+struct HubSlot {
+  int row;  // vertex (= row of the region)
+  int g;    // lanes on the row: 32 or mid_g (a power of two)
+  int l;    // this lane's index among them
+};
+__device__ __forceinline__ HubSlot hub_slot(int w, int lane, int n_full, int mid_g) {
+  if (w < n_full) return HubSlot{w, 32, lane};
+  return HubSlot{n_full + (w - n_full) * (32 / mid_g) + lane / mid_g, mid_g, lane & (mid_g - 1)};
+}
+
+// Sum over the g lanes of each aligned lane group (g uniform over the warp);
+// with g = 32 the butterfly over the whole warp.
+__device__ __forceinline__ void group_sum(float& fx, float& fy, int g) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (o < g) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    }
+  }
+}
+
 // L1 policy of the FP32 gathers.  The layout orders vertices by degree, and a
 // vertex is gathered once per symmetric term, so the first vertices are the
 // most gathered ones (on the 1.4e6-vertex exact kNN graph the first 16,384
@@ -313,27 +339,31 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
   bool own = false;
 
   if ((int)blockIdx.x < A.nb_hub) {
-    // hub rows: one warp per vertex, lanes stride over int4 groups
-    p = (int)blockIdx.x * A.wpb + wib;
-    if (p < A.n_hub) {
-      ym = G.y[p];
-      yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
-      const int beg = A.hub_off[p], end = A.hub_off[p + 1];
-      const int4* row = reinterpret_cast<const int4*>(A.ids + beg);
-      const int ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
-      int g = lane;
-      for (; g + 32 < ng; g += 64) {
+    // hub rows: a warp, or a group of mid_g lanes, per vertex; the lanes of a
+    // row stride over its int4 groups, then sum their partial forces
+    const int w = (int)blockIdx.x * A.wpb + wib;
+    if (w < A.hub_warps) {
+      const HubSlot h = hub_slot(w, lane, A.n_full, A.mid_g);
+      const bool valid = h.row < A.n_hub;
+      int ng = 0;
+      const int4* row = nullptr;
+      if (valid) {
+        p = h.row;
+        ym = G.y[p];
+        yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
+        const int beg = A.hub_off[p], end = A.hub_off[p + 1];
+        row = reinterpret_cast<const int4*>(A.ids + beg);
+        ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
+      }
+      int g = h.l;
+      for (; g + h.g < ng; g += 2 * h.g) {
         const int4 ea = ld_stream_v4(row + g);
-        const int4 eb = ld_stream_v4(row + g + 32);
+        const int4 eb = ld_stream_v4(row + g + h.g);
         visit8<MODE, POS, METRIC>(ea, eb, G, yi, A.c, fx, fy);
       }
       if (g < ng) visit4<MODE, POS, METRIC>(ld_stream_v4(row + g), G, yi, A.c, fx, fy);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-      }
-      own = (lane == 0);
+      group_sum(fx, fy, h.g);
+      own = valid && h.l == 0;
     }
   } else {
     // SELL slice: one thread per vertex, one coalesced int4 per 4 neighbours
@@ -490,7 +520,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
   }
   __syncthreads();
   const uint32_t* ids = IDS_SMEM ? ids_s : A.ids;
-  const int n_items = A.n_hub + A.n_slices;
+  const int n_items = A.hub_warps + A.n_slices;
 
   for (int64_t it = 0; it < n_iter; ++it) {
     const float2* src = (it & 1) ? ys1 : ys0;
@@ -500,24 +530,26 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
       float2 ym = make_float2(0.f, 0.f);
       int p;
       bool own;
-      if (item < A.n_hub) {
-        p = item;
-        ym = src[p];
-        const int beg = A.hub_off[p], end = A.hub_off[p + 1];
-        const int4* row = reinterpret_cast<const int4*>(ids + beg);
-        const int ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
-        int g = lane;
-        for (; g + 32 < ng; g += 64)
-          rvisit8<MODE, METRIC>(row[g], row[g + 32], src, (uint32_t)M, ym, A.c, fx, fy);
-        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, (uint32_t)M, ym, A.c, fx, fy);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          fx += __shfl_xor_sync(0xffffffffu, fx, o);
-          fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      if (item < A.hub_warps) {
+        const HubSlot h = hub_slot(item, lane, A.n_full, A.mid_g);
+        const bool valid = h.row < A.n_hub;
+        int ng = 0;
+        const int4* row = nullptr;
+        p = h.row;
+        if (valid) {
+          ym = src[p];
+          const int beg = A.hub_off[p], end = A.hub_off[p + 1];
+          row = reinterpret_cast<const int4*>(ids + beg);
+          ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
         }
-        own = (lane == 0);
+        int g = h.l;
+        for (; g + h.g < ng; g += 2 * h.g)
+          rvisit8<MODE, METRIC>(row[g], row[g + h.g], src, (uint32_t)M, ym, A.c, fx, fy);
+        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, (uint32_t)M, ym, A.c, fx, fy);
+        group_sum(fx, fy, h.g);
+        own = valid && h.l == 0;
       } else {
-        const int sl = item - A.n_hub;
+        const int sl = item - A.hub_warps;
         p = A.n_hub + sl * 32 + lane;
         own = p < M;
         if (own) ym = src[p];
@@ -606,11 +638,14 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_cluster(const StepArgs 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const uint32_t rank = cluster_rank();
-  const int n_items = A.n_hub + A.n_slices;
+  const int n_items = A.hub_warps + A.n_slices;
   const int it_lo = (int)((int64_t)n_items * rank / kClusterCTAs);
   const int it_hi = (int)((int64_t)n_items * (rank + 1) / kClusterCTAs);
+  // the first vertex of an item: items cover contiguous, ascending vertex ranges
   auto first_vertex = [&](int item) {
-    return item < A.n_hub ? item : A.n_hub + (item - A.n_hub) * 32;
+    if (item < A.n_full) return item;
+    if (item < A.hub_warps) return A.n_full + (item - A.n_full) * (32 / A.mid_g);
+    return A.n_hub + (item - A.hub_warps) * 32;
   };
   const int v_lo = min(M, first_vertex(it_lo)), v_hi = min(M, first_vertex(it_hi));
 
@@ -632,24 +667,26 @@ __global__ void __launch_bounds__(kResidentThreads, 1) k_cluster(const StepArgs 
       float2 ym = make_float2(0.f, 0.f);
       int p;
       bool own;
-      if (item < A.n_hub) {
-        p = item;
-        ym = src[p];
-        const int beg = A.hub_off[p], end = A.hub_off[p + 1];
-        const int4* row = reinterpret_cast<const int4*>(A.ids + beg);
-        const int ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
-        int g = lane;
-        for (; g + 32 < ng; g += 64)
-          rvisit8<MODE, METRIC>(row[g], row[g + 32], src, (uint32_t)M, ym, A.c, fx, fy);
-        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, (uint32_t)M, ym, A.c, fx, fy);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          fx += __shfl_xor_sync(0xffffffffu, fx, o);
-          fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      if (item < A.hub_warps) {
+        const HubSlot h = hub_slot(item, lane, A.n_full, A.mid_g);
+        const bool valid = h.row < A.n_hub;
+        int ng = 0;
+        const int4* row = nullptr;
+        p = h.row;
+        if (valid) {
+          ym = src[p];
+          const int beg = A.hub_off[p], end = A.hub_off[p + 1];
+          row = reinterpret_cast<const int4*>(A.ids + beg);
+          ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
         }
-        own = (lane == 0);
+        int g = h.l;
+        for (; g + h.g < ng; g += 2 * h.g)
+          rvisit8<MODE, METRIC>(row[g], row[g + h.g], src, (uint32_t)M, ym, A.c, fx, fy);
+        if (g < ng) rvisit4<MODE, METRIC>(row[g], src, (uint32_t)M, ym, A.c, fx, fy);
+        group_sum(fx, fy, h.g);
+        own = valid && h.l == 0;
       } else {
-        const int sl = item - A.n_hub;
+        const int sl = item - A.hub_warps;
         p = A.n_hub + sl * 32 + lane;
         own = p < M;
         if (own) ym = src[p];
@@ -773,6 +810,21 @@ static cudaError_t launch_res_ids(const StepArgs& A, int64_t n_iter, int64_t n_s
                    : launch_res<MODE, METRIC, false>(A, n_iter, n_slots, smem, s);
 }
 
+// Warps of the warp-per-vertex region for ctx->vpw rows of medium degree per
+// warp: rows with at least 512 / vpw entries keep a whole warp.
+static void hub_map(const ivhd_ctx* ctx, int32_t* n_full, int32_t* mid_g, int32_t* warps) {
+  const int vpw = ctx->vpw;
+  int64_t full = ctx->n_hub;
+  if (vpw == 2 || vpw == 4 || vpw == 8) {
+    const int t = (vpw == 2) ? 0 : (vpw == 4) ? 1 : 2;  // 256, 128, 64 entries
+    full = ctx->n_ge[t] < ctx->n_hub ? ctx->n_ge[t] : ctx->n_hub;
+  }
+  const int v = (full == ctx->n_hub) ? 1 : vpw;
+  *n_full = (int32_t)full;
+  *mid_g = 32 / v;
+  *warps = (int32_t)(full + (ctx->n_hub - full + v - 1) / v);
+}
+
 cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s) {
   const int mode = resident_mode(ctx);
   if (mode == 0) return cudaErrorInvalidValue;
@@ -790,6 +842,7 @@ cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s) {
   A.n_hub = (int32_t)ctx->n_hub;
   A.n_slices = (int32_t)ctx->n_slices;
   A.n_slots = ctx->n_slots;
+  hub_map(ctx, &A.n_full, &A.mid_g, &A.hub_warps);
   A.c = ctx->c;
   A.a = ctx->p.a;
   A.b = ctx->p.b;
@@ -989,7 +1042,8 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   A.n_slices = (int32_t)ctx->n_slices;
   A.n_slots = ctx->n_slots;
   A.wpb = ctx->block / 32;
-  A.nb_hub = (int32_t)((ctx->n_hub + A.wpb - 1) / A.wpb);
+  hub_map(ctx, &A.n_full, &A.mid_g, &A.hub_warps);
+  A.nb_hub = (int32_t)((A.hub_warps + A.wpb - 1) / A.wpb);
   A.c = ctx->c;
   A.a = ctx->p.a;
   A.b = ctx->p.b;
@@ -1000,7 +1054,9 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
 
 int step_grid(const ivhd_ctx* ctx) {
   const int wpb = ctx->block / 32;
-  const int64_t nb_hub = (ctx->n_hub + wpb - 1) / wpb;
+  int32_t n_full, mid_g, warps;
+  hub_map(ctx, &n_full, &mid_g, &warps);
+  const int64_t nb_hub = (warps + wpb - 1) / wpb;
   const int64_t nb_sell = (ctx->n_slices + wpb - 1) / wpb;
   return (int)(nb_hub + nb_sell);
 }

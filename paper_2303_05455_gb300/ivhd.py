@@ -51,7 +51,8 @@ class Embedding:
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
                  hub_threshold: int = 0, pos_format: str = "f32", adaptive: bool = False,
                  tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, block_size: int = 0,
-                 resident=None, stream=None, device=None, batch=None):
+                 resident=None, vertices_per_warp: int = 0, stream=None, device=None,
+                 batch=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -81,6 +82,7 @@ class Embedding:
         # resident: None (automatic), False (one launch per step), True (one block),
         # "cluster" (8-block cluster)
         p.resident = {None: 0, False: -1, True: 1, "cluster": 2}[resident]
+        p.vertices_per_warp = int(vertices_per_warp)
         p.stream = self.stream.cuda_stream or None
         self.opt = opt
         self.params = p
@@ -234,10 +236,12 @@ class Embedding:
     def autotune(self, trial_steps: int = 20) -> dict:
         bb = ctypes.c_int32()
         bh = ctypes.c_int32()
+        bv = ctypes.c_int32()
         us = ctypes.c_float()
         check(self._L.ivhd_autotune(self._h, int(trial_steps), ctypes.byref(bb), ctypes.byref(bh),
-                                    ctypes.byref(us)), "ivhd_autotune")
-        return {"block": bb.value, "hub_threshold": bh.value, "us_per_step": us.value}
+                                    ctypes.byref(bv), ctypes.byref(us)), "ivhd_autotune")
+        return {"block": bb.value, "hub_threshold": bh.value, "vertices_per_warp": bv.value,
+                "us_per_step": us.value}
 
     def adaptive_state(self) -> dict:
         b = ctypes.c_float()

@@ -103,6 +103,7 @@ def test_create_rejects_bad_sizes(L, M, k, r, c):
     ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
     ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1), ("adaptive", 2),
     ("block_size", 64), ("block_size", 1024), ("resident", 3), ("resident", -2),
+    ("vertices_per_warp", 3), ("vertices_per_warp", 16), ("vertices_per_warp", -1),
 ])
 def test_create_rejects_bad_params(L, field, value):
     p = _lib.Params()
@@ -170,7 +171,7 @@ def test_new_entry_points_reject_null(L):
     assert L.ivhd_resample_random_neighbors(None, 1) == -1
     assert L.ivhd_restrict_nn(None, None, 0, 0) == -1
     assert L.ivhd_adaptive_state(None, None, None, None) == -1
-    assert L.ivhd_autotune(None, 5, None, None, None) == -1
+    assert L.ivhd_autotune(None, 5, None, None, None, None) == -1
     h = ctypes.c_void_p()
     M = np.array([10, 1], np.int64)           # an embedding with a single vertex
     k = np.array([2, 1], np.int32)

@@ -71,7 +71,7 @@ def test_batch_equals_separate_contexts_and_autotune_keeps_state():
     before = emb.positions(host=True)
     cfg = emb.autotune(trial_steps=5)
     assert cfg["block"] in (128, 256, 512) and cfg["hub_threshold"] in (16, 32, 64, 128, 256, 512)
-    assert cfg["us_per_step"] > 0
+    assert cfg["vertices_per_warp"] in (1, 2, 4, 8) and cfg["us_per_step"] > 0
     assert np.array_equal(emb.positions(host=True), before)
     assert emb.info()["steps_done"] == 30
     emb.step(64)  # graph replay with the tuned shape

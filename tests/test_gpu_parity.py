@@ -131,6 +131,27 @@ def test_one_step_and_ten_steps(case, opt, dedup, hub_threshold):
     assert emb.stress() == pytest.approx(oracle.stress(y10, terms, c), rel=1e-5)
 
 
+@pytest.mark.parametrize("vpw", [1, 2, 4, 8])
+@pytest.mark.parametrize("opt", ["momentum", "adadelta"])
+def test_rows_shared_by_a_warp_match_oracle(opt, vpw):
+    # hub threshold 16 makes most rows warp-per-vertex rows; with vpw > 1 the
+    # rows below 512 / vpw entries share a warp, 32 / vpw lanes each
+    knn, r, c = graph_case("hubs5k")
+    a, b = 0.9, 0.002
+    emb = ivhd.Embedding(knn, r=r, c=c, opt=opt, a=a, b=b, seed=5, hub_threshold=16,
+                         vertices_per_warp=vpw, resident=False)
+    rn, _ = oracle.random_neighbors(knn, r, 5)
+    terms = oracle.build_terms(knn, rn)
+    y0 = emb.positions(host=True).astype(np.float64)
+    close(emb.forces(host=True), oracle.forces(y0, terms, c))
+    st = oracle.State.fresh(y0)
+    emb.step(10)
+    oracle.run(st, terms, c, 10, OPT_ID[opt], a=a, b=b)
+    close(emb.positions(host=True), st.Y)
+    y10 = emb.positions(host=True).astype(np.float64)
+    assert emb.stress() == pytest.approx(oracle.stress(y10, terms, c), rel=1e-5)
+
+
 def test_given_positions_and_zero_distance_pairs():
     # all vertices start at one point: every rn pair has d = 0 (zero force),
     # nn forces vanish too; then a spread start through ivhd_set_positions
@@ -169,7 +190,7 @@ def test_bitwise_equal_across_block_sizes(opt):
     out = []
     for bs in (128, 256, 512):
         emb = ivhd.Embedding(knn, r=r, c=c, seed=9, opt=opt, b=0.002, block_size=bs,
-                             hub_threshold=32, resident=False)
+                             hub_threshold=32, vertices_per_warp=4, resident=False)
         emb.step(70)
         out.append(emb.positions(host=True))
         emb.close()

@@ -37,6 +37,7 @@ def case(seed):
                   dedup_mutual=bool(rng.random() < 0.5),
                   hub_threshold=int(rng.choice([0, 1, 16, 128])),
                   block_size=int(rng.choice([0, 128, 256, 512])))
+    params["vertices_per_warp"] = int(rng.choice([0, 1, 2, 4, 8]))
     return knn, r, c, params
 
 

@@ -29,15 +29,17 @@ def graphs():
 GRAPHS = graphs()
 
 
+@pytest.mark.parametrize("vpw", [1, 4])
 @pytest.mark.parametrize("kind", [True, "cluster"])
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 @pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
 @pytest.mark.parametrize("metric", ["l2", "l1"])
-def test_resident_equals_multi_launch_bitwise(name, opt, metric, kind):
+def test_resident_equals_multi_launch_bitwise(name, opt, metric, kind, vpw):
     knn, r, c = GRAPHS[name]
     runs = []
     for resident in (kind, False):
-        e = ivhd.Embedding(knn, r=r, c=c, opt=opt, b=0.002, seed=9, resident=resident)
+        e = ivhd.Embedding(knn, r=r, c=c, opt=opt, b=0.002, seed=9, resident=resident,
+                           hub_threshold=16, vertices_per_warp=vpw)
         if metric == "l1":
             e.set_metric("l1")
         out = []
