@@ -121,9 +121,11 @@ typedef struct {
     int32_t vertices_per_warp; /* warp-per-vertex rows of medium degree processed several
                              to a warp: 1, 2, 4 or 8 rows per warp, each on 32 / that many
                              lanes, for the rows below 512 / that many entries (longer rows
-                             keep a whole warp); 0 = library default: 4 for graphs of at most
-                             ~2e6 stored entries (latency-bound launches), else 1 (a whole
-                             warp per row); see ivhd_autotune */
+                             keep a whole warp); 0 = library default: 1 (a whole warp per
+                             row).  Measured (us per step, hub threshold / rows per warp):
+                             random 200,000-vertex graph with hubs 16/4 11.0 against 12.0
+                             for the best shape with 1; no gain on the exact kNN graphs of
+                             70,000 and 1.4e6 points.  ivhd_autotune searches it */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
 

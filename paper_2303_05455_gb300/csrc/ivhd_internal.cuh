@@ -68,11 +68,13 @@ inline int auto_hub_threshold(int64_t entries) {
   while (h < 256 && (int64_t)(2 * h) * 70000 <= entries) h *= 2;
   return h;
 }
-// Rows of medium degree per warp in the warp-per-vertex region.  Small and
-// mid-size graphs finish a launch in one or two waves of short rows, and
-// packing the rows below 128 entries four to a warp (8 lanes each) shortens
-// the launch; large graphs are request-rate bound and keep a warp per row.
-inline int auto_vertices_per_warp(int64_t entries) { return entries <= 2000000 ? 4 : 1; }
+// Rows of medium degree per warp in the warp-per-vertex region by default: a
+// whole warp per row.  Sharing a warp among rows (8 lanes each) measured
+// faster only with a low hub threshold on some graphs (a random
+// 200,000-vertex graph with hubs: 11.0 against 12.0 us per step), slower or
+// equal on the exact kNN graphs of 70,000 and 1.4e6 points, so it is left to
+// the autotuner.
+inline int auto_vertices_per_warp(int64_t) { return 1; }
 constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
 constexpr int kResidentSmem = 200 * 1024;  // shared memory of the resident whole-run kernel
 
