@@ -117,7 +117,12 @@ typedef struct {
                              positions, updated through distributed shared memory;
                              1: a single block; 0 (default): the cluster for graphs of at
                              most 40,000 stored entries, where it is faster, else one
-                             launch per step; -1: always one launch per step */
+                             launch per step; -1: always one launch per step;
+                             3: a persistent cooperative grid of any size (FP32 gathers,
+                             no adaptive b, else IVHD_ERR_ARG): every block stays
+                             resident for the whole call and the steps are separated by
+                             a grid barrier with a bounded wait (IVHD_ERR_TIMEOUT if it
+                             expires); ivhd_step then synchronises */
     int32_t vertices_per_warp; /* warp-per-vertex rows of medium degree processed several
                              to a warp: 1, 2, 4 or 8 rows per warp, each on 32 / that many
                              lanes, for the rows below 512 / that many entries (longer rows
@@ -602,6 +607,15 @@ ivhd_status ivhd_set_allocator(ivhd_alloc_fn alloc_fn, ivhd_free_fn free_fn, voi
  * released, to check that every error path frees what it took.  Process-wide.
  */
 ivhd_status ivhd_probe_wait_timeout(int32_t polls, void *stream);
+
+/*
+ * ivhd_probe_grid_barrier_timeout runs the persistent grid's barrier in a
+ * cooperative launch of two blocks of which only one arrives, with a limit of
+ * `polls` polls; returns IVHD_ERR_TIMEOUT (the expected result) without
+ * faulting or hanging, after which the library and the stream remain usable.
+ * polls >= 1, else IVHD_ERR_ARG.  Synchronises.
+ */
+ivhd_status ivhd_probe_grid_barrier_timeout(int32_t polls, void *stream);
 
 /*
  * Checked builds (the library compiled with IVHD_CHECKED: build_lib with

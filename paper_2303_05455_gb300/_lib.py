@@ -28,7 +28,7 @@ SYMBOLS = (
     "ivhd_mlp_set_params", "ivhd_mlp_get_params", "ivhd_mlp_loss_grad", "ivhd_mlp_train_step",
     "ivhd_mlp_forward", "ivhd_mlp_launches", "ivhd_probe_wait_timeout", "ivhd_test_fail_alloc",
     "ivhd_test_live_allocs", "ivhd_set_allocator", "ivhd_knn_query", "ivhd_place_nn",
-    "ivhd_check_violations", "ivhd_test_corrupt_layout",
+    "ivhd_check_violations", "ivhd_test_corrupt_layout", "ivhd_probe_grid_barrier_timeout",
 )
 
 # callback types of ivhd_set_allocator
@@ -135,6 +135,8 @@ def load(build_if_missing: bool = False):
     L.ivhd_place_nn.restype = i32
     L.ivhd_probe_wait_timeout.argtypes = [i32, P]
     L.ivhd_probe_wait_timeout.restype = i32
+    L.ivhd_probe_grid_barrier_timeout.argtypes = [i32, P]
+    L.ivhd_probe_grid_barrier_timeout.restype = i32
     L.ivhd_test_fail_alloc.argtypes = [i64]
     L.ivhd_test_fail_alloc.restype = None
     L.ivhd_test_live_allocs.argtypes = []

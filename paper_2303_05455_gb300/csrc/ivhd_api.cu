@@ -151,7 +151,8 @@ bool params_ok(const ivhd_params& p) {
   if (p.adaptive != 0 && p.adaptive != 1) return false;
   if (p.block_size != 0 && p.block_size != 128 && p.block_size != 256 && p.block_size != 512)
     return false;
-  if (p.resident < -1 || p.resident > 2) return false;
+  if (p.resident < -1 || p.resident > 3) return false;
+  if (p.resident == 3 && (p.adaptive || p.pos_format != IVHD_POS_F32)) return false;
   if (p.vertices_per_warp != 0 && p.vertices_per_warp != 1 && p.vertices_per_warp != 2 &&
       p.vertices_per_warp != 4 && p.vertices_per_warp != 8)
     return false;
@@ -194,7 +195,7 @@ void free_ctx(ivhd_ctx* ctx) {
   void* bufs[] = {ctx->knn, ctx->knn_full, ctx->rn, ctx->perm, ctx->inv, ctx->y[0], ctx->y[1],
                   ctx->yh[0], ctx->yh[1], ctx->vbuf[0], ctx->vbuf[1], ctx->s2, ctx->ctl,
                   ctx->red_out, ctx->flag, ctx->seg_of, ctx->seg_lo, ctx->seg_n, ctx->seg_r,
-                  ctx->seg_seed};
+                  ctx->seg_seed, ctx->gbar};
   for (void* b : bufs)
     if (b) dev_free(b, s);
   drop_graphs(ctx);
@@ -525,9 +526,19 @@ ivhd_status ivhd_step(ivhd_ctx* ctx, int64_t n_iter) {
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaSuccess;
   if (n_iter > 0 && !ctx->ctl && resident_mode(ctx) > 0) {
-    // the whole call in one single-block launch (state in shared memory)
+    // the whole call in one launch: one block or a cluster with the state in
+    // shared memory, or the persistent grid (which is waited for here)
     e = launch_resident(ctx, n_iter, s);
     if (e != cudaSuccess) return fail(ctx, e);
+    if (resident_mode(ctx) == 4) {
+      bool timed_out = false;
+      e = grid_timed_out(ctx, &timed_out);
+      if (e != cudaSuccess) return fail(ctx, e);
+      if (timed_out) {
+        ctx->poisoned = true;  // the steps stopped part-way
+        return IVHD_ERR_TIMEOUT;
+      }
+    }
     if (n_iter & 1) ctx->cur ^= 1;
     ctx->launches += 1;
     ctx->steps_done += n_iter;

@@ -204,6 +204,7 @@ struct ivhd_ctx {
   double* red_out = nullptr;
   int32_t* flag = nullptr;
   int64_t n_partials = 0;
+  unsigned char* gbar = nullptr;  // persistent grid: barrier (8 bytes) + error flag (4 bytes)
 
   // CUDA graphs of kGraphSteps steps, per metric and starting parity
   cudaGraphExec_t graph_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -226,6 +227,9 @@ cudaError_t launch_step(ivhd_ctx* ctx, int cur, cudaStream_t s);
 // embeddings whose state fits one SM (resident_mode > 0).
 int resident_mode(const ivhd_ctx* ctx);
 cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s);
+// After a persistent-grid launch: waits for it and reports whether a grid
+// barrier gave up (bounded wait expired).
+cudaError_t grid_timed_out(ivhd_ctx* ctx, bool* timed_out);
 cudaError_t launch_forces(ivhd_ctx* ctx, float2* out_input_order);
 cudaError_t launch_stress(ivhd_ctx* ctx);  // result in ctx->red_out[0], flag in ctx->flag
 cudaError_t launch_unpermute(ivhd_ctx* ctx, float2* out_input_order);

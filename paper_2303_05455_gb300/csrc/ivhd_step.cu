@@ -34,6 +34,15 @@
 
 namespace ivhd {
 
+// FP32 positions read through L2 only (ld.global.cg): the persistent kernel
+// rereads position arrays that other blocks rewrote during the same launch,
+// which the read-only (non-coherent) path may not observe.  Internal format.
+constexpr int kPosF32Coherent = 3;
+template <int POS>
+constexpr bool f32_pos() {
+  return POS == IVHD_POS_F32 || POS == kPosF32Coherent;
+}
+
 // Position of vertex idx as the neighbours see it: the FP32 array, or the
 // rounded FP16 / BF16 copy (one 32-bit word per vertex).
 template <int POS>
@@ -41,6 +50,8 @@ __device__ __forceinline__ float2 load_pos(const float2* __restrict__ y,
                                            const uint32_t* __restrict__ yh, uint32_t idx) {
   if constexpr (POS == IVHD_POS_F32) {
     return __ldg(y + idx);
+  } else if constexpr (POS == kPosF32Coherent) {
+    return __ldcg(y + idx);
   } else {
     const uint32_t w = __ldg(yh + idx);
     if constexpr (POS == IVHD_POS_F16) {
@@ -153,6 +164,8 @@ __device__ __forceinline__ float2 gather(const Gsrc& G, uint32_t e, float2 self)
     if (e == kPad || !index_ok(e & kIdxMask, G.M)) return self;
     const uint32_t idx = e & kIdxMask;
     return (idx < kL1HotF32) ? __ldg(G.y + idx) : load_f32_no_l1(G.y, idx, G.keep);
+  } else if constexpr (POS == kPosF32Coherent) {
+    return (e == kPad || !index_ok(e & kIdxMask, G.M)) ? self : __ldcg(G.y + (e & kIdxMask));
   } else {
     return (e == kPad || !index_ok(e & kIdxMask, G.M)) ? self
                                                        : load_pos<POS>(G.y, G.yh, e & kIdxMask);
@@ -319,15 +332,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // MODE: optimiser epilogue (or forces / stress).  yi is the vertex's own
 // position in the gathered format (differences are taken between equally
 // rounded positions); ym is its FP32 master position.
-template <int MODE, int POS, int METRIC, bool ADAPT>
-__global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
+// One block's share of a step: block vb of the step grid (hub warps, then
+// SELL slices), reading positions y[cur] and writing y[cur ^ 1].  PDL: the
+// step is a programmatic dependent launch, whose successor may start once this
+// block's gathers are done.
+template <int MODE, int POS, int METRIC, bool ADAPT, bool PDL>
+__device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  // launched as a programmatic dependent of the previous step: wait until that
-  // grid has completed and its writes are visible before reading any state
-  // (a no-op for a launch without that attribute)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int cur = ADAPT ? A.ctl->cur : A.cur;
   uint64_t keep;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   const Gsrc G{A.y[cur], A.yh[cur], keep, (uint32_t)A.M};
@@ -338,10 +350,10 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
   int p = -1;
   bool own = false;
 
-  if ((int)blockIdx.x < A.nb_hub) {
+  if (vb < A.nb_hub) {
     // hub rows: a warp, or a group of mid_g lanes, per vertex; the lanes of a
     // row stride over its int4 groups, then sum their partial forces
-    const int w = (int)blockIdx.x * A.wpb + wib;
+    const int w = vb * A.wpb + wib;
     if (w < A.hub_warps) {
       const HubSlot h = hub_slot(w, lane, A.n_full, A.mid_g);
       const bool valid = h.row < A.n_hub;
@@ -349,8 +361,8 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       const int4* row = nullptr;
       if (valid) {
         p = h.row;
-        ym = G.y[p];
-        yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
+        ym = (POS == kPosF32Coherent) ? __ldcg(G.y + p) : G.y[p];
+        yi = f32_pos<POS>() ? ym : load_pos<POS>(G.y, G.yh, p);
         const int beg = A.hub_off[p], end = A.hub_off[p + 1];
         row = reinterpret_cast<const int4*>(A.ids + beg);
         ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
@@ -367,13 +379,13 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
     }
   } else {
     // SELL slice: one thread per vertex, one coalesced int4 per 4 neighbours
-    const int s = ((int)blockIdx.x - A.nb_hub) * A.wpb + wib;
+    const int s = (vb - A.nb_hub) * A.wpb + wib;
     if (s < A.n_slices) {
       p = A.n_hub + s * 32 + lane;
       const bool valid = p < A.M;
       if (valid) {
-        ym = G.y[p];
-        yi = (POS == IVHD_POS_F32) ? ym : load_pos<POS>(G.y, G.yh, p);
+        ym = (POS == kPosF32Coherent) ? __ldcg(G.y + p) : G.y[p];
+        yi = f32_pos<POS>() ? ym : load_pos<POS>(G.y, G.yh, p);
       }
       const int4* base = reinterpret_cast<const int4*>(A.ids + A.slice_off[s]) + lane;
       const int W = row_ok(A.slice_off[s], A.slice_off[s] + (int64_t)A.slice_w[s] * 128, A.n_slots)
@@ -392,7 +404,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
 
   // this block's gathers are done: the next step's grid may start launching
   // (its blocks wait for this grid's completion before reading anything)
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if constexpr (PDL) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   float2* __restrict__ y_out = A.y[cur ^ 1];
   uint32_t* __restrict__ yh_out = A.yh[cur ^ 1];
   const float2* __restrict__ v_in = A.v[ADAPT ? cur : 0];
@@ -406,7 +418,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       momentum_update(A.a, b, fx, fy, ym, v, vn, yn);
       v_out[p] = vn;
       y_out[p] = yn;
-      if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
+      if constexpr (!f32_pos<POS>()) yh_out[p] = round_pos<POS>(yn);
       if (ADAPT) {
         kin_new = fmaf(vn.y, vn.y, vn.x * vn.x);
         kin_old = fmaf(v.y, v.y, v.x * v.x);
@@ -419,7 +431,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       nesterov_update(A.a, b, fx, fy, ym, v, vn, zn);
       v_out[p] = vn;
       y_out[p] = zn;
-      if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(zn);
+      if constexpr (!f32_pos<POS>()) yh_out[p] = round_pos<POS>(zn);
       if (ADAPT) {
         kin_new = fmaf(vn.y, vn.y, vn.x * vn.x);
         kin_old = fmaf(v.y, v.y, v.x * v.x);
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
       v_out[p] = eg;
       A.s2[p] = ex;
       y_out[p] = yn;
-      if (POS != IVHD_POS_F32) yh_out[p] = round_pos<POS>(yn);
+      if constexpr (!f32_pos<POS>()) yh_out[p] = round_pos<POS>(yn);
     }
   } else if (MODE == kForces) {
     if (own) A.f_out[A.perm[p]] = make_float2(fx, fy);
@@ -442,16 +454,88 @@ __global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(co
     __shared__ double red[kMaxStepBlock / 32];
     if (own && !(isfinite(ym.x) && isfinite(ym.y))) atomicOr(A.flag, 1);
     const double t = block_sum(own ? (double)fx : 0.0, red);
-    if (threadIdx.x == 0) A.partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) A.partials[vb] = t;
   }
   if (ADAPT) {
     __shared__ float red2[kMaxStepBlock / 32];
     const double tn = (double)block_sum_f32(kin_new, red2);
     const double to = (double)block_sum_f32(kin_old, red2);
     if (threadIdx.x == 0) {
-      A.partials[2 * blockIdx.x] = tn;
-      A.partials[2 * blockIdx.x + 1] = to;
+      A.partials[2 * vb] = tn;
+      A.partials[2 * vb + 1] = to;
     }
+  }
+}
+
+template <int MODE, int POS, int METRIC, bool ADAPT>
+__global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
+  // launched as a programmatic dependent of the previous step: wait until that
+  // grid has completed and its writes are visible before reading any state
+  // (a no-op for a launch without that attribute)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int cur = ADAPT ? A.ctl->cur : A.cur;
+  step_block<MODE, POS, METRIC, ADAPT, true>(A, (int)blockIdx.x, cur);
+}
+
+// ---- persistent grid kernel ------------------------------------------------------
+//
+// All steps of an ivhd_step call in one cooperative launch: every block is
+// resident, takes the blocks vb = blockIdx.x, blockIdx.x + gridDim.x, ... of
+// the step grid (so each vertex is traversed exactly as by k_step, and the
+// positions agree with the multi-launch path bit for bit), and the steps are
+// separated by a grid barrier instead of kernel launches.  Positions are read
+// through L2 (they are rewritten by other blocks within the launch).  The
+// barrier waits a bounded number of polls; on expiry (or when another block
+// gave up) the block raises *err and the launch ends.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+constexpr unsigned kGridBarrierPolls = 1u << 22;  // x >= 64 ns: > 0.25 s, far above any step
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, int32_t* err, unsigned polls) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &bar->gen;
+    volatile int32_t* verr = err;
+    const unsigned g = *gen;  // the generation this barrier completes
+    __threadfence();          // this block's writes before its arrival
+    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it > polls || *verr) {
+          atomicOr(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();  // the other blocks' writes after the barrier
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Test support: block 0 waits at the barrier, block 1 never arrives.
+__global__ void k_probe_grid_barrier(GridBarrier* bar, int32_t* err, unsigned polls) {
+  if (blockIdx.x != 0) return;
+  grid_barrier(bar, err, polls);
+}
+
+template <int MODE, int METRIC>
+__global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS)
+    k_persist(const StepArgs A, int64_t n_iter, int n_vblocks, GridBarrier* bar, int32_t* err) {
+  int cur = A.cur;
+  for (int64_t it = 0; it < n_iter; ++it) {
+    for (int vb = (int)blockIdx.x; vb < n_vblocks; vb += (int)gridDim.x)
+      step_block<MODE, kPosF32Coherent, METRIC, false, false>(A, vb, cur);
+    if (!grid_barrier(bar, err, kGridBarrierPolls)) return;
+    cur ^= 1;
   }
 }
 
@@ -768,7 +852,7 @@ static size_t resident_bytes(const ivhd_ctx* ctx, bool with_ids) {
 }
 
 // 0: not eligible (adaptive b, half-precision gathers, or too large); 1: ids
-// read through L1; 2: ids in shared memory too.
+// read through L1; 2: ids in shared memory too; 4: persistent grid (resident = 3).
 // 3: thread-block cluster (resident = 2, or automatically for graphs of at
 // most kClusterAutoEntries stored entries, where it measured faster than one
 // launch per step: 2,000-4,000 vertices 2.0-2.5 us against 3.1-3.4 us per step;
@@ -776,6 +860,7 @@ static size_t resident_bytes(const ivhd_ctx* ctx, bool with_ids) {
 constexpr int64_t kClusterAutoEntries = 40000;
 int resident_mode(const ivhd_ctx* ctx) {
   if (ctx->p.resident < 0 || ctx->p.adaptive || ctx->p.pos_format != IVHD_POS_F32) return 0;
+  if (ctx->p.resident == 3) return 4;  // persistent grid: any size
   if (ctx->M > ((int64_t)1 << 20)) return 0;
   if (ctx->p.resident == 0)
     return (ctx->nnz_sym <= kClusterAutoEntries &&
@@ -825,9 +910,12 @@ static void hub_map(const ivhd_ctx* ctx, int32_t* n_full, int32_t* mid_g, int32_
   *warps = (int32_t)(full + (ctx->n_hub - full + v - 1) / v);
 }
 
+static cudaError_t launch_grid(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s);
+
 cudaError_t launch_resident(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s) {
   const int mode = resident_mode(ctx);
   if (mode == 0) return cudaErrorInvalidValue;
+  if (mode == 4) return launch_grid(ctx, n_iter, s);
   StepArgs A{};
   A.ids = ctx->ids;
   A.hub_off = ctx->hub_off;
@@ -1052,6 +1140,67 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   return A;
 }
 
+template <int MODE, int METRIC>
+static cudaError_t launch_persist(const StepArgs& A, int64_t n_iter, int n_vblocks,
+                                  GridBarrier* bar, int32_t* err, cudaStream_t s) {
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<MODE, METRIC>,
+                                                      A.wpb * 32, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // every block resident at once (a cooperative launch refuses more)
+  const int grid = n_vblocks < per_sm * sms ? n_vblocks : per_sm * sms;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)(A.wpb * 32));
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persist<MODE, METRIC>, A, n_iter, n_vblocks, bar, err);
+}
+
+// The whole call on the persistent grid; the barrier state (and its error
+// flag) are reset before the launch.
+static cudaError_t launch_grid(ivhd_ctx* ctx, int64_t n_iter, cudaStream_t s) {
+  if (!ctx->gbar) {
+    cudaError_t e = dev_alloc((void**)&ctx->gbar, 16, s);
+    if (e != cudaSuccess) return e;
+  }
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(ctx->gbar);
+  int32_t* err = reinterpret_cast<int32_t*>(ctx->gbar + 8);
+  cudaError_t e = cudaMemsetAsync(ctx->gbar, 0, 16, s);
+  if (e != cudaSuccess) return e;
+  const StepArgs A = make_args(ctx, ctx->cur);
+  const int nvb = step_grid(ctx);
+  const bool l1 = ctx->metric == IVHD_METRIC_L1;
+  switch (ctx->p.opt) {
+    case IVHD_OPT_NESTEROV:
+      return l1 ? launch_persist<kNesterov, IVHD_METRIC_L1>(A, n_iter, nvb, bar, err, s)
+                : launch_persist<kNesterov, IVHD_METRIC_L2>(A, n_iter, nvb, bar, err, s);
+    case IVHD_OPT_ADADELTA:
+      return l1 ? launch_persist<kAdadelta, IVHD_METRIC_L1>(A, n_iter, nvb, bar, err, s)
+                : launch_persist<kAdadelta, IVHD_METRIC_L2>(A, n_iter, nvb, bar, err, s);
+    default:
+      return l1 ? launch_persist<kMomentum, IVHD_METRIC_L1>(A, n_iter, nvb, bar, err, s)
+                : launch_persist<kMomentum, IVHD_METRIC_L2>(A, n_iter, nvb, bar, err, s);
+  }
+}
+
+cudaError_t grid_timed_out(ivhd_ctx* ctx, bool* timed_out) {
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->gbar + 8, sizeof(h), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  *timed_out = h != 0;
+  return e;
+}
+
 int step_grid(const ivhd_ctx* ctx) {
   const int wpb = ctx->block / 32;
   int32_t n_full, mid_g, warps;
@@ -1248,4 +1397,32 @@ extern "C" ivhd_status ivhd_test_corrupt_layout(ivhd_ctx* ctx, int64_t slot, uin
   (void)value;
   return IVHD_ERR_ARG;
 #endif
+}
+
+extern "C" ivhd_status ivhd_probe_grid_barrier_timeout(int32_t polls, void* stream) {
+  if (polls < 1) return IVHD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* buf = nullptr;
+  if (dev_alloc((void**)&buf, 16, s) != cudaSuccess) return IVHD_ERR_OOM;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 16, s);
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(buf);
+  int32_t* err = reinterpret_cast<int32_t*>(buf + 8);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_probe_grid_barrier, bar, err, (unsigned)polls);
+  }
+  int32_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s);
+  dev_free(buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  return h ? IVHD_ERR_TIMEOUT : IVHD_OK;
 }

@@ -80,8 +80,8 @@ class Embedding:
         p.tau, p.gamma1, p.gamma2 = tau, gamma1, gamma2
         p.block_size = int(block_size)
         # resident: None (automatic), False (one launch per step), True (one block),
-        # "cluster" (8-block cluster)
-        p.resident = {None: 0, False: -1, True: 1, "cluster": 2}[resident]
+        # "cluster" (8-block cluster), "grid" (persistent cooperative grid)
+        p.resident = {None: 0, False: -1, True: 1, "cluster": 2, "grid": 3}[resident]
         p.vertices_per_warp = int(vertices_per_warp)
         p.stream = self.stream.cuda_stream or None
         self.opt = opt

@@ -102,7 +102,7 @@ def test_create_rejects_bad_sizes(L, M, k, r, c):
     ("opt", 3), ("opt", -1), ("a", -0.1), ("a", 1.5), ("a", float("nan")), ("b", 0.0),
     ("b", float("inf")), ("rho", 1.0), ("rho", 0.0), ("eps", 0.0), ("hub_threshold", -1),
     ("hub_threshold", 70000), ("pos_format", 3), ("pos_format", -1), ("adaptive", 2),
-    ("block_size", 64), ("block_size", 1024), ("resident", 3), ("resident", -2),
+    ("block_size", 64), ("block_size", 1024), ("resident", 4), ("resident", -2),
     ("vertices_per_warp", 3), ("vertices_per_warp", 16), ("vertices_per_warp", -1),
 ])
 def test_create_rejects_bad_params(L, field, value):
@@ -164,6 +164,18 @@ def test_create_rejects_bad_adaptive_params(L, opt, field, value):
     knn = np.array([[1], [0], [0]], np.int32)
     st, h = _create(L, knn, 3, 1, 1, 0.1, p)
     assert st == -1 and not h.value
+
+
+def test_persistent_grid_needs_fp32_gathers_without_adaptive_b(L):
+    knn = np.array([[1], [0], [0]], np.int32)
+    for field, value in (("pos_format", 1), ("adaptive", 1)):
+        p = _lib.Params()
+        L.ivhd_default_params(ctypes.byref(p))
+        p.resident = 3
+        setattr(p, field, value)
+        st, h = _create(L, knn, 3, 1, 1, 0.1, p)
+        assert st == -1 and not h.value
+    assert L.ivhd_probe_grid_barrier_timeout(0, None) == -1
 
 
 def test_new_entry_points_reject_null(L):

@@ -43,6 +43,16 @@ def test_wait_timeout_returns_status_and_library_stays_usable(L):
     emb.close()
 
 
+def test_grid_barrier_timeout_returns_status_and_library_stays_usable(L):
+    s = torch.cuda.current_stream().cuda_stream
+    for polls in (1, 1000, 100000):
+        assert L.ivhd_probe_grid_barrier_timeout(polls, s) == -6
+    emb = ivhd.Embedding(synth.random_knn_graph(3000, 3, 2), r=1, c=0.1, seed=1, resident="grid")
+    emb.step(20)
+    assert np.all(np.isfinite(emb.positions(host=True)))
+    emb.close()
+
+
 def _each_failure(L, call, limit=400):
     """Runs call() with the n-th allocation failing, n = 0, 1, ... until call()
     completes without reaching the injected failure; returns that n."""

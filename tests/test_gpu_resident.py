@@ -30,7 +30,7 @@ GRAPHS = graphs()
 
 
 @pytest.mark.parametrize("vpw", [1, 4])
-@pytest.mark.parametrize("kind", [True, "cluster"])
+@pytest.mark.parametrize("kind", [True, "cluster", "grid"])
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 @pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
 @pytest.mark.parametrize("metric", ["l2", "l1"])
@@ -81,3 +81,20 @@ def test_resident_not_used_when_state_does_not_fit_or_not_asked():
     e.step(10)
     assert e.info()["kernel_launches"] == 20  # step kernel + controller per step
     e.close()
+
+
+@pytest.mark.parametrize("opt", ["momentum", "adadelta"])
+def test_persistent_grid_with_several_step_blocks_per_block(opt):
+    # 300,000 vertices: more step-grid blocks than resident blocks, so every
+    # resident block takes several; the positions must equal the multi-launch
+    # path bit for bit
+    knn = synth.random_knn_graph(300_000, 5, 8, hub_frac=0.02, n_hubs=300)
+    out = []
+    for resident in ("grid", False):
+        e = ivhd.Embedding(knn, r=1, c=0.01, opt=opt, b=0.001, seed=2, resident=resident)
+        e.step(3)
+        e.step(40)
+        out.append((e.positions(host=True), e.info()["kernel_launches"]))
+        e.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == 2 and out[1][1] == 43
