@@ -58,6 +58,7 @@ constexpr int kTN = 256;  // candidate columns per accumulator tile
 constexpr int kTStages = 4;
 constexpr int kEpiWarps = 8;  // two warpgroups: each reads one 128-column half of a tile
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
+constexpr int kMaxKnnSegments = 32;  // column segments of one kNN launch (short query sets)
 
 struct KnnSmem {
   static constexpr int a_bytes = kTM * kBK * 2;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_knn_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
              const float* __restrict__ nrm_f, const int32_t* __restrict__ nrm_i,
              const float* __restrict__ qnrm_f, const int32_t* __restrict__ qnrm_i, int Mq, int M,
-             int Kp, bool self, float eps_coef, int32_t* __restrict__ out_ids,
+             int Kp, bool self, int seg_tiles, float eps_coef, int32_t* __restrict__ out_ids,
              float* __restrict__ out_d, int32_t* __restrict__ err) {
   using D = typename std::conditional<U8, int32_t, float>::type;
   extern __shared__ unsigned char smem_raw[];
@@ -123,7 +124,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTM;
   const int nk = Kp / kBK;
-  const int n_tiles = (M + kTN - 1) / kTN;
+  // this CTA's column segment: tiles t0 .. t0 + n_tiles - 1 (blockIdx.y of gridDim.y)
+  const int all_tiles = (M + kTN - 1) / kTN;
+  const int t0 = (int)blockIdx.y * seg_tiles;
+  const int n_tiles = max(0, min(all_tiles - t0, seg_tiles));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTStages; ++s) {
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           unsigned char* sb = sa + KnnSmem::a_bytes;
           mbar_expect_tx(&full[s], KnnSmem::stage_bytes);
           tma_load_2d(sa, &map_a, kt * kBK, m0, &full[s]);
-          tma_load_2d(sb, &map_b, kt * kBK, t * kTN, &full[s]);
+          tma_load_2d(sb, &map_b, kt * kBK, (t0 + t) * kTN, &full[s]);
           *issued = (int)(g + 1);
         }
         if (!ok) break;
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     auto fetch = [&](int t) {
 #pragma unroll
       for (int e = 0; e < kPer; ++e) {
-        const int jc = t * kTN + half * kHalf + e * 32 + lane;
+        const int jc = (t0 + t) * kTN + half * kHalf + e * 32 + lane;
         if constexpr (U8)
           pn[e] = (jc < M) ? nrm_i[jc] : 0;
         else
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       __syncwarp();
       if (t + 1 < n_tiles) fetch(t + 1);
       const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTN + half * kHalf);
-      const int n0 = t * kTN + half * kHalf;
+      const int n0 = (t0 + t) * kTN + half * kHalf;
       for (int c0 = 0; c0 < kHalf && n0 + c0 < M; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(tbase + c0, v);
@@ -315,8 +319,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_arrive(&acc_empty[b]);
     }
     if (ok && i < Mq) {
-      // the row's list for this half: out_ids / out_key [(i * 2 + half) * L + q]
-      const int64_t o = ((int64_t)i * 2 + half) * L;
+      // the row's list for this segment and half:
+      // out_ids / out_key [((i * segments + segment) * 2 + half) * L + q]
+      const int64_t o = (((int64_t)i * gridDim.y + blockIdx.y) * 2 + half) * L;
 #pragma unroll
       for (int q = 0; q < L; ++q) {
         out_ids[o + q] = jl[q];
@@ -432,68 +437,67 @@ __device__ __forceinline__ void warp_sort(float& d, int& j, int lane) {
     for (int m = kk >> 1; m > 0; m >>= 1) cas(d, j, lane, m, (lane & kk) == 0);
 }
 
-// Warp per row: the two half-tile lists (32 candidates each, lane = entry)
-// are re-ranked by the exact FP32 chain, merged, and certified.  A half whose
-// list is full bounds every vertex it left out by its largest key tau_h
-// (d_ij >= tau_h - eps n_i); a half whose list is not full left nothing out.
-// Q: the Mq query rows (X itself for the kNN graph), X: the M base rows.
+// Warp per row: the row's n_lists candidate lists (two half-tile lists per
+// column segment, L candidates each) are re-ranked by the exact FP32 chain and
+// merged into the 32 best, 32 candidates (one or two lists) per pass, and the
+// row is certified.  A list that is full bounds every vertex it left out by
+// its largest key tau_h (d_ij >= tau_h - eps n_i); a list that is not full
+// left nothing out.
 template <int L>
 __global__ void k_rerank(const float* __restrict__ Q, int Mq, const float* __restrict__ X, int M,
-                         int N, int k, const int32_t* __restrict__ cand,
+                         int N, int k, int n_lists, const int32_t* __restrict__ cand,
                          const float* __restrict__ key, const float* __restrict__ qnrm,
                          const float* __restrict__ nrm, float eps_coef, int32_t* __restrict__ out,
                          int32_t* __restrict__ fb_rows, int32_t* __restrict__ n_fb,
                          int32_t* __restrict__ max_err_bits) {
-  static_assert(L == 16 || L == 32, "half lists of 16 or 32 entries");
-  constexpr int kHalves = 32 / L;  // halves that one warp pass covers (lane = entry)
+  static_assert(L == 16 || L == 32, "lists of 16 or 32 entries");
+  constexpr int kPer = 32 / L;  // lists per pass (lane = entry)
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= Mq) return;
   const float* xi = Q + i * N;
-  float dh[2 / kHalves];
-  int jh[2 / kHalves];
   float tau = __int_as_float(0x7f800000);
   float rel = 0.f;
-#pragma unroll
-  for (int pass = 0; pass < 2 / kHalves; ++pass) {
-    // L = 32: pass h reads half h; L = 16: one pass, lanes 0-15 half 0, 16-31 half 1
-    const int h = (L == 32) ? pass : (lane >> 4);
-    const int64_t o = (i * 2 + h) * L + (lane & (L - 1));
+  float d = __int_as_float(0x7f800000);  // the running 32 best, sorted across the lanes
+  int j = INT_MAX;
+  for (int pass = 0; pass < n_lists / kPer; ++pass) {
+    // L = 32: pass p reads list p; L = 16: lanes 0-15 list 2p, lanes 16-31 list 2p + 1
+    const int h = pass * kPer + ((L == 32) ? 0 : (lane >> 4));
+    const int64_t o = (i * n_lists + h) * L + (lane & (L - 1));
     const int j0 = cand[o];
     const float kj = key[o];
-    float d = __int_as_float(0x7f800000);
-    int j = INT_MAX;
+    float dc = __int_as_float(0x7f800000);
+    int jc = INT_MAX;
     if (j0 >= 0 && j0 < M) {
-      d = chain_dist(xi, X + (int64_t)j0 * N, N);
-      j = j0;
+      dc = chain_dist(xi, X + (int64_t)j0 * N, N);
+      jc = j0;
       // the approximate distance is the key plus eps n_j
-      rel = fmaxf(rel, fabsf(fmaf(eps_coef, nrm[j0], kj) - d) / fmaxf(qnrm[i] + nrm[j0], 1e-30f));
+      rel = fmaxf(rel, fabsf(fmaf(eps_coef, nrm[j0], kj) - dc) / fmaxf(qnrm[i] + nrm[j0], 1e-30f));
     }
 #pragma unroll
-    for (int hh = 0; hh < kHalves; ++hh) {
-      // the last entry of each half list present in this pass
+    for (int hh = 0; hh < kPer; ++hh) {
+      // the last entry of each list of this pass
       const int last = hh * L + L - 1;
       const int jlast = __shfl_sync(0xffffffffu, j0, last);
       const float klast = __shfl_sync(0xffffffffu, kj, last);
       if (jlast >= 0 && jlast < M) tau = fminf(tau, klast);
     }
-    warp_sort(d, j, lane);
-    dh[pass] = d;
-    jh[pass] = j;
-  }
-  float d = dh[0];
-  int j = jh[0];
-  if constexpr (L == 32) {
-    // merge: the 32 smallest of both sorted halves form a bitonic sequence
-    // (half 0 ascending against half 1 reversed); a bitonic merge sorts it
-    const float rd = __shfl_sync(0xffffffffu, dh[2 / kHalves - 1], 31 - lane);
-    const int rj = __shfl_sync(0xffffffffu, jh[2 / kHalves - 1], 31 - lane);
-    if (better(rd, rj, d, j)) {
-      d = rd;
-      j = rj;
-    }
+    warp_sort(dc, jc, lane);
+    if (pass == 0) {
+      d = dc;
+      j = jc;
+    } else {
+      // the 32 smallest of two sorted sequences: the running one against the
+      // new one reversed is bitonic, and a bitonic merge sorts it
+      const float rd = __shfl_sync(0xffffffffu, dc, 31 - lane);
+      const int rj = __shfl_sync(0xffffffffu, jc, 31 - lane);
+      if (better(rd, rj, d, j)) {
+        d = rd;
+        j = rj;
+      }
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) cas(d, j, lane, m, true);
+      for (int m = 16; m > 0; m >>= 1) cas(d, j, lane, m, true);
+    }
   }
   float mrel = rel;
 #pragma unroll
@@ -508,29 +512,35 @@ __global__ void k_rerank(const float* __restrict__ Q, int Mq, const float* __res
   if (lane == 0) atomicMax(max_err_bits, __float_as_int(mrel));
 }
 
-// uint8: the two exact half lists of each row (ascending by (distance, index))
+// uint8: the n_lists exact lists of each row (ascending by (distance, index))
 // merged into the k nearest.
 template <int L>
 __global__ void k_merge_u8(const int32_t* __restrict__ ids, const int32_t* __restrict__ keys,
-                           int64_t M, int k, int32_t* __restrict__ out) {
+                           int64_t M, int k, int n_lists, int32_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  const int32_t* ja = ids + i * 2 * L;
-  const int32_t* da = keys + i * 2 * L;
-  const int32_t* jb = ja + L;
-  const int32_t* db = da + L;
-  int a = 0, c = 0;
+  const int32_t* ja = ids + i * n_lists * L;
+  const int32_t* da = keys + i * n_lists * L;
+  int head[2 * kMaxKnnSegments];
+  for (int h = 0; h < n_lists; ++h) head[h] = 0;
   for (int q = 0; q < k; ++q) {
-    const bool take_a = c >= L || (a < L && better(da[a], ja[a], db[c], jb[c]));
-    out[i * k + q] = take_a ? ja[a++] : jb[c++];
+    int bh = -1;
+    for (int h = 0; h < n_lists; ++h) {
+      if (head[h] >= L) continue;
+      const int64_t a = (int64_t)h * L + head[h];
+      const int64_t b = (int64_t)bh * L + (bh < 0 ? 0 : head[bh]);
+      if (bh < 0 || better(da[a], ja[a], da[b], ja[b])) bh = h;
+    }
+    out[i * k + q] = ja[(int64_t)bh * L + head[bh]];
+    ++head[bh];
   }
 }
 
 template <bool U8, int L>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float* nrm_f,
                       const int32_t* nrm_i, const float* qnrm_f, const int32_t* qnrm_i, int Mq,
-                      int M, int Kp, bool self, float eps_coef, int32_t* out_ids, float* out_d,
-                      int32_t* err, cudaStream_t s) {
+                      int M, int Kp, bool self, int segments, int seg_tiles, float eps_coef,
+                      int32_t* out_ids, float* out_d, int32_t* err, cudaStream_t s) {
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -541,9 +551,10 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const float*
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  const unsigned grid = (unsigned)((Mq + kTM - 1) / kTM);
+  const dim3 grid((unsigned)((Mq + kTM - 1) / kTM), (unsigned)segments);
   k_knn_tc<U8, L><<<grid, kTcThreads, KnnSmem::total, s>>>(
-      ma, mb, nrm_f, nrm_i, qnrm_f, qnrm_i, Mq, M, Kp, self, eps_coef, out_ids, out_d, err);
+      ma, mb, nrm_f, nrm_i, qnrm_f, qnrm_i, Mq, M, Kp, self, seg_tiles, eps_coef, out_ids, out_d,
+      err);
   return cudaGetLastError();
 }
 
@@ -600,12 +611,29 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
   if (!make_map(&ma, A, Mq, Kp, Kp, kTM) || !make_map(&mb, B, M, Kp, Kp, kTN))
     return IVHD_ERR_CUDA;
   const float eps_coef = (float)(1.0 / 8192.0 + (double)N / 524288.0);
+  // Short query sets: the columns are split into segments (one CTA per row
+  // block and segment) so that the launch still covers every SM twice; a
+  // segment keeps at least 4 tiles of 256 columns.  Each segment yields its
+  // own lists, merged per row afterwards.
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return IVHD_ERR_CUDA;
+  const int64_t row_blocks = (Mq + kTM - 1) / kTM;
+  const int all_tiles = (int)((M + kTN - 1) / kTN);
+  int want = (int)((2 * (int64_t)sms + row_blocks - 1) / row_blocks);
+  want = want < all_tiles / 4 ? want : all_tiles / 4;
+  want = want < kMaxKnnSegments ? want : kMaxKnnSegments;
+  want = want > 1 ? want : 1;
+  const int seg_tiles = (all_tiles + want - 1) / want;
+  const int segs = (all_tiles + seg_tiles - 1) / seg_tiles;  // every segment has tiles
+  const int n_lists = 2 * segs;
   if (u8) {
     const int L = (k <= 8) ? 8 : kKnnList;
     int32_t* nrm = b.get<int32_t>(M);
     int32_t* qnrm = P.self ? nrm : b.get<int32_t>(Mq);
-    int32_t* lids = b.get<int32_t>(Mq * 2 * L);
-    int32_t* lkeys = b.get<int32_t>(Mq * 2 * L);
+    int32_t* lids = b.get<int32_t>(Mq * n_lists * L);
+    int32_t* lkeys = b.get<int32_t>(Mq * n_lists * L);
     if (!b.ok) return IVHD_ERR_OOM;
     if (e == cudaSuccess) {
       const uint8_t* X = (const uint8_t*)P.X;
@@ -617,24 +645,25 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
         k_norms_u8s<<<blocks(Mq), 256, 0, s>>>(Q, Mq, N, qnrm);
       }
       e = (L == 8) ? launch_tc<true, 8>(ma, mb, nullptr, nrm, nullptr, qnrm, (int)Mq, (int)M, Kp,
-                                        P.self, 0.f, lids, (float*)lkeys, err, s)
+                                        P.self, segs, seg_tiles, 0.f, lids, (float*)lkeys, err,
+                                        s)
                    : launch_tc<true, kKnnList>(ma, mb, nullptr, nrm, nullptr, qnrm, (int)Mq,
-                                               (int)M, Kp, P.self, 0.f, lids, (float*)lkeys, err,
-                                               s);
+                                               (int)M, Kp, P.self, segs, seg_tiles, 0.f, lids,
+                                               (float*)lkeys, err, s);
     }
     if (e == cudaSuccess) {
       if (L == 8)
-        k_merge_u8<8><<<blocks(Mq), 256, 0, s>>>(lids, lkeys, Mq, k, out_knn);
+        k_merge_u8<8><<<blocks(Mq), 256, 0, s>>>(lids, lkeys, Mq, k, n_lists, out_knn);
       else
-        k_merge_u8<kKnnList><<<blocks(Mq), 256, 0, s>>>(lids, lkeys, Mq, k, out_knn);
+        k_merge_u8<kKnnList><<<blocks(Mq), 256, 0, s>>>(lids, lkeys, Mq, k, n_lists, out_knn);
       e = cudaGetLastError();
     }
   } else {
     float* nrm = b.get<float>(M);
     float* qnrm = P.self ? nrm : b.get<float>(Mq);
     const int L = (k <= 8) ? 16 : kKnnList;  // candidates per row and half
-    int32_t* cand = b.get<int32_t>(Mq * 2 * L);
-    float* cd = b.get<float>(Mq * 2 * L);
+    int32_t* cand = b.get<int32_t>(Mq * n_lists * L);
+    float* cd = b.get<float>(Mq * n_lists * L);
     int32_t* fb = b.get<int32_t>(Mq);
     if (!b.ok) return IVHD_ERR_OOM;
     const float* X = (const float*)P.X;
@@ -649,18 +678,20 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
       }
       k_norms_f32<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
       e = (L == 16) ? launch_tc<false, 16>(ma, mb, nrm, nullptr, qnrm, nullptr, (int)Mq, (int)M,
-                                           Kp, P.self, eps_coef, cand, cd, err, s)
+                                           Kp, P.self, segs, seg_tiles, eps_coef, cand, cd, err, s)
                     : launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, qnrm, nullptr, (int)Mq,
-                                                 (int)M, Kp, P.self, eps_coef, cand, cd, err, s);
+                                                 (int)M, Kp, P.self, segs, seg_tiles, eps_coef,
+                                                 cand, cd, err, s);
     }
     if (e == cudaSuccess) {
       const unsigned g8 = (unsigned)((Mq + 7) / 8);
       if (L == 16)
-        k_rerank<16><<<g8, 256, 0, s>>>(Q, (int)Mq, X, (int)M, N, k, cand, cd, qnrm, nrm,
-                                        eps_coef, out_knn, fb, n_fb, maxerr_bits);
+        k_rerank<16><<<g8, 256, 0, s>>>(Q, (int)Mq, X, (int)M, N, k, n_lists, cand, cd, qnrm,
+                                        nrm, eps_coef, out_knn, fb, n_fb, maxerr_bits);
       else
-        k_rerank<kKnnList><<<g8, 256, 0, s>>>(Q, (int)Mq, X, (int)M, N, k, cand, cd, qnrm, nrm,
-                                              eps_coef, out_knn, fb, n_fb, maxerr_bits);
+        k_rerank<kKnnList><<<g8, 256, 0, s>>>(Q, (int)Mq, X, (int)M, N, k, n_lists, cand, cd,
+                                              qnrm, nrm, eps_coef, out_knn, fb, n_fb,
+                                              maxerr_bits);
       e = cudaGetLastError();
     }
     // rows without a certificate: the exact CUDA-core kernel on just those rows

@@ -35,7 +35,8 @@ def test_knn_f32_methods_bit_exact(method, M, N, k):
 
 
 @pytest.mark.parametrize("method", ["tensor_cores", "cuda_cores"])
-@pytest.mark.parametrize("M,N,k", [(300, 64, 5), (1500, 784, 5), (600, 100, 32), (513, 1024, 3)])
+@pytest.mark.parametrize("M,N,k", [(300, 64, 5), (1500, 784, 5), (600, 100, 32), (513, 1024, 3),
+                                   (3000, 64, 12)])
 def test_knn_u8_methods_bit_exact(method, M, N, k):
     X, _ = synth.mnist_like(M, 3, N=N)
     got, st = ivhd.knn_build(torch.from_numpy(X).cuda(), k, method=method, return_stats=True)

@@ -66,6 +66,21 @@ def test_query_equal_to_base_rows_and_ties(dtype):
         assert np.array_equal(got.cpu().numpy(), ref), method
 
 
+@pytest.mark.parametrize("k", [1, 8, 32])
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_short_query_set_split_into_column_segments(dtype, k):
+    # 64 queries against 40,000 base rows: one row block, so the columns are
+    # split into 32 segments whose lists are merged per row
+    if dtype == "f32":
+        Q, X = split_gmm(64, 40_000, 24, 3)
+    else:
+        Z, _ = synth.mnist_like(40_064, 9, N=96)
+        Q, X = Z[:64], Z[64:]
+    got = ivhd.knn_query(torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda(), k,
+                         method="tensor_cores")
+    assert np.array_equal(got.cpu().numpy(), oracle.knn_query(Q, X, k))
+
+
 def test_query_uncertified_rows_are_recomputed():
     Q, X = split_gmm(500, 1200, 20, 5, offset=3000.0)
     got, st = ivhd.knn_query(torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda(), 5,
