@@ -41,6 +41,7 @@
 //                      registers
 // Every wait is bounded; a timeout sets an error flag and all roles stop.
 #include <climits>
+#include <cstdint>
 #include <cstring>
 #include <type_traits>
 
@@ -612,19 +613,26 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
     return IVHD_ERR_CUDA;
   const float eps_coef = (float)(1.0 / 8192.0 + (double)N / 524288.0);
   // Short query sets: the columns are split into segments (one CTA per row
-  // block and segment) so that the launch still covers every SM twice; a
-  // segment keeps at least 4 tiles of 256 columns.  Each segment yields its
-  // own lists, merged per row afterwards.
+  // block and segment, one CTA per SM at a time), choosing the count that
+  // minimises waves x (tiles per segment + a fixed cost of about two tiles per
+  // CTA); a segment keeps at least 4 tiles of 256 columns.  Each segment
+  // yields its own lists, merged per row afterwards.
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return IVHD_ERR_CUDA;
   const int64_t row_blocks = (Mq + kTM - 1) / kTM;
   const int all_tiles = (int)((M + kTN - 1) / kTN);
-  int want = (int)((2 * (int64_t)sms + row_blocks - 1) / row_blocks);
-  want = want < all_tiles / 4 ? want : all_tiles / 4;
-  want = want < kMaxKnnSegments ? want : kMaxKnnSegments;
-  want = want > 1 ? want : 1;
+  int want = 1;
+  int64_t best_cost = INT64_MAX;
+  for (int S = 1; S <= kMaxKnnSegments && (S == 1 || all_tiles / S >= 4); ++S) {
+    const int64_t waves = (row_blocks * S + sms - 1) / sms;
+    const int64_t cost = waves * ((all_tiles + S - 1) / S + 2);
+    if (cost < best_cost) {
+      best_cost = cost;
+      want = S;
+    }
+  }
   const int seg_tiles = (all_tiles + want - 1) / want;
   const int segs = (all_tiles + seg_tiles - 1) / seg_tiles;  // every segment has tiles
   const int n_lists = 2 * segs;
