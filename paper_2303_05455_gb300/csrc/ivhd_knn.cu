@@ -16,6 +16,9 @@
 // point at the mean embedding of its base neighbours: with k = 1 the
 // Progressive UMAP initialisation of a new point (Sec. 2.4.3), the comparator
 // of the learned placement.
+#include <algorithm>
+#include <climits>
+
 #include "ivhd_internal.cuh"
 #include "ivhd_knn_tc.cuh"
 
@@ -26,6 +29,7 @@ constexpr int kTQ = 128;     // queries per CTA
 constexpr int kTC = 128;     // candidates per tile
 constexpr int kDK = 32;      // feature chunk (floats) / 4-byte words (uint8)
 constexpr int kThreads = 256;
+constexpr int kMaxExactSegments = 256;  // column segments of the exact kernel for few rows
 constexpr int kDStride = kTC + 4;  // distance-tile row stride (floats)
 
 struct SmemLayout {
@@ -67,10 +71,15 @@ __device__ __forceinline__ void merge_row(const D* row, int c0, int64_t M, int64
 // Queries: the Mq rows of Q (Q = X and self = true for the kNN graph).
 // rows / n_rows (device, optional): the CTA's queries are entries q0 .. q0+127
 // of the list rows[0 .. *n_rows) instead of rows q0 .. q0+127.
+// Column segments (gridDim.y > 1): CTA (x, y) sweeps candidates
+// [y * seg_cols, (y + 1) * seg_cols) only and writes its sorted list of the
+// k best (padded with (+inf, INT_MAX)) for list entry t to
+// seg_d / seg_j[(t * gridDim.y + y) * k ..]; k_merge_segments combines them.
 __global__ void __launch_bounds__(kThreads)
     k_knn_f32(const float* __restrict__ Q, int64_t Mq, const float* __restrict__ X, int64_t M,
               int N, int k, bool self, int32_t* __restrict__ out,
-              const int32_t* __restrict__ rows, const int32_t* __restrict__ n_rows) {
+              const int32_t* __restrict__ rows, const int32_t* __restrict__ n_rows,
+              int64_t seg_cols, float* __restrict__ seg_d, int32_t* __restrict__ seg_j) {
   extern __shared__ __align__(16) unsigned char smem[];
   float* Qs = reinterpret_cast<float*>(smem);                    // [kDK][kTQ + 4]
   float* Cs = Qs + kDK * (kTQ + 4);                              // [kDK][kTC + 4]
@@ -85,8 +94,10 @@ __global__ void __launch_bounds__(kThreads)
   if (q0 >= nq) return;
   auto qrow = [&](int64_t t) -> int64_t { return rows ? (int64_t)rows[t] : t; };
   int nlist = 0;  // used by threads tid < kTQ
+  const int64_t c_beg = (int64_t)blockIdx.y * seg_cols;
+  const int64_t c_end = min(M, c_beg + seg_cols);
 
-  for (int64_t c0 = 0; c0 < M; c0 += kTC) {
+  for (int64_t c0 = c_beg; c0 < c_end; c0 += kTC) {
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(kThreads)
         const int64_t tq = q0 + row, gc = c0 + row;
         const int d = d0 + dd;
         Qs[dd * (kTQ + 4) + row] = (tq < nq && d < N) ? Q[qrow(tq) * N + d] : 0.f;
-        Cs[dd * (kTC + 4) + row] = (gc < M && d < N) ? X[gc * N + d] : 0.f;
+        Cs[dd * (kTC + 4) + row] = (gc < c_end && d < N) ? X[gc * N + d] : 0.f;
       }
       __syncthreads();
       const int dn = min(kDK, N - d0);
@@ -127,12 +138,49 @@ __global__ void __launch_bounds__(kThreads)
       for (int b = 0; b < 8; ++b) Dt[(ty * 8 + a) * kDStride + tx * 8 + b] = acc[a][b];
     __syncthreads();
     if (tid < kTQ && q0 + tid < nq)
-      merge_row<float>(Dt + tid * kDStride, (int)c0, M, self ? qrow(q0 + tid) : -1, k,
+      merge_row<float>(Dt + tid * kDStride, (int)c0, c_end, self ? qrow(q0 + tid) : -1, k,
                        Ld + tid * k, Lj + tid * k, nlist);
     __syncthreads();
   }
-  if (tid < kTQ && q0 + tid < nq)
-    for (int s = 0; s < k; ++s) out[qrow(q0 + tid) * k + s] = Lj[tid * k + s];
+  if (tid < kTQ && q0 + tid < nq) {
+    if (gridDim.y == 1) {
+      for (int s = 0; s < k; ++s) out[qrow(q0 + tid) * k + s] = Lj[tid * k + s];
+    } else {
+      const int64_t o = ((q0 + tid) * gridDim.y + blockIdx.y) * k;
+      for (int s = 0; s < k; ++s) {
+        seg_d[o + s] = s < nlist ? Ld[tid * k + s] : __int_as_float(0x7f800000);
+        seg_j[o + s] = s < nlist ? Lj[tid * k + s] : INT_MAX;
+      }
+    }
+  }
+}
+
+// The per-segment lists of list entry t (n_seg sorted lists of k) merged into
+// the k best, ties to the lower index.
+__global__ void k_merge_segments(const float* __restrict__ seg_d, const int32_t* __restrict__ seg_j,
+                                 int n_seg, int k, const int32_t* __restrict__ rows,
+                                 const int32_t* __restrict__ n_rows, int32_t* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *n_rows) return;
+  const float* d = seg_d + t * n_seg * k;
+  const int32_t* j = seg_j + t * n_seg * k;
+  int head[kMaxExactSegments];
+  for (int h = 0; h < n_seg; ++h) head[h] = 0;
+  for (int q = 0; q < k; ++q) {
+    int bh = -1;
+    for (int h = 0; h < n_seg; ++h) {
+      if (head[h] >= k) continue;
+      const int64_t a = (int64_t)h * k + head[h];
+      if (bh < 0) {
+        bh = h;
+        continue;
+      }
+      const int64_t b = (int64_t)bh * k + head[bh];
+      if (better(d[a], j[a], d[b], j[b])) bh = h;
+    }
+    out[(int64_t)rows[t] * k + q] = j[(int64_t)bh * k + head[bh]];
+    ++head[bh];
+  }
 }
 
 __global__ void k_norms_u8(const uint8_t* __restrict__ X, int64_t M, int N,
@@ -253,10 +301,51 @@ cudaError_t knn_exact_rows_f32(const KnnProblem& P, const int32_t* rows, const i
   cudaError_t e = cudaFuncSetAttribute(k_knn_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sm);
   if (e != cudaSuccess) return e;
-  // one CTA per 128 possible rows; CTAs past *n_rows return at once
-  k_knn_f32<<<(unsigned)((P.Mq + kTQ - 1) / kTQ), kThreads, sm, s>>>(
-      (const float*)P.Q, P.Mq, (const float*)P.X, P.M, P.N, P.k, P.self, out_knn, rows, n_rows);
-  return cudaGetLastError();
+  const float* Q = (const float*)P.Q;
+  const float* X = (const float*)P.X;
+  if (!rows) {
+    k_knn_f32<<<(unsigned)((P.Mq + kTQ - 1) / kTQ), kThreads, sm, s>>>(
+        Q, P.Mq, X, P.M, P.N, P.k, P.self, out_knn, nullptr, nullptr, P.M, nullptr, nullptr);
+    return cudaGetLastError();
+  }
+  // a row list (rows the tensor-core certificate did not cover): usually a
+  // few rows, so the candidates are split into column segments that run in
+  // parallel (about two CTAs per SM in all), merged per row afterwards
+  int32_t n = 0;
+  e = cudaMemcpyAsync(&n, n_rows, sizeof(n), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || n == 0) return e;
+  int sms = 0, dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int64_t row_blocks = (n + kTQ - 1) / kTQ;
+  int64_t want = (2 * (int64_t)sms + row_blocks - 1) / row_blocks;
+  want = std::min<int64_t>(want, std::min<int64_t>(kMaxExactSegments, P.M / 2048));
+  want = std::max<int64_t>(want, 1);
+  const int64_t seg_cols = ((P.M + want - 1) / want + kTC - 1) / kTC * kTC;
+  const int64_t n_seg = (P.M + seg_cols - 1) / seg_cols;
+  if (n_seg == 1) {
+    k_knn_f32<<<(unsigned)row_blocks, kThreads, sm, s>>>(Q, P.Mq, X, P.M, P.N, P.k, P.self,
+                                                          out_knn, rows, n_rows, P.M, nullptr,
+                                                          nullptr);
+    return cudaGetLastError();
+  }
+  float* seg_d = nullptr;
+  int32_t* seg_j = nullptr;
+  const size_t len = (size_t)n * (size_t)n_seg * (size_t)P.k;
+  e = dev_alloc((void**)&seg_d, len * sizeof(float), s);
+  if (e == cudaSuccess) e = dev_alloc((void**)&seg_j, len * sizeof(int32_t), s);
+  if (e == cudaSuccess) {
+    k_knn_f32<<<dim3((unsigned)row_blocks, (unsigned)n_seg), kThreads, sm, s>>>(
+        Q, P.Mq, X, P.M, P.N, P.k, P.self, out_knn, rows, n_rows, seg_cols, seg_d, seg_j);
+    k_merge_segments<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(seg_d, seg_j, (int)n_seg, P.k,
+                                                                 rows, n_rows, out_knn);
+    e = cudaGetLastError();
+  }
+  dev_free(seg_d, s);
+  dev_free(seg_j, s);
+  return e;
 }
 
 // The CUDA-core build of every query row (k <= 64).

@@ -77,3 +77,13 @@ def test_knn_auto_picks_tensor_cores_and_rejects_out_of_range():
     Xu = torch.from_numpy(synth.mnist_like(300, 1, N=1100)[0]).cuda()
     _, st = ivhd.knn_build(Xu, 5, return_stats=True)    # N > 1024: sums could leave FP32's exact range
     assert st["method"] == "cuda_cores"
+
+
+def test_uncertified_rows_in_column_segments():
+    # 12,000 points with a large common offset: many rows fail the certificate
+    # and the exact kernel sweeps their candidates in parallel column segments
+    X = gmm(12_000, 20, 8, offset=3000.0)
+    got, st = ivhd.knn_build(torch.from_numpy(X).cuda(), 5, method="tensor_cores",
+                             return_stats=True)
+    assert st["fallback_rows"] > 100
+    assert np.array_equal(got.cpu().numpy(), oracle.knn_f32(X, 5))

@@ -89,6 +89,14 @@ def test_query_uncertified_rows_are_recomputed():
     assert np.array_equal(got.cpu().numpy(), oracle.knn_query(Q, X, 5))
 
 
+def test_query_uncertified_rows_in_column_segments():
+    Q, X = split_gmm(300, 20_000, 20, 6, offset=3000.0)
+    got, st = ivhd.knn_query(torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda(), 7,
+                             method="tensor_cores", return_stats=True)
+    assert st["fallback_rows"] > 10
+    assert np.array_equal(got.cpu().numpy(), oracle.knn_query(Q, X, 7))
+
+
 def test_query_edge_sizes_and_errors():
     Q, X = split_gmm(40, 64, 16, 2)
     Qd, Xd = torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda()
