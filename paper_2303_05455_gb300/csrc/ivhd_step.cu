@@ -25,8 +25,17 @@
 //           reports its kinetic-energy sums for the controller kernel.
 //
 // Work split: SELL slices of 32 degree-sorted vertices, one thread per vertex
-// and one coalesced int4 id load per 4 neighbours; vertices of very high
-// degree ("hubs") get a warp each and a fixed-order butterfly reduction.
+// and one coalesced int4 id load per 4 neighbours; vertices of high degree
+// ("hubs") get a warp each (or, with several vertices per warp, a group of
+// 32 / vpw lanes for the rows of medium degree) and a fixed-order butterfly
+// reduction.
+//
+// Launch forms, all with the same per-vertex traversal and arithmetic, so
+// their results agree bit for bit: one k_step launch per step (dependent
+// launches replayed from CUDA graphs; the default), or all steps of a call in
+// one launch -- k_cluster (8-block cluster, positions in every block's shared
+// memory, small embeddings), k_resident (one block), k_persist (cooperative
+// grid with a bounded grid barrier per step).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
