@@ -417,6 +417,30 @@ ivhd_status ivhd_knn_query(const void *Q, int64_t Mq, const void *X, int64_t M, 
                            ivhd_knn_stats_t *stats, void *stream);
 
 /*
+ * ivhd_knn_index_* -- a base set held for repeated ivhd_knn_query calls
+ * (arriving batches of new points against the same embedded data).
+ *
+ * ivhd_knn_index_create copies X (device, M*N elements of `dtype`, rows as in
+ * ivhd_knn_query) and, where the tensor-core method applies (M >= 2, uint8
+ * N <= 1024 or float 3N <= 65536), prepares its GEMM operand and row norms
+ * once (BF16, about M * 2 * N (uint8) or M * 6 * N (float) bytes besides the
+ * copy).  Work runs on `stream`; synchronises.  Arguments as ivhd_knn_query
+ * (k = 1 for the checks), else IVHD_ERR_ARG; IVHD_ERR_OOM.
+ *
+ * ivhd_knn_index_query: ivhd_knn_query(Q, Mq, X, M, dtype, N, k, out,
+ * method, stats) on the index's stream, bit for bit the same lists, without
+ * preparing the base set again.  Synchronises.
+ *
+ * ivhd_knn_index_destroy frees the index (stream-ordered); NULL is a no-op.
+ */
+typedef struct ivhd_knn_index ivhd_knn_index;
+ivhd_status ivhd_knn_index_create(const void *X, int32_t dtype, int64_t M, int32_t N,
+                                  void *stream, ivhd_knn_index **out);
+ivhd_status ivhd_knn_index_query(ivhd_knn_index *idx, const void *Q, int64_t Mq, int32_t k,
+                                 int32_t *out, int32_t method, ivhd_knn_stats_t *stats);
+void ivhd_knn_index_destroy(ivhd_knn_index *idx);
+
+/*
  * ivhd_place_nn -- place new points at the mean embedding of base neighbours.
  *
  * out[q] = (1/k) sum_s Y[ids[q][s]], the sum taken in FP32 in the order

@@ -29,6 +29,7 @@ SYMBOLS = (
     "ivhd_mlp_forward", "ivhd_mlp_launches", "ivhd_probe_wait_timeout", "ivhd_test_fail_alloc",
     "ivhd_test_live_allocs", "ivhd_set_allocator", "ivhd_knn_query", "ivhd_place_nn",
     "ivhd_check_violations", "ivhd_test_corrupt_layout", "ivhd_probe_grid_barrier_timeout",
+    "ivhd_knn_index_create", "ivhd_knn_index_query", "ivhd_knn_index_destroy",
 )
 
 # callback types of ivhd_set_allocator
@@ -131,6 +132,12 @@ def load(build_if_missing: bool = False):
     L.ivhd_test_corrupt_layout.restype = i32
     L.ivhd_knn_query.argtypes = [P, i64, P, i64, i32, i32, i32, P, i32, P, P]
     L.ivhd_knn_query.restype = i32
+    L.ivhd_knn_index_create.argtypes = [P, i32, i64, i32, P, ctypes.POINTER(P)]
+    L.ivhd_knn_index_create.restype = i32
+    L.ivhd_knn_index_query.argtypes = [P, P, i64, i32, P, i32, P]
+    L.ivhd_knn_index_query.restype = i32
+    L.ivhd_knn_index_destroy.argtypes = [P]
+    L.ivhd_knn_index_destroy.restype = None
     L.ivhd_place_nn.argtypes = [P, i64, P, i64, i32, P, P]
     L.ivhd_place_nn.restype = i32
     L.ivhd_probe_wait_timeout.argtypes = [i32, P]

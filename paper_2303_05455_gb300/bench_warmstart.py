@@ -106,8 +106,13 @@ def main():
     knn_h = ivhd.knn_build(Xh_d, k)
     torch.cuda.synchronize()
     out["holdout_knn_seconds_untimed"] = time.perf_counter() - t
+    # the training set held as a kNN index (copied and prepared once)
+    t = time.perf_counter()
+    index = ivhd.KnnIndex(Xtr_d)
+    torch.cuda.synchronize()
+    index_s = time.perf_counter() - t
     e0 = ev()
-    nn_h = ivhd.knn_query(Xh_d, Xtr_d, 1)
+    nn_h = index.query(Xh_d, 1)
     Ynn = ivhd.place_nn(Ytr, nn_h)
     e1 = ev()
     torch.cuda.synchronize()
@@ -155,7 +160,9 @@ def main():
                               "steps_to_plain_final_precision": first_within(warm)}
     out["nn_placement"] = {"rows": args.holdout, "seconds": place_nn_s,
                            "rows_per_s": args.holdout / place_nn_s,
-                           "what": "exact 1-NN query in the training set + its embedding"}
+                           "index_create_seconds": index_s,
+                           "what": "exact 1-NN query in the training set (a KnnIndex built "
+                                   "once) + its embedding"}
     out["nn_placement_ivhd"] = {"curve": nnw, "step_seconds": nnw_s,
                                 "steps_to_plain_final_precision": first_within(nnw)}
 
@@ -180,7 +187,7 @@ def main():
         res["mlp"]["latency_us"].append(t0.elapsed_time(t1) * 1e3)
         res["mlp"]["cf10"].append(cf_vs_train(yb * sd + mu, lb))
         t0 = ev()
-        yn = ivhd.place_nn(Ytr, ivhd.knn_query(xb, Xtr_d, 1))
+        yn = ivhd.place_nn(Ytr, index.query(xb, 1))
         t1 = ev()
         torch.cuda.synchronize()
         res["nn"]["latency_us"].append(t0.elapsed_time(t1) * 1e3)

@@ -17,6 +17,7 @@
 // Progressive UMAP initialisation of a new point (Sec. 2.4.3), the comparator
 // of the learned placement.
 #include <algorithm>
+#include <new>
 #include <climits>
 
 #include "ivhd_internal.cuh"
@@ -383,7 +384,8 @@ static ivhd_status knn_cuda_cores(const KnnProblem& P, int32_t* out_knn, cudaStr
 
 // Method choice, tensor-core or CUDA-core run and statistics for one problem.
 static ivhd_status knn_run(const KnnProblem& P, int32_t* out, int32_t method,
-                           ivhd_knn_stats_t* stats, cudaStream_t s) {
+                           ivhd_knn_stats_t* stats, cudaStream_t s,
+                           const KnnBase* base = nullptr) {
   if (method < IVHD_KNN_AUTO || method > IVHD_KNN_TENSOR_CORES) return IVHD_ERR_ARG;
   const bool tc_ok = knn_tc_supported(P);
   if (method == IVHD_KNN_TENSOR_CORES && !tc_ok) return IVHD_ERR_ARG;
@@ -393,7 +395,7 @@ static ivhd_status knn_run(const KnnProblem& P, int32_t* out, int32_t method,
   ivhd_status r;
   if (use_tc) {
     KnnTcStats t{};
-    r = knn_tc_build(P, out, s, &t);
+    r = knn_tc_build(P, out, s, &t, base);
     st.fallback_rows = t.fallback_rows;
     st.max_rel_err = t.max_rel_err;
     st.eps_coef = t.eps_coef;
@@ -463,4 +465,69 @@ extern "C" ivhd_status ivhd_place_nn(const float* Y, int64_t M, const int32_t* i
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return IVHD_ERR_CUDA;
   return h ? IVHD_ERR_INDEX : IVHD_OK;
+}
+
+// ---- a base set held for repeated queries ----------------------------------
+
+struct ivhd_knn_index {
+  cudaStream_t stream = nullptr;
+  int32_t dtype = 0, N = 0;
+  int64_t M = 0;
+  void* X = nullptr;             // the library's copy of the base rows
+  __nv_bfloat16* B = nullptr;    // prepared tensor-core operand (null: CUDA cores only)
+  void* nrm = nullptr;           // its row norms
+};
+
+static void index_free(ivhd_knn_index* idx) {
+  if (idx->X) dev_free(idx->X, idx->stream);
+  if (idx->B) dev_free(idx->B, idx->stream);
+  if (idx->nrm) dev_free(idx->nrm, idx->stream);
+  delete idx;
+}
+
+extern "C" ivhd_status ivhd_knn_index_create(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                             void* stream, ivhd_knn_index** out) {
+  NvtxScope nvtx_("ivhd_knn_index_create");
+  if (!X || !out || !knn_args_ok(dtype, M, N, 1, M)) return IVHD_ERR_ARG;
+  *out = nullptr;
+  ivhd_knn_index* idx = new (std::nothrow) ivhd_knn_index();
+  if (!idx) return IVHD_ERR_OOM;
+  idx->stream = (cudaStream_t)stream;
+  idx->dtype = dtype;
+  idx->M = M;
+  idx->N = N;
+  cudaStream_t s = idx->stream;
+  const size_t bytes = (size_t)M * (size_t)N * (dtype == IVHD_KNN_U8 ? 1 : 4);
+  cudaError_t e = dev_alloc(&idx->X, bytes, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(idx->X, X, bytes, cudaMemcpyDeviceToDevice, s);
+  // the tensor-core operand, when the tensor-core method applies to this base set
+  const KnnProblem probe{X, 1, X, M, dtype, N, 1, false};
+  if (e == cudaSuccess && knn_tc_supported(probe)) {
+    const int Kp = knn_tc_kp(dtype, N);
+    e = dev_alloc((void**)&idx->B, (size_t)M * Kp * sizeof(__nv_bfloat16), s);
+    if (e == cudaSuccess) e = dev_alloc(&idx->nrm, (size_t)M * 4, s);
+    if (e == cudaSuccess) e = knn_tc_prepare_base(idx->X, dtype, M, N, idx->B, idx->nrm, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    index_free(idx);
+    return e == cudaErrorMemoryAllocation ? IVHD_ERR_OOM : IVHD_ERR_CUDA;
+  }
+  *out = idx;
+  return IVHD_OK;
+}
+
+extern "C" ivhd_status ivhd_knn_index_query(ivhd_knn_index* idx, const void* Q, int64_t Mq,
+                                            int32_t k, int32_t* out, int32_t method,
+                                            ivhd_knn_stats_t* stats) {
+  NvtxScope nvtx_("ivhd_knn_index_query");
+  if (!idx || !Q || !out || Mq < 1 || Mq >= (int64_t)0x7FFFFFFF) return IVHD_ERR_ARG;
+  if (!knn_args_ok(idx->dtype, idx->M, idx->N, k, idx->M)) return IVHD_ERR_ARG;
+  const KnnProblem P{Q, Mq, idx->X, idx->M, idx->dtype, idx->N, k, false};
+  const KnnBase base{idx->B, idx->nrm};
+  return knn_run(P, out, method, stats, idx->stream, idx->B ? &base : nullptr);
+}
+
+extern "C" void ivhd_knn_index_destroy(ivhd_knn_index* idx) {
+  if (idx) index_free(idx);
 }

@@ -592,15 +592,36 @@ struct Bufs {
 };
 }  // namespace
 
+int knn_tc_kp(int32_t dtype, int32_t N) {
+  const int64_t K = dtype == IVHD_KNN_U8 ? (int64_t)N : 3 * (int64_t)N;
+  return (int)(((K + kBK - 1) / kBK) * kBK);
+}
+
+cudaError_t knn_tc_prepare_base(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                __nv_bfloat16* B, void* nrm, cudaStream_t s) {
+  const int Kp = knn_tc_kp(dtype, N);
+  auto blocks = [](int64_t n) { return (unsigned)((n + 255) / 256); };
+  if (dtype == IVHD_KNN_U8) {
+    k_prep_u8<<<blocks(M * Kp), 256, 0, s>>>((const uint8_t*)X, M, N, Kp, B);
+    k_norms_u8s<<<blocks(M), 256, 0, s>>>((const uint8_t*)X, M, N, (int32_t*)nrm);
+  } else {
+    k_prep_f32<<<blocks(M * Kp), 256, 0, s>>>((const float*)X, M, N, Kp, nullptr, B);
+    k_norms_f32<<<blocks(M), 256, 0, s>>>((const float*)X, M, N, (float*)nrm);
+  }
+  return cudaGetLastError();
+}
+
 ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
-                         KnnTcStats* stats) {
+                         KnnTcStats* stats, const KnnBase* base) {
   const bool u8 = P.dtype == IVHD_KNN_U8;
   const int64_t M = P.M, Mq = P.Mq;
   const int N = P.N, k = P.k;
-  const int Kp = (int)((((u8 ? (int64_t)N : 3 * (int64_t)N) + kBK - 1) / kBK) * kBK);
+  const int Kp = knn_tc_kp(P.dtype, N);
+  if (base && P.self) return IVHD_ERR_ARG;
   Bufs b(s);
-  // A: the query rows' operand, B: the base rows'; one array when they coincide (uint8 self)
-  __nv_bfloat16* B = b.get<__nv_bfloat16>(M * Kp);
+  // A: the query rows' operand, B: the base rows' (prepared once in an index,
+  // or here); one array when they coincide (uint8 self)
+  __nv_bfloat16* B = base ? const_cast<__nv_bfloat16*>(base->B) : b.get<__nv_bfloat16>(M * Kp);
   __nv_bfloat16* A = (u8 && P.self) ? B : b.get<__nv_bfloat16>(Mq * Kp);
   int32_t* err = b.get<int32_t>(8);  // err, n_fb, max-err bits
   if (!b.ok) return IVHD_ERR_OOM;
@@ -638,7 +659,7 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
   const int n_lists = 2 * segs;
   if (u8) {
     const int L = (k <= 8) ? 8 : kKnnList;
-    int32_t* nrm = b.get<int32_t>(M);
+    int32_t* nrm = base ? (int32_t*)const_cast<void*>(base->nrm) : b.get<int32_t>(M);
     int32_t* qnrm = P.self ? nrm : b.get<int32_t>(Mq);
     int32_t* lids = b.get<int32_t>(Mq * n_lists * L);
     int32_t* lkeys = b.get<int32_t>(Mq * n_lists * L);
@@ -646,8 +667,10 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
     if (e == cudaSuccess) {
       const uint8_t* X = (const uint8_t*)P.X;
       const uint8_t* Q = (const uint8_t*)P.Q;
-      k_prep_u8<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, B);
-      k_norms_u8s<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
+      if (!base) {
+        k_prep_u8<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, B);
+        k_norms_u8s<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
+      }
       if (!P.self) {
         k_prep_u8<<<blocks(Mq * Kp), 256, 0, s>>>(Q, Mq, N, Kp, A);
         k_norms_u8s<<<blocks(Mq), 256, 0, s>>>(Q, Mq, N, qnrm);
@@ -667,7 +690,7 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
       e = cudaGetLastError();
     }
   } else {
-    float* nrm = b.get<float>(M);
+    float* nrm = base ? (float*)const_cast<void*>(base->nrm) : b.get<float>(M);
     float* qnrm = P.self ? nrm : b.get<float>(Mq);
     const int L = (k <= 8) ? 16 : kKnnList;  // candidates per row and half
     int32_t* cand = b.get<int32_t>(Mq * n_lists * L);
@@ -680,11 +703,11 @@ ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
       if (P.self) {
         k_prep_f32<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, A, B);
       } else {
-        k_prep_f32<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, nullptr, B);
+        if (!base) k_prep_f32<<<blocks(M * Kp), 256, 0, s>>>(X, M, N, Kp, nullptr, B);
         k_prep_f32<<<blocks(Mq * Kp), 256, 0, s>>>(Q, Mq, N, Kp, A, nullptr);
         k_norms_f32<<<blocks(Mq), 256, 0, s>>>(Q, Mq, N, qnrm);
       }
-      k_norms_f32<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
+      if (!base) k_norms_f32<<<blocks(M), 256, 0, s>>>(X, M, N, nrm);
       e = (L == 16) ? launch_tc<false, 16>(ma, mb, nrm, nullptr, qnrm, nullptr, (int)Mq, (int)M,
                                            Kp, P.self, segs, seg_tiles, eps_coef, cand, cd, err, s)
                     : launch_tc<false, kKnnList>(ma, mb, nrm, nullptr, qnrm, nullptr, (int)Mq,

@@ -2,6 +2,7 @@
 // and the exact CUDA-core kernel it falls back to (ivhd_knn.cu).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,10 +35,24 @@ struct KnnProblem {
 // N <= 1024, so that every partial sum is exact in FP32).
 bool knn_tc_supported(const KnnProblem& P);
 
-// Tensor-core build; synchronises the stream.  IVHD_ERR_TIMEOUT if a bounded
-// wait of the kernel expired.
+// A base set prepared once for many queries: its BF16 operand (M x Kp, the
+// layout knn_tc_build makes) and its row norms (float for float data, int32
+// norms of the rows shifted by -128 for uint8).
+struct KnnBase {
+  const __nv_bfloat16* B;
+  const void* nrm;
+};
+// Padded GEMM depth of the operands (K = N for uint8, 3N for float).
+int knn_tc_kp(int32_t dtype, int32_t N);
+// Fills B (M x knn_tc_kp) and nrm (M) for the base set X; stream-ordered.
+cudaError_t knn_tc_prepare_base(const void* X, int32_t dtype, int64_t M, int32_t N,
+                                __nv_bfloat16* B, void* nrm, cudaStream_t s);
+
+// Tensor-core build; synchronises the stream.  base (queries only, may be
+// null): the base set's prepared operand and norms.  IVHD_ERR_TIMEOUT if a
+// bounded wait of the kernel expired.
 ivhd_status knn_tc_build(const KnnProblem& P, int32_t* out_knn, cudaStream_t s,
-                         KnnTcStats* stats);
+                         KnnTcStats* stats, const KnnBase* base = nullptr);
 
 // Exact FP32 kNN rows (the CUDA-core kernel) for the *n_rows query rows listed
 // in rows (device count and list); the other rows of out_knn are left untouched.

@@ -321,6 +321,53 @@ def knn_query(Q: torch.Tensor, X: torch.Tensor, k: int, stream=None, method: str
     return out
 
 
+class KnnIndex:
+    """A base set held for repeated kNN queries (ivhd_knn_index_*): the rows of X
+    (float32 or uint8 CUDA tensor) are copied and prepared once."""
+
+    _DTYPES = {torch.float32: 0, torch.uint8: 1}
+
+    def __init__(self, X: torch.Tensor, stream=None):
+        self._L = _lib.load()
+        if not X.is_cuda or X.dtype not in self._DTYPES:
+            raise ValueError("KnnIndex expects a float32 or uint8 CUDA tensor")
+        X = X.contiguous()
+        self.dtype, self.M, self.N = X.dtype, int(X.shape[0]), int(X.shape[1])
+        self.device = X.device
+        h = ctypes.c_void_p()
+        check(self._L.ivhd_knn_index_create(X.data_ptr(), self._DTYPES[X.dtype], self.M, self.N,
+                                            _stream_ptr(stream), ctypes.byref(h)),
+              "ivhd_knn_index_create")
+        self._h = h
+
+    def query(self, Q: torch.Tensor, k: int, method: str = "auto", return_stats: bool = False):
+        """The k base rows nearest to each row of Q -> int32 [Mq, k] (as knn_query)."""
+        if not Q.is_cuda or Q.dtype != self.dtype or Q.shape[1] != self.N:
+            raise ValueError("Q must be a CUDA tensor of the index's dtype and width")
+        Q = Q.contiguous()
+        out = torch.empty((int(Q.shape[0]), k), dtype=torch.int32, device=Q.device)
+        st = _lib.KnnStats()
+        check(self._L.ivhd_knn_index_query(self._h, Q.data_ptr(), int(Q.shape[0]), int(k),
+                                           out.data_ptr(), KNN_METHODS[method],
+                                           ctypes.byref(st)), "ivhd_knn_index_query")
+        if return_stats:
+            names = {v: n for n, v in KNN_METHODS.items()}
+            return out, {"method": names[st.method], "fallback_rows": st.fallback_rows,
+                         "max_rel_err": st.max_rel_err, "eps_coef": st.eps_coef}
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.ivhd_knn_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def place_nn(Y: torch.Tensor, ids: torch.Tensor, stream=None) -> torch.Tensor:
     """New points at the mean embedding of their base neighbours (ivhd_place_nn) -> [n, 2]."""
     L = _lib.load()

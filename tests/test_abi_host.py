@@ -166,6 +166,16 @@ def test_create_rejects_bad_adaptive_params(L, opt, field, value):
     assert st == -1 and not h.value
 
 
+def test_knn_index_rejects_bad_args(L):
+    h = ctypes.c_void_p()
+    assert L.ivhd_knn_index_create(None, 0, 10, 4, None, ctypes.byref(h)) == -1
+    X = np.zeros((10, 4), np.float32)
+    assert L.ivhd_knn_index_create(X.ctypes.data, 2, 10, 4, None, ctypes.byref(h)) == -1
+    assert L.ivhd_knn_index_create(X.ctypes.data, 0, 0, 4, None, ctypes.byref(h)) == -1
+    assert L.ivhd_knn_index_query(None, X.ctypes.data, 1, 1, X.ctypes.data, 0, None) == -1
+    L.ivhd_knn_index_destroy(None)
+
+
 def test_persistent_grid_needs_fp32_gathers_without_adaptive_b(L):
     knn = np.array([[1], [0], [0]], np.int32)
     for field, value in (("pos_format", 1), ("adaptive", 1)):

@@ -53,6 +53,23 @@ def test_grid_barrier_timeout_returns_status_and_library_stays_usable(L):
     emb.close()
 
 
+def test_knn_index_frees_everything_on_allocation_failure(L):
+    X = torch.randn(3000, 24, generator=torch.Generator().manual_seed(4)).cuda()
+    Q = X[:500].contiguous()
+    base = live(L)
+
+    def one():
+        idx = ivhd.KnnIndex(X)
+        try:
+            idx.query(Q, 5)
+        finally:
+            idx.close()
+
+    n = _each_failure(L, one)
+    assert n >= 3
+    assert live(L) == base
+
+
 def _each_failure(L, call, limit=400):
     """Runs call() with the n-th allocation failing, n = 0, 1, ... until call()
     completes without reaching the injected failure; returns that n."""

@@ -97,6 +97,25 @@ def test_query_uncertified_rows_in_column_segments():
     assert np.array_equal(got.cpu().numpy(), oracle.knn_query(Q, X, 7))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_index_queries_equal_single_queries(dtype):
+    if dtype == "f32":
+        Q, X = split_gmm(900, 5000, 40, 12)
+    else:
+        Z, _ = synth.mnist_like(5900, 13, N=200)
+        Q, X = Z[:900], Z[900:]
+    Qd, Xd = torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda()
+    idx = ivhd.KnnIndex(Xd)
+    Xd.zero_()                                  # the index holds its own copy
+    for method in ("tensor_cores", "cuda_cores"):
+        for lo, hi, k in ((0, 900, 5), (0, 64, 1), (300, 900, 20)):
+            got = idx.query(Qd[lo:hi], k, method=method).cpu().numpy()
+            assert np.array_equal(got, oracle.knn_query(Q[lo:hi], X, k)), (method, lo, k)
+    with pytest.raises(IvhdError):
+        idx.query(Qd, 5001)
+    idx.close()
+
+
 def test_query_edge_sizes_and_errors():
     Q, X = split_gmm(40, 64, 16, 2)
     Qd, Xd = torch.from_numpy(Q).cuda(), torch.from_numpy(X).cuda()
