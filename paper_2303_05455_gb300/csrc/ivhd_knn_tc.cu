@@ -579,7 +579,8 @@ struct Bufs {
   template <class T>
   T* get(int64_t count) {
     void* q = nullptr;
-    if (dev_alloc(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s) != cudaSuccess) {
+    if (n == (int)(sizeof(p) / sizeof(p[0])) ||
+        dev_alloc(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s) != cudaSuccess) {
       ok = false;
       return nullptr;
     }
