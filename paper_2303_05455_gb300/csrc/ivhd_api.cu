@@ -341,7 +341,7 @@ void ivhd_default_params(ivhd_params* p) {
   p->stream = nullptr;
 }
 
-int32_t ivhd_version(void) { return (0 << 16) | (2 << 8) | 0; }
+int32_t ivhd_version(void) { return (0 << 16) | (3 << 8) | 0; }
 
 const char* ivhd_status_string(ivhd_status s) {
   switch (s) {

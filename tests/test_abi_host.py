@@ -65,7 +65,7 @@ def test_params_struct_layout_and_defaults(L):
     assert (p.opt, p.init_uniform, p.dedup_mutual, p.hub_threshold) == (0, 1, 0, 0)
     assert p.a == pytest.approx(0.9) and p.b == pytest.approx(0.01)
     assert p.rho == pytest.approx(0.95) and p.eps == pytest.approx(1e-6)
-    assert L.ivhd_version() == (0 << 16) | (2 << 8)
+    assert L.ivhd_version() == (0 << 16) | (3 << 8)
     assert p.adaptive == 0 and p.tau == pytest.approx(0.5)
     assert p.gamma1 == pytest.approx(1.1) and p.gamma2 == pytest.approx(0.5)
     for s in (0, -1, -2, -3, -4, -5, -6, -7, 42):
