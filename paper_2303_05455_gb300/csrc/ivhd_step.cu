@@ -358,6 +358,17 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
   float2 ym = make_float2(0.f, 0.f);
   int p = -1;
   bool own = false;
+  // the owner's optimiser state is loaded with its position, before the
+  // gathers, so its latency is not added after them
+  constexpr bool kUpdate = MODE == kMomentum || MODE == kNesterov || MODE == kAdadelta;
+  const float2* __restrict__ v_in = A.v[ADAPT ? cur : 0];
+  float2 v_pre = make_float2(0.f, 0.f), s2_pre = make_float2(0.f, 0.f);
+  auto load_state = [&](int q) {
+    if constexpr (kUpdate) {
+      v_pre = v_in[q];
+      if constexpr (MODE == kAdadelta) s2_pre = A.s2[q];
+    }
+  };
 
   if (vb < A.nb_hub) {
     // hub rows: a warp, or a group of mid_g lanes, per vertex; the lanes of a
@@ -372,6 +383,7 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
         p = h.row;
         ym = (POS == kPosF32Coherent) ? __ldcg(G.y + p) : G.y[p];
         yi = f32_pos<POS>() ? ym : load_pos<POS>(G.y, G.yh, p);
+        if (h.l == 0) load_state(p);
         const int beg = A.hub_off[p], end = A.hub_off[p + 1];
         row = reinterpret_cast<const int4*>(A.ids + beg);
         ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
@@ -395,6 +407,7 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
       if (valid) {
         ym = (POS == kPosF32Coherent) ? __ldcg(G.y + p) : G.y[p];
         yi = f32_pos<POS>() ? ym : load_pos<POS>(G.y, G.yh, p);
+        load_state(p);
       }
       const int4* base = reinterpret_cast<const int4*>(A.ids + A.slice_off[s]) + lane;
       const int W = row_ok(A.slice_off[s], A.slice_off[s] + (int64_t)A.slice_w[s] * 128, A.n_slots)
@@ -416,13 +429,12 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
   if constexpr (PDL) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   float2* __restrict__ y_out = A.y[cur ^ 1];
   uint32_t* __restrict__ yh_out = A.yh[cur ^ 1];
-  const float2* __restrict__ v_in = A.v[ADAPT ? cur : 0];
   float2* __restrict__ v_out = A.v[ADAPT ? (cur ^ 1) : 0];
   float kin_new = 0.f, kin_old = 0.f;  // |v'|^2, |v|^2 (FP32; blocks sum them in a fixed order)
 
   if (MODE == kMomentum) {
     if (own) {
-      const float2 v = v_in[p];
+      const float2 v = v_pre;
       float2 vn, yn;
       momentum_update(A.a, b, fx, fy, ym, v, vn, yn);
       v_out[p] = vn;
@@ -435,7 +447,7 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
     }
   } else if (MODE == kNesterov) {
     if (own) {
-      const float2 v = v_in[p];
+      const float2 v = v_pre;
       float2 vn, zn;
       nesterov_update(A.a, b, fx, fy, ym, v, vn, zn);
       v_out[p] = vn;
@@ -448,8 +460,8 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
     }
   } else if (MODE == kAdadelta) {
     if (own) {
-      float2 eg = v_in[p];
-      float2 ex = A.s2[p];
+      float2 eg = v_pre;
+      float2 ex = s2_pre;
       float2 yn;
       adadelta_update(A.rho, A.eps, fx, fy, ym, eg, ex, yn);
       v_out[p] = eg;
