@@ -231,3 +231,15 @@ def test_normal_build_counts_no_violations_and_refuses_corruption(L):
     assert L.ivhd_check_violations(ctypes.byref(v), 0) == 0 and v.value == -1
     assert L.ivhd_check_violations(None, 0) == -1
     assert L.ivhd_test_corrupt_layout(None, 0, 0) == -1
+
+
+def test_binding_rejects_host_tensors_before_any_cuda_call():
+    import torch
+    from paper_2303_05455_gb300 import ivhd
+    X = torch.zeros((10, 4))
+    with pytest.raises(ValueError):
+        ivhd.KnnIndex(X)
+    with pytest.raises(ValueError):
+        ivhd.knn_query(X, X, 2)
+    with pytest.raises(ValueError):
+        ivhd.knn_build(X, 2)
