@@ -589,3 +589,31 @@ def test_run_threads_single_pair_recurrence():
     for q in range(2):
         want = _recurrence(Y0[0, q] - Y0[1, q], 0.0, 4.0, 0.9, 0.01, 37)[0]
         assert s[q] == pytest.approx(want, abs=1e-12)
+
+
+# ---------------------------------------------------------------- toy example
+
+
+def test_two_hypertetrahedra_separate():
+    # Sec. 3.3.1's toy: two regular 18-simplices (19 vertices each, all
+    # pairwise distances equal) in 18-D, one rotated and translated away from
+    # the other; with nn = 2, rn = 1, c = 0.1 the kNN graph has no edge
+    # between them and the random neighbours push them apart, so every
+    # vertex's 2 nearest embedded points lie in its own simplex
+    rng = np.random.default_rng(3)
+    simplex = np.eye(19)                              # regular, in a 18-D affine subspace
+    Rm, _ = np.linalg.qr(rng.standard_normal((19, 19)))
+    X = np.concatenate([simplex, simplex @ Rm + 10.0]).astype(np.float32)
+    labels = np.repeat([0, 1], 19).astype(np.int32)
+    knn = oracle.knn_f32(X, 2)
+    assert np.all((knn // 19) == (np.arange(38) // 19)[:, None])   # no cross-simplex kNN edge
+    rn, _ = oracle.random_neighbors(knn, 1, 7)
+    terms = oracle.build_terms(knn, rn)
+    st = oracle.State.fresh(oracle.init_positions(38, 7))
+    oracle.run(st, terms, 0.1, 3000, oracle.OPT_MOMENTUM, a=0.9, b=0.01)
+    assert oracle.cf(st.Y.astype(np.float32), labels, 2) == 1.0
+    # the two simplices end apart: centroid distance above the largest radius
+    c0, c1 = st.Y[:19].mean(0), st.Y[19:].mean(0)
+    radius = max(np.linalg.norm(st.Y[:19] - c0, axis=1).max(),
+                 np.linalg.norm(st.Y[19:] - c1, axis=1).max())
+    assert np.linalg.norm(c0 - c1) > radius
