@@ -467,7 +467,9 @@ ivhd_status ivhd_place_nn(const float *Y, int64_t M, const int32_t *ids, int64_t
  *   rows     device, nrows int64 row ids in [0, M).
  *   out_lowd device, nrows*k int32 or NULL: the embedded neighbours found.
  *   out_q    host double.
- * Constraints: 1 <= k <= min(M - 1, 128), nrows >= 1.  Synchronises.
+ * Constraints: 1 <= k <= min(M - 1, 128), nrows >= 1.  A row id outside
+ * [0, M) is never dereferenced: the call returns IVHD_ERR_INDEX and leaves
+ * *out_q unwritten.  Synchronises.
  */
 ivhd_status ivhd_eval_qnx(const float *Y, int64_t M, const int32_t *knn, int32_t k,
                           const int64_t *rows, int64_t nrows, int32_t *out_lowd,
@@ -479,7 +481,8 @@ ivhd_status ivhd_eval_qnx(const float *Y, int64_t M, const int32_t *knn, int32_t
  * ivhd_eval_qnx) that carry the label of the query row.
  *
  *   Y device M*2 float32; labels device M int32; rows device nrows int64.
- * Constraints: 1 <= nn <= min(M - 1, 128).  Synchronises.
+ * Constraints: 1 <= nn <= min(M - 1, 128).  Row ids outside [0, M): as
+ * ivhd_eval_qnx (IVHD_ERR_INDEX).  Synchronises.
  */
 ivhd_status ivhd_eval_cf(const float *Y, int64_t M, const int32_t *labels, int32_t nn,
                          const int64_t *rows, int64_t nrows, double *out_cf, void *stream);
@@ -572,16 +575,19 @@ int64_t ivhd_mlp_launches(ivhd_mlp *mlp);
  * device-memory footprint fixed after start-up).  Same arguments, result and
  * rules as ivhd_eval_qnx; the caller still passes every input and output.
  *
- * Scratch: a fixed array of 8193 64-bit counters (about 64 KiB) in the
+ * Scratch: a fixed array of 8194 64-bit counters (about 64 KiB) in the
  * library's own device memory, held by every GPU that loads the library
  * until the process exits.  It limits one call to nrows <= 1,048,576
- * (8192 blocks of 128 rows); larger calls return IVHD_ERR_ARG.  The first
- * call on each device looks up the array's device address (this may load the
- * library's device code), so make that first call before any stream capture.
- * All calls on a device share the array and it keeps the last call's
- * contents: calls whose GPU work overlaps (different streams or unsynchronised
- * host threads) race and may return wrong values; order them on one stream.
- * Calls no cudaMalloc, cudaFree or other allocating routine.  Synchronises.
+ * (8192 blocks of 128 rows); larger calls return IVHD_ERR_ARG.  A row id
+ * outside [0, M) returns IVHD_ERR_INDEX (never dereferenced).  The first
+ * call on each device (and again after the caller re-creates the device's
+ * CUDA context, e.g. with cudaDeviceReset) looks up the array's device
+ * address, which may load the library's device code, so make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents: calls whose GPU work overlaps (different
+ * streams or unsynchronised host threads) race and may return wrong values;
+ * order them on one stream.  Calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Synchronises.
  */
 ivhd_status ivhd_eval_qnx_static(const float *Y, int64_t M, const int32_t *knn, int32_t k,
                                  const int64_t *rows, int64_t nrows, int32_t *out_lowd,

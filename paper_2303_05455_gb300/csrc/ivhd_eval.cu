@@ -7,6 +7,9 @@
 //   Q_NX(k):  hits = |embedded kNN(q) ∩ input kNN row q|       (rank criteria)
 //   cf_nn:    hits = #embedded neighbours with q's class label  (Eq. 4.4)
 // Hits are integer-summed, so the result is exact and order independent.
+// A sampled row id outside [0, M) is never dereferenced: its thread stays
+// inactive and counts it in a second counter, and the call returns
+// IVHD_ERR_INDEX.
 #include "ivhd_internal.cuh"
 
 namespace ivhd {
@@ -22,15 +25,18 @@ __global__ void __launch_bounds__(kEvalThreads) k_lowd(const float2* __restrict_
                                                        const int32_t* __restrict__ knn,
                                                        const int32_t* __restrict__ labels,
                                                        int32_t* __restrict__ out_lowd,
-                                                       unsigned long long* __restrict__ hits) {
+                                                       unsigned long long* __restrict__ hits,
+                                                       unsigned long long* __restrict__ bad) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tile = reinterpret_cast<float2*>(smem);
   float* ld = reinterpret_cast<float*>(tile + kEvalTile) + threadIdx.x * kk;
   int* lj = reinterpret_cast<int*>(reinterpret_cast<float*>(tile + kEvalTile) + kEvalThreads * kk) +
             threadIdx.x * kk;
   const int64_t qi = (int64_t)blockIdx.x * kEvalThreads + threadIdx.x;
-  const bool act = qi < nrows;
-  const int64_t q = act ? rows[qi] : 0;
+  const int64_t q = qi < nrows ? rows[qi] : 0;
+  const bool in_range = q >= 0 && q < M;
+  if (qi < nrows && !in_range) atomicAdd(bad, 1ull);
+  const bool act = qi < nrows && in_range;
   const float2 yq = act ? Y[q] : make_float2(0.f, 0.f);
   int n = 0;
   float worst = INFINITY;
@@ -84,25 +90,26 @@ ivhd_status run_lowd(const float* Y, int64_t M, const int32_t* knn, const int32_
                      void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t sm = (size_t)kEvalTile * sizeof(float2) + (size_t)kEvalThreads * kk * 8;
-  unsigned long long* hits_d = nullptr;
-  cudaError_t e = dev_alloc((void**)&hits_d, sizeof(unsigned long long), s);
+  unsigned long long* hits_d = nullptr;  // [0] hits, [1] rows outside [0, M)
+  cudaError_t e = dev_alloc((void**)&hits_d, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return IVHD_ERR_OOM;
-  e = cudaMemsetAsync(hits_d, 0, sizeof(unsigned long long), s);
+  e = cudaMemsetAsync(hits_d, 0, 2 * sizeof(unsigned long long), s);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lowd<kQnx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess) {
     const unsigned grid = (unsigned)((nrows + kEvalThreads - 1) / kEvalThreads);
     k_lowd<kQnx><<<grid, kEvalThreads, sm, s>>>((const float2*)Y, M, rows, nrows, kk, knn, labels,
-                                               out_lowd, hits_d);
+                                               out_lowd, hits_d, hits_d + 1);
     e = cudaGetLastError();
   }
-  unsigned long long hits = 0;
+  unsigned long long hits[2] = {0, 0};
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&hits, hits_d, sizeof(hits), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(hits, hits_d, sizeof(hits), cudaMemcpyDeviceToHost, s);
   dev_free(hits_d, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return IVHD_ERR_CUDA;
-  *out = (double)hits / ((double)kk * (double)nrows);
+  if (hits[1] != 0) return IVHD_ERR_INDEX;
+  *out = (double)hits[0] / ((double)kk * (double)nrows);
   return IVHD_OK;
 }
 

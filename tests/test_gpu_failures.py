@@ -152,3 +152,22 @@ def test_mlp_frees_everything_on_allocation_failure(L):
 
     assert _each_failure(L, run) > 5
     assert live(L) == base
+
+
+def test_eval_rejects_sampled_row_ids_out_of_range(L):
+    """A row id outside [0, M) is reported as IVHD_ERR_INDEX, never dereferenced."""
+    M, k = 2000, 3
+    knn = torch.from_numpy(synth.random_knn_graph(M, k, 5)).cuda()
+    Y = torch.from_numpy(synth.uniform_positions(M, 6)).cuda()
+    lab = torch.arange(M, dtype=torch.int32, device="cuda") % 5
+    for bad in (M, -1, 1 << 40):
+        rows = torch.arange(300, dtype=torch.int64, device="cuda")
+        rows[211] = bad
+        with pytest.raises(IvhdError) as e:
+            ivhd.eval_qnx(Y, knn, rows)
+        assert e.value.status == -2
+        with pytest.raises(IvhdError) as e:
+            ivhd.eval_cf(Y, lab, 10, rows)
+        assert e.value.status == -2
+    rows = torch.arange(300, dtype=torch.int64, device="cuda")
+    assert 0.0 <= ivhd.eval_qnx(Y, knn, rows) <= 1.0
