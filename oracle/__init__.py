@@ -15,9 +15,13 @@ the readings taken where the paper is ambiguous):
 * ``step`` / ``run``   -- momentum (force-directed), Nesterov, Adadelta.
 * ``run_threads``      -- ``run`` on several host threads (CPU timing).
 * ``knn_f32`` / ``knn_u8`` -- exact brute-force kNN.
+* ``knn_u8_gemm``      -- the same uint8 kNN graph as ``knn_u8`` for full-size
+  inputs, its integer distances formed with a float64 matrix product.
 * ``knn_query``, ``place_nn`` -- kNN of new points in a base set and their
   placement at the mean embedding of those neighbours (Progressive UMAP).
-* ``qnx``, ``cf``      -- Q_NX(k) and neighbour hit cf_nn.
+* ``qnx``, ``cf``      -- Q_NX(k) and neighbour hit cf_nn (``threads`` > 1
+  splits the sampled rows over host threads; integer hit counts, so the
+  result is the serial one exactly).
 """
 from __future__ import annotations
 
@@ -85,6 +89,10 @@ def _L():
         lib.ivo_qnx.restype = dbl
         lib.ivo_cf.argtypes = [P, i64, P, i32, P, i64]
         lib.ivo_cf.restype = dbl
+        lib.ivo_qnx_threads.argtypes = [P, i64, P, i32, P, i64, P, i32]
+        lib.ivo_qnx_threads.restype = dbl
+        lib.ivo_cf_threads.argtypes = [P, i64, P, i32, P, i64, i32]
+        lib.ivo_cf_threads.restype = dbl
         _lib = lib
     return _lib
 
@@ -285,21 +293,70 @@ def place_nn(Y, ids) -> np.ndarray:
     return out
 
 
-def qnx(Y, knn, rows=None, return_lowd: bool = False):
+def qnx(Y, knn, rows=None, return_lowd: bool = False, threads: int = 1):
     Y = _c(Y, np.float32)
     knn = _c(knn, np.int32)
     M, k = knn.shape
     rows_a = None if rows is None else _c(rows, np.int64)
     n = M if rows_a is None else rows_a.shape[0]
     low = np.empty((n, k), dtype=np.int32) if return_lowd else None
-    q = float(_L().ivo_qnx(_p(Y), M, _p(knn), k, _p(rows_a), n, _p(low)))
+    if threads > 1:
+        q = float(_L().ivo_qnx_threads(_p(Y), M, _p(knn), k, _p(rows_a), n, _p(low), int(threads)))
+    else:
+        q = float(_L().ivo_qnx(_p(Y), M, _p(knn), k, _p(rows_a), n, _p(low)))
+    if q < 0:
+        raise MemoryError("oracle qnx")
     return (q, low) if return_lowd else q
 
 
-def cf(Y, labels, nn: int, rows=None) -> float:
+def cf(Y, labels, nn: int, rows=None, threads: int = 1) -> float:
     Y = _c(Y, np.float32)
     labels = _c(labels, np.int32)
     M = Y.shape[0]
     rows_a = None if rows is None else _c(rows, np.int64)
     n = M if rows_a is None else rows_a.shape[0]
-    return float(_L().ivo_cf(_p(Y), M, _p(labels), nn, _p(rows_a), n))
+    if threads > 1:
+        v = float(_L().ivo_cf_threads(_p(Y), M, _p(labels), nn, _p(rows_a), n, int(threads)))
+    else:
+        v = float(_L().ivo_cf(_p(Y), M, _p(labels), nn, _p(rows_a), n))
+    if v < 0:
+        raise MemoryError("oracle cf")
+    return v
+
+
+def knn_u8_gemm(X, k: int, block: int = 1024) -> np.ndarray:
+    """The exact kNN graph of uint8 rows (R10 of the C oracle), for full-size inputs.
+
+    Same definition as ``knn_u8``: for every row q the k other rows with the
+    smallest exact integer squared distance, ascending, ties to the lower
+    index.  Only the way the integers are formed differs: by the identity
+    ||x_q - x_j||^2 = ||x_q||^2 + ||x_j||^2 - 2 x_q . x_j with a float64 matrix
+    product (PyTorch on the host cores).  Every product and partial sum is an
+    integer below 784 * 255^2 * 2 < 2^53, so the product is exact whatever
+    order the library sums in.  The k smallest (distance, index) pairs are
+    picked by a library top-k on the key distance * M + index, which is exact
+    (below 2^53) and distinct per row, so the selection is unique.  Rows are
+    processed ``block`` queries at a time to bound the memory of the distance
+    block; each row's result depends on nothing but that row.
+    """
+    import torch
+
+    X = _c(X, np.uint8)
+    M, N = X.shape
+    if not 1 <= k <= M - 1:
+        raise ValueError("oracle knn: need 1 <= k <= M-1")
+    if N * 255 * 255 * 2 * M >= 2 ** 53:
+        raise ValueError("oracle knn_u8_gemm: integer keys would exceed 2^53")
+    Xd = torch.from_numpy(X).to(torch.float64)
+    nrm = (Xd * Xd).sum(dim=1)                  # exact integers
+    idx = torch.arange(M, dtype=torch.float64)
+    out = np.empty((M, k), dtype=np.int32)
+    for s in range(0, M, block):
+        e = min(M, s + block)
+        G = Xd[s:e] @ Xd.T                      # exact integer dot products
+        D = nrm[s:e, None] + nrm[None, :] - 2.0 * G
+        key = D * float(M) + idx[None, :]
+        key[torch.arange(e - s), torch.arange(s, e)] = float("inf")   # no self
+        _, j = torch.topk(key, k, dim=1, largest=False, sorted=True)
+        out[s:e] = j.numpy().astype(np.int32)
+    return out

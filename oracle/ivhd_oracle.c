@@ -732,6 +732,42 @@ static void ivo_lowd_knn(const float *Y, int64_t M, int64_t q, int kk, float *bd
 }
 
 /*
+ * Hits of Q_NX(k) (Sec. 4.1) over sampled rows qi in [r0, r1): for each, the
+ * k nearest other points n_i of y_i in the embedding, and |v_i ∩ n_i| with
+ * v_i the given high-dimensional kNN row.  lowd_out (optional) receives n_i
+ * at row qi.  bd, bj: scratch of k entries.
+ */
+static int64_t ivo_qnx_hits(const float *Y, int64_t M, const int32_t *knn, int k,
+                            const int64_t *rows, int64_t r0, int64_t r1, int32_t *lowd_out,
+                            float *bd, int32_t *bj)
+{
+    int64_t hits = 0;
+    for (int64_t qi = r0; qi < r1; ++qi) {
+        int64_t q = rows ? rows[qi] : qi;
+        ivo_lowd_knn(Y, M, q, k, bd, bj);
+        for (int s = 0; s < k; ++s) {
+            if (lowd_out) lowd_out[qi * (int64_t)k + s] = bj[s];
+            if (ivo_row_has(knn + q * (int64_t)k, k, bj[s])) ++hits;
+        }
+    }
+    return hits;
+}
+
+/* Hits of cf_nn (Sec. 4.1, Eq. 4.4) over sampled rows qi in [r0, r1). */
+static int64_t ivo_cf_hits(const float *Y, int64_t M, const int32_t *labels, int nn,
+                           const int64_t *rows, int64_t r0, int64_t r1, float *bd, int32_t *bj)
+{
+    int64_t hits = 0;
+    for (int64_t qi = r0; qi < r1; ++qi) {
+        int64_t q = rows ? rows[qi] : qi;
+        ivo_lowd_knn(Y, M, q, nn, bd, bj);
+        for (int s = 0; s < nn; ++s)
+            if (labels[bj[s]] == labels[q]) ++hits;
+    }
+    return hits;
+}
+
+/*
  * Q_NX(k) (Sec. 4.1): the mean over the sampled rows of |v_i ∩ n_i| / k,
  * where v_i is the given high-dimensional kNN row and n_i the k nearest
  * points of y_i in the embedding.  lowd_out (optional, nrows x k) receives n_i.
@@ -747,15 +783,7 @@ double ivo_qnx(const float *Y, int64_t M, const int32_t *knn, int k, const int64
         return -1.0;
     }
     int64_t nq = rows ? nrows : M;
-    int64_t hits = 0;
-    for (int64_t qi = 0; qi < nq; ++qi) {
-        int64_t q = rows ? rows[qi] : qi;
-        ivo_lowd_knn(Y, M, q, k, bd, bj);
-        for (int s = 0; s < k; ++s) {
-            if (lowd_out) lowd_out[qi * (int64_t)k + s] = bj[s];
-            if (ivo_row_has(knn + q * (int64_t)k, k, bj[s])) ++hits;
-        }
-    }
+    int64_t hits = ivo_qnx_hits(Y, M, knn, k, rows, 0, nq, lowd_out, bd, bj);
     free(bd);
     free(bj);
     return (double)hits / ((double)k * (double)nq);
@@ -776,14 +804,94 @@ double ivo_cf(const float *Y, int64_t M, const int32_t *labels, int nn, const in
         return -1.0;
     }
     int64_t nq = rows ? nrows : M;
-    int64_t hits = 0;
-    for (int64_t qi = 0; qi < nq; ++qi) {
-        int64_t q = rows ? rows[qi] : qi;
-        ivo_lowd_knn(Y, M, q, nn, bd, bj);
-        for (int s = 0; s < nn; ++s)
-            if (labels[bj[s]] == labels[q]) ++hits;
-    }
+    int64_t hits = ivo_cf_hits(Y, M, labels, nn, rows, 0, nq, bd, bj);
     free(bd);
     free(bj);
     return (double)hits / ((double)nn * (double)nq);
+}
+
+/*
+ * The same two criteria on several host threads, for the large sampled sets
+ * of full-size runs: thread t counts the hits of the t-th contiguous share of
+ * the sampled rows exactly as above, and the integer hit counts are added, so
+ * the result equals the serial one exactly for any number of threads.
+ */
+typedef struct {
+    const float *Y;
+    int64_t M;
+    const int32_t *knn, *labels;
+    int k;
+    const int64_t *rows;
+    int64_t r0, r1;
+    int32_t *lowd_out;
+    int64_t hits;
+    int rc;
+} ivo_eval_arg;
+
+static void *ivo_eval_main(void *p)
+{
+    ivo_eval_arg *A = (ivo_eval_arg *)p;
+    float *bd = (float *)malloc(sizeof(float) * (size_t)A->k);
+    int32_t *bj = (int32_t *)malloc(sizeof(int32_t) * (size_t)A->k);
+    A->rc = -1;
+    if (bd && bj) {
+        A->hits = A->labels
+                      ? ivo_cf_hits(A->Y, A->M, A->labels, A->k, A->rows, A->r0, A->r1, bd, bj)
+                      : ivo_qnx_hits(A->Y, A->M, A->knn, A->k, A->rows, A->r0, A->r1,
+                                     A->lowd_out, bd, bj);
+        A->rc = 0;
+    }
+    free(bd);
+    free(bj);
+    return NULL;
+}
+
+static double ivo_eval_threads(const float *Y, int64_t M, const int32_t *knn,
+                               const int32_t *labels, int k, const int64_t *rows, int64_t nrows,
+                               int32_t *lowd_out, int n_threads)
+{
+    if (n_threads < 1) return -1.0;
+    int64_t nq = rows ? nrows : M;
+    ivo_eval_arg *args = (ivo_eval_arg *)malloc(sizeof(ivo_eval_arg) * (size_t)n_threads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    char *started = (char *)calloc((size_t)n_threads, 1);
+    double out = -1.0;
+    if (!args || !th || !started) goto done;
+    for (int t = 0; t < n_threads; ++t) {
+        ivo_eval_arg A = {Y, M, knn, labels, k, rows, nq * t / n_threads,
+                          nq * (t + 1) / n_threads, lowd_out, 0, -1};
+        args[t] = A;
+    }
+    for (int t = 1; t < n_threads; ++t)
+        started[t] = pthread_create(&th[t], NULL, ivo_eval_main, &args[t]) == 0;
+    ivo_eval_main(&args[0]);
+    for (int t = 1; t < n_threads; ++t) {
+        if (started[t])
+            pthread_join(th[t], NULL);
+        else
+            ivo_eval_main(&args[t]);  /* a share whose thread did not start runs here */
+    }
+    int64_t hits = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        if (args[t].rc != 0) goto done;
+        hits += args[t].hits;
+    }
+    out = (double)hits / ((double)k * (double)nq);
+done:
+    free(args);
+    free(th);
+    free(started);
+    return out;
+}
+
+double ivo_qnx_threads(const float *Y, int64_t M, const int32_t *knn, int k, const int64_t *rows,
+                       int64_t nrows, int32_t *lowd_out, int n_threads)
+{
+    return ivo_eval_threads(Y, M, knn, NULL, k, rows, nrows, lowd_out, n_threads);
+}
+
+double ivo_cf_threads(const float *Y, int64_t M, const int32_t *labels, int nn,
+                      const int64_t *rows, int64_t nrows, int n_threads)
+{
+    return ivo_eval_threads(Y, M, NULL, labels, nn, rows, nrows, NULL, n_threads);
 }

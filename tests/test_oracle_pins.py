@@ -319,7 +319,49 @@ def test_knn_u8_integer_exact():
     assert np.array_equal(out, order)
 
 
+@pytest.mark.parametrize("M,N,block", [(200, 64, 1024), (337, 784, 64), (97, 10, 13)])
+def test_knn_u8_gemm_is_the_integer_exact_graph(M, N, block):
+    """The GEMM form gives the serial definition's graph, ties and ragged blocks included."""
+    X, _ = synth.mnist_like(M, 11, N=N)
+    X[M // 2:M // 2 + 9] = X[3]                    # exact duplicates: ties decided by index
+    X[M - 5:] = X[:5]
+    k = 7
+    D = ((X.astype(np.int64)[:, None, :] - X.astype(np.int64)[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(D, np.iinfo(np.int64).max)
+    order = np.lexsort((np.broadcast_to(np.arange(M), D.shape), D), axis=1)[:, :k]
+    got = oracle.knn_u8_gemm(X, k, block=block)
+    assert np.array_equal(got, order)
+    assert np.array_equal(got, oracle.knn_u8(X, k))
+
+
+def test_knn_u8_gemm_on_a_line_textbook():
+    M, k = 30, 4
+    Xu = (np.arange(M, dtype=np.int64)[:, None] * 3).clip(0, 255).astype(np.uint8)
+    out = oracle.knn_u8_gemm(Xu, k, block=7)
+    assert out[10].tolist() == [9, 11, 8, 12]
+    assert out[0].tolist() == [1, 2, 3, 4]
+    assert out[M - 1].tolist() == [M - 2, M - 3, M - 4, M - 5]
+
+
 # ---------------------------------------------------------------- metrics
+
+
+@pytest.mark.parametrize("threads", [2, 3, 7, 64])
+def test_threaded_qnx_and_cf_equal_the_serial_ones(threads):
+    """Integer hit counts over row shares: exactly the serial value, ties included."""
+    M, k = 1500, 6
+    knn = synth.random_knn_graph(M, k, 21)
+    Y = synth.uniform_positions(M, 22)
+    Y[:400] = np.round(Y[:400] * 8) / 8           # exact ties in the 2-D neighbour search
+    rows = synth.sample_rows(M, 41, 3)            # fewer rows than some thread counts
+    for r in (rows, None):
+        q, low = oracle.qnx(Y, knn, r, return_lowd=True)
+        qt, lowt = oracle.qnx(Y, knn, r, return_lowd=True, threads=threads)
+        assert qt == q and np.array_equal(lowt, low)
+    lab = (np.arange(M) * 7 % 5).astype(np.int32)
+    for nn in (2, 10, 100):
+        assert oracle.cf(Y, lab, nn, rows, threads=threads) == oracle.cf(Y, lab, nn, rows)
+        assert oracle.cf(Y, lab, nn, None, threads=threads) == oracle.cf(Y, lab, nn)
 
 
 def test_qnx_identity_embedding_is_one():
