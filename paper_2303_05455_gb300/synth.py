@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the benchmark.
 
 This module draws data only: Gaussian-mixture feature matrices, MNIST-shaped
-uint8 images, random kNN-shaped graphs and random 2-D positions.  It holds
+uint8 images, random kNN-shaped graphs (uniform, or with planted clusters)
+and random 2-D positions.  It holds
 none of the IVHD arithmetic (no distances, forces, updates or neighbour
 sampling), so both implementations can consume the same inputs without
 sharing any of the method.
@@ -169,6 +170,43 @@ def random_knn_graph(M: int, k: int, seed: int, *, hub_frac: float = 0.0,
         if todo.size:
             out[todo] = draw(todo.size)
     return out.astype(np.int32)
+
+
+def planted_knn_graph(M: int, k: int, seed: int, *, sizes: np.ndarray, p_out: float = 0.02):
+    """A kNN-shaped graph with planted clusters, and its cluster labels.
+
+    Vertex i belongs to cluster labels[i] (cluster c has sizes[c] vertices,
+    vertex order shuffled).  Each of its k distinct neighbours is drawn
+    uniformly from its own cluster with probability 1 - p_out, otherwise
+    uniformly from all vertices; self and repeated ids are redrawn (whole
+    rows, as in ``random_knn_graph``).  It has the cluster-local structure of
+    the kNN graph of a well-separated Gaussian mixture with these cluster
+    sizes, at sizes where the graph of the mixture itself cannot be computed
+    exactly on the host.  Returns ``(knn int32 [M, k], labels int32 [M])``.
+    """
+    sizes = np.asarray(sizes, dtype=np.int64)
+    assert int(sizes.sum()) == M and int(sizes.min()) > k
+    rng = _rng(seed)
+    labels = rng.permutation(np.repeat(np.arange(sizes.size, dtype=np.int64), sizes))
+    members = np.argsort(labels, kind="stable")          # vertices grouped by cluster
+    start = np.concatenate(([0], np.cumsum(sizes)[:-1]))
+
+    def draw(rows):
+        lab = labels[rows][:, None]
+        inside = members[start[lab] + (rng.random((rows.size, k)) * sizes[lab]).astype(np.int64)]
+        anywhere = rng.integers(0, M, size=(rows.size, k), dtype=np.int64)
+        return np.where(rng.random((rows.size, k)) < p_out, anywhere, inside)
+
+    out = draw(np.arange(M))
+    todo = np.arange(M)
+    while todo.size:
+        rows = out[todo]
+        srt = np.sort(rows, axis=1)
+        bad = (rows == todo[:, None]).any(axis=1) | (srt[:, 1:] == srt[:, :-1]).any(axis=1)
+        todo = todo[bad]
+        if todo.size:
+            out[todo] = draw(todo)
+    return out.astype(np.int32), labels.astype(np.int32)
 
 
 def uniform_positions(M: int, seed: int, *, scale: float = 1.0) -> np.ndarray:
