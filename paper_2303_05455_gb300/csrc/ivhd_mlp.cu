@@ -23,6 +23,7 @@ struct ivhd_mlp {
   cudaStream_t stream = nullptr;
   int64_t n_params = 0;
   int64_t t = 0;          // Adam step counter
+  int last_rows = 0;      // rows of the last batch whose intermediates are held
   bool poisoned = false;
   // parameters: FP32 master, Adam moments, gradients (flat: W1 b1 W2 b2 W3 b3)
   float* w = nullptr;
@@ -262,6 +263,7 @@ cudaError_t refresh_copies(ivhd_mlp* P) {
 cudaError_t forward(ivhd_mlp* P, int B) {
   const Offs o = offsets(P->n_in, P->hidden);
   const int H = P->hidden;
+  P->last_rows = B;
   GemmEpilogue e1{kEpBiasGelu, H, P->z1, P->h1, P->w + o.b1, nullptr, 0};
   cudaError_t e = gemm_bf16_tn(P->xb, P->n_in, P->w1, P->n_in, B, H, P->n_in, e1, P->err, P->stream);
   GemmEpilogue e2{kEpBiasGelu, H, P->z2, P->h2, P->w + o.b2, nullptr, 0};
@@ -524,5 +526,30 @@ ivhd_status ivhd_mlp_forward(ivhd_mlp* P, const void* x, int32_t x_dtype, float 
 }
 
 int64_t ivhd_mlp_launches(ivhd_mlp* P) { return P ? P->launches : -1; }
+
+ivhd_status ivhd_mlp_activations(ivhd_mlp* P, int32_t which, void* out, int64_t* rows) {
+  if (!P || !out || !rows) return IVHD_ERR_ARG;
+  if (P->poisoned) return IVHD_ERR_STATE;
+  const int64_t B = P->last_rows, H = P->hidden;
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (which) {
+    case IVHD_MLP_X: src = P->xb; bytes = (size_t)(B * P->n_in) * 2; break;
+    case IVHD_MLP_Z1: src = P->z1; bytes = (size_t)(B * H) * 4; break;
+    case IVHD_MLP_H1: src = P->h1; bytes = (size_t)(B * H) * 2; break;
+    case IVHD_MLP_Z2: src = P->z2; bytes = (size_t)(B * H) * 4; break;
+    case IVHD_MLP_H2: src = P->h2; bytes = (size_t)(B * H) * 2; break;
+    case IVHD_MLP_Y: src = P->y; bytes = (size_t)(B * 2) * 4; break;
+    case IVHD_MLP_DY: src = P->dy; bytes = (size_t)(B * 2) * 4; break;
+    case IVHD_MLP_DZ2: src = P->dz2; bytes = (size_t)(B * H) * 2; break;
+    case IVHD_MLP_DZ1: src = P->dz1; bytes = (size_t)(B * H) * 2; break;
+    default: return IVHD_ERR_ARG;
+  }
+  *rows = B;
+  if (B == 0) return IVHD_OK;
+  cudaError_t e = cudaMemcpyAsync(out, src, bytes, cudaMemcpyDefault, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  return mlp_fail(P, e);
+}
 
 }  // extern "C"

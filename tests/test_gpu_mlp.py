@@ -1,14 +1,24 @@
 """Learned warm start: the MLP's forward pass, gradients and Adam step vs the FP64 oracle.
 
-The oracle rounds to BF16 at the points where the GPU stores BF16 (inputs,
-W1/W2 copies, h1, h2, dz1, dz2), so the comparison isolates FP32 accumulation
-order; a BF16 rounding that lands on the other side of a tie moves one element
-by 2^-8 relative, hence the norm-wise tolerances below.
+Layer by layer, element by element: every intermediate array of the GPU
+network (read back with ``ivhd_mlp_activations``) and every gradient is
+compared with the oracle's formula evaluated on the GPU's own inputs to that
+layer, within the bound its arithmetic allows (``mlp_bounds``: the FP32
+accumulation bound of a K-term dot product, FP32 GELU error, and a BF16 store
+that may round either way only where its interval straddles a rounding
+boundary).  The input conversion is bit-exact.
+
+The whole network is also compared with the oracle run from the original
+inputs (BF16 rounding emulated at the same points).  There a BF16 store
+whose FP32 value lies next to a rounding boundary may land on the other side
+and move one element by a BF16 step (2^-8 relative), which then propagates;
+that composition is checked norm-wise.
 """
 import numpy as np
 import pytest
 import torch
 
+from mlp_bounds import U, assert_bf16_store, assert_within, dot_radius, gamma, gelu_fp32_radius
 from oracle import mlp as omlp
 from paper_2303_05455_gb300 import ivhd, synth
 
@@ -64,6 +74,57 @@ def test_gradients_and_loss_match_oracle():
     gp = unflat(g.cpu().numpy(), 784, 512)
     for n in p.names():
         assert rel(getattr(gp, n), g_ref[n]) < 5e-3, n
+
+
+def test_each_layer_matches_oracle_at_its_own_inputs():
+    B, n_in, H = 256, 784, 512
+    X, T, net, p = setup(B, n_in, H)
+    T32 = T.astype(np.float32).astype(np.float64)
+    loss, g = net.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).float().cuda(),
+                            x_scale=1 / 255)
+    a = {n: net.activations(n).astype(np.float64)
+         for n in ("x", "z1", "h1", "z2", "h2", "y", "dy", "dz2", "dz1")}
+    # input rows: x * fl32(1/255) in FP32, rounded to BF16 -- bit-exact
+    x_ref = omlp.bf16(X.astype(np.float32) * np.float32(1 / 255))
+    assert np.array_equal(a["x"], x_ref)
+    W1, W2 = omlp.bf16(p.W1), omlp.bf16(p.W2)          # the BF16 weight copies
+    # forward: pre-activations are K-term FP32 dot products, activations BF16 stores
+    z1 = a["x"] @ W1.T + p.b1
+    assert_within(a["z1"], z1, dot_radius(a["x"], W1.T, bias=p.b1), "z1")
+    assert_bf16_store(a["h1"], omlp.gelu(a["z1"]), gelu_fp32_radius(a["z1"]), "h1")
+    z2 = a["h1"] @ W2.T + p.b2
+    assert_within(a["z2"], z2, dot_radius(a["h1"], W2.T, bias=p.b2), "z2")
+    assert_bf16_store(a["h2"], omlp.gelu(a["z2"]), gelu_fp32_radius(a["z2"]), "h2")
+    y = a["h2"] @ p.W3.T + p.b3
+    assert_within(a["y"], y, dot_radius(a["h2"], p.W3.T, bias=p.b3), "y")
+    # loss and backward
+    dy = 2.0 * (a["y"] - T32) / B
+    assert_within(a["dy"], dy, 4 * U * np.abs(dy), "dY")
+    assert loss == pytest.approx(((a["y"] - T32) ** 2).sum() / B, rel=1e-6)
+    gp = unflat(g.cpu().numpy(), n_in, H)
+    assert_within(gp.W3, a["dy"].T @ a["h2"], dot_radius(a["dy"].T, a["h2"]), "dW3")
+    assert_within(gp.b3, a["dy"].sum(axis=0), gamma(B) * np.abs(a["dy"]).sum(axis=0), "db3")
+    dh2 = a["dy"] @ p.W3
+    gg2 = omlp.gelu_grad(a["z2"])
+    pre2 = dh2 * gg2
+    r2 = (dot_radius(a["dy"], p.W3) * np.abs(gg2) + np.abs(dh2) * gelu_fp32_radius(a["z2"])
+          + 2 * U * np.abs(pre2))
+    assert_bf16_store(a["dz2"], pre2, r2, "dZ2")
+    assert_within(gp.W2, a["dz2"].T @ a["h1"], dot_radius(a["dz2"].T, a["h1"], 8), "dW2")
+    assert_within(gp.b2, a["dz2"].sum(axis=0), gamma(B) * np.abs(a["dz2"]).sum(axis=0), "db2")
+    dh1 = a["dz2"] @ W2
+    gg1 = omlp.gelu_grad(a["z1"])
+    pre1 = dh1 * gg1
+    r1 = (dot_radius(a["dz2"], W2) * np.abs(gg1) + np.abs(dh1) * gelu_fp32_radius(a["z1"])
+          + 2 * U * np.abs(pre1))
+    assert_bf16_store(a["dz1"], pre1, r1, "dZ1")
+    assert_within(gp.W1, a["dz1"].T @ a["x"], dot_radius(a["dz1"].T, a["x"], 8), "dW1")
+    assert_within(gp.b1, a["dz1"].sum(axis=0), gamma(B) * np.abs(a["dz1"]).sum(axis=0), "db1")
+    # the bounds are tight enough to mean something: a few BF16 stores at most may round
+    # the other way, and the FP32 accumulation radius stays far below the values
+    for n, pre, rr in (("dz1", pre1, r1), ("dz2", pre2, r2)):
+        assert (a[n] != omlp.bf16(pre)).mean() < 0.01, n
+    assert np.median(dot_radius(a["x"], W1.T, bias=p.b1) / (np.abs(z1) + 1e-30)) < 1e-2
 
 
 def test_adam_step_matches_closed_form():
