@@ -11,6 +11,7 @@ import torch
 
 import oracle
 from paper_2303_05455_gb300 import ivhd, synth
+from step_bounds import close_elem, force_error_bound, step_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -54,9 +55,15 @@ def test_steps_at_full_size(opt):
     assert np.array_equal(y0, oracle.init_positions(w.M, w.seed).astype(np.float32))
     oid = oracle.OPT_MOMENTUM if opt == "momentum" else oracle.OPT_ADADELTA
     st = oracle.State.fresh(y0)
+    F0 = oracle.forces(y0, terms, w.c)
     emb.step(1)
     oracle.step(st, terms, w.c, oid, a=w.a, b=w.b)
-    close(emb.positions(host=True), st.Y)
+    y1 = emb.positions(host=True)
+    close(y1, st.Y)
+    d_ref = st.Y - y0     # the displacement of the step, element by element at its own scale
+    close_elem(y1 - y0, d_ref,
+               step_bound(opt, st.Y, d_ref, F0, force_error_bound(y0, terms, w.c), w.a, w.b),
+               "displacement")
     emb.step(4)
     oracle.run(st, terms, w.c, 4, oid, a=w.a, b=w.b)
     close(emb.positions(host=True), st.Y)

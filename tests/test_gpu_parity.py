@@ -6,6 +6,13 @@ relative, measured against the largest magnitude of the oracle array
 its term magnitudes, far inside 1e-5).  Integer work (random neighbours, kNN
 ids, neighbour sets of the quality criteria, layout counters) must match
 exactly: every such decision is made in the same precision on both sides.
+
+The update is also checked at its own scale: the displacement y' - y of one
+step, element by element, within 1e-5 of the largest oracle displacement
+plus what FP32 arithmetic allows for that element (``step_bound``): the
+force's FP32 summation bound, gamma(n) times the sum of the magnitudes of its
+n terms, carried through the optimiser's sensitivity d(y')/dF, a few
+roundings of the update itself and the roundings of storing y' in FP32.
 """
 import numpy as np
 import pytest
@@ -14,6 +21,7 @@ import torch
 import oracle
 from paper_2303_05455_gb300 import ivhd, synth
 from paper_2303_05455_gb300._lib import IvhdError
+from step_bounds import close_elem, force_error_bound, step_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -117,11 +125,18 @@ def test_one_step_and_ten_steps(case, opt, dedup, hub_threshold):
     rn, _ = oracle.random_neighbors(knn, r, 11)
     terms = oracle.build_terms(knn, rn, dedup=dedup)
     y0 = emb.positions(host=True).astype(np.float64)
-    close(emb.forces(host=True), oracle.forces(y0, terms, c))
+    F0 = oracle.forces(y0, terms, c)
+    close(emb.forces(host=True), F0)
     st = oracle.State.fresh(y0)
     emb.step(1)
     oracle.step(st, terms, c, OPT_ID[opt], a=a, b=b)
-    close(emb.positions(host=True), st.Y)
+    y1 = emb.positions(host=True)
+    close(y1, st.Y)
+    # the displacement of the step, element by element at its own scale
+    d_ref = st.Y - y0
+    close_elem(y1 - y0, d_ref,
+               step_bound(opt, st.Y, d_ref, F0, force_error_bound(y0, terms, c), a, b),
+               "displacement")
     emb.step(9)
     oracle.run(st, terms, c, 9, OPT_ID[opt], a=a, b=b)
     close(emb.positions(host=True), st.Y)
@@ -129,6 +144,59 @@ def test_one_step_and_ten_steps(case, opt, dedup, hub_threshold):
     y10 = emb.positions(host=True).astype(np.float64)
     close(emb.forces(host=True), oracle.forces(y10, terms, c))
     assert emb.stress() == pytest.approx(oracle.stress(y10, terms, c), rel=1e-5)
+
+
+@pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
+def test_one_step_from_a_given_state_at_the_step_scale(opt):
+    """One step from a chosen optimiser state: the momentum term a v, Nesterov's
+    look-ahead and Adadelta's accumulators all enter the displacement."""
+    # every vertex has the same symmetric degree (circulant graph, no random
+    # neighbours), so the internal vertex order is the input order and a
+    # checkpoint's arrays can be written directly
+    M, a, b, c = 3000, 0.9, 0.01, 0.01
+    i = np.arange(M)
+    knn = np.stack([(i + 1) % M, (i + 7) % M, (i + 100) % M], axis=1).astype(np.int32)
+    emb = ivhd.Embedding(knn, r=0, c=c, opt=opt, a=a, b=b, seed=3)
+    rng = np.random.default_rng(5)
+    y = (rng.random((M, 2)) * 3.0).astype(np.float32)
+    s1 = (rng.standard_normal((M, 2)) * 0.02).astype(np.float32)
+    s2 = None
+    if opt == "adadelta":
+        s1 = (rng.random((M, 2)) * 0.5).astype(np.float32)        # E[g^2]
+        s2 = (rng.random((M, 2)) * 1e-4).astype(np.float32)       # E[dx^2]
+    blob = bytearray(emb.get_state())
+    arrays = [y, s1] + ([s2] if s2 is not None else [])
+    head = len(blob) - len(arrays) * M * 8
+    stored_y = y
+    if opt == "nesterov":        # the state holds the look-ahead point y + a v
+        stored_y = (y.astype(np.float64) + np.float32(a) * s1.astype(np.float64)).astype(np.float32)
+    for q, arr in enumerate([stored_y] + arrays[1:]):
+        blob[head + q * M * 8: head + (q + 1) * M * 8] = arr.tobytes()
+    emb.set_state(bytes(blob))
+    y_gpu0 = emb.positions(host=True).astype(np.float64)
+    if opt != "nesterov":
+        assert np.array_equal(y_gpu0, y)                     # input order == internal order
+    rn = np.zeros((M, 0), np.int32)
+    terms = oracle.build_terms(knn, rn)
+    st = oracle.State(y_gpu0.copy(), s1.astype(np.float64),
+                      np.zeros((M, 2)) if s2 is None else s2.astype(np.float64))
+    if opt == "nesterov":        # the oracle's look-ahead y + a v must be the GPU's stored point
+        st.Y = stored_y.astype(np.float64) - a * st.S1
+    y_start = st.Y.copy()
+    F_at = oracle.forces(y_start + (a * st.S1 if opt == "nesterov" else 0.0), terms, c)
+    F_err = force_error_bound(y_start + (a * st.S1 if opt == "nesterov" else 0.0), terms, c)
+    v0 = st.S1.copy() if opt != "adadelta" else None
+    oracle.step(st, terms, c, OPT_ID[opt], a=a, b=b)
+    emb.step(1)
+    y1 = emb.positions(host=True)
+    d_ref = st.Y - y_start
+    bound = step_bound(opt, st.Y, d_ref, F_at, F_err, a, b, v0=v0,
+                       s1=None if opt != "adadelta" else s1.astype(np.float64),
+                       s2=None if s2 is None else s2.astype(np.float64))
+    close_elem(y1 - y_start, d_ref, bound, "displacement from a given state")
+    # the momentum term is a large part of this step: a wrong coefficient would show
+    if opt == "momentum":
+        assert np.abs(a * v0).max() > 100 * bound.max()
 
 
 @pytest.mark.parametrize("vpw", [1, 2, 4, 8])
