@@ -220,6 +220,22 @@ ivhd_status ivhd_autotune(ivhd_ctx *ctx, int32_t trial_steps, int32_t *best_bloc
 ivhd_status ivhd_set_positions(ivhd_ctx *ctx, const float *xy, int32_t on_device);
 
 /*
+ * Warm start with plain IVHD as the fallback (Sec. 3.4: IVHD also serves as,
+ * and can start from, an initial configuration; here the placement of a
+ * learned network or any other method).  Evaluates the stress E (Eq. 3.16)
+ * of the current positions and of the placement xy (M*2 FP32, input vertex
+ * order; host or device per on_device) on the GPU, and keeps the placement
+ * only if its stress is finite and strictly below the current one (a
+ * non-finite current stress counts as +inf); otherwise the current positions
+ * are restored.  *taken (host) receives 1 if the placement was kept, else 0.
+ * Either way the optimiser state is zeroed, as by ivhd_set_positions.  For a
+ * batch context the rule applies to the summed stress of all embeddings.
+ * Synchronises.  Errors: IVHD_ERR_ARG, IVHD_ERR_STATE, IVHD_ERR_OOM,
+ * IVHD_ERR_CUDA.
+ */
+ivhd_status ivhd_warm_start(ivhd_ctx *ctx, const float *xy, int32_t on_device, int32_t *taken);
+
+/*
  * Runs n_iter synchronous steps (Sec. 5.2 scheme: all forces from the same
  * configuration, then all updates).  Each step is one launch of the fused
  * gather-force + optimiser kernel; steps are replayed from a CUDA graph.
@@ -563,6 +579,28 @@ ivhd_status ivhd_mlp_forward(ivhd_mlp *mlp, const void *x, int32_t x_dtype, floa
                              int64_t n, float *y);
 /* Kernels launched by this network so far. */
 int64_t ivhd_mlp_launches(ivhd_mlp *mlp);
+
+/*
+ * Intermediate values of the last batch the network processed (the last
+ * max_batch-row chunk of ivhd_mlp_forward, or the batch of the last
+ * ivhd_mlp_loss_grad / ivhd_mlp_train_step), for inspecting the network layer
+ * by layer.  The paper has no counterpart.  `which` selects one row-major
+ * array of *rows rows:
+ *   IVHD_MLP_X    input rows as BF16 (rows x n_in, 2-byte BF16 bit patterns)
+ *   IVHD_MLP_Z1   W1 x + b1, FP32 (rows x hidden)
+ *   IVHD_MLP_H1   GELU(z1) as BF16     IVHD_MLP_Z2  W2 h1 + b2, FP32
+ *   IVHD_MLP_H2   GELU(z2) as BF16     IVHD_MLP_Y   W3 h2 + b3, FP32 (rows x 2)
+ *   IVHD_MLP_DY   dL/dy = 2 (y - t) / rows, FP32 (rows x 2; training calls)
+ *   IVHD_MLP_DZ2  (dY W3) * GELU'(z2) as BF16 (training calls)
+ *   IVHD_MLP_DZ1  (dZ2 W2) * GELU'(z1) as BF16 (training calls)
+ * out: host or device memory large enough for max_batch rows.  *rows = 0
+ * before the first batch.  Synchronises.  Errors: IVHD_ERR_ARG, IVHD_ERR_STATE.
+ */
+enum {
+    IVHD_MLP_X = 0, IVHD_MLP_Z1 = 1, IVHD_MLP_H1 = 2, IVHD_MLP_Z2 = 3, IVHD_MLP_H2 = 4,
+    IVHD_MLP_Y = 5, IVHD_MLP_DY = 6, IVHD_MLP_DZ2 = 7, IVHD_MLP_DZ1 = 8
+};
+ivhd_status ivhd_mlp_activations(ivhd_mlp *mlp, int32_t which, void *out, int64_t *rows);
 
 /*
  * ivhd_eval_qnx_static -- ivhd_eval_qnx that allocates no device memory.

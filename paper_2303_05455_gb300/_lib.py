@@ -30,6 +30,7 @@ SYMBOLS = (
     "ivhd_test_live_allocs", "ivhd_set_allocator", "ivhd_knn_query", "ivhd_place_nn",
     "ivhd_check_violations", "ivhd_test_corrupt_layout", "ivhd_probe_grid_barrier_timeout",
     "ivhd_knn_index_create", "ivhd_knn_index_query", "ivhd_knn_index_destroy",
+    "ivhd_mlp_activations", "ivhd_warm_start",
 )
 
 # callback types of ivhd_set_allocator
@@ -103,6 +104,8 @@ def load(build_if_missing: bool = False):
                               ctypes.POINTER(P)]
     L.ivhd_create.restype = i32
     L.ivhd_set_positions.argtypes = [P, P, i32]
+    L.ivhd_warm_start.argtypes = [P, P, i32, ctypes.POINTER(ctypes.c_int32)]
+    L.ivhd_warm_start.restype = i32
     L.ivhd_step.argtypes = [P, i64]
     L.ivhd_positions.argtypes = [P, P, i32]
     L.ivhd_forces.argtypes = [P, P, i32]
@@ -197,6 +200,8 @@ def load(build_if_missing: bool = False):
     L.ivhd_mlp_forward.restype = i32
     L.ivhd_mlp_launches.argtypes = [P]
     L.ivhd_mlp_launches.restype = i64
+    L.ivhd_mlp_activations.argtypes = [P, i32, P, ctypes.POINTER(ctypes.c_int64)]
+    L.ivhd_mlp_activations.restype = i32
     _lib = L
     return L
 

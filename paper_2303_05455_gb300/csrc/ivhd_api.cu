@@ -643,6 +643,55 @@ ivhd_status ivhd_stress(ivhd_ctx* ctx, double* out) {
   return flag ? IVHD_ERR_NONFINITE : IVHD_OK;
 }
 
+ivhd_status ivhd_warm_start(ivhd_ctx* ctx, const float* xy, int32_t on_device, int32_t* taken) {
+  NvtxScope nvtx_("ivhd_warm_start");
+  if (!ctx || !xy || !taken) return IVHD_ERR_ARG;
+  if (ctx->poisoned) return IVHD_ERR_STATE;
+  *taken = 0;
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->M;
+  // stress of the current positions (non-finite counts as +inf)
+  double e0 = 0.0;
+  ivhd_status st = ivhd_stress(ctx, &e0);
+  if (st == IVHD_ERR_NONFINITE) e0 = INFINITY;
+  else if (st != IVHD_OK) return st;
+  // keep the current positions (input order) to fall back to
+  float2* keep = nullptr;
+  cudaError_t e = dalloc(&keep, M, s);
+  if (e != cudaSuccess) return fail(ctx, e);
+  e = launch_unpermute(ctx, keep);
+  const float2* src = (const float2*)xy;
+  float2* tmp = nullptr;
+  if (e == cudaSuccess && !on_device) {
+    e = dalloc(&tmp, M, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tmp, xy, (size_t)M * sizeof(float2), cudaMemcpyHostToDevice, s);
+    src = tmp;
+  }
+  if (e == cudaSuccess) e = launch_set_positions(ctx, src);
+  double e1 = INFINITY;
+  if (e == cudaSuccess) {
+    st = ivhd_stress(ctx, &e1);
+    if (st == IVHD_ERR_NONFINITE) {
+      e1 = INFINITY;
+    } else if (st != IVHD_OK) {
+      if (tmp) dev_free(tmp, s);
+      dev_free(keep, s);
+      return st;
+    }
+  }
+  if (e == cudaSuccess) {
+    if (e1 < e0)
+      *taken = 1;
+    else
+      e = launch_set_positions(ctx, keep);  // plain IVHD's start stays, state zeroed
+  }
+  if (tmp) dev_free(tmp, s);
+  dev_free(keep, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return fail(ctx, e);
+}
+
 ivhd_status ivhd_random_neighbors(ivhd_ctx* ctx, int32_t* out, int32_t on_device) {
   if (!ctx || !out) return IVHD_ERR_ARG;
   if (ctx->poisoned) return IVHD_ERR_STATE;

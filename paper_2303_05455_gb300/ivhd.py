@@ -159,23 +159,20 @@ class Embedding:
         return out
 
     def warm_start(self, xy) -> bool:
-        """Starts from the placement xy (M x 2, e.g. the warm-start network's
-        output) when its stress is finite and below that of the current
-        positions (the seeded uniform start right after create); otherwise keeps
-        the current positions, so plain IVHD is the placement's fallback.  Both
-        stresses are evaluated on the GPU (ivhd_stress).  Zeroes the optimiser
-        state either way.  Returns whether the placement was taken."""
-        y0 = self.positions().clone()
-        e0 = self.stress()
-        self.set_positions(xy)
-        try:
-            e1 = self.stress()
-        except IvhdError:
-            e1 = float("inf")
-        if e1 < e0:
-            return True
-        self.set_positions(y0)
-        return False
+        """ivhd_warm_start: starts from the placement xy (M x 2, e.g. the warm-start
+        network's output) when its stress is finite and below that of the current
+        positions, else keeps them (plain IVHD is the fallback).  Zeroes the
+        optimiser state either way.  Returns whether the placement was taken."""
+        taken = ctypes.c_int32()
+        if isinstance(xy, np.ndarray):
+            arr = np.ascontiguousarray(xy, dtype=np.float32)
+            check(self._L.ivhd_warm_start(self._h, arr.ctypes.data, 0, ctypes.byref(taken)),
+                  "ivhd_warm_start")
+            return bool(taken.value)
+        t = xy.to(dtype=torch.float32).contiguous()
+        check(self._L.ivhd_warm_start(self._h, t.data_ptr(), int(t.is_cuda), ctypes.byref(taken)),
+              "ivhd_warm_start")
+        return bool(taken.value)
 
     def stress(self) -> float:
         v = ctypes.c_double()
@@ -489,14 +486,16 @@ def use_torch_allocator(device=None) -> None:
     set_allocator(alloc, free)
 
 
-def gemm_bf16_tn(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+def gemm_bf16_tn(A: torch.Tensor, B: torch.Tensor, stream=None,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
     """C = A @ B.T on the tensor cores: A [M, K], B [N, K] BF16 CUDA tensors -> FP32 [M, N]."""
     L = _lib.load()
     A = A.to(torch.bfloat16).contiguous()
     B = B.to(torch.bfloat16).contiguous()
     M, K = A.shape
     N = B.shape[0]
-    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
+    assert C.dtype == torch.float32 and C.is_contiguous() and tuple(C.shape) == (M, N)
     check(L.ivhd_gemm_bf16_tn(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K,
                               _stream_ptr(stream)), "ivhd_gemm_bf16_tn")
     return C
@@ -587,3 +586,20 @@ class MLP:
 
     def launches(self) -> int:
         return int(self._L.ivhd_mlp_launches(self._h))
+
+    _ACT = {"x": (0, "bf16", "in"), "z1": (1, "f32", "h"), "h1": (2, "bf16", "h"),
+            "z2": (3, "f32", "h"), "h2": (4, "bf16", "h"), "y": (5, "f32", 2),
+            "dy": (6, "f32", 2), "dz2": (7, "bf16", "h"), "dz1": (8, "bf16", "h")}
+
+    def activations(self, which: str) -> np.ndarray:
+        """One intermediate array of the last batch (ivhd_mlp_activations), as float32."""
+        code, kind, width = self._ACT[which]
+        cols = self.n_in if width == "in" else (self.hidden if width == "h" else 2)
+        buf = np.empty((self.max_batch, cols), dtype=np.uint16 if kind == "bf16" else np.float32)
+        rows = ctypes.c_int64()
+        check(self._L.ivhd_mlp_activations(self._h, code, buf.ctypes.data, ctypes.byref(rows)),
+              "ivhd_mlp_activations")
+        out = buf[:rows.value]
+        if kind == "bf16":
+            out = (out.astype(np.uint32) << 16).view(np.float32)
+        return np.ascontiguousarray(out)

@@ -189,6 +189,10 @@ def test_persistent_grid_needs_fp32_gathers_without_adaptive_b(L):
 
 
 def test_new_entry_points_reject_null(L):
+    assert L.ivhd_warm_start(None, None, 0, None) == -1
+    taken = ctypes.c_int32(7)
+    assert L.ivhd_warm_start(None, ctypes.c_void_p(16), 0, ctypes.byref(taken)) == -1
+    assert L.ivhd_mlp_activations(None, 0, None, None) == -1
     assert L.ivhd_set_metric(None, 0) == -1
     assert L.ivhd_resample_random_neighbors(None, 1) == -1
     assert L.ivhd_restrict_nn(None, None, 0, 0) == -1

@@ -105,3 +105,44 @@ def test_warm_start_gains_over_random_start():
     # same kNN precision after the same number of steps
     assert abs(warm[STEPS]["qnx"] - plain[STEPS]["qnx"]) <= 0.01
     assert warm[STEPS]["cf10"] >= plain[STEPS]["cf10"] - 0.01
+
+
+def test_warm_start_rule_through_the_c_abi():
+    """ivhd_warm_start as a C caller sees it: a better placement is kept, a non-finite
+    or worse one leaves the current positions bit for bit; the state is zeroed."""
+    import ctypes
+
+    import oracle
+    from paper_2303_05455_gb300 import _lib
+
+    L = _lib.load()
+    w = synth.WORKLOADS["gmm2k"]
+    X, _ = synth.workload_features(w)
+    knn = oracle.knn_f32(X, w.k)
+    rn, _ = oracle.random_neighbors(knn, w.r, w.seed)
+    terms = oracle.build_terms(knn, rn)
+    st = oracle.State.fresh(oracle.init_positions(w.M, w.seed))
+    oracle.run(st, terms, w.c, 200, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    good = st.Y.astype(np.float32)                       # the oracle's own partial embedding
+    e = ivhd.Embedding(knn, r=w.r, c=w.c, a=w.a, b=w.b, seed=w.seed)
+    e.step(3)                                            # non-zero velocity to be cleared
+    y_cur = e.positions(host=True)
+    taken = ctypes.c_int32(-1)
+    nan = good.copy()
+    nan[5, 1] = np.nan
+    for bad in (nan, good * 1e3):
+        assert L.ivhd_warm_start(e._h, bad.ctypes.data, 0, ctypes.byref(taken)) == 0
+        assert taken.value == 0
+        assert np.array_equal(e.positions(host=True), y_cur)
+    good_d = torch.from_numpy(good).cuda()
+    assert L.ivhd_warm_start(e._h, good_d.data_ptr(), 1, ctypes.byref(taken)) == 0
+    assert taken.value == 1
+    assert np.array_equal(e.positions(host=True), good)
+    assert e.stress() == pytest.approx(oracle.stress(good.astype(np.float64), terms, w.c), rel=1e-5)
+    # the optimiser state was zeroed: the next step is a first step from the placement
+    ref = oracle.State.fresh(good)
+    oracle.step(ref, terms, w.c, oracle.OPT_MOMENTUM, a=w.a, b=w.b)
+    e.step(1)
+    got = e.positions(host=True)
+    assert np.abs(got - ref.Y).max() <= 1e-5 * np.abs(ref.Y).max()
+    e.close()
