@@ -18,6 +18,21 @@ FP64 oracle on a bounded sample of the same workload on one core, and
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference this
 project has) on the same metric; under torchrun only rank 0 runs it.
+
+Besides the headline, the line carries the other workloads, each timed on
+its own with its clocks (``--no-extras`` skips them):
+
+* ``configs.gmm2k`` and ``configs.mnist70k`` (momentum and Adadelta): the same
+  whole-embedding step, its kernel time per iteration against the measured
+  random-gather bound, Q_NX / cf / stress of the result;
+* ``batch64``: 64 embeddings of uneven size in one context (FP32 / FP16 /
+  BF16 gathered positions, autotuned launch shape) against one-by-one FP32;
+* ``warmstart``: the learned warm start (training step, placement of a
+  1.4e6-point held-out set and of 10,000-point batches, IVHD refinement)
+  against plain IVHD from the uniform start.
+
+``--kernel step|knn|gemm|mlp|resident`` runs one kernel family alone (for
+timing and ncu captures) and prints its CUDA-event timings as JSON lines.
 """
 from __future__ import annotations
 
@@ -60,6 +75,21 @@ def parse_args():
     ap.add_argument("--variants", default="f16,bf16",
                     help="half-precision position formats also timed (comma list, or 'none')")
     ap.add_argument("--qnx-rows", type=int, default=10000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the gmm2k / mnist70k / batch64 / warmstart sub-objects")
+    cap = ap.add_argument_group("kernel capture modes (--kernel)")
+    cap.add_argument("--kernel", choices=["step", "knn", "gemm", "mlp", "resident"], default=None)
+    cap.add_argument("--graph", choices=["knn", "random"], default="knn",
+                     help="step: the workload's exact kNN graph or a kNN-shaped random graph")
+    cap.add_argument("--iters", type=int, default=200, help="step: iterations per repetition")
+    cap.add_argument("--reps", type=int, default=2)
+    cap.add_argument("--pos-format", default="f32", choices=["f32", "f16", "bf16"])
+    cap.add_argument("--data", choices=["gmm", "mnist"], default="gmm", help="knn: data set")
+    cap.add_argument("--M", type=int, default=200000, help="knn: rows")
+    cap.add_argument("--N", type=int, default=100, help="knn: float dimensions")
+    cap.add_argument("--shapes", default="8192x8192x8192,4096x512x784,4096x512x512,512x784x4096",
+                     help="gemm: M x N x K list")
+    cap.add_argument("--batch", type=int, default=4096, help="mlp: batch rows")
     return ap.parse_args()
 
 
@@ -493,6 +523,8 @@ def run_ours(args):
         "wall_s_timed_region": wall,
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(run_extras(args, dev, stream, flush, local_rank))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt = host_threads()
         o = oracle_sample(w, args.cpu_seconds, opt=args.opt, threads=nt)
@@ -516,10 +548,228 @@ def run_ours(args):
     return 0
 
 
+# -------------------------------------------------- the other workloads
+
+
+def config_subline(name: str, opts, dev, stream, flush, steps: int, warmup: int,
+                   gpu_index: int) -> dict:
+    """One smaller workload timed like the headline: per optimiser, whole embeddings
+    (create + n_iter steps + read-back) with CUDA events, the kernel time per
+    iteration against the measured random-gather bound, and the quality of the
+    result (Q_NX over every vertex up to 1e5 vertices, cf_2/10/100, stress)."""
+    import torch
+
+    from paper_2303_05455_gb300 import ivhd
+
+    w = synth.WORKLOADS[name]
+    X, labels = synth.workload_features(w)
+    knn = ivhd.knn_build(torch.from_numpy(X).to(dev), w.k)
+    rows = (torch.arange(w.M, dtype=torch.int64, device=dev) if w.M <= 100_000 else
+            torch.from_numpy(synth.sample_rows(w.M, 10_000, 12345)).to(dev))
+    lab = torch.from_numpy(labels).to(dev)
+    out_buf = torch.empty((w.M, 2), dtype=torch.float32, device=dev)
+    gpeak = ivhd.probe_gather(w.M, 16_777_216, 10)
+    res = {"config": workload_config(w, w.n_iter)}
+    for opt in opts:
+        def one(evs=None):
+            emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=opt, a=w.a, b=w.b, seed=w.seed,
+                                 stream=stream, device=dev)
+            if evs is not None:
+                evs[0].record(stream)
+            emb.step(w.n_iter)
+            if evs is not None:
+                evs[1].record(stream)
+            emb.positions(out=out_buf)
+            inf = emb.info()
+            try:
+                E = emb.stress() if evs is None else None
+            except ivhd.IvhdError:
+                E = float("nan")
+            emb.close()
+            return inf, E
+
+        for _ in range(warmup):
+            one()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        clocks = ClockSampler(gpu_index)
+        torch.cuda.synchronize()
+        launches = 0
+        for s_ in range(steps):
+            flush.zero_()
+            ev[s_][0].record(stream)
+            inf, _ = one((ev[s_][2], ev[s_][3]))
+            ev[s_][1].record(stream)
+            launches += inf["setup_launches"] + inf["kernel_launches"] + inf["aux_launches"]
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+        kms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+        inf, E = one()
+        launch_s = kms / 1e3 / w.n_iter
+        t_gather = inf["nnz_sym"] / gpeak
+        res[opt] = {
+            "value": inf["n_terms"] * w.n_iter / (ms / 1e3), "unit": UNIT, "s_to_embed": ms / 1e3,
+            "steps": steps, "warmup": warmup, "launch_us": 1e6 * launch_s,
+            "binding": {"bound": "l2_gather", "t_min_us": 1e6 * t_gather,
+                        "frac": t_gather / launch_s, "gather_peak": gpeak,
+                        "what": "kernel time per iteration against the row entries at the "
+                                "measured random-gather rate (ivhd_probe_gather, same size)"},
+            "quality": {"qnx": ivhd.eval_qnx(out_buf, knn, rows), "rows": int(rows.numel()),
+                        "cf": {str(nn): ivhd.eval_cf(out_buf, lab, nn, rows) for nn in (2, 10, 100)},
+                        "stress": E},
+            "terms": inf["n_terms"], "nnz_sym": inf["nnz_sym"], "gpu_launches": launches,
+            "clocks": clk}
+    return res
+
+
+def run_extras(args, dev, stream, flush, gpu_index: int) -> dict:
+    from paper_2303_05455_gb300 import bench_batch, bench_warmstart
+
+    out = {"configs": {
+        "gmm2k": config_subline("gmm2k", ["momentum"], dev, stream, flush, 5, 3, gpu_index),
+        "mnist70k": config_subline("mnist70k", ["momentum", "adadelta"], dev, stream, flush, 5, 3,
+                                   gpu_index)}}
+    clocks = ClockSampler(gpu_index)
+    out["batch64"] = bench_batch.measure()
+    out["batch64"]["clocks"] = clocks.stop()
+    clocks = ClockSampler(gpu_index)
+    out["warmstart"] = bench_warmstart.measure()
+    out["warmstart"]["clocks"] = clocks.stop()
+    return out
+
+
+# ------------------------------------------------------ kernel capture modes
+
+
+def run_capture(args):
+    """One kernel family alone, for timing and ncu captures (CUDA-event times as JSON)."""
+    import torch
+
+    from paper_2303_05455_gb300 import ivhd
+
+    s = torch.cuda.current_stream()
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    if args.kernel == "step":
+        w = synth.WORKLOADS[args.workload]
+        if args.graph == "knn":
+            X, _ = synth.workload_features(w)
+            knn = ivhd.knn_build(torch.from_numpy(X).cuda(), w.k)
+            del X
+        else:
+            knn = torch.from_numpy(synth.random_knn_graph(
+                w.M, w.k, w.seed + 1, hub_frac=0.02, n_hubs=max(w.k + 1, w.M // 1000))).cuda()
+        torch.cuda.synchronize()
+        for rep in range(args.reps):
+            t0 = time.perf_counter()
+            emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b, seed=w.seed,
+                                 pos_format=args.pos_format)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e0, e1 = events()
+            e0.record(s)
+            emb.step(args.iters)
+            e1.record(s)
+            torch.cuda.synchronize()
+            info = emb.info()
+            emb.close()
+            print(json.dumps({"rep": rep, "create_ms": 1e3 * (t1 - t0),
+                              "us_per_step": 1e3 * e0.elapsed_time(e1) / args.iters,
+                              "n_hub": info["n_hub"], "nnz_sym": info["nnz_sym"],
+                              "max_degree": info["max_degree"]}), flush=True)
+    elif args.kernel == "knn":
+        if args.data == "gmm":
+            X, _ = synth.gaussian_mixture(args.M, args.N, 50, 11)
+            K = -(-3 * args.N // 64) * 64
+        else:
+            X, _ = synth.mnist_like(args.M, 7, N=784)
+            K = -(-784 // 64) * 64
+        Xd = torch.from_numpy(X).cuda()
+        for rep in range(args.reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = ivhd.knn_build(Xd, 5, return_stats=True)
+            dt = time.perf_counter() - t0
+            print(json.dumps({"rep": rep, "seconds": dt,
+                              "tflops": 2.0 * args.M ** 2 * K / dt / 1e12, **st}), flush=True)
+    elif args.kernel == "gemm":
+        res = []
+        for sh in args.shapes.split(","):
+            M, N, K = (int(v) for v in sh.split("x"))
+            g = torch.Generator(device="cuda").manual_seed(M + N + K)
+            A = torch.randn((M, K), device="cuda", generator=g).to(torch.bfloat16)
+            B = torch.randn((N, K), device="cuda", generator=g).to(torch.bfloat16)
+            C = ivhd.gemm_bf16_tn(A, B)
+            e0, e1 = events()
+            e0.record(s)
+            for _ in range(args.reps):
+                ivhd.gemm_bf16_tn(A, B, out=C)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            ref = A[:64].float() @ B.float().T
+            res.append({"M": M, "N": N, "K": K, "ms_per_call": ms,
+                        "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12,
+                        "max_rel_err_rows0_63": float((C[:64] - ref).abs().max() / ref.abs().max())})
+        print(json.dumps(res), flush=True)
+    elif args.kernel == "mlp":
+        B = args.batch
+        net = ivhd.MLP(784, 512, max_batch=B)
+        net.init_params(0)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        X = torch.randint(0, 256, (B * 4, 784), dtype=torch.uint8, device="cuda", generator=g)
+        T = torch.randn((B * 4, 2), device="cuda", generator=g)
+        for _ in range(3):
+            net.train_step(X[:B], T[:B], lr=1e-3, x_scale=1 / 255)
+        torch.cuda.synchronize()
+        e0, e1 = events()
+        t = time.perf_counter()
+        e0.record(s)
+        for i in range(args.iters):
+            b = (i % 4) * B
+            net.train_step(X[b:b + B], T[b:b + B], lr=1e-3, x_scale=1 / 255)
+        e1.record(s)
+        host = time.perf_counter() - t
+        torch.cuda.synchronize()
+        f0, f1 = events()
+        f0.record(s)
+        net.forward(X, x_scale=1 / 255)
+        f1.record(s)
+        torch.cuda.synchronize()
+        print(json.dumps({"steps": args.iters, "gpu_ms_per_step": e0.elapsed_time(e1) / args.iters,
+                          "host_ms_per_step_enqueue": 1e3 * host / args.iters,
+                          "forward_rows": 4 * B, "forward_ms": f0.elapsed_time(f1)}), flush=True)
+        net.close()
+    elif args.kernel == "resident":
+        w = synth.WORKLOADS["gmm2k"]
+        X, _ = synth.workload_features(w)
+        knn = ivhd.knn_build(torch.from_numpy(X).cuda(), w.k)
+        for rep in range(args.reps):
+            out = {"rep": rep}
+            for resident in (True, "cluster", False):
+                emb = ivhd.Embedding(knn, r=w.r, c=w.c, a=w.a, b=w.b, seed=w.seed, opt=args.opt,
+                                     resident=resident)
+                emb.step(16)
+                e0, e1 = events()
+                e0.record(s)
+                emb.step(args.iters)
+                e1.record(s)
+                torch.cuda.synchronize()
+                key = {True: "resident_us", "cluster": "cluster_us", False: "multi_launch_us"}
+                out[key[resident]] = 1e3 * e0.elapsed_time(e1) / args.iters
+                emb.close()
+            print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return run_capture(args)
     return run_ours(args)
 
 

@@ -28,13 +28,10 @@ import torch
 from . import ivhd, synth
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--n-emb", type=int, default=64)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--qnx-rows", type=int, default=2000)
-    ap.add_argument("--formats", default="bf16,f16,f32")
-    args = ap.parse_args()
+def measure(n_emb: int = 64, steps: int = 1000, qnx_rows: int = 2000,
+            formats: str = "bf16,f16,f32") -> dict:
+    """Runs the comparison and returns its figures as a dict (see the module docstring)."""
+    args = argparse.Namespace(n_emb=n_emb, steps=steps, qnx_rows=qnx_rows, formats=formats)
     c, a, b = 0.01, 0.9, 0.001
     work = synth.batch_workload(n_emb=args.n_emb)
     t0 = time.perf_counter()
@@ -124,7 +121,17 @@ def main():
         "batched": batched_runs,
         "knn_build_s_untimed": knn_s,
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-emb", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--qnx-rows", type=int, default=2000)
+    ap.add_argument("--formats", default="bf16,f16,f32")
+    args = ap.parse_args()
+    print(json.dumps(measure(args.n_emb, args.steps, args.qnx_rows, args.formats)), flush=True)
 
 
 if __name__ == "__main__":

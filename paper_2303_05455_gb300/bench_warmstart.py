@@ -33,15 +33,11 @@ import torch
 from . import ivhd, synth
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=200000)
-    ap.add_argument("--holdout", type=int, default=1400000)
-    ap.add_argument("--epochs", type=int, default=10)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--check-every", type=int, default=100)
-    ap.add_argument("--rows", type=int, default=10000)
-    args = ap.parse_args()
+def measure(train: int = 200000, holdout: int = 1400000, epochs: int = 10, steps: int = 2000,
+            check_every: int = 100, rows: int = 10000) -> dict:
+    """Runs the comparison and returns its figures as a dict (see the module docstring)."""
+    args = argparse.Namespace(train=train, holdout=holdout, epochs=epochs, steps=steps,
+                              check_every=check_every, rows=rows)
     k, r, c, a, b = 5, 1, 0.01, 0.9, 0.001
     dev = torch.device("cuda")
     s = torch.cuda.current_stream()
@@ -90,8 +86,10 @@ def main():
                 losses.append(l)
     e1 = ev()
     torch.cuda.synchronize()
+    train_s = e0.elapsed_time(e1) / 1e3
     out["mlp_train"] = {"epochs": args.epochs, "steps": args.epochs * n_batches,
-                        "seconds": e0.elapsed_time(e1) / 1e3, "loss_last_batch_per_epoch": losses}
+                        "seconds": train_s, "ms_per_step": 1e3 * train_s / (args.epochs * n_batches),
+                        "loss_last_batch_per_epoch": losses}
 
     # 3. held-out set: MLP placement, then IVHD refinement vs plain IVHD
     Xh, Lh = synth.mnist_like(args.holdout, 7, noise_seed=2)
@@ -195,7 +193,33 @@ def main():
     rows_tr = torch.from_numpy(synth.sample_rows(args.train, args.rows, 9)).to(dev)
     out["arriving_batches"] = {"batch": 10000, "placed_by": res,
                                "train_embedding_cf10": ivhd.eval_cf(Ytr, Ltr_d, 10, rows_tr)}
-    print(json.dumps(out), flush=True)
+    refine = min(len(warm) - 1, max(1, 100 // args.check_every))
+    out["summary"] = {
+        "train_step_ms": out["mlp_train"]["ms_per_step"],
+        "placement_s": place_s,
+        "batch_10k_ms": {"mlp": float(np.median(res["mlp"]["latency_us"])) / 1e3,
+                         "nn": float(np.median(res["nn"]["latency_us"])) / 1e3},
+        "stress": {"plain_start": plain[0]["stress"], "warm_start": warm[0]["stress"],
+                   f"warm_after_{warm[refine]['step']}_steps": warm[refine]["stress"],
+                   f"plain_after_{plain[-1]['step']}_steps": plain[-1]["stress"],
+                   f"warm_after_{warm[-1]['step']}_steps": warm[-1]["stress"]},
+        "qnx_final": {"plain": plain[-1]["qnx"], "warm": warm[-1]["qnx"], "nn": nnw[-1]["qnx"]},
+        "equal_precision": abs(warm[-1]["qnx"] - plain[-1]["qnx"]) <= 0.01,
+    }
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=200000)
+    ap.add_argument("--holdout", type=int, default=1400000)
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--rows", type=int, default=10000)
+    args = ap.parse_args()
+    print(json.dumps(measure(args.train, args.holdout, args.epochs, args.steps, args.check_every,
+                             args.rows)), flush=True)
 
 
 if __name__ == "__main__":
