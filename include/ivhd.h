@@ -135,8 +135,23 @@ typedef struct {
                              random 200,000-vertex graph with hubs 16/4 11.0 against 12.0
                              for the best shape with 1; no gain on the exact kNN graphs of
                              70,000 and 1.4e6 points.  ivhd_autotune searches it */
+    int32_t order;        /* vertex order of the layout (ivhd_order); default
+                             IVHD_ORDER_DEGREE */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default stream */
 } ivhd_params;
+
+/*
+ * Vertex order of the step kernel's layout.  DEGREE: descending symmetric
+ * degree, ties in input order (rows of equal length share a warp; the paper's
+ * IVHD-CUDA sorts particles by connection count, Sec. 5.2).  DEGREE_CLUSTER:
+ * descending degree, then, among vertices of equal degree, grouped by the
+ * connected component of the undirected kNN graph that the vertex belongs to
+ * (components ordered by their smallest input id), then input order -- so
+ * that positions gathered together are stored together where the graph has
+ * cluster structure.  Results agree with DEGREE within FP32 rounding (the
+ * summation order of a vertex's terms follows the layout).
+ */
+typedef enum { IVHD_ORDER_DEGREE = 0, IVHD_ORDER_DEGREE_CLUSTER = 1 } ivhd_order;
 
 /* Fills *p with the defaults listed above.  p must not be NULL. */
 void ivhd_default_params(ivhd_params *p);
@@ -289,6 +304,10 @@ typedef struct {
     int64_t kernel_launches; /* step kernels launched since create */
     int64_t setup_launches;  /* kernels launched by ivhd_create (layout set-up) */
     int64_t aux_launches;    /* other kernels (positions, forces, stress, set/init) */
+    int32_t launch_form;     /* how ivhd_step runs: 0 one step kernel per step (CUDA-graph
+                                replay), 1 one block for the whole call, 2 a cluster of 8
+                                blocks for the whole call, 3 a persistent grid for the
+                                whole call (see ivhd_params.resident) */
 } ivhd_info_t;
 
 /* Fills *out.  Host only; does not synchronise. */

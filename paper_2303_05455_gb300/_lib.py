@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
         ("adaptive", ctypes.c_int32), ("tau", ctypes.c_float), ("gamma1", ctypes.c_float),
         ("gamma2", ctypes.c_float), ("block_size", ctypes.c_int32),
         ("resident", ctypes.c_int32), ("vertices_per_warp", ctypes.c_int32),
-        ("stream", ctypes.c_void_p),
+        ("order", ctypes.c_int32), ("stream", ctypes.c_void_p),
     ]
 
 
@@ -66,6 +66,7 @@ class Info(ctypes.Structure):
         ("max_degree", ctypes.c_int32), ("empty_rn", ctypes.c_int32),
         ("steps_done", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("setup_launches", ctypes.c_int64), ("aux_launches", ctypes.c_int64),
+        ("launch_form", ctypes.c_int32),
     ]
 
 

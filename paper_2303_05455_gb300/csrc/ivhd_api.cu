@@ -156,6 +156,7 @@ bool params_ok(const ivhd_params& p) {
   if (p.vertices_per_warp != 0 && p.vertices_per_warp != 1 && p.vertices_per_warp != 2 &&
       p.vertices_per_warp != 4 && p.vertices_per_warp != 8)
     return false;
+  if (p.order != IVHD_ORDER_DEGREE && p.order != IVHD_ORDER_DEGREE_CLUSTER) return false;
   if (p.adaptive) {
     if (p.opt == IVHD_OPT_ADADELTA) return false;
     if (!std::isfinite(p.tau) || p.tau <= 0.f) return false;
@@ -248,6 +249,7 @@ uint64_t fingerprint(const ivhd_ctx* ctx) {
   mix(&ctx->p.seed, sizeof(ctx->p.seed));
   mix(&ctx->p.dedup_mutual, sizeof(ctx->p.dedup_mutual));
   mix(&ctx->p.pos_format, sizeof(ctx->p.pos_format));
+  mix(&ctx->p.order, sizeof(ctx->p.order));
   mix(&ctx->p.adaptive, sizeof(ctx->p.adaptive));
   mix(&ctx->nnz_sym, sizeof(ctx->nnz_sym));
   return h;
@@ -719,6 +721,8 @@ ivhd_status ivhd_info(ivhd_ctx* ctx, ivhd_info_t* out) {
   out->kernel_launches = ctx->launches;
   out->setup_launches = ctx->setup_launches;
   out->aux_launches = ctx->aux_launches;
+  const int rm = ctx->ctl ? 0 : resident_mode(ctx);
+  out->launch_form = rm == 0 ? 0 : (rm <= 2 ? 1 : (rm == 3 ? 2 : 3));
   return IVHD_OK;
 }
 

@@ -151,6 +151,58 @@ __global__ void k_count_in(const int32_t* __restrict__ knn, const int32_t* __res
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(mutual, (unsigned long long)__popc(b));
 }
 
+// Connected components of the undirected kNN graph (nn entries only), for the
+// cluster-grouped vertex order: lab[i] ends as the smallest vertex id of i's
+// component, whatever order the atomics take.  Labels only decrease and
+// lab[x] <= x throughout, so every label chain ends at a root.
+__global__ void k_cc_init(int32_t* __restrict__ lab, int64_t M) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) lab[i] = (int32_t)i;
+}
+
+// Hooking: for an edge whose endpoints carry different labels, the larger
+// label's own slot takes the smaller label.
+__global__ void k_cc_hook(const int32_t* __restrict__ knn, int64_t M, int k,
+                          int32_t* __restrict__ lab, int32_t* __restrict__ changed) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * (int64_t)k) return;
+  const int32_t j = knn[e];
+  if (j < 0) return;
+  const int32_t a = lab[e / k], b = lab[j];
+  if (a == b) return;
+  atomicMin(&lab[a > b ? a : b], a < b ? a : b);
+  *changed = 1;
+}
+
+// Pointer jumping: every label is replaced by the root of its chain.
+__global__ void k_cc_jump(int32_t* __restrict__ lab, int64_t M) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  int32_t l = lab[i];
+  for (int64_t t = 0; t < M; ++t) {  // strictly decreasing chain: ends within M links
+    const int32_t n = lab[l];
+    if (n == l) break;
+    l = n;
+  }
+  lab[i] = l;
+}
+
+// (component label, vertex) pairs for the sort, and the degree key of a
+// permuted vertex list.
+__global__ void k_label_keys(const int32_t* __restrict__ lab, int64_t M, uint32_t* __restrict__ key,
+                             int32_t* __restrict__ val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  key[i] = (uint32_t)lab[i];
+  val[i] = (int32_t)i;
+}
+__global__ void k_gather_keys(const uint32_t* __restrict__ by_vertex,
+                              const int32_t* __restrict__ order, int64_t M,
+                              uint32_t* __restrict__ key) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < M) key[e] = by_vertex[order[e]];
+}
+
 // Degree (stored row entries) and the descending-degree sort key; totals
 // are reduced per block before one atomic per block and counter.
 __global__ void __launch_bounds__(256) k_degree(const int32_t* __restrict__ kv,
@@ -665,6 +717,8 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
   IVHD_TRY(cudaGetLastError());
 
   // 4. stable sort by descending degree: two 8-bit passes over the 16-bit key
+  //    (cluster order: first a stable sort by component label, whose order the
+  //    degree passes then keep among vertices of equal degree)
   {
     const int nb = (int)((M + kRadixBlock - 1) / kRadixBlock);
     const int64_t nc = (int64_t)nb * 256;
@@ -674,23 +728,71 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
     int32_t* offs = sc.get<int32_t>(nc + 1);
     int32_t* val1 = sc.get<int32_t>(M);
     if (!sc.ok) return IVHD_ERR_OOM;
-    // pass 0: (key0, val0) -> (key1, val1); pass 1: (key1, val1) -> (key0, perm)
-    for (int pass = 0; pass < 2; ++pass) {
-      const int shift = 8 * pass;
-      const uint32_t* kin = pass ? key1 : key0;
-      const int32_t* vin = pass ? val1 : val0;
-      uint32_t* kout = pass ? key0 : key1;
-      int32_t* vout = pass ? ctx->perm : val1;
+    auto radix_pass = [&](const uint32_t* kin, const int32_t* vin, uint32_t* kout, int32_t* vout,
+                          int shift) -> cudaError_t {
       k_radix_hist<<<nb, kRadixBlock, 0, s>>>(kin, M, shift, nb, counts);
       k_widen<<<nblk(nc), kB, 0, s>>>(counts, c64, nc);
       ctx->setup_launches += 2;
-      IVHD_TRY(cudaGetLastError());
-      IVHD_TRY(scan_i64(c64, o64, nc, s, sc, &ctx->setup_launches));
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      e = scan_i64(c64, o64, nc, s, sc, &ctx->setup_launches);
+      if (e != cudaSuccess) return e;
       k_offsets_i32<<<nblk(nc + 1), kB, 0, s>>>(o64, nc, 0, offs);
       k_radix_scatter<<<nb, kRadixBlock, 0, s>>>(kin, vin, kout, vout, M, shift, nb, offs);
       ctx->setup_launches += 2;
+      return cudaGetLastError();
+    };
+    const uint32_t* deg_kin = key0;
+    const int32_t* deg_vin = val0;
+    if (ctx->p.order == IVHD_ORDER_DEGREE_CLUSTER) {
+      int32_t* lab = sc.get<int32_t>(M);
+      int32_t* changed = sc.get<int32_t>(1);
+      uint32_t* ka = sc.get<uint32_t>(M);
+      uint32_t* kb = sc.get<uint32_t>(M);
+      int32_t* va = sc.get<int32_t>(M);
+      int32_t* vb = sc.get<int32_t>(M);
+      if (!sc.ok) return IVHD_ERR_OOM;
+      k_cc_init<<<nblk(M), kB, 0, s>>>(lab, M);
+      ++ctx->setup_launches;
+      for (int round = 0; round < 64; ++round) {  // converges in a few rounds
+        int32_t h_changed = 0;
+        IVHD_TRY(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
+        k_cc_hook<<<nblk(M * (int64_t)k), kB, 0, s>>>(ctx->knn, M, k, lab, changed);
+        k_cc_jump<<<nblk(M), kB, 0, s>>>(lab, M);
+        ctx->setup_launches += 2;
+        IVHD_TRY(cudaGetLastError());
+        IVHD_TRY(cudaMemcpyAsync(&h_changed, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        IVHD_TRY(cudaStreamSynchronize(s));
+        if (!h_changed) break;
+      }
+      k_label_keys<<<nblk(M), kB, 0, s>>>(lab, M, ka, va);
+      ++ctx->setup_launches;
       IVHD_TRY(cudaGetLastError());
+      int bits = 1;
+      while (bits < 31 && ((int64_t)1 << bits) < M) ++bits;
+      uint32_t* kin = ka;
+      int32_t* vin = va;
+      uint32_t* kout = kb;
+      int32_t* vout = vb;
+      for (int shift = 0; shift < bits; shift += 8) {
+        IVHD_TRY(radix_pass(kin, vin, kout, vout, shift));
+        uint32_t* kt = kin;
+        kin = kout;
+        kout = kt;
+        int32_t* vt = vin;
+        vin = vout;
+        vout = vt;
+      }
+      // vin: vertices by component; kout (free): their degree keys
+      k_gather_keys<<<nblk(M), kB, 0, s>>>(key0, vin, M, kout);
+      ++ctx->setup_launches;
+      IVHD_TRY(cudaGetLastError());
+      deg_kin = kout;
+      deg_vin = vin;
     }
+    // pass 0: (deg_kin, deg_vin) -> (key1, val1); pass 1: (key1, val1) -> (key0, perm)
+    IVHD_TRY(radix_pass(deg_kin, deg_vin, key1, val1, 0));
+    IVHD_TRY(radix_pass(key1, val1, key0, ctx->perm, 8));
   }
 
   // 5. sizes and offsets

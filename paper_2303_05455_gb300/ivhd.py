@@ -25,6 +25,7 @@ from ._lib import IvhdError, Info, Params, check
 OPTS = {"momentum": 0, "nesterov": 1, "adadelta": 2}
 POS_FORMATS = {"f32": 0, "f16": 1, "bf16": 2}
 METRICS = {"l2": 0, "l1": 1}
+ORDERS = {"degree": 0, "degree_cluster": 1}
 
 
 def _stream_ptr(stream) -> int | None:
@@ -51,8 +52,8 @@ class Embedding:
                  seed: int = 0, dedup_mutual: bool = False, init_uniform: bool = True,
                  hub_threshold: int = 0, pos_format: str = "f32", adaptive: bool = False,
                  tau: float = 0.5, gamma1: float = 1.1, gamma2: float = 0.5, block_size: int = 0,
-                 resident=None, vertices_per_warp: int = 0, stream=None, device=None,
-                 batch=None):
+                 resident=None, vertices_per_warp: int = 0, order: str = "degree",
+                 stream=None, device=None, batch=None):
         self._L = _lib.load()
         if device is None:
             device = torch.device("cuda", torch.cuda.current_device())
@@ -83,6 +84,7 @@ class Embedding:
         # "cluster" (8-block cluster), "grid" (persistent cooperative grid)
         p.resident = {None: 0, False: -1, True: 1, "cluster": 2, "grid": 3}[resident]
         p.vertices_per_warp = int(vertices_per_warp)
+        p.order = ORDERS[order]
         p.stream = self.stream.cuda_stream or None
         self.opt = opt
         self.params = p

@@ -396,3 +396,52 @@ def test_full_run_gmm2k_precision_matches_oracle(opt):
 def test_probe_gather_rate_is_plausible():
     rate = ivhd.probe_gather(1_400_000, 1 << 22, 3)
     assert 1e9 < rate < 1e13
+
+
+@pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
+@pytest.mark.parametrize("case", ["gmm2k", "hubs5k", "ragged37", "star"])
+def test_cluster_order_matches_oracle(case, opt):
+    """The cluster-grouped vertex order changes only where rows are stored (and so the
+    FP32 summation order): forces, steps and stress still match the oracle."""
+    knn, r, c = graph_case(case)
+    a, b = 0.9, 0.01
+    emb = ivhd.Embedding(knn, r=r, c=c, opt=opt, a=a, b=b, seed=11, order="degree_cluster",
+                         resident=False)
+    rn, _ = oracle.random_neighbors(knn, r, 11)
+    assert np.array_equal(emb.random_neighbors(), rn)
+    terms = oracle.build_terms(knn, rn)
+    y0 = emb.positions(host=True).astype(np.float64)
+    F0 = oracle.forces(y0, terms, c)
+    close(emb.forces(host=True), F0)
+    st = oracle.State.fresh(y0)
+    emb.step(1)
+    oracle.step(st, terms, c, OPT_ID[opt], a=a, b=b)
+    y1 = emb.positions(host=True)
+    close(y1, st.Y)
+    d_ref = st.Y - y0
+    close_elem(y1 - y0, d_ref,
+               step_bound(opt, st.Y, d_ref, F0, force_error_bound(y0, terms, c), a, b),
+               "displacement")
+    emb.step(9)
+    oracle.run(st, terms, c, 9, OPT_ID[opt], a=a, b=b)
+    close(emb.positions(host=True), st.Y)
+    y10 = emb.positions(host=True).astype(np.float64)
+    assert emb.stress() == pytest.approx(oracle.stress(y10, terms, c), rel=1e-5)
+
+
+def test_cluster_order_in_a_batch_matches_separate_contexts():
+    """Several embeddings in one context form separate components; the cluster order
+    keeps each embedding's results equal to its own context's within FP32 rounding."""
+    graphs = [graph_case("gmm2k")[0], synth.random_knn_graph(3000, 4, 9),
+              synth.random_knn_graph(500, 3, 10)]
+    seeds = [5, 6, 7]
+    emb = ivhd.Embedding.batch(graphs, r=1, seeds=seeds, c=0.01, a=0.9, b=0.01,
+                               order="degree_cluster")
+    emb.step(10)
+    Y = emb.positions(host=True)
+    lo = 0
+    for g, sd in zip(graphs, seeds):
+        one = ivhd.Embedding(g, r=1, c=0.01, a=0.9, b=0.01, seed=sd, resident=False)
+        one.step(10)
+        close(Y[lo:lo + g.shape[0]], one.positions(host=True).astype(np.float64))
+        lo += g.shape[0]
