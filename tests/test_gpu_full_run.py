@@ -11,7 +11,7 @@ graph: they are compared through what a run is judged by.
   near its random level (isotropic clusters carry no within-cluster structure
   a 2-D map could keep), so the neighbour hit and the stress are the
   discriminating checks.
-* Final stress E (Eq. 3.16) within STRESS_BAND (relative) of the oracle's.
+* Final stress E (Eq. 3.16) within 0.5 % (relative) of the oracle's.
 
 Inputs (never built by the CUDA path):
 
@@ -44,7 +44,8 @@ pytestmark = pytest.mark.gpu
 THREADS = max(1, len(os.sched_getaffinity(0)))
 QNX_BAND = 0.01     # the equal-kNN-precision bar
 CF_BAND = 0.01
-STRESS_BAND = 0.02  # relative; two runs of a chaotic iteration from the same start
+STRESS_BAND = 0.005  # relative; the final stress of two runs from the same start that
+#                     differ in rounding (FP32 or half-precision gathers vs FP64)
 OPT_ID = {"momentum": oracle.OPT_MOMENTUM, "adadelta": oracle.OPT_ADADELTA}
 
 _cache = {}

@@ -54,7 +54,15 @@ def test_one_step_with_rounded_gathers(fmt, opt, hub_threshold):
     np.testing.assert_array_equal(emb.positions(host=True), y1.astype(np.float32))
 
 
-@pytest.mark.parametrize("fmt", ["f32", "f16", "bf16"])
+# BF16 keeps 8 significant bits: at |y| ~ 20 its spacing is 0.125, coarser than
+# the within-cluster distances the nn terms pull towards 0, so the 2-D
+# neighbour sets of the 2,000-point run differ (Q_NX 0.069 against the
+# oracle's 0.085).  It does not reach equal kNN precision here; the test keeps
+# the 0.01 bar and is expected to fail for BF16.
+@pytest.mark.parametrize("fmt", [
+    "f32", "f16",
+    pytest.param("bf16", marks=pytest.mark.xfail(strict=True, reason="BF16 gathered positions "
+                                                 "miss the 0.01 Q_NX band on this workload"))])
 def test_full_run_error_vs_oracle(fmt, record_property):
     w = synth.WORKLOADS["gmm2k"]
     X, _ = synth.workload_features(w)
@@ -74,5 +82,4 @@ def test_full_run_error_vs_oracle(fmt, record_property):
     record_property("qnx_oracle", q_ref)
     record_property("stress_rel_err", (E - E_ref) / E_ref)
     print(f"{fmt}: Q_NX {q:.4f} (oracle {q_ref:.4f}), stress {E:.5g} (oracle {E_ref:.5g})")
-    tol = {"f32": 0.01, "f16": 0.01, "bf16": 0.05}[fmt]
-    assert abs(q - q_ref) <= tol
+    assert abs(q - q_ref) <= 0.01      # the equal-kNN-precision bar, every format
