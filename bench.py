@@ -83,7 +83,10 @@ def parse_args():
                      help="step: the workload's exact kNN graph or a kNN-shaped random graph")
     cap.add_argument("--iters", type=int, default=200, help="step: iterations per repetition")
     cap.add_argument("--reps", type=int, default=2)
-    cap.add_argument("--pos-format", default="f32", choices=["f32", "f16", "bf16"])
+    cap.add_argument("--pos-format", default="f32",
+                     help="step: gathered position formats, comma list of f32, f16, bf16")
+    cap.add_argument("--order", default="degree",
+                     help="step: layout orders, comma list of degree, degree_cluster")
     cap.add_argument("--data", choices=["gmm", "mnist"], default="gmm", help="knn: data set")
     cap.add_argument("--M", type=int, default=200000, help="knn: rows")
     cap.add_argument("--N", type=int, default=100, help="knn: float dimensions")
@@ -607,18 +610,45 @@ def config_subline(name: str, opts, dev, stream, flush, steps: int, warmup: int,
         inf, E = one()
         launch_s = kms / 1e3 / w.n_iter
         t_gather = inf["nnz_sym"] / gpeak
+        form = ["one step kernel per step", "one block per call", "8-block cluster per call",
+                "persistent grid per call"][inf["launch_form"]]
+        if inf["launch_form"] in (1, 2):
+            # positions live in shared memory: no L2 gathers to bound the step
+            binding = {"bound": "launch form", "launch_form": form, "frac": None,
+                       "what": "all steps of a call run in one launch with the positions in "
+                               "shared memory; the random-gather bound does not apply"}
+        else:
+            binding = {"bound": "l2_gather", "launch_form": form, "t_min_us": 1e6 * t_gather,
+                       "frac": t_gather / launch_s, "gather_peak": gpeak,
+                       "what": "kernel time per iteration against the row entries at the "
+                               "measured random-gather rate (ivhd_probe_gather, same size)"}
+        qnx = ivhd.eval_qnx(out_buf, knn, rows)
         res[opt] = {
             "value": inf["n_terms"] * w.n_iter / (ms / 1e3), "unit": UNIT, "s_to_embed": ms / 1e3,
-            "steps": steps, "warmup": warmup, "launch_us": 1e6 * launch_s,
-            "binding": {"bound": "l2_gather", "t_min_us": 1e6 * t_gather,
-                        "frac": t_gather / launch_s, "gather_peak": gpeak,
-                        "what": "kernel time per iteration against the row entries at the "
-                                "measured random-gather rate (ivhd_probe_gather, same size)"},
-            "quality": {"qnx": ivhd.eval_qnx(out_buf, knn, rows), "rows": int(rows.numel()),
+            "steps": steps, "warmup": warmup, "launch_us": 1e6 * launch_s, "binding": binding,
+            "quality": {"qnx": qnx, "rows": int(rows.numel()),
                         "cf": {str(nn): ivhd.eval_cf(out_buf, lab, nn, rows) for nn in (2, 10, 100)},
                         "stress": E},
             "terms": inf["n_terms"], "nnz_sym": inf["nnz_sym"], "gpu_launches": launches,
             "clocks": clk}
+        if opt == "momentum":
+            # half-precision gathered positions, same graph and seed, against this FP32 run
+            half = {}
+            for fmt in ("f16", "bf16"):
+                emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=opt, a=w.a, b=w.b, seed=w.seed,
+                                     stream=stream, device=dev, pos_format=fmt)
+                emb.step(w.n_iter)
+                emb.positions(out=out_buf)
+                try:
+                    Eh = emb.stress()
+                except ivhd.IvhdError:
+                    Eh = float("nan")
+                emb.close()
+                qh = ivhd.eval_qnx(out_buf, knn, rows)
+                half[fmt] = {"qnx": qh, "qnx_minus_f32": qh - qnx, "stress": Eh,
+                             "stress_rel_to_f32": (Eh - E) / E if E else None,
+                             "equal_precision": abs(qh - qnx) <= 0.01}
+            res[opt]["half_precision"] = half
     return res
 
 
@@ -662,23 +692,28 @@ def run_capture(args):
             knn = torch.from_numpy(synth.random_knn_graph(
                 w.M, w.k, w.seed + 1, hub_frac=0.02, n_hubs=max(w.k + 1, w.M // 1000))).cuda()
         torch.cuda.synchronize()
-        for rep in range(args.reps):
-            t0 = time.perf_counter()
-            emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b, seed=w.seed,
-                                 pos_format=args.pos_format)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            e0, e1 = events()
-            e0.record(s)
-            emb.step(args.iters)
-            e1.record(s)
-            torch.cuda.synchronize()
-            info = emb.info()
-            emb.close()
-            print(json.dumps({"rep": rep, "create_ms": 1e3 * (t1 - t0),
-                              "us_per_step": 1e3 * e0.elapsed_time(e1) / args.iters,
-                              "n_hub": info["n_hub"], "nnz_sym": info["nnz_sym"],
-                              "max_degree": info["max_degree"]}), flush=True)
+        for order in args.order.split(","):
+            for fmt in args.pos_format.split(","):
+                for rep in range(args.reps):
+                    t0 = time.perf_counter()
+                    emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b,
+                                         seed=w.seed, pos_format=fmt, order=order)
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    e0, e1 = events()
+                    e0.record(s)
+                    emb.step(args.iters)
+                    e1.record(s)
+                    torch.cuda.synchronize()
+                    info = emb.info()
+                    emb.close()
+                    print(json.dumps({"workload": w.name, "opt": args.opt, "order": order,
+                                      "pos_format": fmt, "rep": rep,
+                                      "create_ms": 1e3 * (t1 - t0),
+                                      "us_per_step": 1e3 * e0.elapsed_time(e1) / args.iters,
+                                      "n_hub": info["n_hub"], "nnz_sym": info["nnz_sym"],
+                                      "max_degree": info["max_degree"],
+                                      "launch_form": info["launch_form"]}), flush=True)
     elif args.kernel == "knn":
         if args.data == "gmm":
             X, _ = synth.gaussian_mixture(args.M, args.N, 50, 11)

@@ -88,7 +88,8 @@ def measure(train: int = 200000, holdout: int = 1400000, epochs: int = 10, steps
     torch.cuda.synchronize()
     train_s = e0.elapsed_time(e1) / 1e3
     out["mlp_train"] = {"epochs": args.epochs, "steps": args.epochs * n_batches,
-                        "seconds": train_s, "ms_per_step": 1e3 * train_s / (args.epochs * n_batches),
+                        "seconds": train_s,
+                        "ms_per_step_with_shuffling": 1e3 * train_s / (args.epochs * n_batches),
                         "loss_last_batch_per_epoch": losses}
 
     # 3. held-out set: MLP placement, then IVHD refinement vs plain IVHD
@@ -193,6 +194,17 @@ def measure(train: int = 200000, holdout: int = 1400000, epochs: int = 10, steps
     rows_tr = torch.from_numpy(synth.sample_rows(args.train, args.rows, 9)).to(dev)
     out["arriving_batches"] = {"batch": 10000, "placed_by": res,
                                "train_embedding_cf10": ivhd.eval_cf(Ytr, Ltr_d, 10, rows_tr)}
+    # the Adam step alone (last, so the network used above is not changed):
+    # 50 steps on resident batches, no shuffling in between
+    Xs, Ts = Xtr_d[:4 * B].contiguous(), T[:4 * B].contiguous()
+    torch.cuda.synchronize()
+    e2 = ev()
+    for i in range(50):
+        net.train_step(Xs[(i % 4) * B:(i % 4 + 1) * B], Ts[(i % 4) * B:(i % 4 + 1) * B], lr=1e-3,
+                       x_scale=1 / 255)
+    e3 = ev()
+    torch.cuda.synchronize()
+    out["mlp_train"]["ms_per_step"] = e2.elapsed_time(e3) / 50
     refine = min(len(warm) - 1, max(1, 100 // args.check_every))
     out["summary"] = {
         "train_step_ms": out["mlp_train"]["ms_per_step"],
