@@ -6,18 +6,23 @@
 // carries the dense layers of the learned warm start (an MLP that maps features
 // to 2-D positions, trained on IVHD embeddings).
 //
-// One CTA computes one 128 x BN tile:
+// Persistent kernel, one CTA per SM, looping over 128 x BN output tiles
+// (BN = 256, or 128 when that keeps more SMs busy or pads N less):
 //   warp 0, one lane   TMA producer: 128 x 64 A and BN x 64 B tiles into a
-//                      4-stage shared-memory ring (128-byte swizzle), one
+//                      4- or 6-stage shared-memory ring (128-byte swizzle), one
 //                      mbarrier with a transaction count per stage
-//   warp 1, one lane   MMA issuer: four tcgen05.mma (K = 16 each) per stage,
-//                      accumulating in tensor memory; tcgen05.commit frees the
-//                      stage, a final commit signals the epilogue
-//   warps 0-3          epilogue: tcgen05.ld of their 32 accumulator lanes,
-//                      fused element-wise op, global stores
+//   warp 1, one lane   MMA issuer: four tcgen05.mma (K = 16 each) per stage into
+//                      one of two tensor-memory accumulators; tcgen05.commit
+//                      frees the stage, a commit per tile hands the
+//                      accumulator to the epilogue
+//   warps 2-5          epilogue: tcgen05.ld of their 32 accumulator lanes, fused
+//                      element-wise op, vector global stores; while they drain
+//                      one accumulator the MMA warp fills the other
 // Every mbarrier wait is bounded; on timeout the kernel raises an error flag,
 // drains its copies in flight (again bounded), frees tensor memory and returns.
+#include <atomic>
 #include <mutex>
+#include <unordered_map>
 
 #include "ivhd_gemm.cuh"
 #include "ivhd_internal.cuh"
@@ -55,6 +60,51 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, in
          CUDA_SUCCESS;
 }
 
+// Encoded maps of the operands seen so far, keyed by address and geometry: an
+// encoding depends on nothing else, so a cached map equals a fresh one.  The
+// GEMMs of the warm-start network reuse a few fixed buffers, so this removes
+// the host-side encoding from every call after the first.
+namespace {
+struct MapKey {
+  const void* base;
+  int64_t rows, cols, ld;
+  int box_rows;
+  bool operator==(const MapKey& o) const {
+    return base == o.base && rows == o.rows && cols == o.cols && ld == o.ld &&
+           box_rows == o.box_rows;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    uint64_t h = (uint64_t)(uintptr_t)k.base;
+    for (uint64_t v : {(uint64_t)k.rows, (uint64_t)k.cols, (uint64_t)k.ld, (uint64_t)k.box_rows})
+      h = (h ^ v) * 0x100000001b3ull;
+    return (size_t)h;
+  }
+};
+constexpr size_t kMapCacheMax = 1024;
+}  // namespace
+
+bool make_map_cached(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                     int box_rows) {
+  static std::mutex mu;
+  static auto* cache = new std::unordered_map<MapKey, CUtensorMap, MapKeyHash>;
+  const MapKey key{base, rows, cols, ld, box_rows};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache->find(key);
+    if (it != cache->end()) {
+      *map = it->second;
+      return true;
+    }
+  }
+  if (!make_map(map, base, rows, cols, ld, box_rows)) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache->size() >= kMapCacheMax) cache->clear();
+  (*cache)[key] = *map;
+  return true;
+}
+
 }  // namespace tc
 
 namespace {
@@ -62,8 +112,7 @@ namespace {
 using namespace tc;
 
 constexpr int kBM = 128;
-constexpr int kStages = 4;
-constexpr int kGemmThreads = 128;
+constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
 __device__ __forceinline__ float gelu(float x) {
   return 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
@@ -74,73 +123,165 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return cdf + x * pdf;
 }
 
-__device__ __forceinline__ void ep_apply(const GemmEpilogue& ep, int row, int col0, int N,
-                                         const float* v) {
-  // v[q] is C[row, col0 + q]
-  if (ep.kind == kEpStoreF32) {
-    float* o = ep.out_f32 + (int64_t)row * ep.ld_out + col0;
+__device__ __forceinline__ bool aligned16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
+// 32 BF16 values (round to nearest even) stored as four 16-byte words.
+__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* o, const float* t) {
+  uint32_t w[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (col0 + q < N) o[q] = v[q];
+  for (int q = 0; q < 16; ++q) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(t[2 * q], t[2 * q + 1]);
+    memcpy(&w[q], &h, 4);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    reinterpret_cast<uint4*>(o)[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+}
+
+// Epilogue of 32 consecutive accumulator columns of one row: v[q] = C[row, col0 + q].
+// Vector stores where the 32 columns are in range and 16-byte aligned, else
+// element by element; the value written per element is the same either way.
+__device__ __forceinline__ void ep_apply32(const GemmEpilogue& ep, int row, int col0, int N,
+                                           const float* v) {
+  const int64_t off = (int64_t)row * ep.ld_out + col0;
+  const bool full = col0 + 32 <= N;
+  if (ep.kind == kEpStoreF32) {
+    float* o = ep.out_f32 + off;
+    if (full && aligned16(o)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        reinterpret_cast<float4*>(o)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (col0 + q < N) o[q] = v[q];
+    }
   } else if (ep.kind == kEpBiasGelu) {
     // z = acc + bias is kept (FP32) for the backward pass; h = GELU(z) in BF16
-    float* z = ep.out_f32 + (int64_t)row * ep.ld_out + col0;
-    __nv_bfloat16* h = ep.out_bf16 + (int64_t)row * ep.ld_out + col0;
+    float* z = ep.out_f32 + off;
+    __nv_bfloat16* h = ep.out_bf16 + off;
+    float t[32], g[32];
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (col0 + q < N) {
-        const float t = v[q] + ep.bias[col0 + q];
-        z[q] = t;
-        h[q] = __float2bfloat16_rn(gelu(t));
-      }
+    for (int q = 0; q < 32; ++q) {
+      t[q] = (col0 + q < N) ? v[q] + ep.bias[col0 + q] : 0.f;
+      g[q] = gelu(t[q]);
+    }
+    if (full && aligned16(z) && aligned16(h)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        reinterpret_cast<float4*>(z)[q] = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
+      store_bf16x32(h, g);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (col0 + q < N) {
+          z[q] = t[q];
+          h[q] = __float2bfloat16_rn(g[q]);
+        }
+    }
   } else if (ep.kind == kEpGeluGrad) {
     // dZ = acc * GELU'(z) in BF16 (acc is dH)
-    const float* z = ep.aux_f32 + (int64_t)row * ep.ld_out + col0;
-    __nv_bfloat16* o = ep.out_bf16 + (int64_t)row * ep.ld_out + col0;
+    const float* z = ep.aux_f32 + off;
+    __nv_bfloat16* o = ep.out_bf16 + off;
+    float zz[32], t[32];
+    if (full && aligned16(z)) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (col0 + q < N) o[q] = __float2bfloat16_rn(v[q] * gelu_grad(z[q]));
+      for (int q = 0; q < 8; ++q) {
+        const float4 f = reinterpret_cast<const float4*>(z)[q];
+        zz[4 * q] = f.x;
+        zz[4 * q + 1] = f.y;
+        zz[4 * q + 2] = f.z;
+        zz[4 * q + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) zz[q] = (col0 + q < N) ? z[q] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) t[q] = v[q] * gelu_grad(zz[q]);
+    if (full && aligned16(o)) {
+      store_bf16x32(o, t);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (col0 + q < N) o[q] = __float2bfloat16_rn(t[q]);
+    }
   }
 }
 
-template <int BN>
+template <int BN, int STAGES>
 struct GemmSmem {
   static constexpr int a_bytes = kBM * kBK * 2;
   static constexpr int b_bytes = BN * kBK * 2;
   static constexpr int stage_bytes = a_bytes + b_bytes;
-  static constexpr int bar_offset = kStages * stage_bytes;
+  static constexpr int bar_offset = STAGES * stage_bytes;
   static constexpr int total = bar_offset + 256 + 1024;  // + alignment slack
 };
 
-template <int BN>
+// A work unit: output tile (tm, tn) and split-K slice z with its k-tiles
+// [kt0, kt0 + nk).  Units are numbered so that the ones running at the same
+// time on different SMs share operand tiles in L2: tiles go in groups of 8
+// tile rows, column by column within a group.
+struct Unit {
+  int tm, tn, z, kt0, nk;
+};
+__device__ __forceinline__ Unit unit_of(int u, int tiles_m, int tiles_n, int splits, int nk_all) {
+  constexpr int G = 8;
+  const int per_z = tiles_m * tiles_n;
+  const int z = u / per_z;
+  const int t = u - z * per_z;
+  const int first_m = (t / (G * tiles_n)) * G;
+  const int gm = min(G, tiles_m - first_m);
+  const int local = t - first_m * tiles_n;
+  Unit r;
+  r.tm = first_m + local % gm;
+  r.tn = local / gm;
+  r.z = z;
+  const int per = (nk_all + splits - 1) / splits;
+  r.kt0 = z * per;
+  r.nk = max(0, min(nk_all, r.kt0 + per) - r.kt0);
+  return r;
+}
+
+// Persistent: each CTA (one per SM) takes units blockIdx.x, blockIdx.x +
+// gridDim.x, ...  Two accumulators in tensor memory (2 x BN columns): the MMA
+// warp fills one while the epilogue warps drain the other.
+//   full[s] / empty[s]      shared-memory stage s loaded (TMA) / consumed (MMA commit)
+//   acc_full[b]             accumulator b complete (MMA commit)
+//   acc_empty[b]            accumulator b read out (one arrival per epilogue warp)
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16_tn(const __grid_constant__ CUtensorMap map_a,
                    const __grid_constant__ CUtensorMap map_b, GemmEpilogue ep, int M, int N,
-                   int K, int32_t* __restrict__ err) {
+                   int K, int splits, int32_t* __restrict__ err) {
+  using S = GemmSmem<BN, STAGES>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + GemmSmem<BN>::bar_offset);
-  uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  int* issued = abort_flag + 1;
-  constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::bar_offset);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* issued = abort_flag + 1;  // k-tile loads issued (for the drain after an abort)
+  constexpr uint32_t kTmemCols = 2 * BN;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
-  // split-K: slice z of gridDim.z takes k-tiles [kt0, kt0 + nk)
+  const int tiles_m = (M + kBM - 1) / kBM, tiles_n = (N + BN - 1) / BN;
   const int nk_all = (K + kBK - 1) / kBK;
-  const int per = (nk_all + gridDim.z - 1) / gridDim.z;
-  const int kt0 = blockIdx.z * per;
-  const int nk = max(0, min(nk_all, kt0 + per) - kt0);
+  const int units = tiles_m * tiles_n * splits;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
     *abort_flag = 0;
     *issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -156,73 +297,112 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // producer
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % kStages;
-      if (kt >= kStages && !mbar_wait(&empty[s], ((kt / kStages) - 1) & 1)) {
-        atomicOr(err, 1);
-        *(volatile int*)abort_flag = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer
+      int it = 0;
+      for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x) {
+        const Unit w = unit_of(u, tiles_m, tiles_n, splits, nk_all);
+        for (int kt = 0; kt < w.nk; ++kt, ++it) {
+          const int s = it % STAGES;
+          if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1)) {
+            atomicOr(err, 1);
+            *abort_flag = 1;
+            break;
+          }
+          if (*abort_flag) break;
+          unsigned char* sa = smem + s * S::stage_bytes;
+          unsigned char* sb = sa + S::a_bytes;
+          mbar_expect_tx(&full[s], S::stage_bytes);
+          tma_load_2d(sa, &map_a, (w.kt0 + kt) * kBK, w.tm * kBM, &full[s]);
+          tma_load_2d(sb, &map_b, (w.kt0 + kt) * kBK, w.tn * BN, &full[s]);
+          *issued = it + 1;
+        }
       }
-      if (*(volatile int*)abort_flag) break;
-      unsigned char* sa = smem + s * GemmSmem<BN>::stage_bytes;
-      unsigned char* sb = sa + GemmSmem<BN>::a_bytes;
-      mbar_expect_tx(&full[s], GemmSmem<BN>::stage_bytes);
-      tma_load_2d(sa, &map_a, (kt0 + kt) * kBK, m0, &full[s]);
-      tma_load_2d(sb, &map_b, (kt0 + kt) * kBK, n0, &full[s]);
-      *(volatile int*)issued = kt + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = instr_desc_bf16(kBM, BN);
-    int kt = 0;
-    for (; kt < nk; ++kt) {
-      const int s = kt % kStages;
-      if (!mbar_wait(&full[s], (kt / kStages) & 1)) {
-        atomicOr(err, 2);
-        *(volatile int*)abort_flag = 1;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      constexpr uint32_t idesc = instr_desc_bf16(kBM, BN);
+      int it = 0, j = 0;
+      for (int u = blockIdx.x; u < units && !*abort_flag; u += gridDim.x, ++j) {
+        const Unit w = unit_of(u, tiles_m, tiles_n, splits, nk_all);
+        const int b = j & 1;
+        if (j >= 2 && !mbar_wait(&acc_empty[b], ((j >> 1) - 1) & 1)) {
+          atomicOr(err, 8);
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+        bool ok = true;
+        for (int kt = 0; kt < w.nk; ++kt, ++it) {
+          const int s = it % STAGES;
+          if (!mbar_wait(&full[s], (it / STAGES) & 1)) {
+            atomicOr(err, 2);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sa = smem_u32(smem + s * S::stage_bytes);
+          const uint32_t sb = sa + S::a_bytes;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            umma_bf16(d, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc,
+                      (kt > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[b]);  // this unit's MMAs (an empty slice arrives at once)
+      }
+    }
+  } else {
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    int j = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++j) {
+      const Unit w = unit_of(u, tiles_m, tiles_n, splits, nk_all);
+      const int b = j & 1;
+      // warp-uniform decisions: tcgen05.ld below is executed by all 32 lanes together
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], (j >> 1) & 1))) {
+        if (lane == 0) atomicOr(err, 4);
+        *abort_flag = 1;
         break;
       }
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sa = smem_u32(smem + s * GemmSmem<BN>::stage_bytes);
-      const uint32_t sb = sa + GemmSmem<BN>::a_bytes;
-#pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)
-        umma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), idesc,
-                  (kt > 0 || kk > 0) ? 1u : 0u);
-      umma_commit(&empty[s]);
-    }
-    umma_commit(done);  // covers every MMA issued above
-  }
-  __syncwarp();
-  // epilogue: all four warps, 32 accumulator lanes (rows) each
-  const bool ok = mbar_wait(done, 0);
-  if (!ok && threadIdx.x == 0) atomicOr(err, 4);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  __syncthreads();
-  const bool aborted = *(volatile int*)abort_flag != 0 || !ok;
-  if (!aborted) {
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    GemmEpilogue epz = ep;
-    if (gridDim.z > 1) epz.out_f32 += (int64_t)blockIdx.z * ep.split_stride;
+      const int row = w.tm * kBM + q * 32 + lane;
+      GemmEpilogue epz = ep;
+      if (splits > 1) epz.out_f32 += (int64_t)w.z * ep.split_stride;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      if (nk > 0) {
-        tmem_ld16(trow + c0, v);
-      } else {
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        if (w.nk > 0) {
+          uint32_t r[32];
+          tmem_ld32(taddr + (uint32_t)c, r);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = 0.f;  // an empty K slice contributes zero
+          for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < 32; ++t) v[t] = 0.f;  // an empty K slice contributes zero
+        }
+        const int col0 = w.tn * BN + c;
+        if (row < M && col0 < N) ep_apply32(epz, row, col0, N, v);
       }
-      if (row < M) ep_apply(epz, row, n0 + c0, N, v);
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
-  } else if (threadIdx.x == 0) {
+  }
+
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) {
     // drain copies still in flight before the shared memory goes away
-    const int iss = *(volatile int*)issued;
-    for (int kt = (iss > kStages ? iss - kStages : 0); kt < iss; ++kt)
-      mbar_wait(&full[kt % kStages], (kt / kStages) & 1);
+    const int iss = *issued;
+    for (int kt = (iss > STAGES ? iss - STAGES : 0); kt < iss; ++kt)
+      mbar_wait(&full[kt % STAGES], (kt / STAGES) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -231,23 +411,38 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                  "r"(kTmemCols));
 }
 
-// ---- host side: tensor maps -------------------------------------------------
+// ---- host side --------------------------------------------------------------
 
-template <int BN>
+int sm_count() {
+  static int count[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!count[dev]) {
+    int c = 0;
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1)
+      c = 148;
+    count[dev] = c;
+  }
+  return count[dev];
+}
+
+template <int BN, int STAGES>
 cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEpilogue& ep, int M,
                       int N, int K, int splits, int32_t* err, cudaStream_t s) {
-  const int smem = GemmSmem<BN>::total;
+  const int smem = GemmSmem<BN, STAGES>::total;
   static bool attr_set[64] = {};  // one attribute call per instantiation and device
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kBM - 1) / kBM), (unsigned)splits);
-  k_gemm_bf16_tn<BN><<<grid, kGemmThreads, smem, s>>>(ma, mb, ep, M, N, K, err);
+  const int64_t units = (int64_t)((M + kBM - 1) / kBM) * ((N + BN - 1) / BN) * splits;
+  const int grid = (int)(units < sm_count() ? units : sm_count());
+  k_gemm_bf16_tn<BN, STAGES><<<grid, kGemmThreads, smem, s>>>(ma, mb, ep, M, N, K, splits, err);
   return cudaGetLastError();
 }
 
@@ -256,13 +451,17 @@ cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEp
 cudaError_t gemm_bf16_tn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb,
                          int M, int N, int K, const GemmEpilogue& ep, int32_t* err,
                          cudaStream_t s, int splits) {
-  const int BN = N <= 64 ? 64 : 128;
   if (splits < 1 || (splits > 1 && ep.kind != kEpStoreF32)) return cudaErrorInvalidValue;
+  // 256-column tiles when they keep every SM busy and pad N no more than 128-column ones
+  const int64_t tiles_m = (M + kBM - 1) / kBM;
+  const int64_t n256 = (N + 255) / 256, n128 = (N + 127) / 128;
+  const bool wide = tiles_m * n256 * splits >= sm_count() && n256 * 256 <= n128 * 128;
+  const int BN = wide ? 256 : 128;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, M, K, lda, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&mb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
-  if (BN == 64) return launch_bn<64>(ma, mb, ep, M, N, K, splits, err, s);
-  return launch_bn<128>(ma, mb, ep, M, N, K, splits, err, s);
+  if (!make_map_cached(&ma, A, M, K, lda, kBM)) return cudaErrorInvalidValue;
+  if (!make_map_cached(&mb, B, N, K, ldb, BN)) return cudaErrorInvalidValue;
+  if (wide) return launch_bn<256, 4>(ma, mb, ep, M, N, K, splits, err, s);
+  return launch_bn<128, 6>(ma, mb, ep, M, N, K, splits, err, s);
 }
 
 // out[i] = sum_z part[z * stride + i] over `splits` slices in order (deterministic).
@@ -285,16 +484,24 @@ cudaError_t sum_slices(const float* part, int64_t n, int64_t stride, int splits,
 
 using namespace ivhd;
 
+// Error flags of ivhd_gemm_bf16_tn calls: a fixed set of slots in the
+// library's device memory, taken in turn, so a call allocates nothing.  A slot
+// is reused only after kErrSlots later calls; each call clears its slot first.
+constexpr int kErrSlots = 256;
+static __device__ int32_t g_gemm_err[kErrSlots];
+
 extern "C" ivhd_status ivhd_gemm_bf16_tn(const void* A, const void* B, float* C, int64_t M,
                                          int64_t N, int64_t K, void* stream) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 1) return IVHD_ERR_ARG;
   if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30) || (K % 8) != 0) return IVHD_ERR_ARG;
   if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)C & 15)) return IVHD_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  int32_t* err = nullptr;
+  static std::atomic<uint32_t> next{0};
+  int32_t* slots = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&slots, g_gemm_err);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  int32_t* err = slots + (next.fetch_add(1) % kErrSlots);
   int32_t herr = 0;
-  cudaError_t e = dev_alloc((void**)&err, sizeof(int32_t), s);
-  if (e != cudaSuccess) return IVHD_ERR_OOM;
   e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
   GemmEpilogue ep{};
   ep.kind = kEpStoreF32;
@@ -305,7 +512,6 @@ extern "C" ivhd_status ivhd_gemm_bf16_tn(const void* A, const void* B, float* C,
     e = gemm_bf16_tn((const __nv_bfloat16*)A, K, (const __nv_bfloat16*)B, K, (int)M, (int)N,
                      (int)K, ep, err, s, 1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
-  dev_free(err, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e == cudaErrorInvalidValue ? IVHD_ERR_ARG : IVHD_ERR_CUDA;
   return herr ? IVHD_ERR_TIMEOUT : IVHD_OK;

@@ -160,6 +160,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
 // encoding is rejected.
 bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
               int box_rows);
+// make_map through a process-wide cache keyed by address and geometry.
+bool make_map_cached(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
+                     int box_rows);
 
 }  // namespace tc
 }  // namespace ivhd
