@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <new>
+#include <vector>
 
 #include "ivhd_gemm.cuh"
 #include "ivhd_internal.cuh"
@@ -45,6 +46,15 @@ struct ivhd_mlp {
   double* loss_out = nullptr;
   int32_t* err = nullptr;
   int64_t launches = 0;
+  // the training step captured as a CUDA graph for batch size graph_B; the
+  // nodes that read the call's inputs and learning rate are patched per call
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_B = 0;            // batch size of the captured step (0: none)
+  int direct_B = 0;           // batch size of the last step run without the graph
+  int64_t graph_launches = 0; // kernels per replay
+  cudaGraphNode_t node_x = nullptr, node_loss = nullptr, node_adam = nullptr;
+  cudaKernelNodeParams kp_x{}, kp_loss{}, kp_adam{};
 };
 
 namespace ivhd {
@@ -358,6 +368,111 @@ ivhd_status check_err(ivhd_mlp* P) {
 
 bool batch_ok(const ivhd_mlp* P, int64_t B) { return B >= 8 && B <= P->max_batch && B % 8 == 0; }
 
+// One Adam step: load the batch, loss and gradients, update, refresh the BF16
+// weight copies.
+cudaError_t train_step_direct(ivhd_mlp* P, const void* x, int dtype, float scale,
+                              const float* targets, int B, float lr, float c1, float c2) {
+  cudaError_t e = load_x(P, x, dtype, scale, B);
+  if (e == cudaSuccess) e = loss_grad(P, targets, B);
+  if (e == cudaSuccess) {
+    k_adam<<<nb(P->n_params), 256, 0, P->stream>>>(P->w, P->m, P->v, P->g, P->n_params, lr, c1, c2);
+    ++P->launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = refresh_copies(P);
+  return e;
+}
+
+// Captures train_step_direct for batch size B on a private stream and keeps
+// the handles of the three kernel nodes whose arguments change per call.
+cudaError_t capture_train_step(ivhd_mlp* P, int B) {
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  P->graph_exec = nullptr;
+  P->graph = nullptr;
+  P->graph_B = 0;
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaStream_t saved = P->stream;
+  const int64_t launches0 = P->launches;
+  P->stream = cap;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    // placeholder inputs: the patched nodes get the real ones at every replay
+    cudaError_t e1 = train_step_direct(P, P->xb, 0, 1.f, P->y, B, 1e-3f, 1.f, 1.f);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    e = e1 != cudaSuccess ? e1 : e2;
+    if (e == cudaSuccess) P->graph = g;
+    else if (g) cudaGraphDestroy(g);
+  }
+  P->stream = saved;
+  P->graph_launches = P->launches - launches0;
+  P->launches = launches0;
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return e;
+  size_t n = 0;
+  e = cudaGraphGetNodes(P->graph, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e == cudaSuccess && n) e = cudaGraphGetNodes(P->graph, nodes.data(), &n);
+  for (size_t q = 0; q < n && e == cudaSuccess; ++q) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[q], &t);
+    if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp{};
+    e = cudaGraphKernelNodeGetParams(nodes[q], &kp);
+    if (e != cudaSuccess) break;
+    if (kp.func == (void*)k_convert_x) {
+      P->node_x = nodes[q];
+      P->kp_x = kp;
+    } else if (kp.func == (void*)k_loss) {
+      P->node_loss = nodes[q];
+      P->kp_loss = kp;
+    } else if (kp.func == (void*)k_adam) {
+      P->node_adam = nodes[q];
+      P->kp_adam = kp;
+    }
+  }
+  if (e == cudaSuccess && (!P->node_x || !P->node_loss || !P->node_adam))
+    e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph_exec, P->graph, 0);
+  if (e == cudaSuccess) P->graph_B = B;
+  return e;
+}
+
+// Replays the captured step with this call's inputs, targets and learning rate.
+cudaError_t replay_train_step(ivhd_mlp* P, const void* x, int dtype, float scale,
+                              const float* targets, int B, float lr, float c1, float c2) {
+  int64_t n_x = (int64_t)B * P->n_in;
+  __nv_bfloat16* xb = P->xb;
+  void* ax[] = {(void*)&x, (void*)&dtype, (void*)&scale, (void*)&n_x, (void*)&xb};
+  cudaKernelNodeParams kx = P->kp_x;
+  kx.kernelParams = ax;
+  kx.extra = nullptr;
+  float* y = P->y;
+  float* dy = P->dy;
+  double* part = P->loss_part;
+  void* al[] = {(void*)&y, (void*)&targets, (void*)&B, (void*)&dy, (void*)&part};
+  cudaKernelNodeParams kl = P->kp_loss;
+  kl.kernelParams = al;
+  kl.extra = nullptr;
+  float *w = P->w, *m = P->m, *v = P->v;
+  const float* g = P->g;
+  int64_t np = P->n_params;
+  void* aa[] = {(void*)&w, (void*)&m, (void*)&v, (void*)&g, (void*)&np, (void*)&lr, (void*)&c1,
+                (void*)&c2};
+  cudaKernelNodeParams ka = P->kp_adam;
+  ka.kernelParams = aa;
+  ka.extra = nullptr;
+  cudaError_t e = cudaGraphExecKernelNodeSetParams(P->graph_exec, P->node_x, &kx);
+  if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(P->graph_exec, P->node_loss, &kl);
+  if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(P->graph_exec, P->node_adam, &ka);
+  if (e == cudaSuccess) e = cudaGraphLaunch(P->graph_exec, P->stream);
+  if (e == cudaSuccess) P->launches += P->graph_launches;
+  return e;
+}
+
 }  // namespace
 }  // namespace ivhd
 
@@ -432,6 +547,8 @@ ivhd_status ivhd_mlp_create(int32_t n_in, int32_t hidden, int32_t max_batch, voi
 
 void ivhd_mlp_destroy(ivhd_mlp* P) {
   if (!P) return;
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
   void* bufs[] = {P->w, P->m, P->v, P->g, P->w1, P->w2, P->w2t, P->xb, P->xt, P->z1, P->z2,
                   P->h1, P->h1t, P->h2, P->dz2, P->dz2t, P->dz1, P->dz1t, P->y, P->dy,
                   P->part, P->loss_part, P->loss_out, P->err};
@@ -490,16 +607,18 @@ ivhd_status ivhd_mlp_train_step(ivhd_mlp* P, const void* x, int32_t x_dtype, flo
   if (!P || !x || !targets || x_dtype < 0 || x_dtype > 2 || !batch_ok(P, B) || !(lr > 0.f))
     return IVHD_ERR_ARG;
   if (P->poisoned) return IVHD_ERR_STATE;
-  cudaError_t e = load_x(P, x, x_dtype, x_scale, B);
-  if (e == cudaSuccess) e = loss_grad(P, targets, B);
-  if (e == cudaSuccess) {
-    P->t += 1;
-    const float c1 = 1.f - powf(0.9f, (float)P->t), c2 = 1.f - powf(0.999f, (float)P->t);
-    k_adam<<<nb(P->n_params), 256, 0, P->stream>>>(P->w, P->m, P->v, P->g, P->n_params, lr, c1, c2);
-    ++P->launches;
-    e = cudaGetLastError();
+  P->t += 1;
+  const float c1 = 1.f - powf(0.9f, (float)P->t), c2 = 1.f - powf(0.999f, (float)P->t);
+  cudaError_t e = cudaSuccess;
+  if (P->graph_B != B && P->direct_B == B) e = capture_train_step(P, B);
+  if (e != cudaSuccess) return mlp_fail(P, e);
+  if (P->graph_B == B) {
+    e = replay_train_step(P, x, x_dtype, x_scale, targets, B, lr, c1, c2);
+  } else {
+    // first step at this batch size: run directly (the next one captures it)
+    e = train_step_direct(P, x, x_dtype, x_scale, targets, B, lr, c1, c2);
+    P->direct_B = B;
   }
-  if (e == cudaSuccess) e = refresh_copies(P);
   if (e == cudaSuccess && loss)
     e = cudaMemcpyAsync(loss, P->loss_out, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
   if (e != cudaSuccess) return mlp_fail(P, e);

@@ -164,3 +164,37 @@ def test_training_fits_and_chunked_forward_is_consistent():
     y = net.forward(xt[:3000])
     y_parts = torch.cat([net.forward(xt[:1000]), net.forward(xt[1000:3000])])
     assert torch.equal(y, y_parts)
+
+
+def test_replayed_training_steps_follow_adam():
+    """From the second step at a batch size on, the step is a replayed CUDA graph whose
+    input, target and learning-rate nodes are patched per call: with new batches at new
+    addresses every step, each update still equals Adam's closed form from that batch's
+    gradient (computed by the direct path)."""
+    B = 256
+    X, T, net, p = setup(B=4 * B)
+    xs = [torch.from_numpy(X[i * B:(i + 1) * B].copy()).cuda() for i in range(4)]
+    ts = [torch.from_numpy(T[i * B:(i + 1) * B].copy()).float().cuda() for i in range(4)]
+    m = v = None
+    w = net.get_params().astype(np.float64)
+    lrs = [1e-3, 2e-3, 5e-4, 1e-3]
+    u = 2.0 ** -24
+    for t in range(1, 5):
+        loss_g, g = net.loss_grad(xs[t - 1], ts[t - 1], x_scale=1 / 255)
+        g = g.cpu().numpy().astype(np.float64)
+        loss = net.train_step(xs[t - 1], ts[t - 1], lr=lrs[t - 1], x_scale=1 / 255, want_loss=True)
+        assert loss == loss_g
+        m_prev = np.zeros_like(g) if m is None else m
+        m = 0.1 * g if m is None else 0.9 * m + 0.1 * g
+        v = 0.001 * g * g if v is None else 0.999 * v + 0.001 * g * g
+        c1, c2 = 1 - 0.9 ** t, 1 - 0.999 ** t
+        den = np.sqrt(v / c2) + 1e-8
+        want = w - lrs[t - 1] * (m / c1) / den
+        w_new = net.get_params().astype(np.float64)
+        ulp = np.spacing(np.abs(w).astype(np.float32)).astype(np.float64)
+        # FP32 state and arithmetic: the weight's own rounding, a relative error of the
+        # update, and the first moment's rounding relative to its terms (0.9 m + 0.1 g
+        # may cancel), carried over the steps
+        mom = lrs[t - 1] / c1 * 32 * t * u * (0.9 * np.abs(m_prev) + 0.1 * np.abs(g)) / den
+        assert np.all(np.abs(w_new - want) <= 4 * ulp + 1e-5 * np.abs(want - w) + mom), t
+        w = w_new
