@@ -318,7 +318,8 @@ __global__ void k_sorted_info(const int32_t* __restrict__ perm, const int32_t* _
                               const int32_t* __restrict__ kv, const int32_t* __restrict__ rc,
                               int64_t M, int hub_thr, int32_t* __restrict__ inv,
                               int32_t* __restrict__ deg_p, int32_t* __restrict__ outc_p,
-                              int32_t* n_hub, int32_t* n_long, int32_t* n_ge) {
+                              int32_t* n_hub, int32_t* n_long, int32_t* n_ge,
+                              int32_t* n_wide) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= M) return;
   const int32_t i = perm[p];
@@ -328,6 +329,7 @@ __global__ void k_sorted_info(const int32_t* __restrict__ perm, const int32_t* _
   outc_p[p] = kv[i] + rc[i];
   if (d >= hub_thr) atomicAdd(n_hub, 1);
   if (d > kShortRow && (p + 1 == M || deg[perm[p + 1]] <= kShortRow)) *n_long = (int32_t)(p + 1);
+  if (d >= kWideRow && (p + 1 == M || deg[perm[p + 1]] < kWideRow)) *n_wide = (int32_t)(p + 1);
   // rows with at least 256, 128 and 64 entries (the order is by descending degree)
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
@@ -631,7 +633,7 @@ struct HostTotals {
   int32_t max_deg;
   int32_t n_long;
   int32_t n_ge[3];
-  int32_t pad;
+  int32_t n_wide;
   unsigned long long sum_kv;
   unsigned long long sum_deg;
   unsigned long long sum_rc;
@@ -798,7 +800,7 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
   // 5. sizes and offsets
   k_sorted_info<<<nblk(M), kB, 0, s>>>(ctx->perm, deg, kv, rc, M, ctx->hub_threshold, ctx->inv,
                                        deg_p, outc_p, &tot_d->n_hub, &tot_d->n_long,
-                                       tot_d->n_ge);
+                                       tot_d->n_ge, &tot_d->n_wide);
   ++ctx->setup_launches;
   const int64_t max_slices = (M + 31) / 32;
   int64_t* hub_sz = sc.get<int64_t>(M);
@@ -822,6 +824,7 @@ ivhd_status build_layout(ivhd_ctx* ctx, bool draw_rn, uint64_t rn_epoch) {
 
   ctx->n_hub = h.n_hub;
   for (int t = 0; t < 3; ++t) ctx->n_ge[t] = h.n_ge[t];
+  ctx->n_wide = h.n_wide < h.n_hub ? h.n_wide : h.n_hub;  // wide rows are hub rows
   ctx->n_slices = (M - h.n_hub + 31) / 32;
   ctx->n_slots = h.hub_total + h.sell_total;
   ctx->nnz_sym = (int64_t)h.sum_deg;

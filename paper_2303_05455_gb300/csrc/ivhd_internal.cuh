@@ -76,6 +76,8 @@ inline int auto_hub_threshold(int64_t entries) {
 // the autotuner.
 inline int auto_vertices_per_warp(int64_t) { return 1; }
 constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
+constexpr int kWideRow = 512;        // rows with at least this many entries get kWideWarps warps
+constexpr int kWideWarps = 4;
 constexpr int kResidentSmem = 200 * 1024;  // shared memory of the resident whole-run kernel
 
 enum Mode { kMomentum = 0, kNesterov = 1, kAdadelta = 2, kForces = 3, kStress = 4 };
@@ -148,6 +150,9 @@ struct StepArgs {
   // warp-per-vertex rows: the first n_full take a whole warp each, the others
   // share a warp, mid_g lanes per row; hub_warps warps cover all of them
   int32_t n_full, mid_g, hub_warps;
+  // the first n_wide rows (the longest) take kWideWarps warps each, in the
+  // first nb_wide blocks, before the hub warps
+  int32_t n_wide, nb_wide;
   int64_t n_slots;  // layout entries (checked builds test row extents against it)
   float c, a, b, rho, eps;
 };
@@ -188,6 +193,7 @@ struct ivhd_ctx {
   int32_t* slice_w = nullptr;
   int64_t n_slots = 0, n_hub = 0, n_slices = 0;
   int64_t n_ge[3] = {0, 0, 0};  // rows with at least 256, 128, 64 entries (all hub rows)
+  int64_t n_wide = 0;           // hub rows with at least kWideRow entries (kWideWarps warps each)
 
   // state
   float2* y[2] = {nullptr, nullptr};

@@ -370,17 +370,62 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
     }
   };
 
-  if (vb < A.nb_hub) {
+  if (vb < A.nb_wide) {
+    // the longest rows: 4 warps (128 lanes) per vertex whatever the block size
+    // (a block of 8 or 16 warps takes 2 or 4 such rows); the lanes stride over
+    // the row's int4 groups, then the partial forces are summed in a fixed
+    // order (the butterfly within each warp, then the 4 warps in order)
+    __shared__ float wred[2][kMaxStepBlock / 32];
+    const int grp = wib / kWideWarps;
+    const int gl = (int)threadIdx.x - grp * kWideWarps * 32;
+    const int r = vb * (A.wpb / kWideWarps) + grp;
+    const bool valid = r < A.n_wide;
+    int ng = 0;
+    const int4* row = nullptr;
+    if (valid) {
+      p = r;
+      ym = (POS == kPosF32Coherent) ? __ldcg(G.y + p) : G.y[p];
+      yi = f32_pos<POS>() ? ym : load_pos<POS>(G.y, G.yh, p);
+      if (gl == 0) load_state(p);
+      const int beg = A.hub_off[p], end = A.hub_off[p + 1];
+      row = reinterpret_cast<const int4*>(A.ids + beg);
+      ng = row_ok(beg, end, A.n_slots) ? (end - beg) >> 2 : 0;
+    }
+    constexpr int nt = kWideWarps * 32;
+    int g = gl;
+    for (; g + nt < ng; g += 2 * nt) {
+      const int4 ea = ld_stream_v4(row + g);
+      const int4 eb = ld_stream_v4(row + g + nt);
+      visit8<MODE, POS, METRIC>(ea, eb, G, yi, A.c, fx, fy);
+    }
+    if (g < ng) visit4<MODE, POS, METRIC>(ld_stream_v4(row + g), G, yi, A.c, fx, fy);
+    group_sum(fx, fy, 32);
+    if (lane == 0) {
+      wred[0][wib] = fx;
+      wred[1][wib] = fy;
+    }
+    __syncthreads();
+    if (valid && gl == 0) {
+      const int w0 = grp * kWideWarps;
+      fx = wred[0][w0];
+      fy = wred[1][w0];
+      for (int q = 1; q < kWideWarps; ++q) {
+        fx += wred[0][w0 + q];
+        fy += wred[1][w0 + q];
+      }
+    }
+    own = valid && gl == 0;
+  } else if (vb < A.nb_wide + A.nb_hub) {
     // hub rows: a warp, or a group of mid_g lanes, per vertex; the lanes of a
     // row stride over its int4 groups, then sum their partial forces
-    const int w = vb * A.wpb + wib;
+    const int w = (vb - A.nb_wide) * A.wpb + wib;
     if (w < A.hub_warps) {
       const HubSlot h = hub_slot(w, lane, A.n_full, A.mid_g);
-      const bool valid = h.row < A.n_hub;
+      const bool valid = A.n_wide + h.row < A.n_hub;
       int ng = 0;
       const int4* row = nullptr;
       if (valid) {
-        p = h.row;
+        p = A.n_wide + h.row;
         ym = (POS == kPosF32Coherent) ? __ldcg(G.y + p) : G.y[p];
         yi = f32_pos<POS>() ? ym : load_pos<POS>(G.y, G.yh, p);
         if (h.l == 0) load_state(p);
@@ -400,7 +445,7 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
     }
   } else {
     // SELL slice: one thread per vertex, one coalesced int4 per 4 neighbours
-    const int s = (vb - A.nb_hub) * A.wpb + wib;
+    const int s = (vb - A.nb_wide - A.nb_hub) * A.wpb + wib;
     if (s < A.n_slices) {
       p = A.n_hub + s * 32 + lane;
       const bool valid = p < A.M;
@@ -488,8 +533,16 @@ __device__ __forceinline__ void step_block(const StepArgs& A, int vb, int cur) {
   }
 }
 
+// Register cap of the step kernel: the optimiser's code fits 48 registers (50
+// for Adadelta's two accumulators) without spilling; more would cost a block
+// of residency per SM on this request-rate-bound kernel.
+template <int MODE>
+constexpr int step_max_regs() {
+  return MODE == kAdadelta ? 50 : 48;
+}
+
 template <int MODE, int POS, int METRIC, bool ADAPT>
-__global__ void __launch_bounds__(kMaxStepBlock, IVHD_STEP_MIN_BLOCKS) k_step(const StepArgs A) {
+__global__ void __maxnreg__(step_max_regs<MODE>()) k_step(const StepArgs A) {
   // launched as a programmatic dependent of the previous step: wait until that
   // grid has completed and its writes are visible before reading any state
   // (a no-op for a launch without that attribute)
@@ -882,6 +935,9 @@ constexpr int64_t kClusterAutoEntries = 40000;
 int resident_mode(const ivhd_ctx* ctx) {
   if (ctx->p.resident < 0 || ctx->p.adaptive || ctx->p.pos_format != IVHD_POS_F32) return 0;
   if (ctx->p.resident == 3) return 4;  // persistent grid: any size
+  // the whole-call kernels give every row at most a warp; graphs with rows of
+  // kWideRow entries or more run one step kernel per step instead
+  if (ctx->n_wide > 0) return 0;
   if (ctx->M > ((int64_t)1 << 20)) return 0;
   if (ctx->p.resident == 0)
     return (ctx->nnz_sym <= kClusterAutoEntries &&
@@ -1152,6 +1208,12 @@ static StepArgs make_args(const ivhd_ctx* ctx, int cur) {
   A.n_slots = ctx->n_slots;
   A.wpb = ctx->block / 32;
   hub_map(ctx, &A.n_full, &A.mid_g, &A.hub_warps);
+  // the wide rows lead the full-warp rows (both are the longest rows, in
+  // descending degree); the hub warps take the rows after them
+  A.n_wide = (int32_t)ctx->n_wide;
+  A.nb_wide = (int32_t)((A.n_wide + A.wpb / kWideWarps - 1) / (A.wpb / kWideWarps));
+  A.n_full -= A.n_wide;
+  A.hub_warps -= A.n_wide;
   A.nb_hub = (int32_t)((A.hub_warps + A.wpb - 1) / A.wpb);
   A.c = ctx->c;
   A.a = ctx->p.a;
@@ -1226,9 +1288,11 @@ int step_grid(const ivhd_ctx* ctx) {
   const int wpb = ctx->block / 32;
   int32_t n_full, mid_g, warps;
   hub_map(ctx, &n_full, &mid_g, &warps);
-  const int64_t nb_hub = (warps + wpb - 1) / wpb;
+  const int64_t rows_per_block = wpb / kWideWarps;
+  const int64_t nb_wide = (ctx->n_wide + rows_per_block - 1) / rows_per_block;
+  const int64_t nb_hub = (warps - ctx->n_wide + wpb - 1) / wpb;
   const int64_t nb_sell = (ctx->n_slices + wpb - 1) / wpb;
-  return (int)(nb_hub + nb_sell);
+  return (int)(nb_wide + nb_hub + nb_sell);
 }
 
 template <int MODE, int POS, int METRIC, bool ADAPT>

@@ -62,10 +62,33 @@ def graph_case(name):
             others = rng.choice(np.setdiff1d(np.arange(1, M), [i]), 2, replace=False)
             g[i] = [0, *others]
         return g, 1, 0.02
+    if name == "star3k":
+        # vertex 0 is a neighbour of every other vertex (degree ~3,000): one of the
+        # rows long enough to be processed by 4 warps
+        M = 3000
+        rng = np.random.default_rng(10)
+        g = np.empty((M, 3), np.int32)
+        g[0] = [1, 2, 3]
+        i = np.arange(1, M)
+        a = rng.integers(1, M, size=M - 1)
+        b = rng.integers(1, M, size=M - 1)
+        bad = (a == i) | (b == i) | (a == b)
+        while bad.any():
+            a[bad] = rng.integers(1, M, size=int(bad.sum()))
+            b[bad] = rng.integers(1, M, size=int(bad.sum()))
+            bad = (a == i) | (b == i) | (a == b)
+        g[1:, 0], g[1:, 1], g[1:, 2] = 0, a, b
+        return g, 1, 0.02
     raise KeyError(name)
 
 
-CASES = ["gmm2k", "hubs5k", "ragged37", "pair", "triangle", "star"]
+CASES = ["gmm2k", "hubs5k", "ragged37", "pair", "triangle", "star", "star3k"]
+
+
+def stable_b(case):
+    # momentum is stable only while b lambda_max < 2 (1 + a); star3k's hub has degree
+    # ~3,000 (lambda_max ~ 6,000), where b = 0.01 would blow up within a few steps
+    return 5e-4 if case == "star3k" else 0.01
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -119,7 +142,7 @@ def test_layout_counts_match_term_list(case, dedup):
 @pytest.mark.parametrize("case", CASES)
 def test_one_step_and_ten_steps(case, opt, dedup, hub_threshold):
     knn, r, c = graph_case(case)
-    a, b = 0.9, 0.01
+    a, b = 0.9, stable_b(case)
     emb = ivhd.Embedding(knn, r=r, c=c, opt=opt, a=a, b=b, seed=11, dedup_mutual=dedup,
                          hub_threshold=hub_threshold)
     rn, _ = oracle.random_neighbors(knn, r, 11)
@@ -259,6 +282,22 @@ def test_bitwise_equal_across_block_sizes(opt):
     for bs in (128, 256, 512):
         emb = ivhd.Embedding(knn, r=r, c=c, seed=9, opt=opt, b=0.002, block_size=bs,
                              hub_threshold=32, vertices_per_warp=4, resident=False)
+        emb.step(70)
+        out.append(emb.positions(host=True))
+        emb.close()
+    assert np.all(np.isfinite(out[0]))
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("opt", ["momentum", "adadelta"])
+def test_long_rows_bitwise_equal_across_block_sizes(opt):
+    # rows of 512 entries or more take 4 warps whatever the block size, so the
+    # block size still only groups rows into blocks
+    knn, r, c = graph_case("star3k")
+    out = []
+    for bs in (128, 256, 512):
+        emb = ivhd.Embedding(knn, r=r, c=c, seed=9, opt=opt, b=stable_b("star3k"),
+                             block_size=bs, resident=False)
         emb.step(70)
         out.append(emb.positions(host=True))
         emb.close()

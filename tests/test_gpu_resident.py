@@ -57,6 +57,27 @@ def test_resident_equals_multi_launch_bitwise(name, opt, metric, kind, vpw):
     assert ia["kernel_launches"] == 4 and ib["kernel_launches"] == 202
 
 
+def test_resident_not_used_for_rows_of_512_entries_or_more():
+    # the whole-call kernels give a row at most a warp; such graphs run one step
+    # kernel per step (and the persistent grid), with equal results
+    M = 3000
+    knn = synth.random_knn_graph(M, 3, 12)
+    knn[1:, 0] = 0                         # vertex 0: a neighbour of every other vertex
+    knn[0] = [1, 2, 3]
+    bad = (knn[:, 1] == 0) | (knn[:, 2] == 0) | (knn[:, 1] == knn[:, 2])
+    knn[bad, 1], knn[bad, 2] = (np.arange(M)[bad] + 1) % M, (np.arange(M)[bad] + 2) % M
+    knn[0] = [1, 2, 3]
+    runs = []
+    for resident in (True, "cluster", "grid", False):
+        e = ivhd.Embedding(knn, r=1, c=0.02, seed=3, b=5e-4, resident=resident)
+        e.step(40)
+        runs.append((e.positions(host=True), e.info()))
+        e.close()
+    for (y, inf), resident in zip(runs, (True, "cluster", "grid", False)):
+        assert np.array_equal(y, runs[-1][0])
+        assert inf["launch_form"] == (3 if resident == "grid" else 0)
+
+
 def test_resident_not_used_when_state_does_not_fit_or_not_asked():
     knn = synth.random_knn_graph(20000, 5, 3)
     e = ivhd.Embedding(knn, r=1, c=0.01, seed=1, resident=True)
