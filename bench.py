@@ -87,6 +87,9 @@ def parse_args():
                      help="step: gathered position formats, comma list of f32, f16, bf16")
     cap.add_argument("--order", default="degree",
                      help="step: layout orders, comma list of degree, degree_cluster")
+    cap.add_argument("--shapes-step", default="0:0:0",
+                     help="step: launch shapes hub_threshold:vertices_per_warp:block_size, "
+                          "comma list (0 = library default)")
     cap.add_argument("--data", choices=["gmm", "mnist"], default="gmm", help="knn: data set")
     cap.add_argument("--M", type=int, default=200000, help="knn: rows")
     cap.add_argument("--N", type=int, default=100, help="knn: float dimensions")
@@ -692,28 +695,32 @@ def run_capture(args):
             knn = torch.from_numpy(synth.random_knn_graph(
                 w.M, w.k, w.seed + 1, hub_frac=0.02, n_hubs=max(w.k + 1, w.M // 1000))).cuda()
         torch.cuda.synchronize()
-        for order in args.order.split(","):
-            for fmt in args.pos_format.split(","):
-                for rep in range(args.reps):
-                    t0 = time.perf_counter()
-                    emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b,
-                                         seed=w.seed, pos_format=fmt, order=order)
-                    torch.cuda.synchronize()
-                    t1 = time.perf_counter()
-                    e0, e1 = events()
-                    e0.record(s)
-                    emb.step(args.iters)
-                    e1.record(s)
-                    torch.cuda.synchronize()
-                    info = emb.info()
-                    emb.close()
-                    print(json.dumps({"workload": w.name, "opt": args.opt, "order": order,
-                                      "pos_format": fmt, "rep": rep,
-                                      "create_ms": 1e3 * (t1 - t0),
-                                      "us_per_step": 1e3 * e0.elapsed_time(e1) / args.iters,
-                                      "n_hub": info["n_hub"], "nnz_sym": info["nnz_sym"],
-                                      "max_degree": info["max_degree"],
-                                      "launch_form": info["launch_form"]}), flush=True)
+        combos = [(o, f, sh) for o in args.order.split(",") for f in args.pos_format.split(",")
+                  for sh in args.shapes_step.split(",")]
+        for order, fmt, shape in combos:
+            hub, vpw, block = (int(v) for v in shape.split(":"))
+            for rep in range(args.reps):
+                t0 = time.perf_counter()
+                emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b,
+                                     seed=w.seed, pos_format=fmt, order=order,
+                                     hub_threshold=hub, vertices_per_warp=vpw,
+                                     block_size=block)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                e0, e1 = events()
+                e0.record(s)
+                emb.step(args.iters)
+                e1.record(s)
+                torch.cuda.synchronize()
+                info = emb.info()
+                emb.close()
+                print(json.dumps({"workload": w.name, "opt": args.opt, "order": order,
+                                  "pos_format": fmt, "shape": shape, "rep": rep,
+                                  "create_ms": 1e3 * (t1 - t0),
+                                  "us_per_step": 1e3 * e0.elapsed_time(e1) / args.iters,
+                                  "n_hub": info["n_hub"], "nnz_sym": info["nnz_sym"],
+                                  "max_degree": info["max_degree"],
+                                  "launch_form": info["launch_form"]}), flush=True)
     elif args.kernel == "knn":
         if args.data == "gmm":
             X, _ = synth.gaussian_mixture(args.M, args.N, 50, 11)
