@@ -140,6 +140,16 @@ __device__ __forceinline__ void store_bf16x32(__nv_bfloat16* o, const float* t) 
     reinterpret_cast<uint4*>(o)[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }
 
+// The transposed copy of 32 BF16 values of one row: column col0 + q of this
+// row goes to out_t[(col0 + q) * ld_t + row].  The lanes of a warp hold
+// consecutive rows, so each of the 32 stores is one contiguous 64-byte run.
+__device__ __forceinline__ void store_bf16_t(__nv_bfloat16* out_t, int64_t ld_t, int row,
+                                             int col0, int N, const float* t) {
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    if (col0 + q < N) out_t[(int64_t)(col0 + q) * ld_t + row] = __float2bfloat16_rn(t[q]);
+}
+
 // Epilogue of 32 consecutive accumulator columns of one row: v[q] = C[row, col0 + q].
 // Vector stores where the 32 columns are in range and 16-byte aligned, else
 // element by element; the value written per element is the same either way.
@@ -181,6 +191,7 @@ __device__ __forceinline__ void ep_apply32(const GemmEpilogue& ep, int row, int 
           h[q] = __float2bfloat16_rn(g[q]);
         }
     }
+    if (ep.out_bf16_t) store_bf16_t(ep.out_bf16_t, ep.ld_t, row, col0, N, g);
   } else if (ep.kind == kEpGeluGrad) {
     // dZ = acc * GELU'(z) in BF16 (acc is dH)
     const float* z = ep.aux_f32 + off;
@@ -208,6 +219,7 @@ __device__ __forceinline__ void ep_apply32(const GemmEpilogue& ep, int row, int 
       for (int q = 0; q < 32; ++q)
         if (col0 + q < N) o[q] = __float2bfloat16_rn(t[q]);
     }
+    if (ep.out_bf16_t) store_bf16_t(ep.out_bf16_t, ep.ld_t, row, col0, N, t);
   }
 }
 

@@ -21,6 +21,9 @@ struct GemmEpilogue {
   const float* bias;
   const float* aux_f32;
   int64_t split_stride;  // split-K: slice z writes out_f32 + z * split_stride
+  // optional (BF16 kinds): the same BF16 values transposed, out_bf16_t[col * ld_t + row]
+  __nv_bfloat16* out_bf16_t = nullptr;
+  int64_t ld_t = 0;
 };
 
 // C = A B^T for BF16 A (M x K, row stride lda) and B (N x K, row stride ldb),
