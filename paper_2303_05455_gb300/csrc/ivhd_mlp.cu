@@ -165,11 +165,32 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
   }
 }
 
-__global__ void k_loss_final(const double* __restrict__ part, int n, int B, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+// dW3 (2 x H) and db3 (2) from the chunk partials of k_grad3_part (summed over
+// the chunks in order, as k_chunk_sum does), and the batch loss from the
+// per-block partials of k_loss (summed in order, divided by B).
+__global__ void k_grad3_final(const float* __restrict__ part, int chunks, int H,
+                              float* __restrict__ gW3, float* __restrict__ gb3,
+                              const double* __restrict__ loss_part, int n_loss, int B,
+                              double* __restrict__ loss_out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = 2 * (H + 1);
+  if (q < n) {
+    float t = 0.f;
+#pragma unroll 8
+    for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * n + q];
+    const int j = q / (H + 1), i = q - j * (H + 1);
+    if (i < H)
+      gW3[(int64_t)j * H + i] = t;
+    else
+      gb3[j] = t;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    // the loss: lane l sums partials l, l + 32, ... in order, then a fixed butterfly
     double t = 0.0;
-    for (int i = 0; i < n; ++i) t += part[i];
-    out[0] = t / B;
+    for (int i = (int)threadIdx.x; i < n_loss; i += 32) t += loss_part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) loss_out[0] = t / B;
   }
 }
 
@@ -182,6 +203,7 @@ __global__ void k_grad3_part(const float* __restrict__ dy, const __nv_bfloat16* 
   if (i > H) return;
   const int r0 = c * kRowChunk, r1 = min(B, r0 + kRowChunk);
   float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
   for (int b = r0; b < r1; ++b) {
     const float h = (i < H) ? __bfloat162float(h2[(int64_t)b * H + i]) : 1.f;
     s0 = fmaf(dy[2 * (int64_t)b], h, s0);
@@ -199,6 +221,7 @@ __global__ void k_colsum_part(const __nv_bfloat16* __restrict__ a, int B, int H,
   if (i >= H) return;
   const int r0 = c * kRowChunk, r1 = min(B, r0 + kRowChunk);
   float s = 0.f;
+#pragma unroll 8
   for (int b = r0; b < r1; ++b) s += __bfloat162float(a[(int64_t)b * H + i]);
   part[(int64_t)c * H + i] = s;
 }
@@ -209,20 +232,35 @@ __global__ void k_chunk_sum(const float* __restrict__ part, int chunks, int n,
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   float t = 0.f;
+#pragma unroll 8
   for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * n + q];
   out[q] = t;
 }
 
-// dZ2 = (dY W3) * GELU'(z2) in BF16.
+// dZ2 = (dY W3) * GELU'(z2) in BF16, written row-major (B x H) and transposed
+// (H x B) for the weight-gradient GEMM: a 32 x 32 tile per block, staged in
+// shared memory so that both stores are coalesced.
+constexpr int kTile = 32;
 __global__ void k_dz2(const float* __restrict__ dy, const float* __restrict__ W3,
                       const float* __restrict__ z2, int B, int H,
-                      __nv_bfloat16* __restrict__ dz2) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)B * H) return;
-  const int64_t b = e / H;
-  const int i = (int)(e % H);
-  const float dh = fmaf(dy[2 * b], W3[i], dy[2 * b + 1] * W3[H + i]);
-  dz2[e] = __float2bfloat16_rn(dh * gelu_grad_dev(z2[e]));
+                      __nv_bfloat16* __restrict__ dz2, __nv_bfloat16* __restrict__ dz2t) {
+  __shared__ __nv_bfloat16 t[kTile][kTile + 2];
+  const int i0 = blockIdx.x * kTile, b0 = blockIdx.y * kTile;
+  for (int r = threadIdx.y; r < kTile; r += blockDim.y) {
+    const int b = b0 + r, i = i0 + threadIdx.x;
+    if (b < B && i < H) {
+      const int64_t e = (int64_t)b * H + i;
+      const float dh = fmaf(dy[2 * (int64_t)b], W3[i], dy[2 * (int64_t)b + 1] * W3[H + i]);
+      const __nv_bfloat16 v = __float2bfloat16_rn(dh * gelu_grad_dev(z2[e]));
+      dz2[e] = v;
+      t[r][threadIdx.x] = v;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < kTile; r += blockDim.y) {
+    const int i = i0 + r, b = b0 + threadIdx.x;
+    if (b < B && i < H) dz2t[(int64_t)i * B + b] = t[threadIdx.x][r];
+  }
 }
 
 // Bias gradient: column sums of a B x H BF16 matrix, chunk partials then an ordered sum.
@@ -235,9 +273,17 @@ cudaError_t colsum(ivhd_mlp* P, const __nv_bfloat16* a, int B, int H, float* out
   return cudaGetLastError();
 }
 
-// Adam on the flat FP32 parameters (bias-corrected, Kingma and Ba).
+// Adam on the flat FP32 parameters (bias-corrected, Kingma and Ba).  The
+// updated W1 and W2 are also written as the BF16 copies the tensor cores read
+// (W1, W2 and the transposed W2), the same values refresh_copies would make.
+struct BF16Copies {
+  int64_t w1_off, w2_off;  // offsets of W1 (H x n_in) and W2 (H x H) in the flat vector
+  int n_in, H;
+  __nv_bfloat16 *w1, *w2, *w2t;
+};
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                       const float* __restrict__ g, int64_t n, float lr, float c1, float c2) {
+                       const float* __restrict__ g, int64_t n, float lr, float c1, float c2,
+                       BF16Copies cp) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
   const float gi = g[e];
@@ -245,7 +291,16 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
   const float vi = fmaf(0.999f, v[e], 0.001f * gi * gi);
   m[e] = mi;
   v[e] = vi;
-  w[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+  const float wn = w[e] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+  w[e] = wn;
+  const int64_t a = e - cp.w1_off, q = e - cp.w2_off;
+  if (a >= 0 && a < (int64_t)cp.H * cp.n_in) {
+    cp.w1[a] = __float2bfloat16_rn(wn);
+  } else if (q >= 0 && q < (int64_t)cp.H * cp.H) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(wn);
+    cp.w2[q] = h;
+    cp.w2t[(q % cp.H) * cp.H + q / cp.H] = h;
+  }
 }
 
 __global__ void k_to_bf16(const float* __restrict__ a, int64_t n, __nv_bfloat16* __restrict__ out) {
@@ -269,12 +324,17 @@ cudaError_t refresh_copies(ivhd_mlp* P) {
   return transpose(P->w2, H, H, P->w2t, P->stream);
 }
 
-// Forward pass of B rows already in P->xb: z1, h1, z2, h2, y.
-cudaError_t forward(ivhd_mlp* P, int B) {
+// Forward pass of B rows already in P->xb: z1, h1, z2, h2, y.  For training
+// the first layer also writes h1 transposed (the weight gradient's operand).
+cudaError_t forward(ivhd_mlp* P, int B, bool train = false) {
   const Offs o = offsets(P->n_in, P->hidden);
   const int H = P->hidden;
   P->last_rows = B;
   GemmEpilogue e1{kEpBiasGelu, H, P->z1, P->h1, P->w + o.b1, nullptr, 0};
+  if (train) {
+    e1.out_bf16_t = P->h1t;
+    e1.ld_t = B;
+  }
   cudaError_t e = gemm_bf16_tn(P->xb, P->n_in, P->w1, P->n_in, B, H, P->n_in, e1, P->err, P->stream);
   GemmEpilogue e2{kEpBiasGelu, H, P->z2, P->h2, P->w + o.b2, nullptr, 0};
   if (e == cudaSuccess) e = gemm_bf16_tn(P->h1, H, P->w2, H, B, H, H, e2, P->err, P->stream);
@@ -291,50 +351,42 @@ cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B) {
   const Offs o = offsets(P->n_in, P->hidden);
   const int H = P->hidden, n_in = P->n_in;
   cudaStream_t s = P->stream;
-  cudaError_t e = forward(P, B);
+  cudaError_t e = forward(P, B, true);
   if (e != cudaSuccess) return e;
   k_loss<<<kLossBlocks, 256, 0, s>>>(P->y, tgt, B, P->dy, P->loss_part);
-  k_loss_final<<<1, 32, 0, s>>>(P->loss_part, kLossBlocks, B, P->loss_out);
   {
     // dW3 (2 x H) and db3 (2): rows [j][0..H) of the (2, H + 1) chunk sums, bias in column H
     const int chunks = (B + kRowChunk - 1) / kRowChunk;
     k_grad3_part<<<dim3(nb(H + 1), (unsigned)chunks), 256, 0, s>>>(P->dy, P->h2, B, H, P->part);
-    float* sums = P->part + (int64_t)chunks * 2 * (H + 1);
-    k_chunk_sum<<<nb(2 * (int64_t)(H + 1)), 256, 0, s>>>(P->part, chunks, 2 * (H + 1), sums);
-    for (int j = 0; j < 2; ++j) {
-      e = cudaMemcpyAsync(P->g + o.W3 + (int64_t)j * H, sums + (int64_t)j * (H + 1),
-                          (size_t)H * sizeof(float), cudaMemcpyDeviceToDevice, s);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P->g + o.b3 + j, sums + (int64_t)j * (H + 1) + H, sizeof(float),
-                            cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) return e;
-    }
+    k_grad3_final<<<nb(2 * (int64_t)(H + 1)), 256, 0, s>>>(P->part, chunks, H, P->g + o.W3,
+                                                            P->g + o.b3, P->loss_part,
+                                                            kLossBlocks, B, P->loss_out);
   }
-  k_dz2<<<nb((int64_t)B * H), 256, 0, s>>>(P->dy, P->w + o.W3, P->z2, B, H, P->dz2);
-  P->launches += 5;
+  k_dz2<<<dim3((unsigned)((H + kTile - 1) / kTile), (unsigned)((B + kTile - 1) / kTile)),
+          dim3(kTile, 8), 0, s>>>(P->dy, P->w + o.W3, P->z2, B, H, P->dz2, P->dz2t);
+  P->launches += 4;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = colsum(P, P->dz2, B, H, P->g + o.b2)) != cudaSuccess) return e;
-  // dW2 = dZ2^T H1
-  if ((e = transpose(P->dz2, B, H, P->dz2t, s)) != cudaSuccess) return e;
-  if ((e = transpose(P->h1, B, H, P->h1t, s)) != cudaSuccess) return e;
+  // dW2 = dZ2^T H1 (dZ2^T from k_dz2, H1^T from the forward pass)
   GemmEpilogue gw2{kEpStoreF32, H, P->part, nullptr, nullptr, nullptr, (int64_t)H * H};
   if ((e = gemm_bf16_tn(P->dz2t, B, P->h1t, B, H, H, B, gw2, P->err, s, kSplitK)) != cudaSuccess)
     return e;
   if ((e = sum_slices(P->part, (int64_t)H * H, (int64_t)H * H, kSplitK, P->g + o.W2, s)) !=
       cudaSuccess)
     return e;
-  // dZ1 = (dZ2 W2) * GELU'(z1)
+  // dZ1 = (dZ2 W2) * GELU'(z1), also written transposed
   GemmEpilogue gz1{kEpGeluGrad, H, nullptr, P->dz1, nullptr, P->z1, 0};
+  gz1.out_bf16_t = P->dz1t;
+  gz1.ld_t = B;
   if ((e = gemm_bf16_tn(P->dz2, H, P->w2t, H, B, H, H, gz1, P->err, s)) != cudaSuccess) return e;
   if ((e = colsum(P, P->dz1, B, H, P->g + o.b1)) != cudaSuccess) return e;
   // dW1 = dZ1^T X
-  if ((e = transpose(P->dz1, B, H, P->dz1t, s)) != cudaSuccess) return e;
   if ((e = transpose(P->xb, B, n_in, P->xt, s)) != cudaSuccess) return e;
   GemmEpilogue gw1{kEpStoreF32, n_in, P->part, nullptr, nullptr, nullptr, (int64_t)H * n_in};
   if ((e = gemm_bf16_tn(P->dz1t, B, P->xt, B, H, n_in, B, gw1, P->err, s, kSplitK)) != cudaSuccess)
     return e;
   e = sum_slices(P->part, (int64_t)H * n_in, (int64_t)H * n_in, kSplitK, P->g + o.W1, s);
-  P->launches += 10;
+  P->launches += 7;
   return e;
 }
 
@@ -375,11 +427,13 @@ cudaError_t train_step_direct(ivhd_mlp* P, const void* x, int dtype, float scale
   cudaError_t e = load_x(P, x, dtype, scale, B);
   if (e == cudaSuccess) e = loss_grad(P, targets, B);
   if (e == cudaSuccess) {
-    k_adam<<<nb(P->n_params), 256, 0, P->stream>>>(P->w, P->m, P->v, P->g, P->n_params, lr, c1, c2);
+    const Offs o = offsets(P->n_in, P->hidden);
+    const BF16Copies cp{o.W1, o.W2, P->n_in, P->hidden, P->w1, P->w2, P->w2t};
+    k_adam<<<nb(P->n_params), 256, 0, P->stream>>>(P->w, P->m, P->v, P->g, P->n_params, lr, c1,
+                                                   c2, cp);
     ++P->launches;
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = refresh_copies(P);
   return e;
 }
 
@@ -460,8 +514,10 @@ cudaError_t replay_train_step(ivhd_mlp* P, const void* x, int dtype, float scale
   float *w = P->w, *m = P->m, *v = P->v;
   const float* g = P->g;
   int64_t np = P->n_params;
+  const Offs o = offsets(P->n_in, P->hidden);
+  BF16Copies cp{o.W1, o.W2, P->n_in, P->hidden, P->w1, P->w2, P->w2t};
   void* aa[] = {(void*)&w, (void*)&m, (void*)&v, (void*)&g, (void*)&np, (void*)&lr, (void*)&c1,
-                (void*)&c2};
+                (void*)&c2, (void*)&cp};
   cudaKernelNodeParams ka = P->kp_adam;
   ka.kernelParams = aa;
   ka.extra = nullptr;
