@@ -68,13 +68,16 @@ inline int auto_hub_threshold(int64_t entries) {
   while (h < 256 && (int64_t)(2 * h) * 70000 <= entries) h *= 2;
   return h;
 }
-// Rows of medium degree per warp in the warp-per-vertex region by default: a
-// whole warp per row.  Sharing a warp among rows (8 lanes each) measured
-// faster only with a low hub threshold on some graphs (a random
-// 200,000-vertex graph with hubs: 11.0 against 12.0 us per step), slower or
-// equal on the exact kNN graphs of 70,000 and 1.4e6 points, so it is left to
-// the autotuner.
-inline int auto_vertices_per_warp(int64_t) { return 1; }
+// Rows of medium degree per warp in the warp-per-vertex region by default.
+// With the lowest hub threshold (graphs below ~2.2M symmetric entries) most
+// warp-per-vertex rows have 16-31 entries, i.e. 4-8 int4 groups for 32 lanes:
+// two rows share a warp (16 lanes each), which halves those warps and brings
+// a 70,000-vertex launch to about one wave (exact kNN graph of the
+// MNIST-shaped set: 5.9 against 6.6 us per step; 4 rows per warp 6.4 us).
+// Larger graphs keep a whole warp per row (1.4e6 points: equal within noise).
+inline int auto_vertices_per_warp(int64_t entries) {
+  return auto_hub_threshold(entries) <= 16 ? 2 : 1;
+}
 constexpr int kMaxStepBlock = 512;   // the autotuner tries 128, 256 and 512
 constexpr int kWideRow = 512;        // rows with at least this many entries get kWideWarps warps
 constexpr int kWideWarps = 4;
