@@ -72,8 +72,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU seconds of the oracle baseline sample")
-    ap.add_argument("--variants", default="f16,bf16",
-                    help="half-precision position formats also timed (comma list, or 'none')")
+    ap.add_argument("--variants", default="f16,bf16,f32:degree_cluster,f16:degree_cluster,"
+                                          "bf16:degree_cluster",
+                    help="position formats / layout orders also timed, format[:order] "
+                         "(comma list, or 'none')")
     ap.add_argument("--qnx-rows", type=int, default=10000)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the gmm2k / mnist70k / batch64 / warmstart sub-objects")
@@ -88,8 +90,9 @@ def parse_args():
     cap.add_argument("--order", default="degree",
                      help="step: layout orders, comma list of degree, degree_cluster")
     cap.add_argument("--shapes-step", default="0:0:0",
-                     help="step: launch shapes hub_threshold:vertices_per_warp:block_size, "
-                          "comma list (0 = library default)")
+                     help="step: launch shapes hub_threshold:vertices_per_warp:block_size"
+                          "[:form], comma list (0 = library default; form auto, multi, "
+                          "grid, cluster, block)")
     cap.add_argument("--data", choices=["gmm", "mnist"], default="gmm", help="knn: data set")
     cap.add_argument("--M", type=int, default=200000, help="knn: rows")
     cap.add_argument("--N", type=int, default=100, help="knn: float dimensions")
@@ -355,9 +358,9 @@ def run_ours(args):
     out = torch.empty((w.M, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def one_embedding(knn_in, out_buf, evs=None, pos_format="f32"):
+    def one_embedding(knn_in, out_buf, evs=None, pos_format="f32", order="degree"):
         emb = ivhd.Embedding(knn_in, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b, seed=w.seed,
-                             stream=stream, device=dev, pos_format=pos_format)
+                             stream=stream, device=dev, pos_format=pos_format, order=order)
         if evs is not None:
             evs[0].record(stream)
         emb.step(n_iter)
@@ -418,9 +421,9 @@ def run_ours(args):
         rows = torch.from_numpy(synth.sample_rows(w.M, args.qnx_rows, 12345)).to(dev)
     lab = torch.from_numpy(labels).to(dev)
 
-    def quality(pos_format="f32"):
+    def quality(pos_format="f32", order="degree"):
         emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b, seed=w.seed,
-                             stream=stream, device=dev, pos_format=pos_format)
+                             stream=stream, device=dev, pos_format=pos_format, order=order)
         emb.step(n_iter)
         emb.positions(out=out)
         try:
@@ -435,10 +438,12 @@ def run_ours(args):
     q32 = quality()
     qnx_f32 = q32["qnx"]
 
-    # half-precision gathered positions: same graph, same seed, same step
+    # half-precision gathered positions and the cluster-grouped layout order:
+    # same graph, same seed, same step
     variants = {}
-    for fmt in [v for v in args.variants.split(",") if v and v != "none"]:
-        one_embedding(knn, out, pos_format=fmt)
+    for var in [v for v in args.variants.split(",") if v and v != "none"]:
+        fmt, order = (var.split(":") + ["degree"])[:2]
+        one_embedding(knn, out, pos_format=fmt, order=order)
         vs, ve = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         vk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
@@ -446,14 +451,14 @@ def run_ours(args):
         for s_ in range(args.steps):
             flush.zero_()
             vs.record(stream)
-            one_embedding(knn, out, vk[s_], pos_format=fmt)
+            one_embedding(knn, out, vk[s_], pos_format=fmt, order=order)
             ve.record(stream)
             torch.cuda.synchronize()
             vt.append(vs.elapsed_time(ve))
         vms = statistics.mean(vt)
         vkms = statistics.mean(a.elapsed_time(b) for a, b in vk)
-        qv = quality(fmt)
-        variants[fmt] = {"value": terms * n_iter / (vms / 1e3), "s_to_embed": vms / 1e3,
+        qv = quality(fmt, order)
+        variants[var] = {"value": terms * n_iter / (vms / 1e3), "s_to_embed": vms / 1e3,
                          "launch_us": 1e3 * vkms / n_iter, "qnx": qv["qnx"], "cf": qv["cf"],
                          "stress": qv["stress"], "finite": qv["finite"],
                          "qnx_minus_f32": qv["qnx"] - qnx_f32,
@@ -525,7 +530,7 @@ def run_ours(args):
         "qnx": {"value": qnx_f32, "k": w.k, "rows": int(rows.numel()),
                 "what": "Q_NX(k) of the final embedding on sampled rows (input kNN edges recovered)"},
         "quality_f32": q32,
-        "half_precision": variants,
+        "variants": variants,
         "wall_s_timed_region": wall,
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
     }
@@ -697,14 +702,18 @@ def run_capture(args):
         torch.cuda.synchronize()
         combos = [(o, f, sh) for o in args.order.split(",") for f in args.pos_format.split(",")
                   for sh in args.shapes_step.split(",")]
+        forms = {"auto": None, "multi": False, "grid": "grid", "cluster": "cluster",
+                 "block": True}
         for order, fmt, shape in combos:
-            hub, vpw, block = (int(v) for v in shape.split(":"))
+            parts = shape.split(":")
+            hub, vpw, block = (int(v) for v in parts[:3])
+            resident = forms[parts[3]] if len(parts) > 3 else None
             for rep in range(args.reps):
                 t0 = time.perf_counter()
                 emb = ivhd.Embedding(knn, r=w.r, c=w.c, opt=args.opt, a=w.a, b=w.b,
                                      seed=w.seed, pos_format=fmt, order=order,
                                      hub_threshold=hub, vertices_per_warp=vpw,
-                                     block_size=block)
+                                     block_size=block, resident=resident)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 e0, e1 = events()
