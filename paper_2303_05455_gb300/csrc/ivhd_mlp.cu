@@ -62,7 +62,7 @@ namespace {
 
 constexpr int kLossBlocks = 256;
 constexpr int kSplitK = 8;       // K = batch products (weight gradients) are split 8 ways
-constexpr int kRowChunk = 64;    // rows per partial of the batch reductions
+constexpr int kRowChunk = 32;    // rows per partial of the batch reductions
 
 // GELU'(x) = Phi(x) + x phi(x) for the exact GELU x Phi(x).
 __device__ __forceinline__ float gelu_grad_dev(float x) {
@@ -88,19 +88,57 @@ Offs offsets(int n_in, int H) {
 
 inline unsigned nb(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
-// Input rows to BF16: uint8 * scale, FP32, or BF16 as given.
+// Input rows to BF16: uint8 * scale, FP32, or BF16 as given.  Eight
+// consecutive elements per thread (one 16-byte store), element by element at a
+// ragged end or for an input that is not 16-byte aligned; each value is
+// (float)x * scale rounded to BF16 either way.
 __global__ void k_convert_x(const void* __restrict__ x, int dtype, float scale, int64_t n,
                             __nv_bfloat16* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  float v;
-  if (dtype == 1)
-    v = (float)((const uint8_t*)x)[e] * scale;
-  else if (dtype == 2)
-    v = ((const float*)x)[e] * scale;
-  else
-    v = __bfloat162float(((const __nv_bfloat16*)x)[e]) * scale;
-  out[e] = __float2bfloat16_rn(v);
+  const int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+  if (e0 >= n) return;
+  const bool vec = e0 + 8 <= n && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  float v[8];
+  if (vec) {
+    if (dtype == 1) {
+      const uint2 w = *reinterpret_cast<const uint2*>((const uint8_t*)x + e0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[q] = (float)((w.x >> (8 * q)) & 255u) * scale;
+        v[4 + q] = (float)((w.y >> (8 * q)) & 255u) * scale;
+      }
+    } else if (dtype == 2) {
+      const float4 a = reinterpret_cast<const float4*>((const float*)x + e0)[0];
+      const float4 b = reinterpret_cast<const float4*>((const float*)x + e0)[1];
+      v[0] = a.x * scale; v[1] = a.y * scale; v[2] = a.z * scale; v[3] = a.w * scale;
+      v[4] = b.x * scale; v[5] = b.y * scale; v[6] = b.z * scale; v[7] = b.w * scale;
+    } else {
+      const uint4 w = *reinterpret_cast<const uint4*>((const __nv_bfloat16*)x + e0);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[2 * q] = __uint_as_float(ws[q] << 16) * scale;
+        v[2 * q + 1] = __uint_as_float(ws[q] & 0xFFFF0000u) * scale;
+      }
+    }
+    uint32_t o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+      memcpy(&o[q], &h, 4);
+    }
+    *reinterpret_cast<uint4*>(out + e0) = make_uint4(o[0], o[1], o[2], o[3]);
+    return;
+  }
+  for (int64_t e = e0; e < e0 + 8 && e < n; ++e) {
+    float f;
+    if (dtype == 1)
+      f = (float)((const uint8_t*)x)[e] * scale;
+    else if (dtype == 2)
+      f = ((const float*)x)[e] * scale;
+    else
+      f = __bfloat162float(((const __nv_bfloat16*)x)[e]) * scale;
+    out[e] = __float2bfloat16_rn(f);
+  }
 }
 
 // Tiled BF16 transpose: out[c][r] = in[r][c] for an R x C matrix.
@@ -392,7 +430,7 @@ cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B) {
 
 cudaError_t load_x(ivhd_mlp* P, const void* x, int dtype, float scale, int64_t rows) {
   const int64_t n = rows * P->n_in;
-  k_convert_x<<<nb(n), 256, 0, P->stream>>>(x, dtype, scale, n, P->xb);
+  k_convert_x<<<nb((n + 7) / 8), 256, 0, P->stream>>>(x, dtype, scale, n, P->xb);
   ++P->launches;
   return cudaGetLastError();
 }
