@@ -41,9 +41,16 @@ struct ivhd_mlp {
   __nv_bfloat16 *h1 = nullptr, *h1t = nullptr, *h2 = nullptr;
   __nv_bfloat16 *dz2 = nullptr, *dz2t = nullptr, *dz1 = nullptr, *dz1t = nullptr;
   float *y = nullptr, *dy = nullptr;
-  float* part = nullptr;       // split-K slices and batch-chunk partial sums
+  float* part = nullptr;       // split-K slices (dW1) and batch-chunk partial sums
+  float* part2 = nullptr;      // split-K slices of dW2
+  float* cs_part = nullptr;    // chunk partials of the bias gradients (side stream)
+  float* g3_part = nullptr;    // chunk partials of the output-layer gradient (side stream)
   double* loss_part = nullptr;
   double* loss_out = nullptr;
+  // side stream for the work off the GEMM chain (the transposed input, the
+  // bias gradients), ordered against the main stream by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[6] = {};
   int32_t* err = nullptr;
   int64_t launches = 0;
   // the training step captured as a CUDA graph for batch size graph_B; the
@@ -301,12 +308,13 @@ __global__ void k_dz2(const float* __restrict__ dy, const float* __restrict__ W3
   }
 }
 
-// Bias gradient: column sums of a B x H BF16 matrix, chunk partials then an ordered sum.
-cudaError_t colsum(ivhd_mlp* P, const __nv_bfloat16* a, int B, int H, float* out) {
+// Bias gradient: column sums of a B x H BF16 matrix, chunk partials (in buf)
+// then an ordered sum.
+cudaError_t colsum(ivhd_mlp* P, const __nv_bfloat16* a, int B, int H, float* out, float* buf,
+                   cudaStream_t s) {
   const int chunks = (B + kRowChunk - 1) / kRowChunk;
-  k_colsum_part<<<dim3((unsigned)((H + 255) / 256), (unsigned)chunks), 256, 0, P->stream>>>(
-      a, B, H, P->part);
-  k_chunk_sum<<<(unsigned)((H + 255) / 256), 256, 0, P->stream>>>(P->part, chunks, H, out);
+  k_colsum_part<<<dim3((unsigned)((H + 255) / 256), (unsigned)chunks), 256, 0, s>>>(a, B, H, buf);
+  k_chunk_sum<<<(unsigned)((H + 255) / 256), 256, 0, s>>>(buf, chunks, H, out);
   P->launches += 2;
   return cudaGetLastError();
 }
@@ -314,27 +322,42 @@ cudaError_t colsum(ivhd_mlp* P, const __nv_bfloat16* a, int B, int H, float* out
 // Adam on the flat FP32 parameters (bias-corrected, Kingma and Ba).  The
 // updated W1 and W2 are also written as the BF16 copies the tensor cores read
 // (W1, W2 and the transposed W2), the same values refresh_copies would make.
+// Given the split-K slices of the W1 and W2 gradients it adds them itself
+// (slice order, as k_sum_slices does) instead of reading g there.
 struct BF16Copies {
   int64_t w1_off, w2_off;  // offsets of W1 (H x n_in) and W2 (H x H) in the flat vector
   int n_in, H;
   __nv_bfloat16 *w1, *w2, *w2t;
+  const float *s_w1, *s_w2;  // gradient slices [splits][H x n_in], [splits][H x H], or null
+  int splits;
 };
 __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, int64_t n, float lr, float c1, float c2,
                        BF16Copies cp) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n) return;
-  const float gi = g[e];
+  const int64_t a = e - cp.w1_off, q = e - cp.w2_off;
+  const int64_t n1 = (int64_t)cp.H * cp.n_in, n2 = (int64_t)cp.H * cp.H;
+  const bool in1 = a >= 0 && a < n1, in2 = q >= 0 && q < n2;
+  float gi;
+  if (in1 && cp.s_w1) {
+    gi = 0.f;
+    for (int z = 0; z < cp.splits; ++z) gi += cp.s_w1[z * n1 + a];
+  } else if (in2 && cp.s_w2) {
+    gi = 0.f;
+    for (int z = 0; z < cp.splits; ++z) gi += cp.s_w2[z * n2 + q];
+  } else {
+    gi = g[e];
+  }
   const float mi = fmaf(0.9f, m[e], 0.1f * gi);
   const float vi = fmaf(0.999f, v[e], 0.001f * gi * gi);
   m[e] = mi;
   v[e] = vi;
   const float wn = w[e] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
   w[e] = wn;
-  const int64_t a = e - cp.w1_off, q = e - cp.w2_off;
-  if (a >= 0 && a < (int64_t)cp.H * cp.n_in) {
+  if (in1) {
     cp.w1[a] = __float2bfloat16_rn(wn);
-  } else if (q >= 0 && q < (int64_t)cp.H * cp.H) {
+  } else if (in2) {
     const __nv_bfloat16 h = __float2bfloat16_rn(wn);
     cp.w2[q] = h;
     cp.w2t[(q % cp.H) * cp.H + q / cp.H] = h;
@@ -385,46 +408,71 @@ cudaError_t forward(ivhd_mlp* P, int B, bool train = false) {
 }
 
 // Loss and gradients of B rows (inputs in P->xb, targets tgt) into P->g.
-cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B) {
+// With sum_weights false the split-K slices of dW1 (P->part) and dW2
+// (P->part2) are left for k_adam to add, in the same order.
+// The transposed input, the output-layer gradient and the bias gradients run
+// on the side stream beside the GEMMs; the side stream's work is joined before
+// returning.
+cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B, bool sum_weights = true) {
   const Offs o = offsets(P->n_in, P->hidden);
   const int H = P->hidden, n_in = P->n_in;
-  cudaStream_t s = P->stream;
-  cudaError_t e = forward(P, B, true);
+  cudaStream_t s = P->stream, side = P->side;
+  cudaError_t e = cudaEventRecord(P->ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(side, P->ev[0], 0);
+  if (e == cudaSuccess) e = transpose(P->xb, B, n_in, P->xt, side);  // X^T for dW1
+  if (e == cudaSuccess) e = cudaEventRecord(P->ev[1], side);
+  ++P->launches;
+  if (e == cudaSuccess) e = forward(P, B, true);
   if (e != cudaSuccess) return e;
   k_loss<<<kLossBlocks, 256, 0, s>>>(P->y, tgt, B, P->dy, P->loss_part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(P->ev[5], s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(side, P->ev[5], 0)) != cudaSuccess) return e;
   {
     // dW3 (2 x H) and db3 (2): rows [j][0..H) of the (2, H + 1) chunk sums, bias in column H
     const int chunks = (B + kRowChunk - 1) / kRowChunk;
-    k_grad3_part<<<dim3(nb(H + 1), (unsigned)chunks), 256, 0, s>>>(P->dy, P->h2, B, H, P->part);
-    k_grad3_final<<<nb(2 * (int64_t)(H + 1)), 256, 0, s>>>(P->part, chunks, H, P->g + o.W3,
-                                                            P->g + o.b3, P->loss_part,
-                                                            kLossBlocks, B, P->loss_out);
+    k_grad3_part<<<dim3(nb(H + 1), (unsigned)chunks), 256, 0, side>>>(P->dy, P->h2, B, H,
+                                                                       P->g3_part);
+    k_grad3_final<<<nb(2 * (int64_t)(H + 1)), 256, 0, side>>>(P->g3_part, chunks, H,
+                                                               P->g + o.W3, P->g + o.b3,
+                                                               P->loss_part, kLossBlocks, B,
+                                                               P->loss_out);
   }
   k_dz2<<<dim3((unsigned)((H + kTile - 1) / kTile), (unsigned)((B + kTile - 1) / kTile)),
           dim3(kTile, 8), 0, s>>>(P->dy, P->w + o.W3, P->z2, B, H, P->dz2, P->dz2t);
   P->launches += 4;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = colsum(P, P->dz2, B, H, P->g + o.b2)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(P->ev[2], s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(side, P->ev[2], 0)) != cudaSuccess) return e;
+  if ((e = colsum(P, P->dz2, B, H, P->g + o.b2, P->cs_part, side)) != cudaSuccess) return e;
   // dW2 = dZ2^T H1 (dZ2^T from k_dz2, H1^T from the forward pass)
-  GemmEpilogue gw2{kEpStoreF32, H, P->part, nullptr, nullptr, nullptr, (int64_t)H * H};
+  GemmEpilogue gw2{kEpStoreF32, H, P->part2, nullptr, nullptr, nullptr, (int64_t)H * H};
   if ((e = gemm_bf16_tn(P->dz2t, B, P->h1t, B, H, H, B, gw2, P->err, s, kSplitK)) != cudaSuccess)
     return e;
-  if ((e = sum_slices(P->part, (int64_t)H * H, (int64_t)H * H, kSplitK, P->g + o.W2, s)) !=
-      cudaSuccess)
+  if (sum_weights &&
+      (e = sum_slices(P->part2, (int64_t)H * H, (int64_t)H * H, kSplitK, P->g + o.W2, s)) !=
+          cudaSuccess)
     return e;
   // dZ1 = (dZ2 W2) * GELU'(z1), also written transposed
   GemmEpilogue gz1{kEpGeluGrad, H, nullptr, P->dz1, nullptr, P->z1, 0};
   gz1.out_bf16_t = P->dz1t;
   gz1.ld_t = B;
   if ((e = gemm_bf16_tn(P->dz2, H, P->w2t, H, B, H, H, gz1, P->err, s)) != cudaSuccess) return e;
-  if ((e = colsum(P, P->dz1, B, H, P->g + o.b1)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(P->ev[3], s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(side, P->ev[3], 0)) != cudaSuccess) return e;
+  if ((e = colsum(P, P->dz1, B, H, P->g + o.b1, P->cs_part, side)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(P->ev[4], side)) != cudaSuccess) return e;
   // dW1 = dZ1^T X
-  if ((e = transpose(P->xb, B, n_in, P->xt, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s, P->ev[1], 0)) != cudaSuccess) return e;
   GemmEpilogue gw1{kEpStoreF32, n_in, P->part, nullptr, nullptr, nullptr, (int64_t)H * n_in};
   if ((e = gemm_bf16_tn(P->dz1t, B, P->xt, B, H, n_in, B, gw1, P->err, s, kSplitK)) != cudaSuccess)
     return e;
-  e = sum_slices(P->part, (int64_t)H * n_in, (int64_t)H * n_in, kSplitK, P->g + o.W1, s);
-  P->launches += 7;
+  if (sum_weights) {
+    e = sum_slices(P->part, (int64_t)H * n_in, (int64_t)H * n_in, kSplitK, P->g + o.W1, s);
+    P->launches += 2;
+  }
+  P->launches += 3;  // the three GEMMs
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, P->ev[4], 0);  // join the side stream
   return e;
 }
 
@@ -463,10 +511,11 @@ bool batch_ok(const ivhd_mlp* P, int64_t B) { return B >= 8 && B <= P->max_batch
 cudaError_t train_step_direct(ivhd_mlp* P, const void* x, int dtype, float scale,
                               const float* targets, int B, float lr, float c1, float c2) {
   cudaError_t e = load_x(P, x, dtype, scale, B);
-  if (e == cudaSuccess) e = loss_grad(P, targets, B);
+  if (e == cudaSuccess) e = loss_grad(P, targets, B, false);
   if (e == cudaSuccess) {
     const Offs o = offsets(P->n_in, P->hidden);
-    const BF16Copies cp{o.W1, o.W2, P->n_in, P->hidden, P->w1, P->w2, P->w2t};
+    const BF16Copies cp{o.W1,   o.W2,    P->n_in,  P->hidden, P->w1,
+                        P->w2,  P->w2t,  P->part,  P->part2,  kSplitK};
     k_adam<<<nb(P->n_params), 256, 0, P->stream>>>(P->w, P->m, P->v, P->g, P->n_params, lr, c1,
                                                    c2, cp);
     ++P->launches;
@@ -553,7 +602,8 @@ cudaError_t replay_train_step(ivhd_mlp* P, const void* x, int dtype, float scale
   const float* g = P->g;
   int64_t np = P->n_params;
   const Offs o = offsets(P->n_in, P->hidden);
-  BF16Copies cp{o.W1, o.W2, P->n_in, P->hidden, P->w1, P->w2, P->w2t};
+  BF16Copies cp{o.W1, o.W2, P->n_in, P->hidden, P->w1, P->w2, P->w2t, P->part, P->part2,
+                kSplitK};
   void* aa[] = {(void*)&w, (void*)&m, (void*)&v, (void*)&g, (void*)&np, (void*)&lr, (void*)&c1,
                 (void*)&c2, (void*)&cp};
   cudaKernelNodeParams ka = P->kp_adam;
@@ -621,10 +671,16 @@ ivhd_status ivhd_mlp_create(int32_t n_in, int32_t hidden, int32_t max_batch, voi
     const int64_t wide = H > n_in ? H : n_in;
     const int64_t a1 = (int64_t)kSplitK * H * wide, a2 = (chunks + 1) * 2 * (H + 1);
     A(&P->part, a1 > a2 ? a1 : a2);
+    A(&P->part2, (int64_t)kSplitK * H * H);
+    A(&P->cs_part, chunks * H);
+    A(&P->g3_part, chunks * 2 * (H + 1));
   }
   A(&P->loss_part, kLossBlocks);
   A(&P->loss_out, 1);
   A(&P->err, 1);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+  for (cudaEvent_t& ev : P->ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->w, 0, o.total * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->m, 0, o.total * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->v, 0, o.total * sizeof(float), s);
@@ -645,10 +701,13 @@ void ivhd_mlp_destroy(ivhd_mlp* P) {
   if (P->graph) cudaGraphDestroy(P->graph);
   void* bufs[] = {P->w, P->m, P->v, P->g, P->w1, P->w2, P->w2t, P->xb, P->xt, P->z1, P->z2,
                   P->h1, P->h1t, P->h2, P->dz2, P->dz2t, P->dz1, P->dz1t, P->y, P->dy,
-                  P->part, P->loss_part, P->loss_out, P->err};
+                  P->part, P->part2, P->cs_part, P->g3_part, P->loss_part, P->loss_out, P->err};
   for (void* b : bufs)
     if (b) dev_free(b, P->stream);
   cudaStreamSynchronize(P->stream);
+  for (cudaEvent_t ev : P->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (P->side) cudaStreamDestroy(P->side);
   delete P;
 }
 
