@@ -210,32 +210,49 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y,
   }
 }
 
-// dW3 (2 x H) and db3 (2) from the chunk partials of k_grad3_part (summed over
-// the chunks in order, as k_chunk_sum does), and the batch loss from the
-// per-block partials of k_loss (summed in order, divided by B).
+// Column sums of chunk partials, out[q] = sum_c part[c * n + q], on blocks of
+// (32, kSumWarps) threads: a block takes 32 columns (coalesced loads), warp w
+// sums the chunks c = w, w + kSumWarps, ... in order, then thread (x, 0) adds
+// the kSumWarps partial sums in order (a fixed order: deterministic).
+constexpr int kSumWarps = 8;
+__device__ __forceinline__ float chunk_col_sum(const float* __restrict__ part, int chunks, int n,
+                                               int q) {
+  __shared__ float sh[kSumWarps][33];
+  float t = 0.f;
+  if (q < n)
+#pragma unroll 4
+    for (int c = (int)threadIdx.y; c < chunks; c += kSumWarps) t += part[(int64_t)c * n + q];
+  sh[threadIdx.y][threadIdx.x] = t;
+  __syncthreads();
+  float s = sh[0][threadIdx.x];
+#pragma unroll
+  for (int w = 1; w < kSumWarps; ++w) s += sh[w][threadIdx.x];
+  return s;
+}
+
+// dW3 (2 x H) and db3 (2) from the chunk partials of k_grad3_part, and the
+// batch loss from the per-block partials of k_loss (lane l sums partials l,
+// l + 32, ... in order, then a fixed butterfly; divided by B).
 __global__ void k_grad3_final(const float* __restrict__ part, int chunks, int H,
                               float* __restrict__ gW3, float* __restrict__ gb3,
                               const double* __restrict__ loss_part, int n_loss, int B,
                               double* __restrict__ loss_out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x * 32 + threadIdx.x;
   const int n = 2 * (H + 1);
-  if (q < n) {
-    float t = 0.f;
-#pragma unroll 8
-    for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * n + q];
+  const float t = chunk_col_sum(part, chunks, n, q);
+  if (threadIdx.y == 0 && q < n) {
     const int j = q / (H + 1), i = q - j * (H + 1);
     if (i < H)
       gW3[(int64_t)j * H + i] = t;
     else
       gb3[j] = t;
   }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {
-    // the loss: lane l sums partials l, l + 32, ... in order, then a fixed butterfly
-    double t = 0.0;
-    for (int i = (int)threadIdx.x; i < n_loss; i += 32) t += loss_part[i];
+  if (blockIdx.x == 0 && threadIdx.y == 1) {
+    double l = 0.0;
+    for (int i = (int)threadIdx.x; i < n_loss; i += 32) l += loss_part[i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) loss_out[0] = t / B;
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (threadIdx.x == 0) loss_out[0] = l / B;
   }
 }
 
@@ -271,15 +288,12 @@ __global__ void k_colsum_part(const __nv_bfloat16* __restrict__ a, int B, int H,
   part[(int64_t)c * H + i] = s;
 }
 
-// out[q] = sum over chunks c (in order) of part[c * n + q].
+// out[q] = sum over chunks c of part[c * n + q] (order of chunk_col_sum).
 __global__ void k_chunk_sum(const float* __restrict__ part, int chunks, int n,
                             float* __restrict__ out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  float t = 0.f;
-#pragma unroll 8
-  for (int c = 0; c < chunks; ++c) t += part[(int64_t)c * n + q];
-  out[q] = t;
+  const int q = blockIdx.x * 32 + threadIdx.x;
+  const float t = chunk_col_sum(part, chunks, n, q);
+  if (threadIdx.y == 0 && q < n) out[q] = t;
 }
 
 // dZ2 = (dY W3) * GELU'(z2) in BF16, written row-major (B x H) and transposed
@@ -314,7 +328,7 @@ cudaError_t colsum(ivhd_mlp* P, const __nv_bfloat16* a, int B, int H, float* out
                    cudaStream_t s) {
   const int chunks = (B + kRowChunk - 1) / kRowChunk;
   k_colsum_part<<<dim3((unsigned)((H + 255) / 256), (unsigned)chunks), 256, 0, s>>>(a, B, H, buf);
-  k_chunk_sum<<<(unsigned)((H + 255) / 256), 256, 0, s>>>(buf, chunks, H, out);
+  k_chunk_sum<<<(unsigned)((H + 31) / 32), dim3(32, kSumWarps), 0, s>>>(buf, chunks, H, out);
   P->launches += 2;
   return cudaGetLastError();
 }
@@ -433,10 +447,9 @@ cudaError_t loss_grad(ivhd_mlp* P, const float* tgt, int B, bool sum_weights = t
     const int chunks = (B + kRowChunk - 1) / kRowChunk;
     k_grad3_part<<<dim3(nb(H + 1), (unsigned)chunks), 256, 0, side>>>(P->dy, P->h2, B, H,
                                                                        P->g3_part);
-    k_grad3_final<<<nb(2 * (int64_t)(H + 1)), 256, 0, side>>>(P->g3_part, chunks, H,
-                                                               P->g + o.W3, P->g + o.b3,
-                                                               P->loss_part, kLossBlocks, B,
-                                                               P->loss_out);
+    k_grad3_final<<<(unsigned)((2 * (H + 1) + 31) / 32), dim3(32, kSumWarps), 0, side>>>(
+        P->g3_part, chunks, H, P->g + o.W3, P->g + o.b3, P->loss_part, kLossBlocks, B,
+        P->loss_out);
   }
   k_dz2<<<dim3((unsigned)((H + kTile - 1) / kTile), (unsigned)((B + kTile - 1) / kTile)),
           dim3(kTile, 8), 0, s>>>(P->dy, P->w + o.W3, P->z2, B, H, P->dz2, P->dz2t);

@@ -17,8 +17,9 @@ Inputs (never built by the CUDA path):
 
 * mnist70k: the 70,000 MNIST-shaped uint8 images, their exact kNN graph from
   the oracle (``oracle.knn_u8_gemm``, pinned equal to the serial definition),
-  k = 5, r = 1, c = 0.01, 2,000 steps of momentum (a = 0.9, b = 1e-3) and of
-  Adadelta.  The GPU's own kNN build is also compared with that graph, every
+  k = 5, r = 1, c = 0.01, 2,000 steps of momentum (a = 0.9, b = 1e-3), of
+  Nesterov (same a and b; b lambda_max ~ 0.93 is inside its stability limit
+  2 (1 + a) / (1 + 2 a) ~ 1.36) and of Adadelta.  The GPU's own kNN build is also compared with that graph, every
   row, bit for bit.
 * 1.4e6 vertices: a kNN-shaped graph with 50 planted clusters whose sizes are
   the power law of the gmm1p4m mixture (``synth.planted_knn_graph``), k = 5,
@@ -46,7 +47,8 @@ QNX_BAND = 0.01     # the equal-kNN-precision bar
 CF_BAND = 0.01
 STRESS_BAND = 0.005  # relative; the final stress of two runs from the same start that
 #                     differ in rounding (FP32 or half-precision gathers vs FP64)
-OPT_ID = {"momentum": oracle.OPT_MOMENTUM, "adadelta": oracle.OPT_ADADELTA}
+OPT_ID = {"momentum": oracle.OPT_MOMENTUM, "nesterov": oracle.OPT_NESTEROV,
+          "adadelta": oracle.OPT_ADADELTA}
 
 _cache = {}
 
@@ -128,7 +130,7 @@ def test_knn_build_mnist70k_equals_the_oracle_graph_on_every_row():
     assert np.array_equal(got, knn_ref)
 
 
-@pytest.mark.parametrize("opt", ["momentum", "adadelta"])
+@pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
 def test_full_run_mnist70k_matches_oracle(opt):
     data = _mnist70k()
     Y_ref, ref = _oracle_run("c2", data, opt)

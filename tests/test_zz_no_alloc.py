@@ -11,7 +11,9 @@ before the call is still pending after it (the next allocating call consumes
 it).  This file is collected last so that a run stopping at the first failure
 has run everything else already.
 """
+import contextlib
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -31,6 +33,18 @@ def _static_qnx(L, Y, knn, rows, lowd):
     return st, q.value
 
 
+@contextlib.contextmanager
+def _no_collection():
+    """Objects of earlier tests are freed first, and not while counting (their
+    destructors would lower the library's live-allocation count mid-call)."""
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
+
+
 def _alloc_counters(L):
     torch.cuda.synchronize()
     stats = torch.cuda.memory_stats()
@@ -47,10 +61,11 @@ def test_static_qnx_matches_allocating_entry_point_on_consecutive_calls():
     for call, n in enumerate((30_000, 1_000)):          # second call: fewer rows, stale scratch
         rows = torch.from_numpy(synth.sample_rows(M, n, 100 + call)).cuda()
         low = torch.empty((n, k), dtype=torch.int32, device="cuda")
-        before = _alloc_counters(L)
-        st, q = _static_qnx(L, Y, knn, rows, low)
-        assert st == 0, st
-        assert _alloc_counters(L) == before
+        with _no_collection():
+            before = _alloc_counters(L)
+            st, q = _static_qnx(L, Y, knn, rows, low)
+            assert st == 0, st
+            assert _alloc_counters(L) == before
         q_ref, low_ref = ivhd.eval_qnx(Y, knn, rows, return_lowd=True)
         assert q == q_ref
         assert torch.equal(low, low_ref)
