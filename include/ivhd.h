@@ -308,6 +308,7 @@ typedef struct {
                                 replay), 1 one block for the whole call, 2 a cluster of 8
                                 blocks for the whole call, 3 a persistent grid for the
                                 whole call (see ivhd_params.resident) */
+    int32_t step_blocks;     /* blocks of one step-kernel launch (launch form 0) */
 } ivhd_info_t;
 
 /* Fills *out.  Host only; does not synchronise. */
@@ -536,6 +537,21 @@ ivhd_status ivhd_eval_cf(const float *Y, int64_t M, const int32_t *labels, int32
  */
 ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers, int32_t repeats,
                               double *gathers_per_s, void *stream);
+
+/*
+ * Launch floor of the step loop: writes to *us_per_launch the device time per
+ * launch of a CUDA graph of n_launches chained programmatic dependent launches
+ * (the form ivhd_step replays) of an empty kernel of `grid` blocks of `block`
+ * threads; each block waits for its predecessor grid and releases its
+ * successor, as the step kernel does, and does nothing else.  A step kernel
+ * of the same grid cannot take less per step.  Allocates nothing on the
+ * device; the graph is captured on a private stream and timed on `stream`.
+ * Constraints: 1 <= grid <= 2^20, block a multiple of 32 in [32, 1024],
+ * 1 <= n_launches <= 100000.  Synchronises.  Errors: IVHD_ERR_ARG,
+ * IVHD_ERR_CUDA.
+ */
+ivhd_status ivhd_probe_launch(int32_t grid, int32_t block, int32_t n_launches,
+                              double *us_per_launch, void *stream);
 
 /*
  * C = A B^T on the tensor cores (tcgen05, TMA-fed, FP32 accumulation): A is

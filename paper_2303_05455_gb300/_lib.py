@@ -22,7 +22,7 @@ SYMBOLS = (
     "ivhd_forces", "ivhd_stress", "ivhd_random_neighbors", "ivhd_info", "ivhd_state_size",
     "ivhd_get_state", "ivhd_set_state", "ivhd_destroy", "ivhd_status_string", "ivhd_version",
     "ivhd_knn_build", "ivhd_knn_build_ex", "ivhd_eval_qnx", "ivhd_eval_cf", "ivhd_eval_qnx_static",
-    "ivhd_probe_gather", "ivhd_set_metric", "ivhd_resample_random_neighbors",
+    "ivhd_probe_gather", "ivhd_probe_launch", "ivhd_set_metric", "ivhd_resample_random_neighbors",
     "ivhd_restrict_nn", "ivhd_adaptive_state", "ivhd_create_batch", "ivhd_autotune",
     "ivhd_gemm_bf16_tn", "ivhd_mlp_create", "ivhd_mlp_destroy", "ivhd_mlp_num_params",
     "ivhd_mlp_set_params", "ivhd_mlp_get_params", "ivhd_mlp_loss_grad", "ivhd_mlp_train_step",
@@ -67,6 +67,7 @@ class Info(ctypes.Structure):
         ("steps_done", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("setup_launches", ctypes.c_int64), ("aux_launches", ctypes.c_int64),
         ("launch_form", ctypes.c_int32),
+        ("step_blocks", ctypes.c_int32),
     ]
 
 
@@ -163,6 +164,8 @@ def load(build_if_missing: bool = False):
     L.ivhd_eval_qnx_static.restype = i32
     L.ivhd_probe_gather.argtypes = [i64, i64, i32, ctypes.POINTER(ctypes.c_double), P]
     L.ivhd_probe_gather.restype = i32
+    L.ivhd_probe_launch.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_double), P]
+    L.ivhd_probe_launch.restype = i32
     L.ivhd_set_metric.argtypes = [P, i32]
     L.ivhd_set_metric.restype = i32
     L.ivhd_resample_random_neighbors.argtypes = [P, u64]

@@ -90,6 +90,80 @@ extern "C" ivhd_status ivhd_probe_gather(int64_t n_positions, int64_t n_gathers,
   return IVHD_OK;
 }
 
+// ---- launch floor ------------------------------------------------------------
+//
+// The step loop replays one kernel per step, each a programmatic dependent
+// launch of the previous one.  For a small embedding the step's work is a few
+// microseconds of dependent L2 accesses, and the cost of dispatching the
+// grid's blocks and handing over between launches is a large share of it.
+// This probe times that cost alone: the same chain of launches of a kernel
+// whose blocks only wait for the previous grid and release the next one.
+namespace ivhd {
+namespace {
+
+__global__ void k_probe_empty() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+}  // namespace
+}  // namespace ivhd
+
+extern "C" ivhd_status ivhd_probe_launch(int32_t grid, int32_t block, int32_t n_launches,
+                                         double* us_per_launch, void* stream) {
+  if (!us_per_launch || grid < 1 || grid > (1 << 20) || block < 32 || block > 1024 ||
+      block % 32 || n_launches < 1 || n_launches > 100000)
+    return IVHD_ERR_ARG;
+  NvtxScope nvtx_("ivhd_probe_launch");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t el = cudaSuccess;
+    for (int i = 0; i < n_launches && el == cudaSuccess; ++i) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)grid);
+      cfg.blockDim = dim3((unsigned)block);
+      cfg.stream = cap;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      el = cudaLaunchKernelEx(&cfg, k_probe_empty);
+    }
+    e = cudaStreamEndCapture(cap, &graph);
+    if (el != cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);  // warm-up (uploads the graph)
+  float best = 0.f;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+    float ms = 0.f;
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (rep == 0 || ms < best)) best = ms;
+  }
+  cudaStreamSynchronize(s);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return IVHD_ERR_CUDA;
+  *us_per_launch = 1e3 * (double)best / n_launches;
+  return IVHD_OK;
+}
+
 // ---- bounded-wait check ------------------------------------------------------
 //
 // The tensor-core kernels wait on mbarriers with a bounded number of polls and

@@ -417,6 +417,16 @@ def probe_gather(n_positions: int, n_gathers: int = 16_777_216, repeats: int = 2
     return v.value
 
 
+def probe_launch(grid: int, block: int = 128, n_launches: int = 2000, stream=None) -> float:
+    """Device microseconds per launch of a graph of chained programmatic
+    dependent launches of an empty kernel of ``grid`` x ``block`` threads."""
+    L = _lib.load()
+    v = ctypes.c_double()
+    check(L.ivhd_probe_launch(int(grid), int(block), int(n_launches), ctypes.byref(v),
+                              _stream_ptr(stream)), "ivhd_probe_launch")
+    return v.value
+
+
 # Every callback pair ever registered stays referenced: blocks keep the free
 # routine of the allocator that made them after the setting changes.
 _ALLOCATORS: list = []

@@ -149,6 +149,14 @@ def test_knn_build_and_eval_reject_bad_args(L):
     assert L.ivhd_probe_gather(1000, 100, 1, ctypes.byref(out), None) == -1
     assert L.ivhd_probe_gather(1000, 1 << 20, 0, ctypes.byref(out), None) == -1
     assert L.ivhd_probe_gather(1000, 1 << 20, 1, None, None) == -1
+    us = ctypes.c_double()
+    assert L.ivhd_probe_launch(0, 128, 10, ctypes.byref(us), None) == -1         # grid < 1
+    assert L.ivhd_probe_launch((1 << 20) + 1, 128, 10, ctypes.byref(us), None) == -1
+    assert L.ivhd_probe_launch(152, 100, 10, ctypes.byref(us), None) == -1       # not 32 k
+    assert L.ivhd_probe_launch(152, 2048, 10, ctypes.byref(us), None) == -1      # > 1024
+    assert L.ivhd_probe_launch(152, 128, 0, ctypes.byref(us), None) == -1        # n < 1
+    assert L.ivhd_probe_launch(152, 128, 100001, ctypes.byref(us), None) == -1
+    assert L.ivhd_probe_launch(152, 128, 10, None, None) == -1
 
 
 @pytest.mark.parametrize("opt,field,value", [

@@ -437,6 +437,28 @@ def test_probe_gather_rate_is_plausible():
     assert 1e9 < rate < 1e13
 
 
+def test_probe_launch_floor_is_plausible_and_below_the_step_of_the_same_grid():
+    small = ivhd.probe_launch(152, 128, 500)
+    large = ivhd.probe_launch(152 * 30, 128, 500)
+    assert 0.05 < small < 50 and small < large        # more blocks take longer to dispatch
+    M = 70_000
+    knn = synth.random_knn_graph(M, 5, 7)
+    emb = ivhd.Embedding(torch.from_numpy(knn).cuda(), r=1, c=0.01, a=0.9, b=1e-3, seed=1)
+    emb.step(50)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    emb.step(500)
+    e1.record()
+    torch.cuda.synchronize()
+    inf = emb.info()
+    emb.close()
+    step_us = 1e3 * e0.elapsed_time(e1) / 500
+    floor = ivhd.probe_launch(inf["step_blocks"], 128, 500)
+    assert inf["launch_form"] == 0 and inf["step_blocks"] > 0
+    assert step_us >= 0.8 * floor, (step_us, floor)
+
+
 @pytest.mark.parametrize("opt", ["momentum", "nesterov", "adadelta"])
 @pytest.mark.parametrize("case", ["gmm2k", "hubs5k", "ragged37", "star"])
 def test_cluster_order_matches_oracle(case, opt):
