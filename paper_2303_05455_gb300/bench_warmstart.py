@@ -59,8 +59,10 @@ def measure(train: int = 200000, holdout: int = 1400000, epochs: int = 10, steps
     mu, sd = Ytr.mean(0), Ytr.std(0)
     T = ((Ytr - mu) / sd).contiguous()
 
-    # 2. MLP training
-    net = ivhd.MLP(784, 512, max_batch=4096)
+    # 2. MLP training (batches of 4,096); forward passes run in chunks of up to
+    # max_batch rows, and chunks of 65,536 make the placement's GEMMs several
+    # waves long (the outputs do not depend on the chunking)
+    net = ivhd.MLP(784, 512, max_batch=65536)
     rng = np.random.Generator(np.random.PCG64(5))
     init = []
     for fo, fi, sc in ((512, 784, 1.0), (512, None, 0.0), (512, 512, 1.0), (512, None, 0.0),
