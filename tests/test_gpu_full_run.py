@@ -150,17 +150,33 @@ def test_full_run_planted_1p4m_matches_oracle():
     _compare(got, ref)
 
 
-@pytest.mark.parametrize("where", ["c2", "c3"])
-def test_full_run_fp16_positions_match_oracle(where):
+# Adadelta with half-precision gathered positions is not equal precision: its
+# per-coordinate step sqrt(E[dx^2] + eps) / sqrt(E[g^2] + eps) normalises the
+# gradient, so near convergence the rounding noise of the half-precision
+# differences keeps the steps from shrinking, and the run ends at a higher
+# stress than the oracle's (measured at mnist70k: FP16 1,554 and BF16 2,481
+# against 1,480; Q_NX and cf stay within 0.01, as they do for any embedding
+# that keeps the clusters apart).  Momentum and Nesterov scale the noise by b.
+def _adadelta_half(fmt, gap):
+    return pytest.param("c2", "adadelta", marks=pytest.mark.xfail(
+        strict=True, reason=f"{fmt} gathers with Adadelta: final stress {gap} above the "
+                            "oracle's, outside the 0.5 % band (not equal precision)"))
+
+
+HALF_CASES = [("c2", "momentum"), ("c2", "nesterov"), ("c3", "momentum")]
+
+
+@pytest.mark.parametrize("where,opt", HALF_CASES + [_adadelta_half("FP16", "5 %")])
+def test_full_run_fp16_positions_match_oracle(where, opt):
     data = _mnist70k() if where == "c2" else _planted1p4m()
-    _, ref = _oracle_run(where, data, "momentum")
-    _, got = _gpu_run(data, "momentum", "f16")
+    _, ref = _oracle_run(where, data, opt)
+    _, got = _gpu_run(data, opt, "f16")
     _compare(got, ref)
 
 
-@pytest.mark.parametrize("where", ["c2", "c3"])
-def test_full_run_bf16_positions_match_oracle(where):
+@pytest.mark.parametrize("where,opt", HALF_CASES + [_adadelta_half("BF16", "68 %")])
+def test_full_run_bf16_positions_match_oracle(where, opt):
     data = _mnist70k() if where == "c2" else _planted1p4m()
-    _, ref = _oracle_run(where, data, "momentum")
-    _, got = _gpu_run(data, "momentum", "bf16")
+    _, ref = _oracle_run(where, data, opt)
+    _, got = _gpu_run(data, opt, "bf16")
     _compare(got, ref)
