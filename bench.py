@@ -633,7 +633,8 @@ def config_subline(name: str, opts, dev, stream, flush, steps: int, warmup: int,
             if inf["launch_form"] == 0:
                 # the chained launches alone, with this step grid (ivhd_probe_launch)
                 binding["step_blocks"] = inf["step_blocks"]
-                binding["launch_floor_us"] = ivhd.probe_launch(inf["step_blocks"], 128, 2000)
+                binding["launch_floor_us"] = ivhd.probe_launch(inf["step_blocks"],
+                                                               inf["step_threads"], 2000)
         qnx = ivhd.eval_qnx(out_buf, knn, rows)
         res[opt] = {
             "value": inf["n_terms"] * w.n_iter / (ms / 1e3), "unit": UNIT, "s_to_embed": ms / 1e3,

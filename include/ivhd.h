@@ -309,6 +309,7 @@ typedef struct {
                                 blocks for the whole call, 3 a persistent grid for the
                                 whole call (see ivhd_params.resident) */
     int32_t step_blocks;     /* blocks of one step-kernel launch (launch form 0) */
+    int32_t step_threads;    /* threads per block of the step kernel */
 } ivhd_info_t;
 
 /* Fills *out.  Host only; does not synchronise. */

@@ -68,6 +68,7 @@ class Info(ctypes.Structure):
         ("setup_launches", ctypes.c_int64), ("aux_launches", ctypes.c_int64),
         ("launch_form", ctypes.c_int32),
         ("step_blocks", ctypes.c_int32),
+        ("step_threads", ctypes.c_int32),
     ]
 
 

@@ -724,6 +724,7 @@ ivhd_status ivhd_info(ivhd_ctx* ctx, ivhd_info_t* out) {
   const int rm = ctx->ctl ? 0 : resident_mode(ctx);
   out->launch_form = rm == 0 ? 0 : (rm <= 2 ? 1 : (rm == 3 ? 2 : 3));
   out->step_blocks = step_grid(ctx);
+  out->step_threads = ctx->block;
   return IVHD_OK;
 }
 

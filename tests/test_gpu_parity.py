@@ -454,8 +454,8 @@ def test_probe_launch_floor_is_plausible_and_below_the_step_of_the_same_grid():
     inf = emb.info()
     emb.close()
     step_us = 1e3 * e0.elapsed_time(e1) / 500
-    floor = ivhd.probe_launch(inf["step_blocks"], 128, 500)
-    assert inf["launch_form"] == 0 and inf["step_blocks"] > 0
+    floor = ivhd.probe_launch(inf["step_blocks"], inf["step_threads"], 500)
+    assert inf["launch_form"] == 0 and inf["step_blocks"] > 0 and inf["step_threads"] == 128
     assert step_us >= 0.8 * floor, (step_us, floor)
 
 
