@@ -167,7 +167,7 @@ def measure(train: int = 200000, holdout: int = 1400000, epochs: int = 10, steps
     out["nn_placement_ivhd"] = {"curve": nnw, "step_seconds": nnw_s,
                                 "steps_to_plain_final_precision": first_within(nnw)}
 
-    # 4. arriving batches, judged against the training embedding they are placed into
+    # 4. arriving batches, assessed against the training embedding they are placed into
     Xa, La = synth.mnist_like(10 * 10000, 7, noise_seed=3)
     Xa_d = torch.from_numpy(Xa).to(dev)
     La_d = torch.from_numpy(La).to(dev)

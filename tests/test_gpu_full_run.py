@@ -1,10 +1,10 @@
 """Full runs at the benchmark's sizes against the oracle's own full runs.
 
 The method is the iteration of Sec. 3.3.3 (Eq. 3.34 and the optimiser
-variants of Sec. 3.3.2) run for the whole schedule; an embedding is judged by
+variants of Sec. 3.3.2) run for the whole schedule; an embedding is assessed by
 the criteria of Sec. 4.1.  The dynamics amplify rounding, so after 2,000 steps
 the FP32 GPU run and the FP64 oracle run are different embeddings of the same
-graph: they are compared through what a run is judged by.
+graph: they are compared through the criteria a run is evaluated by.
 
 * Q_NX(k) within 0.01 of the oracle's (the equal-kNN-precision bar).
 * cf_2 / cf_10 / cf_100 within 0.01 of the oracle's.  On these inputs Q_NX is
