@@ -623,8 +623,8 @@ int64_t ivhd_mlp_launches(ivhd_mlp *mlp);
  * by layer.  The paper has no counterpart.  `which` selects one row-major
  * array of *rows rows:
  *   IVHD_MLP_X    input rows as BF16 (rows x n_in, 2-byte BF16 bit patterns)
- *   IVHD_MLP_Z1   W1 x + b1, FP32 (rows x hidden)
- *   IVHD_MLP_H1   GELU(z1) as BF16     IVHD_MLP_Z2  W2 h1 + b2, FP32
+ *   IVHD_MLP_Z1   W1 x + b1, FP32 (rows x hidden; training calls)
+ *   IVHD_MLP_H1   GELU(z1) as BF16     IVHD_MLP_Z2  W2 h1 + b2, FP32 (training calls)
  *   IVHD_MLP_H2   GELU(z2) as BF16     IVHD_MLP_Y   W3 h2 + b3, FP32 (rows x 2)
  *   IVHD_MLP_DY   dL/dy = 2 (y - t) / rows, FP32 (rows x 2; training calls)
  *   IVHD_MLP_DZ2  (dY W3) * GELU'(z2) as BF16 (training calls)

@@ -176,8 +176,9 @@ __device__ __forceinline__ void ep_apply32(const GemmEpilogue& ep, int row, int 
         if (col0 + q < N) o[q] = v[q];
     }
   } else if (ep.kind == kEpBiasGelu) {
-    // z = acc + bias is kept (FP32) for the backward pass; h = GELU(z) in BF16
-    float* z = ep.out_f32 + off;
+    // z = acc + bias is kept (FP32) for the backward pass (when out_f32 is
+    // given: training); h = GELU(z) in BF16
+    float* z = ep.out_f32 ? ep.out_f32 + off : nullptr;
     __nv_bfloat16* h = ep.out_bf16 + off;
     float t[32], g[32];
 #pragma unroll
@@ -185,16 +186,19 @@ __device__ __forceinline__ void ep_apply32(const GemmEpilogue& ep, int row, int 
       t[q] = (col0 + q < N) ? v[q] + ep.bias[col0 + q] : 0.f;
       g[q] = gelu(t[q]);
     }
-    if (full && aligned16(z) && aligned16(h)) {
+    if (full && (!z || aligned16(z)) && aligned16(h)) {
+      if (z) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        reinterpret_cast<float4*>(z)[q] = make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
+        for (int q = 0; q < 8; ++q)
+          reinterpret_cast<float4*>(z)[q] =
+              make_float4(t[4 * q], t[4 * q + 1], t[4 * q + 2], t[4 * q + 3]);
+      }
       store_bf16x32(h, g);
     } else {
 #pragma unroll
       for (int q = 0; q < 32; ++q)
         if (col0 + q < N) {
-          z[q] = t[q];
+          if (z) z[q] = t[q];
           h[q] = __float2bfloat16_rn(g[q]);
         }
     }

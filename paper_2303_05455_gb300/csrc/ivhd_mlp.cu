@@ -399,19 +399,20 @@ cudaError_t refresh_copies(ivhd_mlp* P) {
   return transpose(P->w2, H, H, P->w2t, P->stream);
 }
 
-// Forward pass of B rows already in P->xb: z1, h1, z2, h2, y.  For training
-// the first layer also writes h1 transposed (the weight gradient's operand).
+// Forward pass of B rows already in P->xb: h1, h2, y, and for training also
+// the pre-activations z1, z2 (GELU' of the backward pass reads them) and h1
+// transposed (the weight gradient's operand).
 cudaError_t forward(ivhd_mlp* P, int B, bool train = false) {
   const Offs o = offsets(P->n_in, P->hidden);
   const int H = P->hidden;
   P->last_rows = B;
-  GemmEpilogue e1{kEpBiasGelu, H, P->z1, P->h1, P->w + o.b1, nullptr, 0};
+  GemmEpilogue e1{kEpBiasGelu, H, train ? P->z1 : nullptr, P->h1, P->w + o.b1, nullptr, 0};
   if (train) {
     e1.out_bf16_t = P->h1t;
     e1.ld_t = B;
   }
   cudaError_t e = gemm_bf16_tn(P->xb, P->n_in, P->w1, P->n_in, B, H, P->n_in, e1, P->err, P->stream);
-  GemmEpilogue e2{kEpBiasGelu, H, P->z2, P->h2, P->w + o.b2, nullptr, 0};
+  GemmEpilogue e2{kEpBiasGelu, H, train ? P->z2 : nullptr, P->h2, P->w + o.b2, nullptr, 0};
   if (e == cudaSuccess) e = gemm_bf16_tn(P->h1, H, P->w2, H, B, H, H, e2, P->err, P->stream);
   if (e == cudaSuccess) {
     k_layer3<<<nb((int64_t)B * 32), 256, 0, P->stream>>>(P->h2, P->w + o.W3, P->w + o.b3, B, H, P->y);
