@@ -164,17 +164,36 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int R, in
   }
 }
 
-// y[b][j] = sum_i W3[j][i] h2[b][i] + b3[j], one warp per row, fixed lane order.
+// y[b][j] = sum_i W3[j][i] h2[b][i] + b3[j], one warp per row: lane l takes the
+// 8 consecutive elements 8 l + 256 t (16-byte loads of h2 and of both W3 rows;
+// H % 16 == 0 and W3 sits at a multiple of 16 floats in the parameter vector),
+// then the lanes are summed by a fixed butterfly.
 __global__ void k_layer3(const __nv_bfloat16* __restrict__ h2, const float* __restrict__ W3,
                          const float* __restrict__ b3, int B, int H, float* __restrict__ y) {
   const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= B) return;
   float s0 = 0.f, s1 = 0.f;
-  for (int i = lane; i < H; i += 32) {
-    const float h = __bfloat162float(h2[(int64_t)row * H + i]);
-    s0 = fmaf(W3[i], h, s0);
-    s1 = fmaf(W3[H + i], h, s1);
+  const __nv_bfloat16* hr = h2 + (int64_t)row * H;
+  for (int i = lane * 8; i < H; i += 256) {
+    const uint4 v = *reinterpret_cast<const uint4*>(hr + i);
+    // W3 rows as 16-byte loads too: consecutive lanes read consecutive 32 bytes
+    const float4* w0 = reinterpret_cast<const float4*>(W3 + i);
+    const float4* w1 = reinterpret_cast<const float4*>(W3 + H + i);
+    const float4 a0 = w0[0], a1 = w0[1], c0 = w1[0], c1 = w1[1];
+    const float wa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float wc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __nv_bfloat162 p2;
+      memcpy(&p2, &w[q], 4);
+      const float2 f = __bfloat1622float2(p2);
+      s0 = fmaf(wa[2 * q], f.x, s0);
+      s0 = fmaf(wa[2 * q + 1], f.y, s0);
+      s1 = fmaf(wc[2 * q], f.x, s1);
+      s1 = fmaf(wc[2 * q + 1], f.y, s1);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
