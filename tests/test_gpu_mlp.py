@@ -166,6 +166,29 @@ def test_training_fits_and_chunked_forward_is_consistent():
     assert torch.equal(y, y_parts)
 
 
+def test_forward_rows_do_not_depend_on_the_chunking():
+    """Rows are independent: each output element's K sum runs in the same order
+    whatever the number of rows or the tile width, so a row's output is the
+    same bits in any chunk, including a ragged last chunk (8,197 rows, not a
+    multiple of 8) and a slice that crosses a chunk boundary, and with a
+    network whose chunks are 16 times larger."""
+    n_in, H = 784, 512
+    X, _ = synth.mnist_like(8197, 11, N=n_in)
+    p = flat(omlp.init_params(n_in, H, 2, 4))
+    xd = torch.from_numpy(X).cuda()
+    small = ivhd.MLP(n_in, H, max_batch=512)
+    large = ivhd.MLP(n_in, H, max_batch=8192)
+    small.set_params(p)
+    large.set_params(p)
+    y = small.forward(xd, x_scale=1 / 255)
+    assert y.shape == (8197, 2) and torch.isfinite(y).all()
+    assert torch.equal(y, large.forward(xd, x_scale=1 / 255))
+    assert torch.equal(y[500:1037], small.forward(xd[500:1037], x_scale=1 / 255))
+    assert torch.equal(y[8190:], large.forward(xd[8190:], x_scale=1 / 255))
+    small.close()
+    large.close()
+
+
 def test_replayed_training_steps_follow_adam():
     """From the second step at a batch size on, the step is a replayed CUDA graph whose
     input, target and learning-rate nodes are patched per call: with new batches at new
