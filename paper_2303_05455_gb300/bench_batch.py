@@ -41,21 +41,31 @@ def measure(n_emb: int = 64, steps: int = 1000, qnx_rows: int = 2000,
     s = torch.cuda.current_stream()
 
     def timed(fn):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        """fn(span) runs its embeddings, calling span() before each create and
+        span() again once its positions are read back; the seconds of those
+        spans are summed (create + steps + read-back; the contexts' teardown
+        between them is not timed)."""
+        evs = []
+
+        def span():
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(s)
+            evs.append(e)
+
         torch.cuda.synchronize()
-        e0.record(s)
-        out = fn()
-        e1.record(s)
+        out = fn(span)
         torch.cuda.synchronize()
-        return out, e0.elapsed_time(e1) / 1e3
+        return out, sum(evs[q].elapsed_time(evs[q + 1]) for q in range(0, len(evs), 2)) / 1e3
 
     # one by one, FP32
-    def one_by_one():
+    def one_by_one(span=lambda: None):
         pos, terms = [], 0
         for w, g in zip(work, graphs):
+            span()
             emb = ivhd.Embedding(g, r=w["r"], c=c, a=a, b=b, seed=w["seed"])
             emb.step(args.steps)
             pos.append(emb.positions())
+            span()
             terms += emb.info()["n_terms"]
             emb.close()
         return pos, terms
@@ -84,18 +94,22 @@ def measure(n_emb: int = 64, steps: int = 1000, qnx_rows: int = 2000,
         tune_s = time.perf_counter() - t
         emb0.close()
 
-        def batched():
+        def batched(span=lambda: None):
+            span()
             emb = create(tuned)
             emb.step(args.steps)
             y = emb.positions()
+            span()
             n = emb.info()["n_terms"]
             emb.close()
             return y, n
 
-        def batched_untuned():
+        def batched_untuned(span=lambda: None):
+            span()
             emb = create()
             emb.step(args.steps)
             y = emb.positions()
+            span()
             emb.close()
             return y
 
