@@ -8,8 +8,10 @@
 // cores from BF16 copies with FP32 accumulation (ivhd_gemm.cu), with the bias
 // and GELU (forward) or GELU derivative (backward) fused into the GEMM
 // epilogue; the 2-wide output layer and the reductions over the batch run on
-// the CUDA cores in FP32 with fixed summation orders.  Everything on the
-// context stream; training steps need no host synchronisation.
+// the CUDA cores in FP32 with fixed summation orders.  Everything is ordered
+// on the context stream (within a training step a second stream runs the work
+// off the GEMM chain, forked and joined by events); training steps need no
+// host synchronisation.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -48,7 +50,7 @@ struct ivhd_mlp {
   double* loss_part = nullptr;
   double* loss_out = nullptr;
   // side stream for the work off the GEMM chain (the transposed input, the
-  // bias gradients), ordered against the main stream by events
+  // output-layer and bias gradients), ordered against the main stream by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev[6] = {};
   int32_t* err = nullptr;
