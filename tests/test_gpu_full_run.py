@@ -103,10 +103,10 @@ def _oracle_run(key, data, opt):
     return _cache[ck]
 
 
-def _gpu_run(data, opt, pos_format):
+def _gpu_run(data, opt, pos_format, order="degree"):
     w, _, labels, knn, rows = data
     emb = ivhd.Embedding(torch.from_numpy(knn).cuda(), r=w.r, c=w.c, opt=opt, a=w.a, b=w.b,
-                         seed=w.seed, pos_format=pos_format)
+                         seed=w.seed, pos_format=pos_format, order=order)
     emb.step(w.n_iter)
     Y = emb.positions()
     crit = _criteria_gpu(Y, knn, labels, rows)
@@ -179,4 +179,14 @@ def test_full_run_bf16_positions_match_oracle(where, opt):
     data = _mnist70k() if where == "c2" else _planted1p4m()
     _, ref = _oracle_run(where, data, opt)
     _, got = _gpu_run(data, opt, "bf16")
+    _compare(got, ref)
+
+
+@pytest.mark.parametrize("pos_format", ["f32", "f16"])
+def test_full_run_cluster_grouped_order_matches_oracle(pos_format):
+    """The cluster-grouped layout order changes only where rows sit and so the
+    summation order of the steps; the full run is held to the same bars."""
+    data = _planted1p4m()
+    _, ref = _oracle_run("c3", data, "momentum")
+    _, got = _gpu_run(data, "momentum", pos_format, order="degree_cluster")
     _compare(got, ref)
